@@ -1,0 +1,212 @@
+"""Brute-force state-vector simulation -- TEST INFRASTRUCTURE ONLY.
+
+Used to pin the tableau and frame oracles on small circuits (Section 5.5 of
+the paper checks gate tableaus against unitaries the same way). Holds its own
+tiny parser and the gate unitaries as plain matrices; noise channels are
+ignored (noiseless semantics only).
+
+* ``reference(text)``: the outcome-0 noiseless sample: each measurement whose
+  outcome is random (P(0) = 1/2) is projected onto 0, otherwise onto its
+  deterministic outcome; also returns the per-measurement deterministic flag.
+* ``branches(text)``: every record the noiseless circuit can produce, by
+  enumerating both outcomes of every random measurement.
+"""
+from __future__ import annotations
+
+import re
+
+import numpy as np
+
+_S2 = 1 / np.sqrt(2)
+UNITARY = {
+    "H": np.array([[1, 1], [1, -1]], complex) * _S2,
+    "S": np.diag([1, 1j]).astype(complex),
+    "X": np.array([[0, 1], [1, 0]], complex),
+    # two-qubit gates in the basis |a b> with a the first target
+    "CX": np.array([[1, 0, 0, 0], [0, 1, 0, 0], [0, 0, 0, 1], [0, 0, 1, 0]], complex),
+    "CZ": np.diag([1, 1, 1, -1]).astype(complex),
+}
+PAULI = {
+    "I": np.eye(2, dtype=complex),
+    "X": np.array([[0, 1], [1, 0]], complex),
+    "Y": np.array([[0, -1j], [1j, 0]], complex),
+    "Z": np.array([[1, 0], [0, -1]], complex),
+}
+NOISE = {"X_ERROR", "Z_ERROR", "DEPOLARIZE1", "DEPOLARIZE2"}
+
+
+def parse(text: str):
+    """Flatten the circuit into (name, targets) pairs. DETECTOR targets are
+    absolute measurement indices."""
+    stack = [[]]
+    reps = []
+    for raw in text.splitlines():
+        line = raw.split("#", 1)[0].strip()
+        if not line:
+            continue
+        if line == "}":
+            body = stack.pop()
+            stack[-1].append(("REPEAT", reps.pop(), body))
+            continue
+        m = re.fullmatch(r"REPEAT\s+(\d+)\s*\{", line)
+        if m:
+            stack.append([])
+            reps.append(int(m.group(1)))
+            continue
+        m = re.fullmatch(r"([A-Z_0-9]+)(\([^)]*\))?(.*)", line)
+        name = m.group(1)
+        if name == "CNOT":
+            name = "CX"
+        toks = m.group(3).split()
+        if name == "DETECTOR":
+            tg = [int(re.fullmatch(r"rec\[-(\d+)\]", t).group(1)) for t in toks]
+        else:
+            tg = [int(t) for t in toks]
+        stack[-1].append((name, tg))
+    assert len(stack) == 1
+
+    flat = []
+    count = [0]
+
+    def walk(items):
+        for it in items:
+            if it[0] == "REPEAT":
+                for _ in range(it[1]):
+                    walk(it[2])
+                continue
+            name, tg = it
+            if name == "DETECTOR":
+                flat.append((name, [count[0] - k for k in tg]))
+            else:
+                flat.append((name, tg))
+                if name in ("M", "MR"):
+                    count[0] += len(tg)
+
+    walk(stack[0])
+    return flat
+
+
+def num_qubits(ops) -> int:
+    n = 0
+    for name, tg in ops:
+        if name != "DETECTOR" and tg:
+            n = max(n, max(tg) + 1)
+    return n
+
+
+class State:
+    """n-qubit state vector; qubit q is bit q of the basis index."""
+
+    def __init__(self, n: int):
+        self.n = n
+        self.psi = np.zeros((2,) * n, complex)
+        self.psi[(0,) * n] = 1
+
+    def _ax(self, q):
+        return self.n - 1 - q
+
+    def apply1(self, U, q):
+        ax = self._ax(q)
+        self.psi = np.moveaxis(np.tensordot(U, self.psi, axes=([1], [ax])), 0, ax)
+
+    def apply2(self, U, a, b):
+        U4 = U.reshape(2, 2, 2, 2)
+        axa, axb = self._ax(a), self._ax(b)
+        out = np.tensordot(U4, self.psi, axes=([2, 3], [axa, axb]))
+        self.psi = np.moveaxis(out, [0, 1], [axa, axb])
+
+    def prob0(self, q):
+        sl = [slice(None)] * self.n
+        sl[self._ax(q)] = 0
+        return float(np.sum(np.abs(self.psi[tuple(sl)]) ** 2))
+
+    def project(self, q, outcome):
+        sl = [slice(None)] * self.n
+        sl[self._ax(q)] = 1 - outcome
+        self.psi[tuple(sl)] = 0
+        self.psi /= np.linalg.norm(self.psi)
+
+    def copy(self):
+        s = State.__new__(State)
+        s.n = self.n
+        s.psi = self.psi.copy()
+        return s
+
+
+def _measure_kind(p0: float):
+    if p0 > 1 - 1e-9:
+        return "det", 0
+    if p0 < 1e-9:
+        return "det", 1
+    assert abs(p0 - 0.5) < 1e-6, p0
+    return "rand", None
+
+
+def reference(text: str):
+    ops = parse(text)
+    st = State(num_qubits(ops))
+    ref, det = [], []
+    for name, tg in ops:
+        if name in ("H", "S"):
+            for q in tg:
+                st.apply1(UNITARY[name], q)
+        elif name in ("CX", "CZ"):
+            for a, b in zip(tg[::2], tg[1::2]):
+                st.apply2(UNITARY[name], a, b)
+        elif name in ("M", "MR", "R"):
+            for q in tg:
+                kind, val = _measure_kind(st.prob0(q))
+                r = 0 if kind == "rand" else val
+                st.project(q, r)
+                if name != "R":
+                    ref.append(r)
+                    det.append(1 if kind == "det" else 0)
+                if name != "M" and r == 1:
+                    st.apply1(UNITARY["X"], q)
+    return np.array(ref, np.uint8), np.array(det, np.uint8)
+
+
+def branches(text: str, max_random: int = 14):
+    """All record tuples of the noiseless circuit with their probabilities,
+    as a dict, by branching on both outcomes of every random measurement."""
+    ops = []
+    for name, tg in parse(text):
+        if name in ("M", "MR", "R"):
+            ops += [(name, [q]) for q in tg]    # broadcast runs left to right
+        else:
+            ops.append((name, tg))
+    n = num_qubits(ops)
+    out = {}
+
+    def run(i, st, rec, prob, nrand):
+        while i < len(ops):
+            name, tg = ops[i]
+            if name in ("H", "S"):
+                for q in tg:
+                    st.apply1(UNITARY[name], q)
+            elif name in ("CX", "CZ"):
+                for a, b in zip(tg[::2], tg[1::2]):
+                    st.apply2(UNITARY[name], a, b)
+            elif name in ("M", "MR", "R"):
+                q = tg[0]
+                kind, val = _measure_kind(st.prob0(q))
+                if kind == "rand":
+                    assert nrand < max_random, "too many random measurements"
+                    for r in (0, 1):
+                        s2 = st.copy()
+                        s2.project(q, r)
+                        if name != "M" and r == 1:
+                            s2.apply1(UNITARY["X"], q)
+                        run(i + 1, s2, rec + ([r] if name != "R" else []), prob / 2, nrand + 1)
+                    return
+                st.project(q, val)
+                if name != "R":
+                    rec = rec + [val]
+                if name != "M" and val == 1:
+                    st.apply1(UNITARY["X"], q)
+            i += 1
+        key = tuple(rec)
+        out[key] = out.get(key, 0.0) + prob
+
+    run(0, State(n), [], 1.0, 0)
+    return out
