@@ -1,0 +1,160 @@
+/*
+ * stimgb.h -- C ABI of the GB300 bulk stabilizer-circuit sampler.
+ *
+ * The library implements the bulk-sampling path of Gidney, "Stim: a fast
+ * stabilizer circuit simulator" (Quantum 2021): a circuit is compiled once,
+ * one noiseless reference sample is taken with the inverse-tableau simulator
+ * (Section 4), and then many shots are sampled by propagating bit-packed
+ * Pauli frames through the circuit (Section 3) and XORing them against the
+ * reference; detection events are XORs of measurement flips (Section 5.6).
+ *
+ * Conventions shared by every call:
+ *   - Every function returns an int status: STIM_OK (0) or a negative
+ *     STIM_E_* code. stim_last_error() gives a per-thread message for the
+ *     last failure on the calling thread.
+ *   - The library owns circuit handles; the caller owns every output buffer
+ *     and must size it as documented.
+ *   - Bit-packed arrays are little-endian within uint64 words: bit j of a row
+ *     is bit (j % 64) of word (j / 64) (the LSB-first order of the paper's
+ *     b8 output format, Section 5.6). Padding bits past the row's end are 0.
+ *   - A flags word says whether output pointers are host or device memory and
+ *     which layout they use. Device pointers must be memory of the current
+ *     CUDA device. Host pointers may be pageable or pinned.
+ *   - `stream` is a cudaStream_t (NULL = the legacy default stream). Calls
+ *     with device outputs are asynchronous on `stream`; calls with host
+ *     outputs return after the data has landed in host memory.
+ *   - Calls on one handle are not thread-safe; distinct handles may be used
+ *     from distinct threads.
+ *   - Results depend only on (circuit text, seed, global shot index); they do
+ *     not depend on layout, tile shape, batch split, shot offset or any other
+ *     work running on the GPU.
+ */
+#ifndef STIMGB_H
+#define STIMGB_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* ---- status codes ------------------------------------------------------ */
+#define STIM_OK              0
+#define STIM_E_PARSE        (-1)  /* circuit text rejected (message has line) */
+#define STIM_E_INVALID_ARG  (-2)  /* NULL handle, bad flags, size out of range */
+#define STIM_E_OOM          (-3)  /* host or device allocation failed */
+#define STIM_E_CUDA         (-4)  /* a CUDA runtime call failed */
+#define STIM_E_TIMEOUT      (-5)  /* a bounded device wait ran out */
+#define STIM_E_BUSY         (-6)  /* resource in use (server admission) */
+#define STIM_E_UNSUPPORTED  (-7)  /* circuit exceeds a documented limit */
+
+/* ---- flags --------------------------------------------------------------- */
+#define STIM_MEAS_MAJOR   0x0  /* row r = measurement/detector r; bit s = shot s */
+#define STIM_SHOT_MAJOR   0x1  /* row s = shot s; bit r = measurement/detector r */
+#define STIM_DEVICE       0x0  /* output pointers are device memory */
+#define STIM_HOST         0x2  /* output pointers are host memory */
+#define STIM_RECOMPUTE    0x4  /* stim_reference_sample: ignore the cached sample */
+
+typedef struct stim_circuit stim_circuit;
+
+typedef struct {
+    uint32_t num_qubits;         /* max qubit target + 1 */
+    uint64_t num_measurements;   /* M: targets of M and MR, in order */
+    uint64_t num_detectors;      /* D: DETECTOR instructions, in order */
+    uint64_t num_gate_targets;   /* H/S/M/MR/R targets plus CX/CZ pairs */
+    uint64_t num_noise_targets;  /* X_ERROR/Z_ERROR/DEPOLARIZE1 targets plus DEPOLARIZE2 pairs */
+    uint64_t num_instructions;   /* instruction lines after REPEAT flattening */
+    uint64_t num_layers;         /* fused layers executed per shot (loops unrolled) */
+    uint64_t num_program_layers; /* fused layers stored (loop bodies once) */
+} stim_info;
+
+/* Tile choice for the frame kernel; zero fields mean "let the library pick". */
+typedef struct {
+    uint32_t words_per_cta;    /* 64-shot words held by one CTA: 1, 2, 4, 8 or 16 */
+    uint32_t threads;          /* threads per CTA: 32..1024, multiple of 32 */
+    uint32_t frame_in_global;  /* 1: keep frames in global memory even if the tile fits shared memory */
+} stim_tile_hint;
+
+/*
+ * stim_compile -- parse and compile circuit text (Section 5.8 line format).
+ *
+ * Gate set: H, S, CX (alias CNOT), CZ, M, MR, R, X_ERROR(p), Z_ERROR(p),
+ * DEPOLARIZE1(p), DEPOLARIZE2(p), DETECTOR rec[-k]... (optional parenthesised
+ * coordinates on DETECTOR are ignored), REPEAT N { ... }, '#' comments.
+ * Broadcast targets run left to right (pairs for two-qubit gates).
+ *
+ * text/len: the circuit (need not be NUL-terminated). *out receives a new
+ * handle on success; the caller frees it with stim_free(). Compilation is
+ * host-only; device memory is allocated on the current device at the first
+ * sampling call. Errors: STIM_E_PARSE (unknown gate, bad target, odd target
+ * count or repeated qubit pair on a two-qubit gate, p outside [0, 1], wrong
+ * argument count, rec[-k] before the first measurement or k = 0, unbalanced
+ * or zero REPEAT), STIM_E_UNSUPPORTED (more than 2^24 qubits, 2^28
+ * flattened instructions or 2^32 measurements), STIM_E_INVALID_ARG,
+ * STIM_E_OOM.
+ */
+int stim_compile(const char *text, size_t len, stim_circuit **out);
+
+/* Counts of a compiled circuit. */
+int stim_info_get(const stim_circuit *c, stim_info *out);
+
+/* Frees the handle and its device memory (synchronizes the device first). */
+void stim_free(stim_circuit *c);
+
+/* Copies the calling thread's last error message into buf (NUL-terminated,
+ * truncated to len). Returns the message length. */
+int stim_last_error(char *buf, size_t len);
+
+/*
+ * stim_reference_sample -- one noiseless sample from the inverse-tableau
+ * simulator (Section 4, "Tracking the Tableau"), computed on the GPU.
+ *
+ * Gates are folded by prepending their inverse; a measurement reads the
+ * Z_q column; a random measurement is resolved by appending CNOTs from a
+ * pivot, a single-qubit collapse and, because the paper leaves the coin
+ * open, always takes outcome 0 (an X is appended when the sign is -).
+ * A reset is a measurement followed by forcing the sign to +.
+ *
+ * ref_bits: ceil(M/64) words; bit m = outcome of measurement m.
+ * det_bits: optional (may be NULL), ceil(M/64) words; bit m = 1 when
+ *   measurement m was deterministic given the earlier outcomes.
+ * flags: STIM_HOST or STIM_DEVICE for both pointers, optionally
+ *   STIM_RECOMPUTE to bypass the sample cached on the handle (used to time
+ *   the time-to-first-sample).
+ * The sample is cached on the handle and reused by stim_frame_sample.
+ * Errors: STIM_E_INVALID_ARG, STIM_E_OOM, STIM_E_CUDA, STIM_E_TIMEOUT.
+ */
+int stim_reference_sample(stim_circuit *c, uint64_t *ref_bits, uint64_t *det_bits,
+                          int flags, void *stream);
+
+/*
+ * stim_frame_sample -- bulk Pauli-frame sampling (Section 3): num_shots shots
+ * with global shot indices 0..num_shots-1 under `seed`.
+ *
+ * meas_out: may be NULL. MEAS_MAJOR: M rows of ceil(num_shots/64) words.
+ *   SHOT_MAJOR: num_shots rows of ceil(M/64) words.
+ * det_out: may be NULL. Detection events (XOR of the flips of a detector's
+ *   measurements, Section 5.6). MEAS_MAJOR: D rows of ceil(num_shots/64)
+ *   words. SHOT_MAJOR: num_shots rows of ceil(D/64) words.
+ * The reference sample is computed first if the handle has none.
+ * Errors: STIM_E_INVALID_ARG, STIM_E_OOM, STIM_E_CUDA, STIM_E_TIMEOUT.
+ */
+int stim_frame_sample(stim_circuit *c, uint64_t num_shots, uint64_t seed,
+                      uint64_t *meas_out, uint64_t *det_out, int flags, void *stream);
+
+/*
+ * stim_frame_sample_ex -- as stim_frame_sample for global shot indices
+ * shot_offset .. shot_offset+num_shots-1. shot_offset must be a multiple of
+ * 64 (it selects 64-shot RNG words); the outputs hold the num_shots shots
+ * starting at row/bit 0. hint may be NULL.
+ */
+int stim_frame_sample_ex(stim_circuit *c, uint64_t num_shots, uint64_t seed,
+                         uint64_t shot_offset, uint64_t *meas_out, uint64_t *det_out,
+                         int flags, const stim_tile_hint *hint, void *stream);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* STIMGB_H */

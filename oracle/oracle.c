@@ -582,28 +582,48 @@ int orc_string_mul(size_t nw, uint64_t *dx, uint64_t *dz, const uint64_t *sx, co
     return string_mul(dx, dz, sx, sz, nw);
 }
 
+/* The tableau is stored column-major (column c = the n-term image of its
+ * generator) while gates are folded, and row-major (row r = term r of every
+ * column) during bursts of random measurements, as the paper's Section 5.1
+ * describes: prepending is a column operation, the appends of the random-
+ * measurement elimination are row operations. */
 typedef struct {
     uint32_t n;
-    size_t nw;
+    size_t nw;         /* words per column (n rows) */
+    size_t cw;         /* words per row (2n columns) */
+    int rows;          /* 1 while the data lives in rx / rz / rs */
     uint64_t *x;       /* [2n][nw]: column 2q = image of X_q, 2q+1 = image of Z_q */
     uint64_t *z;
     uint8_t *sign;     /* [2n] */
+    uint64_t *rx;      /* [n][cw] */
+    uint64_t *rz;
+    uint64_t *rs;      /* [cw] sign bits */
 } tableau;
 
 #define TX(T, c) ((T)->x + (size_t)(c) * (T)->nw)
 #define TZ(T, c) ((T)->z + (size_t)(c) * (T)->nw)
+#define RX(T, r) ((T)->rx + (size_t)(r) * (T)->cw)
+#define RZ(T, r) ((T)->rz + (size_t)(r) * (T)->cw)
 #define GETB(a, q) ((int)(((a)[(q) >> 6] >> ((q) & 63)) & 1))
 #define FLIPB(a, q) ((a)[(q) >> 6] ^= (uint64_t)1 << ((q) & 63))
+#define SETB(a, q, v) ((a)[(q) >> 6] = ((a)[(q) >> 6] & ~((uint64_t)1 << ((q) & 63))) | ((uint64_t)(v) << ((q) & 63)))
 
 static int tableau_init(tableau *T, uint32_t n) {
     T->n = n;
     T->nw = (n + 63) / 64;
     if (T->nw == 0) T->nw = 1;
+    T->cw = (2 * (size_t)n + 63) / 64;
+    if (T->cw == 0) T->cw = 1;
+    T->rows = 0;
     size_t words = (size_t)2 * n * T->nw;
+    size_t rwords = (size_t)n * T->cw;
     T->x = (uint64_t *)calloc(words ? words : 1, sizeof(uint64_t));
     T->z = (uint64_t *)calloc(words ? words : 1, sizeof(uint64_t));
     T->sign = (uint8_t *)calloc(2 * (size_t)n + 1, 1);
-    if (!T->x || !T->z || !T->sign) return -1;
+    T->rx = (uint64_t *)calloc(rwords ? rwords : 1, sizeof(uint64_t));
+    T->rz = (uint64_t *)calloc(rwords ? rwords : 1, sizeof(uint64_t));
+    T->rs = (uint64_t *)calloc(T->cw, sizeof(uint64_t));
+    if (!T->x || !T->z || !T->sign || !T->rx || !T->rz || !T->rs) return -1;
     for (uint32_t q = 0; q < n; q++) {
         FLIPB(TX(T, 2 * q), q);
         FLIPB(TZ(T, 2 * q + 1), q);
@@ -615,6 +635,48 @@ static void tableau_free(tableau *T) {
     free(T->x);
     free(T->z);
     free(T->sign);
+    free(T->rx);
+    free(T->rz);
+    free(T->rs);
+}
+
+static void to_rows(tableau *T) {
+    if (T->rows) return;
+    memset(T->rx, 0, (size_t)T->n * T->cw * sizeof(uint64_t));
+    memset(T->rz, 0, (size_t)T->n * T->cw * sizeof(uint64_t));
+    memset(T->rs, 0, T->cw * sizeof(uint64_t));
+    for (uint32_t c = 0; c < 2 * T->n; c++) {
+        for (size_t w = 0; w < T->nw; w++) {
+            uint64_t v = TX(T, c)[w];
+            while (v) { FLIPB(RX(T, w * 64 + (size_t)__builtin_ctzll(v)), c); v &= v - 1; }
+            v = TZ(T, c)[w];
+            while (v) { FLIPB(RZ(T, w * 64 + (size_t)__builtin_ctzll(v)), c); v &= v - 1; }
+        }
+        if (T->sign[c]) FLIPB(T->rs, c);
+    }
+    T->rows = 1;
+}
+
+static void to_cols(tableau *T) {
+    if (!T->rows) return;
+    memset(T->x, 0, (size_t)2 * T->n * T->nw * sizeof(uint64_t));
+    memset(T->z, 0, (size_t)2 * T->n * T->nw * sizeof(uint64_t));
+    for (uint32_t r = 0; r < T->n; r++) {
+        for (size_t w = 0; w < T->cw; w++) {
+            uint64_t v = RX(T, r)[w];
+            while (v) { FLIPB(TX(T, w * 64 + (size_t)__builtin_ctzll(v)), r); v &= v - 1; }
+            v = RZ(T, r)[w];
+            while (v) { FLIPB(TZ(T, w * 64 + (size_t)__builtin_ctzll(v)), r); v &= v - 1; }
+        }
+    }
+    for (uint32_t c = 0; c < 2 * T->n; c++) T->sign[c] = (uint8_t)GETB(T->rs, c);
+    T->rows = 0;
+}
+
+
+static void set_sign(tableau *T, uint32_t c, int v) {
+    if (T->rows) SETB(T->rs, c, v);
+    else T->sign[c] = (uint8_t)v;
 }
 
 /* Prepend (fold) gate g on qubits q[0..k): new column for generator h is
@@ -624,6 +686,7 @@ static void tableau_prepend(tableau *T, int g, const uint32_t *q, uint64_t *tmpx
     spauli img[4];
     int k = gate_images(g, img);
     size_t nw = T->nw;
+    to_cols(T);
     for (int h = 0; h < 2 * k; h++) {
         uint64_t *ox = tmpx + (size_t)h * nw, *oz = tmpz + (size_t)h * nw;
         memset(ox, 0, nw * sizeof(uint64_t));
@@ -653,62 +716,122 @@ static void tableau_prepend(tableau *T, int g, const uint32_t *q, uint64_t *tmpx
     }
 }
 
-/* Append gate g on start-of-time qubits q[0..k): every column P becomes
- * g^dagger P g. */
-static void tableau_append(tableau *T, int g, const uint32_t *q) {
-    spauli img[4];
-    int k = gate_images(g, img);
-    for (uint32_t c = 0; c < 2 * T->n; c++) {
-        uint64_t *cx = TX(T, c), *cz = TZ(T, c);
-        uint8_t x = 0, z = 0;
-        for (int j = 0; j < k; j++) {
-            x |= (uint8_t)(GETB(cx, q[j]) << j);
-            z |= (uint8_t)(GETB(cz, q[j]) << j);
-        }
-        uint8_t rx, rz;
-        int ph;
-        /* image of the Hermitian local factor = i^ph * (Hermitian output) */
-        conj_local(img, k, x, z, &rx, &rz, &ph);
-        if (ph & 1) { fprintf(stderr, "oracle: non-Hermitian append result\n"); abort(); }
-        T->sign[c] ^= (uint8_t)(ph >> 1);
-        for (int j = 0; j < k; j++) {
-            if (((x ^ rx) >> j) & 1) FLIPB(cx, q[j]);
-            if (((z ^ rz) >> j) & 1) FLIPB(cz, q[j]);
+/* Appending gate g on start-of-time qubits conjugates every column P into
+ * g^dagger P g. In row-major form that is word-wide logic across columns on
+ * the gate's rows; the four rules below are checked against the generic
+ * conjugation (conj_local, itself pinned against matrices) by
+ * check_row_rules() before every reference sample.
+ *   CX(p->k): s ^= x_p z_k (x_k ^ z_p ^ 1); x_k ^= x_p; z_p ^= z_k
+ *   H(p):     s ^= x_p z_p; swap(x_p, z_p)
+ *   S(p):     s ^= x_p ~z_p; z_p ^= x_p
+ *   X(p):     s ^= z_p                                                   */
+static void row_cx(tableau *T, uint32_t p, uint32_t k) {
+    uint64_t *xp = RX(T, p), *zp = RZ(T, p), *xk = RX(T, k), *zk = RZ(T, k);
+    for (size_t w = 0; w < T->cw; w++) {
+        T->rs[w] ^= xp[w] & zk[w] & ~(xk[w] ^ zp[w]);
+        xk[w] ^= xp[w];
+        zp[w] ^= zk[w];
+    }
+}
+
+static void row_1q(tableau *T, int g, uint32_t p) {
+    uint64_t *xp = RX(T, p), *zp = RZ(T, p);
+    for (size_t w = 0; w < T->cw; w++) {
+        uint64_t x = xp[w], z = zp[w];
+        if (g == OG_H) { T->rs[w] ^= x & z; xp[w] = z; zp[w] = x; }
+        else if (g == OG_S) { T->rs[w] ^= x & ~z; zp[w] = z ^ x; }
+        else { T->rs[w] ^= z; }   /* OG_X */
+    }
+}
+
+static void check_row_rules(void) {
+    static int checked = 0;
+    if (checked) return;
+    for (int g = 0; g < 3; g++) {
+        int gate = g == 0 ? OG_H : g == 1 ? OG_S : OG_X;
+        spauli img[4];
+        gate_images(gate, img);
+        for (int bits = 0; bits < 4; bits++) {
+            tableau T;
+            tableau_init(&T, 1);
+            to_rows(&T);
+            T.rx[0] = (uint64_t)(bits & 1);
+            T.rz[0] = (uint64_t)(bits >> 1);
+            T.rs[0] = 0;
+            row_1q(&T, gate, 0);
+            uint8_t ox, oz;
+            int ph;
+            conj_local(img, 1, (uint8_t)(bits & 1), (uint8_t)(bits >> 1), &ox, &oz, &ph);
+            if ((T.rx[0] & 1) != ox || (T.rz[0] & 1) != oz || (int)(T.rs[0] & 1) != ph / 2) {
+                fprintf(stderr, "oracle: row rule mismatch for gate %d\n", gate);
+                abort();
+            }
+            tableau_free(&T);
         }
     }
+    spauli img[4];
+    gate_images(OG_CX, img);
+    for (int bits = 0; bits < 16; bits++) {
+        tableau T;
+        tableau_init(&T, 2);
+        to_rows(&T);
+        /* rows 0 (control) and 1 (target), one column (bit 0 of each word) */
+        T.rx[0] = (uint64_t)(bits & 1);
+        T.rz[0] = (uint64_t)((bits >> 1) & 1);
+        T.rx[T.cw] = (uint64_t)((bits >> 2) & 1);
+        T.rz[T.cw] = (uint64_t)((bits >> 3) & 1);
+        T.rs[0] = 0;
+        row_cx(&T, 0, 1);
+        uint8_t ox, oz;
+        int ph;
+        conj_local(img, 2, (uint8_t)((bits & 1) | (((bits >> 2) & 1) << 1)),
+                   (uint8_t)(((bits >> 1) & 1) | (((bits >> 3) & 1) << 1)), &ox, &oz, &ph);
+        uint8_t gx = (uint8_t)((T.rx[0] & 1) | ((T.rx[T.cw] & 1) << 1));
+        uint8_t gz = (uint8_t)((T.rz[0] & 1) | ((T.rz[T.cw] & 1) << 1));
+        if (gx != ox || gz != oz || (int)(T.rs[0] & 1) != ph / 2) {
+            fprintf(stderr, "oracle: row rule mismatch for CX\n");
+            abort();
+        }
+        tableau_free(&T);
+    }
+    checked = 1;
 }
 
 /* Measure Z_q; returns the outcome, sets *det to 1 if it was deterministic. */
 static int tableau_measure(tableau *T, uint32_t q, int *det) {
     uint32_t cz = 2 * q + 1;
-    uint64_t *mx = TX(T, cz);
+    if (!T->rows) {
+        const uint64_t *mx = TX(T, cz);
+        int any = 0;
+        for (size_t w = 0; w < T->nw; w++) any |= mx[w] != 0;
+        if (!any) {
+            *det = 1;
+            return T->sign[cz];
+        }
+        to_rows(T);     /* a random measurement: switch to rows for the elimination */
+    }
     int64_t pivot = -1;
-    for (size_t w = 0; w < T->nw && pivot < 0; w++)
-        if (mx[w]) pivot = (int64_t)(w * 64 + (size_t)__builtin_ctzll(mx[w]));
+    for (uint32_t r = 0; r < T->n && pivot < 0; r++)
+        if (GETB(RX(T, r), cz)) pivot = r;
     if (pivot < 0) {
         *det = 1;
-        return T->sign[cz];
+        return GETB(T->rs, cz);
     }
     *det = 0;
     uint32_t p = (uint32_t)pivot;
-    for (uint32_t k = p + 1; k < T->n; k++) {
-        if (GETB(TX(T, cz), k)) {
-            uint32_t qq[2] = {p, k};
-            tableau_append(T, OG_CX, qq);
-        }
-    }
-    if (GETB(TZ(T, cz), p)) {          /* Y on the pivot: S maps it to X */
-        tableau_append(T, OG_S, &p);
-    }
-    tableau_append(T, OG_H, &p);       /* X on the pivot -> Z */
-    if (T->sign[cz]) tableau_append(T, OG_X, &p);   /* outcome 0 */
-    return T->sign[cz];
+    for (uint32_t k = p + 1; k < T->n; k++)
+        if (GETB(RX(T, k), cz)) row_cx(T, p, k);          /* CNOT pivot -> k */
+    if (GETB(RZ(T, p), cz)) row_1q(T, OG_S, p);           /* Y on the pivot: S maps it to X */
+    row_1q(T, OG_H, p);                                   /* X on the pivot -> Z */
+    if (GETB(T->rs, cz)) row_1q(T, OG_X, p);              /* outcome 0 */
+    return GETB(T->rs, cz);
 }
 
 /* Reference sample: outcome of every measurement (outcome 0 when random),
  * plus a flag telling whether it was deterministic. */
 int orc_reference(const orc_circuit *c, uint8_t *ref, uint8_t *detflag) {
     tableau T;
+    check_row_rules();
     if (tableau_init(&T, c->n) < 0) return -1;
     size_t nw = T.nw;
     uint64_t *tmpx = (uint64_t *)malloc(4 * nw * sizeof(uint64_t));
@@ -733,7 +856,7 @@ int orc_reference(const orc_circuit *c, uint8_t *ref, uint8_t *detflag) {
                     if (detflag) detflag[m] = (uint8_t)det;
                     m++;
                 }
-                if (o->gate != OG_M) T.sign[2 * o->t[j] + 1] = 0;   /* force |0> */
+                if (o->gate != OG_M) set_sign(&T, 2 * o->t[j] + 1, 0);   /* force |0> */
             }
             break;
         default:

@@ -1,0 +1,238 @@
+"""GB300-native bulk stabilizer-circuit sampler (the bulk-sampling path of
+Gidney, "Stim: a fast stabilizer circuit simulator", Quantum 2021).
+
+This module is a thin ctypes binding of the C ABI in ``include/stimgb.h``:
+the functions ``stim_compile``, ``stim_info_get``, ``stim_reference_sample``,
+``stim_frame_sample``, ``stim_frame_sample_ex``, ``stim_free`` and
+``stim_last_error`` take the same arguments as their C counterparts (device
+or host pointers as integers, a CUDA stream handle as an integer) and only
+marshal arguments; every step of the path runs in the CUDA library. The
+``Circuit`` class wraps them with torch tensors for convenience.
+
+The library is built in-tree by ``paper_2103_02202_gb300.build`` (or
+``__graft_entry__.build()``). Importing this package does not load it;
+the first call does, and raises ``RuntimeError`` if it has not been built --
+there is no CPU fallback.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import threading
+
+import numpy as np
+
+from . import workloads  # noqa: F401  (seeded input generators)
+
+__all__ = [
+    "STIM_OK", "STIM_E_PARSE", "STIM_E_INVALID_ARG", "STIM_E_OOM", "STIM_E_CUDA",
+    "STIM_E_TIMEOUT", "STIM_E_BUSY", "STIM_E_UNSUPPORTED",
+    "STIM_MEAS_MAJOR", "STIM_SHOT_MAJOR", "STIM_DEVICE", "STIM_HOST", "STIM_RECOMPUTE",
+    "StimError", "library", "library_path", "stim_compile", "stim_info_get", "stim_free",
+    "stim_last_error", "stim_reference_sample", "stim_frame_sample", "stim_frame_sample_ex",
+    "Circuit", "EXPORTED_SYMBOLS",
+]
+
+STIM_OK = 0
+STIM_E_PARSE = -1
+STIM_E_INVALID_ARG = -2
+STIM_E_OOM = -3
+STIM_E_CUDA = -4
+STIM_E_TIMEOUT = -5
+STIM_E_BUSY = -6
+STIM_E_UNSUPPORTED = -7
+
+STIM_MEAS_MAJOR = 0x0
+STIM_SHOT_MAJOR = 0x1
+STIM_DEVICE = 0x0
+STIM_HOST = 0x2
+STIM_RECOMPUTE = 0x4
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_LIB_PATH = os.path.join(_HERE, "_build", "libstimgb.so")
+_lock = threading.Lock()
+_lib = None
+
+
+class StimError(RuntimeError):
+    def __init__(self, code: int, msg: str):
+        super().__init__("stimgb error %d: %s" % (code, msg))
+        self.code = code
+
+
+class StimInfo(ctypes.Structure):
+    _fields_ = [("num_qubits", ctypes.c_uint32), ("num_measurements", ctypes.c_uint64),
+                ("num_detectors", ctypes.c_uint64), ("num_gate_targets", ctypes.c_uint64),
+                ("num_noise_targets", ctypes.c_uint64), ("num_instructions", ctypes.c_uint64),
+                ("num_layers", ctypes.c_uint64), ("num_program_layers", ctypes.c_uint64)]
+
+
+class StimTileHint(ctypes.Structure):
+    _fields_ = [("words_per_cta", ctypes.c_uint32), ("threads", ctypes.c_uint32),
+                ("frame_in_global", ctypes.c_uint32)]
+
+
+_VP = ctypes.c_void_p
+_U64 = ctypes.c_uint64
+# name -> (restype, argtypes); every entry is declared in include/stimgb.h
+_SIGNATURES = {
+    "stim_compile": (ctypes.c_int, [ctypes.c_char_p, ctypes.c_size_t, ctypes.POINTER(_VP)]),
+    "stim_info_get": (ctypes.c_int, [_VP, ctypes.POINTER(StimInfo)]),
+    "stim_free": (None, [_VP]),
+    "stim_last_error": (ctypes.c_int, [ctypes.c_char_p, ctypes.c_size_t]),
+    "stim_reference_sample": (ctypes.c_int, [_VP, _VP, _VP, ctypes.c_int, _VP]),
+    "stim_frame_sample": (ctypes.c_int, [_VP, _U64, _U64, _VP, _VP, ctypes.c_int, _VP]),
+    "stim_frame_sample_ex": (ctypes.c_int, [_VP, _U64, _U64, _U64, _VP, _VP, ctypes.c_int,
+                                            ctypes.POINTER(StimTileHint), _VP]),
+}
+EXPORTED_SYMBOLS = tuple(_SIGNATURES)
+
+
+def library_path() -> str:
+    return _LIB_PATH
+
+
+def library():
+    """Load libstimgb.so (raises if it was not built)."""
+    global _lib
+    with _lock:
+        if _lib is None:
+            if not os.path.exists(_LIB_PATH):
+                raise RuntimeError("libstimgb.so is not built (%s); run __graft_entry__.build() "
+                                   "or python -m paper_2103_02202_gb300.build" % _LIB_PATH)
+            L = ctypes.CDLL(_LIB_PATH)
+            for name, (res, args) in _SIGNATURES.items():
+                f = getattr(L, name)
+                f.restype = res
+                f.argtypes = args
+            _lib = L
+    return _lib
+
+
+def stim_last_error() -> str:
+    buf = ctypes.create_string_buffer(1024)
+    library().stim_last_error(buf, 1024)
+    return buf.value.decode(errors="replace")
+
+
+def _check(rc: int):
+    if rc != STIM_OK:
+        raise StimError(rc, stim_last_error())
+
+
+def stim_compile(text: str) -> int:
+    """Compile circuit text; returns an opaque handle (int)."""
+    b = text.encode()
+    h = _VP()
+    _check(library().stim_compile(b, len(b), ctypes.byref(h)))
+    return h.value
+
+
+def stim_info_get(handle: int) -> dict:
+    info = StimInfo()
+    _check(library().stim_info_get(handle, ctypes.byref(info)))
+    return {k: int(getattr(info, k)) for k, _ in StimInfo._fields_}
+
+
+def stim_free(handle: int) -> None:
+    if handle:
+        library().stim_free(handle)
+
+
+def stim_reference_sample(handle: int, ref_bits: int, det_bits: int = 0, flags: int = 0,
+                          stream: int = 0) -> None:
+    _check(library().stim_reference_sample(handle, ref_bits or None, det_bits or None, flags,
+                                           stream or None))
+
+
+def stim_frame_sample(handle: int, num_shots: int, seed: int, meas_out: int = 0, det_out: int = 0,
+                      flags: int = 0, stream: int = 0) -> None:
+    _check(library().stim_frame_sample(handle, num_shots, seed & (2**64 - 1), meas_out or None,
+                                       det_out or None, flags, stream or None))
+
+
+def stim_frame_sample_ex(handle: int, num_shots: int, seed: int, shot_offset: int = 0,
+                         meas_out: int = 0, det_out: int = 0, flags: int = 0, hint=None,
+                         stream: int = 0) -> None:
+    h = None
+    if hint is not None:
+        hint = tuple(hint) + (0,) * (3 - len(hint))
+        h = ctypes.byref(StimTileHint(int(hint[0]), int(hint[1]), int(hint[2])))
+    _check(library().stim_frame_sample_ex(handle, num_shots, seed & (2**64 - 1), shot_offset,
+                                          meas_out or None, det_out or None, flags, h,
+                                          stream or None))
+
+
+def _words(bits: int) -> int:
+    return (bits + 63) // 64
+
+
+class Circuit:
+    """Compiled circuit with torch-tensor helpers (outputs are int64 tensors
+    holding uint64 bit words; use ``.cpu().numpy().view(np.uint64)``)."""
+
+    def __init__(self, text: str):
+        self.handle = stim_compile(text)
+        self.info = stim_info_get(self.handle)
+        self.num_qubits = self.info["num_qubits"]
+        self.num_measurements = self.info["num_measurements"]
+        self.num_detectors = self.info["num_detectors"]
+
+    def close(self):
+        if getattr(self, "handle", None):
+            stim_free(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def reference(self, *, recompute: bool = False, stream=None):
+        """(ref_words, deterministic_words) as device int64 tensors."""
+        import torch
+        w = max(_words(self.num_measurements), 1)
+        ref = torch.zeros(w, dtype=torch.int64, device="cuda")
+        det = torch.zeros(w, dtype=torch.int64, device="cuda")
+        s = stream if stream is not None else torch.cuda.current_stream()
+        stim_reference_sample(self.handle, ref.data_ptr(), det.data_ptr(),
+                              STIM_RECOMPUTE if recompute else 0, s.cuda_stream)
+        return ref, det
+
+    def sample(self, num_shots: int, seed: int, *, shot_offset: int = 0, shot_major: bool = False,
+               meas: bool = True, dets: bool = True, hint=None, stream=None):
+        """Sample on the device; returns (meas, dets) int64 tensors (None when not asked)."""
+        import torch
+        M, D = self.num_measurements, self.num_detectors
+        if shot_major:
+            ms = (num_shots, _words(M))
+            ds = (num_shots, _words(D))
+        else:
+            ms = (M, _words(num_shots))
+            ds = (D, _words(num_shots))
+        mt = torch.empty(ms, dtype=torch.int64, device="cuda") if meas else None
+        dt = torch.empty(ds, dtype=torch.int64, device="cuda") if dets else None
+        s = stream if stream is not None else torch.cuda.current_stream()
+        flags = STIM_SHOT_MAJOR if shot_major else STIM_MEAS_MAJOR
+        stim_frame_sample_ex(self.handle, num_shots, seed, shot_offset,
+                             mt.data_ptr() if mt is not None and mt.numel() else 0,
+                             dt.data_ptr() if dt is not None and dt.numel() else 0,
+                             flags, hint, s.cuda_stream)
+        return mt, dt
+
+    def sample_host(self, num_shots: int, seed: int, *, shot_offset: int = 0, shot_major: bool = False,
+                    meas: bool = True, dets: bool = True, hint=None):
+        """Sample into host numpy uint64 arrays through the STIM_HOST path."""
+        M, D = self.num_measurements, self.num_detectors
+        if shot_major:
+            ms, ds = (num_shots, _words(M)), (num_shots, _words(D))
+        else:
+            ms, ds = (M, _words(num_shots)), (D, _words(num_shots))
+        ma = np.zeros(ms, np.uint64) if meas else None
+        da = np.zeros(ds, np.uint64) if dets else None
+        flags = STIM_HOST | (STIM_SHOT_MAJOR if shot_major else 0)
+        stim_frame_sample_ex(self.handle, num_shots, seed, shot_offset,
+                             ma.ctypes.data if ma is not None and ma.size else 0,
+                             da.ctypes.data if da is not None and da.size else 0, flags, hint, 0)
+        return ma, da

@@ -1,0 +1,400 @@
+// api.cu -- the C ABI declared in include/stimgb.h.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cstdio>
+#include <cstring>
+#include <new>
+#include <string>
+
+#include "../../include/stimgb.h"
+#include "internal.h"
+#include "kernels.h"
+
+using namespace stimgb;
+
+namespace {
+
+thread_local std::string g_last_error;
+
+int fail(int code, const std::string &msg) {
+    g_last_error = msg;
+    return code;
+}
+
+int cuda_fail(cudaError_t e, const char *what) {
+    std::string msg = std::string(what) + ": " + cudaGetErrorString(e);
+    return fail(e == cudaErrorMemoryAllocation ? STIM_E_OOM : STIM_E_CUDA, msg);
+}
+
+#define STIMGB_CK(call, what)                       \
+    do {                                            \
+        cudaError_t _e = (call);                    \
+        if (_e != cudaSuccess) return cuda_fail(_e, what); \
+    } while (0)
+
+template <typename T>
+int upload(T **dst, const std::vector<T> &src, const char *what) {
+    size_t bytes = std::max<size_t>(src.size(), 1) * sizeof(T);
+    STIMGB_CK(cudaMalloc((void **)dst, bytes), what);
+    if (!src.empty()) STIMGB_CK(cudaMemcpy(*dst, src.data(), src.size() * sizeof(T), cudaMemcpyHostToDevice), what);
+    return STIM_OK;
+}
+
+// Grow-only device scratch buffer (words of 8 bytes).
+int grow(uint64_t **p, size_t *cap, size_t words, const char *what) {
+    if (words <= *cap) return STIM_OK;
+    if (*p) {
+        cudaFree(*p);
+        *p = nullptr;
+        *cap = 0;
+    }
+    STIMGB_CK(cudaMalloc((void **)p, std::max<size_t>(words, 1) * 8), what);
+    *cap = words;
+    return STIM_OK;
+}
+
+}  // namespace
+
+struct stim_circuit {
+    HostProgram hp;
+    int device = -1;
+    ProgEntry *d_prog = nullptr;
+    DevOp *d_ops = nullptr;
+    uint64_t *d_geo = nullptr;
+    uint64_t *d_det_ptr = nullptr;
+    uint32_t *d_det_meas = nullptr;
+    uint64_t *d_ref = nullptr;
+    uint64_t *d_detflag = nullptr;
+    int *d_status = nullptr;
+    bool ref_valid = false;
+    size_t ref_words = 1;
+    uint64_t *d_rec = nullptr;
+    size_t rec_cap = 0;
+    uint64_t *d_det = nullptr;
+    size_t det_cap = 0;
+    uint64_t *d_tr = nullptr;
+    size_t tr_cap = 0;
+    uint64_t *d_gframe = nullptr;
+    size_t gframe_cap = 0;
+};
+
+namespace {
+
+int ensure_device(stim_circuit *c) {
+    int dev = 0;
+    STIMGB_CK(cudaGetDevice(&dev), "cudaGetDevice");
+    if (c->device >= 0) {
+        if (c->device != dev) return fail(STIM_E_INVALID_ARG, "circuit handle was uploaded to another device");
+        return STIM_OK;
+    }
+    const HostProgram &hp = c->hp;
+    int r;
+    if ((r = upload(&c->d_prog, hp.prog, "upload program")) != STIM_OK) return r;
+    if ((r = upload(&c->d_ops, hp.ops, "upload ops")) != STIM_OK) return r;
+    if ((r = upload(&c->d_geo, hp.geo, "upload noise tables")) != STIM_OK) return r;
+    if ((r = upload(&c->d_det_ptr, hp.det_ptr, "upload detectors")) != STIM_OK) return r;
+    if ((r = upload(&c->d_det_meas, hp.det_meas, "upload detectors")) != STIM_OK) return r;
+    c->ref_words = std::max<size_t>((hp.num_meas + 63) / 64, 1);
+    STIMGB_CK(cudaMalloc((void **)&c->d_ref, c->ref_words * 8), "alloc reference");
+    STIMGB_CK(cudaMalloc((void **)&c->d_detflag, c->ref_words * 8), "alloc reference");
+    STIMGB_CK(cudaMalloc((void **)&c->d_status, sizeof(int)), "alloc status");
+    STIMGB_CK(cudaMemset(c->d_ref, 0, c->ref_words * 8), "memset");
+    STIMGB_CK(cudaMemset(c->d_detflag, 0, c->ref_words * 8), "memset");
+    STIMGB_CK(cudaMemset(c->d_status, 0, sizeof(int)), "memset");
+    c->device = dev;
+    return STIM_OK;
+}
+
+int compute_reference(stim_circuit *c, cudaStream_t st) {
+    const HostProgram &hp = c->hp;
+    const uint32_t n = hp.num_qubits;
+    STIMGB_CK(cudaMemsetAsync(c->d_ref, 0, c->ref_words * 8, st), "memset");
+    STIMGB_CK(cudaMemsetAsync(c->d_detflag, 0, c->ref_words * 8, st), "memset");
+    if (n == 0 || hp.num_meas == 0) {
+        STIMGB_CK(cudaStreamSynchronize(st), "sync");
+        c->ref_valid = true;
+        return STIM_OK;
+    }
+    const uint32_t nw = (n + 63) / 64;
+    const size_t col_words = (size_t)2 * n * nw;
+    TabArgs a{};
+    a.prog = c->d_prog;
+    a.nprog = (uint32_t)hp.prog.size();
+    a.ops = c->d_ops;
+    a.n = n;
+    a.nw = nw;
+    a.ref = c->d_ref;
+    a.detflag = c->d_detflag;
+    a.status = c->d_status;
+    char *blob = nullptr;
+    const size_t bytes_tx = col_words * 8, bytes_sign = (size_t)2 * n * 4, bytes_klist = (size_t)n * 4 + 64;
+    const size_t bytes_kmask = (size_t)nw * 8 + 64, bytes_rnd = (size_t)std::max<uint32_t>(hp.max_layer_ops, 1) * 4 + 64;
+    const size_t total = 2 * bytes_tx + 2 * bytes_sign + bytes_klist + bytes_kmask + bytes_rnd + 256 + 1024;
+    STIMGB_CK(cudaMalloc((void **)&blob, total), "alloc tableau");
+    size_t off = 0;
+    auto take = [&](size_t b) {
+        char *p = blob + off;
+        off += (b + 255) & ~(size_t)255;
+        return p;
+    };
+    a.tx = (uint64_t *)take(bytes_tx);
+    a.tz = (uint64_t *)take(bytes_tx);
+    a.sign = (uint32_t *)take(bytes_sign);
+    a.perm = (uint32_t *)take(bytes_sign);
+    a.klist = (uint32_t *)take(bytes_klist);
+    a.kmask = (uint64_t *)take(bytes_kmask);
+    a.rnd = (uint32_t *)take(bytes_rnd);
+    a.ctl = (TabCtl *)take(sizeof(TabCtl));
+    int rc = STIM_OK;
+    cudaError_t e = cudaMemsetAsync(blob, 0, total, st);
+    if (e == cudaSuccess) e = cudaMemsetAsync(c->d_status, 0, sizeof(int), st);
+    if (e == cudaSuccess) e = launch_tableau_init(a, st);
+    if (e == cudaSuccess) {
+        const uint32_t threads = 512;
+        const int maxb = tableau_max_blocks(threads, c->device);
+        uint64_t want = (col_words + 16383) / 16384;
+        if (want < 1) want = 1;
+        uint32_t blocks = (uint32_t)std::min<uint64_t>(want, (uint64_t)maxb);
+        e = launch_tableau(a, blocks, threads, st);
+    }
+    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+    int status = 0;
+    if (e == cudaSuccess) e = cudaMemcpy(&status, c->d_status, sizeof(int), cudaMemcpyDeviceToHost);
+    cudaFree(blob);
+    if (e != cudaSuccess) return cuda_fail(e, "reference sample");
+    if (status == DEV_TIMEOUT) return fail(STIM_E_TIMEOUT, "tableau grid barrier timed out");
+    if (status != 0) return fail(STIM_E_CUDA, "tableau kernel reported a malformed program");
+    c->ref_valid = true;
+    return rc;
+}
+
+bool valid_flags(int flags, int allowed) { return (flags & ~allowed) == 0; }
+
+}  // namespace
+
+extern "C" {
+
+int stim_last_error(char *buf, size_t len) {
+    if (buf && len) {
+        size_t k = std::min(len - 1, g_last_error.size());
+        memcpy(buf, g_last_error.data(), k);
+        buf[k] = 0;
+    }
+    return (int)g_last_error.size();
+}
+
+int stim_compile(const char *text, size_t len, stim_circuit **out) {
+    if (!out || (!text && len)) return fail(STIM_E_INVALID_ARG, "stim_compile: null argument");
+    *out = nullptr;
+    stim_circuit *c = new (std::nothrow) stim_circuit();
+    if (!c) return fail(STIM_E_OOM, "stim_compile: out of host memory");
+    std::string err;
+    int r = compile_circuit(text ? text : "", len, &c->hp, &err);
+    if (r != 0) {
+        delete c;
+        return fail(r, err);
+    }
+    *out = c;
+    return STIM_OK;
+}
+
+int stim_info_get(const stim_circuit *c, stim_info *out) {
+    if (!c || !out) return fail(STIM_E_INVALID_ARG, "stim_info_get: null argument");
+    const HostProgram &hp = c->hp;
+    out->num_qubits = hp.num_qubits;
+    out->num_measurements = hp.num_meas;
+    out->num_detectors = hp.num_det;
+    out->num_gate_targets = hp.num_gate_targets;
+    out->num_noise_targets = hp.num_noise_targets;
+    out->num_instructions = hp.num_instr;
+    out->num_layers = hp.num_layers_exec;
+    out->num_program_layers = hp.num_layers_stored;
+    return STIM_OK;
+}
+
+void stim_free(stim_circuit *c) {
+    if (!c) return;
+    if (c->device >= 0) {
+        int cur = -1;
+        cudaGetDevice(&cur);
+        if (cur != c->device) cudaSetDevice(c->device);
+        cudaDeviceSynchronize();
+        cudaFree(c->d_prog);
+        cudaFree(c->d_ops);
+        cudaFree(c->d_geo);
+        cudaFree(c->d_det_ptr);
+        cudaFree(c->d_det_meas);
+        cudaFree(c->d_ref);
+        cudaFree(c->d_detflag);
+        cudaFree(c->d_status);
+        cudaFree(c->d_rec);
+        cudaFree(c->d_det);
+        cudaFree(c->d_tr);
+        cudaFree(c->d_gframe);
+        if (cur >= 0 && cur != c->device) cudaSetDevice(cur);
+    }
+    delete c;
+}
+
+int stim_reference_sample(stim_circuit *c, uint64_t *ref_bits, uint64_t *det_bits, int flags, void *stream) {
+    if (!c) return fail(STIM_E_INVALID_ARG, "stim_reference_sample: null handle");
+    if (!valid_flags(flags, STIM_HOST | STIM_RECOMPUTE))
+        return fail(STIM_E_INVALID_ARG, "stim_reference_sample: unknown flags");
+    cudaStream_t st = (cudaStream_t)stream;
+    int r = ensure_device(c);
+    if (r != STIM_OK) return r;
+    if (!c->ref_valid || (flags & STIM_RECOMPUTE)) {
+        r = compute_reference(c, st);
+        if (r != STIM_OK) return r;
+    }
+    const size_t words = (c->hp.num_meas + 63) / 64;
+    const cudaMemcpyKind kind = (flags & STIM_HOST) ? cudaMemcpyDeviceToHost : cudaMemcpyDeviceToDevice;
+    if (ref_bits && words) STIMGB_CK(cudaMemcpyAsync(ref_bits, c->d_ref, words * 8, kind, st), "copy reference");
+    if (det_bits && words) STIMGB_CK(cudaMemcpyAsync(det_bits, c->d_detflag, words * 8, kind, st), "copy flags");
+    if (flags & STIM_HOST) STIMGB_CK(cudaStreamSynchronize(st), "sync");
+    return STIM_OK;
+}
+
+int stim_frame_sample_ex(stim_circuit *c, uint64_t num_shots, uint64_t seed, uint64_t shot_offset,
+                         uint64_t *meas_out, uint64_t *det_out, int flags, const stim_tile_hint *hint,
+                         void *stream) {
+    if (!c) return fail(STIM_E_INVALID_ARG, "stim_frame_sample: null handle");
+    if (!valid_flags(flags, STIM_HOST | STIM_SHOT_MAJOR))
+        return fail(STIM_E_INVALID_ARG, "stim_frame_sample: unknown flags");
+    if (shot_offset % 64) return fail(STIM_E_INVALID_ARG, "stim_frame_sample: shot_offset must be a multiple of 64");
+    if ((shot_offset + num_shots + 63) / 64 > (1ull << 32))
+        return fail(STIM_E_UNSUPPORTED, "stim_frame_sample: global shot index above 2^38");
+    cudaStream_t st = (cudaStream_t)stream;
+    int r = ensure_device(c);
+    if (r != STIM_OK) return r;
+    if (!c->ref_valid) {
+        r = compute_reference(c, st);
+        if (r != STIM_OK) return r;
+    }
+    if (num_shots == 0) return STIM_OK;
+    const HostProgram &hp = c->hp;
+    const uint32_t n = hp.num_qubits;
+    const uint64_t M = hp.num_meas, D = hp.num_det;
+    const uint64_t nwords = (num_shots + 63) / 64;
+    const uint64_t last_mask = (num_shots % 64) ? ((1ull << (num_shots % 64)) - 1) : ~0ull;
+    const bool shot_major = (flags & STIM_SHOT_MAJOR) != 0, host = (flags & STIM_HOST) != 0;
+
+    // ---- tile choice ----
+    int sms = 0, smem_optin = 0;
+    STIMGB_CK(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, c->device), "attr");
+    STIMGB_CK(cudaDeviceGetAttribute(&smem_optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, c->device), "attr");
+    int W = 0;
+    uint32_t threads = 256;
+    if (hint && hint->words_per_cta) {
+        W = (int)hint->words_per_cta;
+        if (W != 1 && W != 2 && W != 4 && W != 8 && W != 16)
+            return fail(STIM_E_INVALID_ARG, "tile hint: words_per_cta must be 1, 2, 4, 8 or 16");
+    }
+    if (hint && hint->threads) {
+        threads = hint->threads;
+        if (threads < 32 || threads > 1024 || threads % 32)
+            return fail(STIM_E_INVALID_ARG, "tile hint: threads must be a multiple of 32 in [32, 1024]");
+    }
+    const size_t per_word = (size_t)n * 16;
+    bool gmem = per_word > (size_t)smem_optin || (hint && hint->frame_in_global);
+    if (W == 0) {
+        W = 1;
+        for (int w : {8, 4, 2}) {
+            if (!gmem && per_word * w > (size_t)smem_optin / 2 && w > 1) continue;
+            if ((nwords + w - 1) / w >= (uint64_t)sms * 2) {
+                W = w;
+                break;
+            }
+        }
+    }
+    if (!gmem && per_word * W > (size_t)smem_optin) gmem = true;
+    const uint64_t grid = (nwords + W - 1) / W;
+    if (grid > 0x7FFFFFFFull) return fail(STIM_E_UNSUPPORTED, "too many shots for one call");
+
+    // ---- record buffers ----
+    const bool meas_direct = meas_out && !shot_major && !host;
+    const bool need_rec = (meas_out || det_out) && M > 0;
+    uint64_t *rec = nullptr;
+    if (need_rec) {
+        if (meas_direct) {
+            rec = meas_out;
+        } else {
+            if ((r = grow(&c->d_rec, &c->rec_cap, M * nwords, "alloc records")) != STIM_OK) return r;
+            rec = c->d_rec;
+        }
+    }
+    uint64_t *gframe = nullptr;
+    uint64_t gstride = grid * W;
+    if (gmem && n > 0) {
+        if ((r = grow(&c->d_gframe, &c->gframe_cap, 2 * (size_t)n * gstride, "alloc frame")) != STIM_OK) return r;
+        gframe = c->d_gframe;
+    }
+
+    if (n > 0) {
+        FrameArgs a{};
+        a.prog = c->d_prog;
+        a.nprog = (uint32_t)hp.prog.size();
+        a.ops = c->d_ops;
+        a.geo = c->d_geo;
+        a.ref = c->d_ref;
+        a.n = n;
+        a.k0 = (uint32_t)seed;
+        a.k1 = (uint32_t)(seed >> 32);
+        a.word0 = shot_offset / 64;
+        a.nwords = nwords;
+        a.last_mask = last_mask;
+        a.rec = rec;
+        a.rec_stride = nwords;
+        a.gframe = gframe;
+        a.gstride = gstride;
+        a.status = c->d_status;
+        STIMGB_CK(launch_frame(a, W, gmem, (uint32_t)grid, threads, gmem ? 0 : per_word * W, st), "frame kernel");
+    }
+
+    // ---- detectors ----
+    uint64_t *det = nullptr;
+    const bool det_direct = det_out && !shot_major && !host;
+    if (det_out && D > 0) {
+        if (det_direct) {
+            det = det_out;
+        } else {
+            if ((r = grow(&c->d_det, &c->det_cap, D * nwords, "alloc detectors")) != STIM_OK) return r;
+            det = c->d_det;
+        }
+        STIMGB_CK(launch_detectors(rec, nwords, c->d_det_ptr, c->d_det_meas, c->d_ref, D, nwords, last_mask, det,
+                                   nwords, st),
+                  "detector kernel");
+    }
+
+    // ---- output layouts ----
+    auto emit = [&](uint64_t *src, uint64_t rows, uint64_t *dst) -> int {
+        if (!dst || rows == 0) return STIM_OK;
+        if (shot_major) {
+            const uint64_t out_stride = (rows + 63) / 64;
+            uint64_t *tgt = dst;
+            if (host) {
+                int rr = grow(&c->d_tr, &c->tr_cap, num_shots * out_stride, "alloc transpose");
+                if (rr != STIM_OK) return rr;
+                tgt = c->d_tr;
+            }
+            STIMGB_CK(launch_transpose(src, rows, nwords, num_shots, tgt, out_stride, st), "transpose kernel");
+            if (host)
+                STIMGB_CK(cudaMemcpyAsync(dst, tgt, num_shots * out_stride * 8, cudaMemcpyDeviceToHost, st), "copy out");
+        } else if (host) {
+            STIMGB_CK(cudaMemcpyAsync(dst, src, rows * nwords * 8, cudaMemcpyDeviceToHost, st), "copy out");
+        }
+        return STIM_OK;
+    };
+    if (meas_out && !meas_direct && (r = emit(rec, M, meas_out)) != STIM_OK) return r;
+    if (det_out && !det_direct && (r = emit(det, D, det_out)) != STIM_OK) return r;
+    if (host) STIMGB_CK(cudaStreamSynchronize(st), "sync");
+    return STIM_OK;
+}
+
+int stim_frame_sample(stim_circuit *c, uint64_t num_shots, uint64_t seed, uint64_t *meas_out, uint64_t *det_out,
+                      int flags, void *stream) {
+    return stim_frame_sample_ex(c, num_shots, seed, 0, meas_out, det_out, flags, nullptr, stream);
+}
+
+}  // extern "C"

@@ -1,0 +1,515 @@
+// compiler.cpp -- circuit text -> device program (host side).
+//
+// Parses the line format of the paper's Section 5.8 (one instruction per
+// line, broadcast targets, '#' comments, REPEAT N { ... }) and emits the
+// program described in internal.h:
+//   * every target (or target pair) becomes one 16-byte op carrying its RNG
+//     key material (flattened instruction ordinal, slot) and, for M/MR, its
+//     measurement index;
+//   * ops of a straight-line segment are fused into layers by as-soon-as-
+//     possible scheduling on qubit dependencies, so ops in one layer touch
+//     disjoint qubits and commute; collapsing ops keep their relative source
+//     order (the outcome-0 reference sample depends on that order);
+//   * REPEAT bodies are compiled once and wrapped in LOOP entries;
+//   * DETECTOR lookbacks rec[-k] are resolved to absolute measurement indices
+//     in a flattened CSR list;
+//   * each distinct noise probability gets a 64-entry geometric threshold
+//     table (Section 5.4's gap sampling, in exact integer form).
+#include <algorithm>
+#include <cctype>
+#include <cerrno>
+#include <cmath>
+#include <cstdio>
+#include <cstdlib>
+#include <cstring>
+#include <map>
+#include <memory>
+
+#include "../../include/stimgb.h"
+#include "internal.h"
+
+namespace stimgb {
+
+void geometric_table(double p, uint64_t G[64]) {
+    const unsigned __int128 one = (unsigned __int128)1 << 32;
+    long long t = llrint(ldexp(p, 32));     // default rounding: nearest, ties to even
+    if (t < 0) t = 0;
+    if (t > (1LL << 32)) t = 1LL << 32;
+    unsigned __int128 survive = one;       // S_k: 2^32 * P(no error in the next k slots)
+    for (int k = 0; k < 64; k++) {
+        survive = (survive * (one - (unsigned __int128)t)) >> 32;
+        G[k] = (uint64_t)(one - survive);
+    }
+}
+
+namespace {
+
+enum ParsedGate {
+    PG_H, PG_S, PG_CX, PG_CZ, PG_M, PG_MR, PG_R, PG_XERR, PG_ZERR, PG_DEP1, PG_DEP2, PG_DET
+};
+
+struct Instr {
+    int gate = 0;
+    double p = 0;
+    std::vector<uint32_t> targets;   // qubits, or lookbacks k for DETECTOR
+    int line = 0;
+};
+
+struct Node;
+struct Block {
+    uint64_t reps = 1;
+    std::vector<Node> items;
+};
+struct Node {
+    std::unique_ptr<Block> block;   // non-null for REPEAT
+    Instr ins;
+};
+
+struct ParseError {
+    int code;
+    std::string msg;
+};
+
+class Parser {
+  public:
+    Parser(const char *s, size_t n) : s_(s), n_(n) {}
+
+    Block parse() {
+        Block root;
+        parse_into(&root, 0);
+        return root;
+    }
+
+  private:
+    const char *s_;
+    size_t n_;
+    size_t pos_ = 0;
+    int line_ = 0;
+
+    [[noreturn]] void fail(size_t col, const char *what, const std::string &extra = "") {
+        char buf[96];
+        snprintf(buf, sizeof buf, "line %d, column %zu: ", line_, col + 1);
+        throw ParseError{STIM_E_PARSE, std::string(buf) + what + extra};
+    }
+
+    static bool space(char c) { return c == ' ' || c == '\t' || c == '\r'; }
+
+    // Returns true if a closing brace ended the block.
+    bool parse_into(Block *blk, int depth) {
+        while (pos_ < n_) {
+            size_t b = pos_;
+            size_t e = b;
+            while (e < n_ && s_[e] != '\n') e++;
+            pos_ = e < n_ ? e + 1 : e;
+            line_++;
+            const char *ln = s_ + b;
+            size_t len = e - b;
+            for (size_t i = 0; i < len; i++)
+                if (ln[i] == '#') { len = i; break; }
+            size_t lo = 0, hi = len;
+            while (lo < hi && space(ln[lo])) lo++;
+            while (hi > lo && space(ln[hi - 1])) hi--;
+            if (lo == hi) continue;
+            if (ln[lo] == '}') {
+                if (hi - lo != 1) fail(lo + 1, "unexpected text after '}'");
+                if (depth == 0) fail(lo, "'}' without REPEAT");
+                return true;
+            }
+            if (hi - lo > 6 && memcmp(ln + lo, "REPEAT", 6) == 0 && space(ln[lo + 6])) {
+                size_t i = lo + 6;
+                while (i < hi && space(ln[i])) i++;
+                if (i >= hi || ln[i] < '0' || ln[i] > '9') fail(i, "REPEAT needs a count");
+                uint64_t reps = 0;
+                while (i < hi && ln[i] >= '0' && ln[i] <= '9') {
+                    reps = reps * 10 + (uint64_t)(ln[i] - '0');
+                    if (reps > 1000000000ull) fail(i, "REPEAT count too large");
+                    i++;
+                }
+                while (i < hi && space(ln[i])) i++;
+                if (i + 1 != hi || ln[i] != '{') fail(i, "expected '{' ending the REPEAT line");
+                if (reps == 0) fail(lo, "REPEAT 0 is not allowed");
+                Node nd;
+                nd.block.reset(new Block);
+                nd.block->reps = reps;
+                int open_line = line_;
+                if (!parse_into(nd.block.get(), depth + 1)) {
+                    line_ = open_line;
+                    fail(lo, "REPEAT block is never closed");
+                }
+                blk->items.push_back(std::move(nd));
+                continue;
+            }
+            Node nd;
+            parse_instruction(ln, lo, hi, &nd.ins);
+            blk->items.push_back(std::move(nd));
+        }
+        return false;
+    }
+
+    void parse_instruction(const char *ln, size_t lo, size_t hi, Instr *ins) {
+        size_t i = lo;
+        while (i < hi && (isupper((unsigned char)ln[i]) || isdigit((unsigned char)ln[i]) || ln[i] == '_')) i++;
+        std::string name(ln + lo, i - lo);
+        static const std::map<std::string, int> kNames = {
+            {"H", PG_H}, {"S", PG_S}, {"CX", PG_CX}, {"CNOT", PG_CX}, {"CZ", PG_CZ},
+            {"M", PG_M}, {"MR", PG_MR}, {"R", PG_R}, {"X_ERROR", PG_XERR},
+            {"Z_ERROR", PG_ZERR}, {"DEPOLARIZE1", PG_DEP1}, {"DEPOLARIZE2", PG_DEP2},
+            {"DETECTOR", PG_DET}};
+        auto it = kNames.find(name);
+        if (name.empty() || it == kNames.end()) {
+            size_t j = i;
+            while (j < hi && !space(ln[j]) && ln[j] != '(') j++;
+            fail(lo, "unknown gate '", std::string(ln + lo, j - lo) + "'");
+        }
+        ins->gate = it->second;
+        ins->line = line_;
+        std::vector<double> args;
+        if (i < hi && ln[i] == '(') {
+            size_t close = i;
+            while (close < hi && ln[close] != ')') close++;
+            if (close >= hi) fail(i, "unterminated '('");
+            size_t a = i + 1;
+            while (a <= close) {
+                size_t b = a;
+                while (b < close && ln[b] != ',') b++;
+                std::string tok(ln + a, b - a);
+                char *endp = nullptr;
+                errno = 0;
+                double v = strtod(tok.c_str(), &endp);
+                while (endp && space(*endp)) endp++;
+                if (tok.empty() || endp == tok.c_str() || *endp) fail(a, "bad numeric argument");
+                args.push_back(v);
+                a = b + 1;
+            }
+            i = close + 1;
+        }
+        bool noise = ins->gate >= PG_XERR && ins->gate <= PG_DEP2;
+        if (noise) {
+            if (args.size() != 1) fail(lo, "noise channel takes exactly one probability");
+            ins->p = args[0];
+            if (!(ins->p >= 0.0 && ins->p <= 1.0)) fail(lo, "probability outside [0, 1]");
+        } else if (ins->gate != PG_DET && !args.empty()) {
+            fail(lo, "gate takes no arguments");
+        }
+        if (i < hi && !space(ln[i])) fail(i, "expected a space before the targets");
+        while (i < hi) {
+            while (i < hi && space(ln[i])) i++;
+            if (i >= hi) break;
+            size_t t0 = i;
+            uint64_t v = 0;
+            if (ins->gate == PG_DET) {
+                if (hi - i < 6 || memcmp(ln + i, "rec[-", 5) != 0) fail(i, "expected a rec[-k] target");
+                i += 5;
+                if (i >= hi || !isdigit((unsigned char)ln[i])) fail(i, "expected a rec[-k] target");
+                while (i < hi && isdigit((unsigned char)ln[i])) {
+                    v = v * 10 + (uint64_t)(ln[i] - '0');
+                    if (v > 0xFFFFFFFFull) fail(t0, "lookback too large");
+                    i++;
+                }
+                if (i >= hi || ln[i] != ']') fail(i, "expected ']'");
+                i++;
+                if (v == 0) fail(t0, "rec[-0] does not name a measurement");
+            } else {
+                if (!isdigit((unsigned char)ln[i])) fail(i, "qubit targets are non-negative integers");
+                while (i < hi && isdigit((unsigned char)ln[i])) {
+                    v = v * 10 + (uint64_t)(ln[i] - '0');
+                    if (v > kQubitMask) throw ParseError{STIM_E_UNSUPPORTED, "qubit index above 2^24 - 1"};
+                    i++;
+                }
+            }
+            if (i < hi && !space(ln[i])) fail(i, "bad target");
+            ins->targets.push_back((uint32_t)v);
+        }
+        bool pair = ins->gate == PG_CX || ins->gate == PG_CZ || ins->gate == PG_DEP2;
+        if (pair) {
+            if (ins->targets.size() % 2) fail(lo, "two-qubit gate needs an even number of targets");
+            for (size_t k = 0; k < ins->targets.size(); k += 2)
+                if (ins->targets[k] == ins->targets[k + 1]) fail(lo, "two-qubit gate applied to one qubit");
+        }
+    }
+};
+
+uint32_t opcode_of(int pg) {
+    switch (pg) {
+        case PG_H: return OP_H;
+        case PG_S: return OP_S;
+        case PG_CX: return OP_CX;
+        case PG_CZ: return OP_CZ;
+        case PG_M: return OP_M;
+        case PG_MR: return OP_MR;
+        case PG_R: return OP_R;
+        case PG_XERR: return OP_XERR;
+        case PG_ZERR: return OP_ZERR;
+        case PG_DEP1: return OP_DEP1;
+        default: return OP_DEP2;
+    }
+}
+
+struct Counts {
+    uint64_t instr = 0, meas = 0, det = 0, det_entries = 0;
+    uint64_t gate_t = 0, noise_t = 0;
+    uint64_t targets[OP_COUNT] = {0};
+};
+
+// Counts of a block body executed once (nested loops multiplied out).
+void count_block(const Block &b, Counts *c, uint32_t *max_qubit, bool *any_qubit) {
+    for (const Node &nd : b.items) {
+        if (nd.block) {
+            Counts inner;
+            count_block(*nd.block, &inner, max_qubit, any_qubit);
+            uint64_t r = nd.block->reps;
+            auto mul = [&](uint64_t v) -> uint64_t {
+                if (v && r > UINT64_MAX / v) throw ParseError{STIM_E_UNSUPPORTED, "circuit too large"};
+                return v * r;
+            };
+            c->instr += mul(inner.instr);
+            c->meas += mul(inner.meas);
+            c->det += mul(inner.det);
+            c->det_entries += mul(inner.det_entries);
+            c->gate_t += mul(inner.gate_t);
+            c->noise_t += mul(inner.noise_t);
+            for (int k = 0; k < (int)OP_COUNT; k++) c->targets[k] += mul(inner.targets[k]);
+            if (c->instr > kMaxInstr) throw ParseError{STIM_E_UNSUPPORTED, "more than 2^28 instructions after flattening"};
+            continue;
+        }
+        const Instr &in = nd.ins;
+        c->instr++;
+        if (in.gate == PG_DET) {
+            c->det++;
+            c->det_entries += in.targets.size();
+            continue;
+        }
+        for (uint32_t q : in.targets) {
+            if (!*any_qubit || q > *max_qubit) *max_qubit = q;
+            *any_qubit = true;
+        }
+        uint32_t op = opcode_of(in.gate);
+        uint64_t slots = op_is_pair(op) ? in.targets.size() / 2 : in.targets.size();
+        c->targets[op] += slots;
+        if (op_is_noise(op)) c->noise_t += slots;
+        else c->gate_t += slots;
+        if (in.gate == PG_M || in.gate == PG_MR) c->meas += in.targets.size();
+    }
+}
+
+class Emitter {
+  public:
+    Emitter(HostProgram *hp, uint32_t n) : hp_(hp), stamp_(n, 0), last_(n, 0) {}
+
+    // Emit the body of `b` for its first iteration, with the given starting
+    // instruction ordinal and measurement index. Returns layer executions.
+    uint64_t emit(const Block &b, uint64_t instr, uint64_t meas, uint32_t depth) {
+        if (depth > hp_->max_loop_depth) hp_->max_loop_depth = depth;
+        if (depth > (uint32_t)kMaxLoopDepth) throw ParseError{STIM_E_UNSUPPORTED, "REPEAT nested more than 16 deep"};
+        uint64_t exec = 0;
+        begin_segment();
+        for (const Node &nd : b.items) {
+            if (nd.block) {
+                exec += flush();
+                Counts inner;
+                uint32_t mq = 0;
+                bool any = false;
+                count_block(*nd.block, &inner, &mq, &any);
+                size_t begin_idx = hp_->prog.size();
+                ProgEntry e{};
+                e.kind = ENT_LOOP_BEGIN;
+                e.reps = (uint32_t)nd.block->reps;
+                e.instr_stride = (uint32_t)inner.instr;
+                e.meas_stride = (uint32_t)inner.meas;
+                hp_->prog.push_back(e);
+                uint64_t body = emit(*nd.block, instr, meas, depth + 1);
+                if (hp_->prog.size() == begin_idx + 1) {
+                    hp_->prog.pop_back();       // body without layers: nothing to repeat
+                } else {
+                    ProgEntry f = e;
+                    f.kind = ENT_LOOP_END;
+                    f.op_begin = (uint32_t)begin_idx;
+                    hp_->prog.push_back(f);
+                    hp_->prog[begin_idx].op_begin = (uint32_t)(hp_->prog.size() - 1);
+                }
+                exec += body * nd.block->reps;
+                instr += inner.instr * nd.block->reps;
+                meas += inner.meas * nd.block->reps;
+                begin_segment();
+                continue;
+            }
+            const Instr &in = nd.ins;
+            if (in.gate != PG_DET) {
+                uint32_t op = opcode_of(in.gate);
+                uint32_t table = 0;
+                if (op_is_noise(op)) {
+                    if (in.p == 0.0) {      // p = 0 channels are no-ops and draw nothing
+                        instr++;
+                        continue;
+                    }
+                    table = table_for(in.p);
+                }
+                bool pair = op_is_pair(op);
+                size_t step = pair ? 2 : 1;
+                for (size_t k = 0; k < in.targets.size(); k += step) {
+                    DevOp d{};
+                    uint32_t qa = in.targets[k];
+                    uint32_t qb = pair ? in.targets[k + 1] : qa;
+                    d.a = (op << 24) | qa;
+                    d.instr = (uint32_t)instr;
+                    d.slot = (uint32_t)(k / step);
+                    if (op == OP_M || op == OP_MR) {
+                        d.b = (uint32_t)meas++;
+                    } else if (pair) {
+                        d.b = qb | (table << 24);
+                    } else {
+                        d.b = table << 24;
+                    }
+                    place(d, qa, qb, op_is_collapse(op));
+                }
+            }
+            instr++;
+        }
+        exec += flush();
+        return exec;
+    }
+
+  private:
+    struct LayerBuild {
+        std::vector<DevOp> gate, noise, collapse;
+    };
+    HostProgram *hp_;
+    std::vector<uint32_t> stamp_;
+    std::vector<uint32_t> last_;      // layer index + 1 of the last op on a qubit (this segment)
+    uint32_t seg_ = 0;
+    std::vector<LayerBuild> layers_;
+    uint32_t last_collapse_ = 0;      // layer index + 1 of the last collapsing op
+    std::map<uint64_t, uint32_t> tables_;
+
+    void begin_segment() {
+        seg_++;
+        layers_.clear();
+        last_collapse_ = 0;
+    }
+
+    uint32_t lastq(uint32_t q) const { return stamp_[q] == seg_ ? last_[q] : 0; }
+
+    void place(const DevOp &d, uint32_t qa, uint32_t qb, bool collapse) {
+        uint32_t L = lastq(qa);
+        uint32_t Lb = lastq(qb);
+        if (Lb > L) L = Lb;
+        // L is the first layer index after every layer touching the qubits
+        if (collapse && last_collapse_ > 0 && last_collapse_ - 1 > L) L = last_collapse_ - 1;
+        if (L >= layers_.size()) layers_.resize(L + 1);
+        uint32_t op = d.a >> 24;
+        if (op_is_gate(op)) layers_[L].gate.push_back(d);
+        else if (op_is_noise(op)) layers_[L].noise.push_back(d);
+        else layers_[L].collapse.push_back(d);
+        stamp_[qa] = seg_;
+        last_[qa] = L + 1;
+        stamp_[qb] = seg_;
+        last_[qb] = L + 1;
+        if (collapse) last_collapse_ = L + 1;
+    }
+
+    uint64_t flush() {
+        uint64_t n = 0;
+        for (LayerBuild &lb : layers_) {
+            // group gates and noise by opcode to keep warps uniform; collapsing
+            // ops stay in source order
+            auto by_op = [](const DevOp &x, const DevOp &y) { return (x.a >> 24) < (y.a >> 24); };
+            std::stable_sort(lb.gate.begin(), lb.gate.end(), by_op);
+            std::stable_sort(lb.noise.begin(), lb.noise.end(), by_op);
+            ProgEntry e{};
+            e.kind = ENT_LAYER;
+            e.op_begin = (uint32_t)hp_->ops.size();
+            e.n_gate = (uint32_t)lb.gate.size();
+            e.n_noise = (uint32_t)lb.noise.size();
+            e.n_collapse = (uint32_t)lb.collapse.size();
+            uint32_t tot = e.n_gate + e.n_noise + e.n_collapse;
+            if (tot == 0) continue;
+            if (tot > hp_->max_layer_ops) hp_->max_layer_ops = tot;
+            hp_->ops.insert(hp_->ops.end(), lb.gate.begin(), lb.gate.end());
+            hp_->ops.insert(hp_->ops.end(), lb.noise.begin(), lb.noise.end());
+            hp_->ops.insert(hp_->ops.end(), lb.collapse.begin(), lb.collapse.end());
+            hp_->prog.push_back(e);
+            hp_->num_layers_stored++;
+            n++;
+        }
+        layers_.clear();
+        return n;
+    }
+
+    uint32_t table_for(double p) {
+        uint64_t bits;
+        memcpy(&bits, &p, sizeof bits);
+        auto it = tables_.find(bits);
+        if (it != tables_.end()) return it->second;
+        uint32_t id = (uint32_t)hp_->table_p.size();
+        if (id >= 256) throw ParseError{STIM_E_UNSUPPORTED, "more than 256 distinct noise probabilities"};
+        hp_->table_p.push_back(p);
+        hp_->geo.resize(hp_->geo.size() + 64);
+        geometric_table(p, &hp_->geo[hp_->geo.size() - 64]);
+        tables_[bits] = id;
+        return id;
+    }
+};
+
+// Flattened detector list: absolute measurement index of every rec[-k].
+void collect_detectors(const Block &b, uint64_t *meas, HostProgram *hp) {
+    for (const Node &nd : b.items) {
+        if (nd.block) {
+            for (uint64_t r = 0; r < nd.block->reps; r++) collect_detectors(*nd.block, meas, hp);
+            continue;
+        }
+        const Instr &in = nd.ins;
+        if (in.gate == PG_M || in.gate == PG_MR) {
+            *meas += in.targets.size();
+        } else if (in.gate == PG_DET) {
+            for (uint32_t k : in.targets) {
+                if (k > *meas) {
+                    char buf[128];
+                    snprintf(buf, sizeof buf, "line %d: rec[-%u] reaches before the first measurement", in.line, k);
+                    throw ParseError{STIM_E_PARSE, buf};
+                }
+                hp->det_meas.push_back((uint32_t)(*meas - k));
+            }
+            hp->det_ptr.push_back(hp->det_meas.size());
+        }
+    }
+}
+
+}  // namespace
+
+int compile_circuit(const char *text, size_t len, HostProgram *out, std::string *err) {
+    try {
+        Parser ps(text, len);
+        Block root = ps.parse();
+        Counts c;
+        uint32_t maxq = 0;
+        bool any = false;
+        count_block(root, &c, &maxq, &any);
+        if (c.meas > 0xFFFFFFFFull) throw ParseError{STIM_E_UNSUPPORTED, "more than 2^32 - 1 measurements"};
+        if (c.det_entries > (1ull << 34)) throw ParseError{STIM_E_UNSUPPORTED, "detector lists too large"};
+        HostProgram hp;
+        hp.num_qubits = any ? maxq + 1 : 0;
+        hp.num_meas = c.meas;
+        hp.num_det = c.det;
+        hp.num_gate_targets = c.gate_t;
+        hp.num_noise_targets = c.noise_t;
+        hp.num_instr = c.instr;
+        for (int k = 0; k < (int)OP_COUNT; k++) hp.exec_targets[k] = c.targets[k];
+        hp.det_ptr.reserve(c.det + 1);
+        hp.det_ptr.push_back(0);
+        hp.det_meas.reserve(c.det_entries);
+        uint64_t m = 0;
+        collect_detectors(root, &m, &hp);
+        Emitter em(&hp, hp.num_qubits ? hp.num_qubits : 1);
+        hp.num_layers_exec = em.emit(root, 0, 0, 0);
+        *out = std::move(hp);
+        return 0;
+    } catch (const ParseError &e) {
+        *err = e.msg;
+        return e.code;
+    } catch (const std::bad_alloc &) {
+        *err = "out of host memory while compiling";
+        return STIM_E_OOM;
+    }
+}
+
+}  // namespace stimgb

@@ -1,0 +1,93 @@
+// internal.h -- data shared between the host compiler and the CUDA kernels.
+//
+// A compiled circuit is a small program of entries (fused layers and loop
+// markers) over a flat array of 16-byte op records. REPEAT blocks are kept as
+// loops: an op inside a loop body stores the instruction ordinal and the
+// measurement index of its first iteration, and the kernels add
+// iteration * stride at run time, so ordinals are those of the flattened
+// circuit (the RNG keys depend on them) while the stored program stays the
+// size of one loop body.
+#pragma once
+
+#include <cstddef>
+#include <cstdint>
+#include <string>
+#include <vector>
+
+namespace stimgb {
+
+enum Opcode : uint32_t {
+    OP_H = 0, OP_S, OP_CX, OP_CZ,          // Clifford gates
+    OP_M, OP_MR, OP_R,                     // collapsing operations
+    OP_XERR, OP_ZERR, OP_DEP1, OP_DEP2,    // Pauli noise channels
+    OP_COUNT
+};
+
+inline bool op_is_gate(uint32_t o) { return o <= OP_CZ; }
+inline bool op_is_collapse(uint32_t o) { return o >= OP_M && o <= OP_R; }
+inline bool op_is_noise(uint32_t o) { return o >= OP_XERR && o <= OP_DEP2; }
+inline bool op_is_pair(uint32_t o) { return o == OP_CX || o == OP_CZ || o == OP_DEP2; }
+
+constexpr uint32_t kQubitBits = 24;
+constexpr uint32_t kQubitMask = (1u << kQubitBits) - 1;
+constexpr uint32_t kMaxInstr = 1u << 28;       // instruction ordinals share a counter word with a 4-bit tag
+constexpr int kMaxLoopDepth = 16;
+
+// One target (or target pair) of one instruction.
+//   a:     opcode << 24 | qubit a
+//   b:     qubit b | table << 24 (two-qubit ops, noise table in the top byte)
+//          table << 24 (one-qubit noise)
+//          measurement index of the first loop iteration (M, MR)
+//   instr: flattened instruction ordinal of the first loop iteration
+//   slot:  target index (one-qubit ops) or pair index (two-qubit ops)
+struct DevOp {
+    uint32_t a, b, instr, slot;
+};
+
+// Device status words written by kernels (read by the host after a sync).
+enum : int { DEV_OK = 0, DEV_TIMEOUT = 1, DEV_BAD_PROGRAM = 2 };
+
+enum : uint32_t { ENT_LAYER = 0, ENT_LOOP_BEGIN = 1, ENT_LOOP_END = 2 };
+
+// Program entry (32 bytes).
+//   LAYER:      ops [op_begin, op_begin + n_gate + n_noise + n_collapse), stored
+//               as gates, then noise, then collapsing ops in source order.
+//   LOOP_BEGIN: reps iterations of the entries up to the matching LOOP_END;
+//               each iteration advances instruction ordinals by instr_stride
+//               and measurement indices by meas_stride.
+//   LOOP_END:   op_begin = index of the matching LOOP_BEGIN.
+struct ProgEntry {
+    uint32_t kind;
+    uint32_t op_begin;
+    uint32_t n_gate, n_noise, n_collapse;
+    uint32_t reps;
+    uint32_t instr_stride, meas_stride;
+};
+
+struct HostProgram {
+    uint32_t num_qubits = 0;
+    uint64_t num_meas = 0, num_det = 0;
+    uint64_t num_gate_targets = 0, num_noise_targets = 0, num_instr = 0;
+    uint64_t num_layers_exec = 0;           // layer executions with loops unrolled
+    uint64_t num_layers_stored = 0;
+    uint32_t max_layer_ops = 0;
+    uint32_t max_loop_depth = 0;
+    std::vector<ProgEntry> prog;
+    std::vector<DevOp> ops;
+    std::vector<uint64_t> geo;              // [num_tables][64] geometric thresholds
+    std::vector<double> table_p;
+    std::vector<uint64_t> det_ptr;          // D + 1 offsets into det_meas
+    std::vector<uint32_t> det_meas;         // absolute measurement indices
+    // per-op-type target counts with loops unrolled (for bench accounting)
+    uint64_t exec_targets[OP_COUNT] = {0};
+};
+
+// Parse + compile. Returns 0 or a STIM_E_* code with *err filled.
+int compile_circuit(const char *text, size_t len, HostProgram *out, std::string *err);
+
+// Exact geometric table of the keyed noise procedure:
+//   t = round-half-even(p * 2^32), S_0 = 2^32, S_{k+1} = floor(S_k (2^32 - t) / 2^32),
+//   G[k] = 2^32 - S_{k+1}.
+void geometric_table(double p, uint64_t G[64]);
+
+}  // namespace stimgb

@@ -1,0 +1,78 @@
+// kernels.h -- argument blocks and launchers of the CUDA kernels (host view).
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include <cstdint>
+
+#include "internal.h"
+
+namespace stimgb {
+
+struct FrameArgs {
+    const ProgEntry *prog;
+    uint32_t nprog;
+    const DevOp *ops;
+    const uint64_t *geo;       // [tables][64]
+    const uint64_t *ref;       // packed reference sample (ceil(M/64) words)
+    uint32_t n;                // qubits
+    uint32_t k0, k1;           // Philox key = (seed lo, seed hi)
+    uint64_t word0;            // global 64-shot word of this call's word 0
+    uint64_t nwords;           // words written by this call
+    uint64_t last_mask;        // valid bits of the last word
+    uint64_t *rec;             // measurement-major records [M][rec_stride], or null
+    uint64_t rec_stride;
+    uint64_t *gframe;          // global frame [2][n][gstride] when the tile is not in smem
+    uint64_t gstride;
+    int *status;
+};
+
+cudaError_t launch_frame(const FrameArgs &a, int W, bool gmem, uint32_t grid, uint32_t threads, size_t smem,
+                         cudaStream_t stream);
+
+struct TabCtl {
+    unsigned bar_count;
+    unsigned bar_gen;
+    int abort;
+    uint32_t next_j;
+    uint32_t has_random;
+    uint32_t pivot;
+    uint32_t nk;
+    uint32_t pivot_is_y;
+    uint32_t fix_x;
+    uint32_t use_mask;
+};
+
+struct TabArgs {
+    const ProgEntry *prog;
+    uint32_t nprog;
+    const DevOp *ops;
+    uint32_t n, nw;            // qubits, words per column plane
+    uint64_t *tx, *tz;         // [2n][nw] physical columns
+    uint32_t *sign;            // [2n] physical
+    uint32_t *perm;            // [2n] logical column -> physical column
+    uint64_t *ref;             // packed outcomes (zeroed before launch)
+    uint64_t *detflag;         // packed deterministic flags (zeroed before launch)
+    uint32_t *klist;           // [n] scratch: CNOT targets of the current random measurement
+    uint64_t *kmask;           // [nw] scratch: the same targets as a mask
+    uint32_t *rnd;             // [max collapse ops per layer] scratch: random flags
+    TabCtl *ctl;               // zeroed before launch
+    int *status;
+};
+
+cudaError_t launch_tableau_init(const TabArgs &a, cudaStream_t stream);
+// Cooperative launch; blocks * threads must be co-resident.
+cudaError_t launch_tableau(const TabArgs &a, uint32_t blocks, uint32_t threads, cudaStream_t stream);
+int tableau_max_blocks(uint32_t threads, int device);
+
+// det[k][w] = XOR over m in D_k of rec[m][w] ^ ref(m), padding bits cleared.
+cudaError_t launch_detectors(const uint64_t *rec, uint64_t rec_stride, const uint64_t *det_ptr,
+                             const uint32_t *det_meas, const uint64_t *ref, uint64_t ndet, uint64_t nwords,
+                             uint64_t last_mask, uint64_t *det, uint64_t det_stride, cudaStream_t stream);
+
+// Bit transpose: in has `rows` rows of in_stride words (bit s of a row = column s);
+// out gets `cols` rows of out_stride = ceil(rows/64) words.
+cudaError_t launch_transpose(const uint64_t *in, uint64_t rows, uint64_t in_stride, uint64_t cols,
+                             uint64_t *out, uint64_t out_stride, cudaStream_t stream);
+
+}  // namespace stimgb

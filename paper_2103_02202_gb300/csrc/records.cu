@@ -1,0 +1,120 @@
+// records.cu -- detection events and record layout conversion.
+//
+// Detection events (Section 5.6 of the paper): a detector is a set of
+// measurements whose XOR is deterministic without noise; its event bit is the
+// XOR of the measurements' flips, i.e. of (record ^ reference) over its set.
+//
+// Layout conversion: measurement-major rows (one row per measurement, bit s =
+// shot s) become shot-major rows (one row per shot, bit m = measurement m,
+// the LSB-first order of the b8 format of Section 5.6). One warp transposes a
+// 64 x 64 bit block: lane l holds block rows l and l + 32; a 32-bit-distance
+// swap inside the lane and five shuffle-xor stages exchange the off-diagonal
+// sub-blocks.
+#include <cuda_runtime.h>
+
+#include "device.cuh"
+#include "kernels.h"
+
+namespace stimgb {
+
+__global__ void detector_kernel(const uint64_t *__restrict__ rec, uint64_t rec_stride,
+                                const uint64_t *__restrict__ det_ptr, const uint32_t *__restrict__ det_meas,
+                                const uint64_t *__restrict__ ref, uint64_t ndet, uint64_t nwords,
+                                uint64_t last_mask, uint64_t *__restrict__ det, uint64_t det_stride) {
+    const uint64_t total = ndet * nwords;
+    for (uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; i < total;
+         i += (uint64_t)gridDim.x * blockDim.x) {
+        const uint64_t k = i / nwords, w = i % nwords;
+        const uint64_t b = __ldg(det_ptr + k), e = __ldg(det_ptr + k + 1);
+        uint64_t v = 0;
+        for (uint64_t t = b; t < e; t++) {
+            const uint32_t m = __ldg(det_meas + t);
+            const uint64_t refm = 0ull - ((__ldg(ref + (m >> 6)) >> (m & 63)) & 1ull);
+            v ^= rec[(uint64_t)m * rec_stride + w] ^ refm;
+        }
+        if (w == nwords - 1) v &= last_mask;
+        det[k * det_stride + w] = v;
+    }
+}
+
+__device__ __forceinline__ void transpose64_warp(uint64_t &a0, uint64_t &a1, uint32_t lane) {
+    // stage 32: rows r and r + 32 live in the same lane
+    {
+        const uint64_t m = 0x00000000FFFFFFFFull;
+        const uint64_t t = ((a0 >> 32) ^ a1) & m;
+        a1 ^= t;
+        a0 ^= t << 32;
+    }
+    const uint64_t masks[5] = {0x0000FFFF0000FFFFull, 0x00FF00FF00FF00FFull, 0x0F0F0F0F0F0F0F0Full,
+                               0x3333333333333333ull, 0x5555555555555555ull};
+#pragma unroll
+    for (int s = 0; s < 5; s++) {
+        const int j = 16 >> s;
+        const uint64_t m = masks[s];
+        const uint64_t p0 = __shfl_xor_sync(0xffffffffu, a0, j);
+        const uint64_t p1 = __shfl_xor_sync(0xffffffffu, a1, j);
+        if ((lane & j) == 0) {      // this lane holds the upper row r, partner row r + j
+            a0 ^= (((a0 >> j) ^ p0) & m) << j;
+            a1 ^= (((a1 >> j) ^ p1) & m) << j;
+        } else {                    // this lane holds row r + j, partner row r
+            a0 ^= ((p0 >> j) ^ a0) & m;
+            a1 ^= ((p1 >> j) ^ a1) & m;
+        }
+    }
+}
+
+// One warp per 64 x 64 block; a CTA's warps take consecutive row blocks of the
+// same column block so that each output row receives a contiguous run.
+__global__ void __launch_bounds__(256) transpose_kernel(const uint64_t *__restrict__ in, uint64_t rows,
+                                                        uint64_t in_stride, uint64_t cols,
+                                                        uint64_t *__restrict__ out, uint64_t out_stride) {
+    const uint32_t lane = threadIdx.x & 31;
+    const uint32_t wpb = blockDim.x >> 5;
+    const uint64_t row_blocks = (rows + 63) / 64;
+    const uint64_t col_blocks = (cols + 63) / 64;
+    const uint64_t rb_groups = (row_blocks + wpb - 1) / wpb;
+    const uint64_t total = rb_groups * col_blocks;
+    for (uint64_t g = blockIdx.x; g < total; g += gridDim.x) {
+        const uint64_t cb = g / rb_groups;
+        const uint64_t rb = (g % rb_groups) * wpb + (threadIdx.x >> 5);
+        if (rb >= row_blocks) continue;
+        const uint64_t r0 = rb * 64 + lane, r1 = r0 + 32;
+        uint64_t a0 = r0 < rows ? __ldg(in + r0 * in_stride + cb) : 0;
+        uint64_t a1 = r1 < rows ? __ldg(in + r1 * in_stride + cb) : 0;
+        transpose64_warp(a0, a1, lane);
+        const uint64_t c0 = cb * 64 + lane, c1 = c0 + 32;
+        if (c0 < cols) out[c0 * out_stride + rb] = a0;
+        if (c1 < cols) out[c1 * out_stride + rb] = a1;
+    }
+}
+
+static uint32_t grid_for(uint64_t items, uint32_t threads) {
+    uint64_t g = (items + threads - 1) / threads;
+    if (g < 1) g = 1;
+    if (g > 65535ull * 32) g = 65535ull * 32;
+    return (uint32_t)g;
+}
+
+cudaError_t launch_detectors(const uint64_t *rec, uint64_t rec_stride, const uint64_t *det_ptr,
+                             const uint32_t *det_meas, const uint64_t *ref, uint64_t ndet, uint64_t nwords,
+                             uint64_t last_mask, uint64_t *det, uint64_t det_stride, cudaStream_t stream) {
+    if (ndet == 0 || nwords == 0) return cudaSuccess;
+    const uint32_t threads = 256;
+    detector_kernel<<<grid_for(ndet * nwords, threads), threads, 0, stream>>>(
+        rec, rec_stride, det_ptr, det_meas, ref, ndet, nwords, last_mask, det, det_stride);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_transpose(const uint64_t *in, uint64_t rows, uint64_t in_stride, uint64_t cols,
+                             uint64_t *out, uint64_t out_stride, cudaStream_t stream) {
+    if (rows == 0 || cols == 0) return cudaSuccess;
+    const uint32_t threads = 256;
+    const uint64_t row_blocks = (rows + 63) / 64, col_blocks = (cols + 63) / 64;
+    const uint64_t groups = ((row_blocks + 7) / 8) * col_blocks;
+    uint64_t grid = groups < 1 ? 1 : groups;
+    if (grid > 1u << 20) grid = 1u << 20;
+    transpose_kernel<<<(uint32_t)grid, threads, 0, stream>>>(in, rows, in_stride, cols, out, out_stride);
+    return cudaGetLastError();
+}
+
+}  // namespace stimgb

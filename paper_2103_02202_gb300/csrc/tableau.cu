@@ -1,0 +1,443 @@
+// tableau.cu -- noiseless reference sample by inverse-tableau simulation
+// (Section 4 of the paper, "Tracking the Tableau").
+//
+// The tableau T tracks the inverse of the circuit so far: logical column 2q
+// holds the start-of-time image of X_q, column 2q+1 that of Z_q, each as an
+// n-term Pauli string (x words, z words) with a sign. Columns are stored
+// column-major ([column][nw] words per plane) behind a permutation, so an H
+// (which swaps the X_q and Z_q columns) is a swap of two permutation entries.
+//
+// Folding a gate prepends its inverse: new column(g) = T(G^dagger g G),
+//   S:  X_a <- -i X_a Z_a
+//   CX: X_c <- X_c X_t,  Z_t <- Z_t Z_c
+//   CZ: X_a <- X_a Z_b,  X_b <- X_b Z_a
+// each a column product whose phase is accumulated with the two-bit-counter
+// method of the paper's Pauli-multiplication figure (one warp per product,
+// warp-reduced popcounts).
+//
+// A measurement of Z_q is deterministic when column Z_q has no X/Y term; the
+// outcome is its sign. Otherwise a pivot p (lowest X/Y row) is chosen, CNOTs
+// p -> k are appended for every other X/Y row k, then S (if the pivot term is
+// Y) and H turn the pivot term into Z, and -- because the paper leaves the coin
+// open -- an X is appended on the pivot when the sign is -, so the outcome is
+// always 0. Appends act on rows of every column; the sign update of the CNOT
+// chain uses the closed form
+//   flips = popcount(z & (z_p ? x : ~x) & K) + C(popcount(z & K), 2)  (mod 2).
+// A reset is a measurement followed by forcing the sign of column Z_q to +.
+//
+// Work inside a layer is spread over the whole grid; a bounded software grid
+// barrier (cooperative launch, so all CTAs are resident) separates phases.
+// Collapsing ops of a layer are first checked in parallel; outcomes before the
+// first random one are written in parallel; from there a leader warp walks
+// the ops in source order and every random one costs two grid barriers.
+#include <cuda_runtime.h>
+
+#include "device.cuh"
+#include "kernels.h"
+
+namespace stimgb {
+
+namespace {
+
+constexpr uint64_t kBarrierTimeoutNs = 2000000000ull;   // 2 s per wait
+constexpr uint32_t kListLimit = 16;                     // CNOT targets handled by list, else by mask
+
+__device__ __forceinline__ bool tab_barrier(const TabArgs &a) {
+    if (gridDim.x == 1) {
+        __syncthreads();
+        return true;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        volatile unsigned *gen = &a.ctl->bar_gen;
+        const unsigned g = *gen;
+        __threadfence();
+        const unsigned arrived = atomicAdd(&a.ctl->bar_count, 1u);
+        if (arrived == gridDim.x - 1) {
+            atomicExch(&a.ctl->bar_count, 0u);
+            __threadfence();
+            atomicAdd(&a.ctl->bar_gen, 1u);
+        } else {
+            const uint64_t t0 = globaltimer_ns();
+            while (*gen == g) {
+                if (*(volatile int *)&a.ctl->abort) break;
+                __nanosleep(64);
+                if (globaltimer_ns() - t0 > kBarrierTimeoutNs) {
+                    atomicExch(&a.ctl->abort, 1);
+                    atomicExch(a.status, DEV_TIMEOUT);
+                    break;
+                }
+            }
+        }
+        __threadfence();
+    }
+    __syncthreads();
+    return *(volatile int *)&a.ctl->abort == 0;
+}
+
+__device__ __forceinline__ uint32_t ld_u32(const uint32_t *p) { return __ldcg(p); }
+__device__ __forceinline__ uint64_t ld_u64(const uint64_t *p) { return __ldcg(p); }
+
+// dst column := dst * src (logical columns); extra = additional power of i.
+__device__ void column_product(const TabArgs &a, uint32_t dst, uint32_t src, uint32_t extra, uint32_t lane) {
+    const uint32_t pd = ld_u32(a.perm + dst), ps = ld_u32(a.perm + src);
+    uint64_t *dx = a.tx + (uint64_t)pd * a.nw, *dz = a.tz + (uint64_t)pd * a.nw;
+    const uint64_t *sx = a.tx + (uint64_t)ps * a.nw, *sz = a.tz + (uint64_t)ps * a.nw;
+    uint64_t c1 = 0, c2 = 0;   // per-bit two-bit counters of the phase exponent
+    for (uint32_t w = lane; w < a.nw; w += 32) {
+        const uint64_t x1 = ld_u64(dx + w), z1 = ld_u64(dz + w);
+        const uint64_t x2 = ld_u64(sx + w), z2 = ld_u64(sz + w);
+        const uint64_t nx = x1 ^ x2, nz = z1 ^ z2;
+        const uint64_t x1z2 = x1 & z2;
+        const uint64_t anti = (x2 & z1) ^ x1z2;            // positions that anticommute
+        c2 ^= (c1 ^ nx ^ nz ^ x1z2) & anti;               // +1 or -1 per anticommuting position
+        c1 ^= anti;
+        __stcg(dx + w, nx);
+        __stcg(dz + w, nz);
+    }
+    uint32_t ph = (uint32_t)(__popcll(c1) + 2 * __popcll(c2));
+    for (int d = 16; d > 0; d >>= 1) ph += __shfl_xor_sync(0xffffffffu, ph, d);
+    if (lane == 0) {
+        const uint32_t tot = (ph + extra + 2u * ld_u32(a.sign + pd) + 2u * ld_u32(a.sign + ps)) & 3u;
+        __stcg(a.sign + pd, tot >> 1);   // tot is even: the product of the images is Hermitian
+    }
+}
+
+__device__ __forceinline__ void write_outcome(const TabArgs &a, uint32_t opc, uint32_t m, uint32_t bit,
+                                              uint32_t det) {
+    if (opc == OP_R) return;
+    const unsigned long long b = 1ull << (m & 63);
+    if (bit) atomicOr((unsigned long long *)(a.ref + (m >> 6)), b);
+    if (det) atomicOr((unsigned long long *)(a.detflag + (m >> 6)), b);
+}
+
+// Leader warp: walk collapsing ops from j in source order. Deterministic ones
+// are resolved here; at the first random one the elimination data is
+// published for the grid. Returns nothing; results go to a.ctl.
+__device__ void leader_walk(const TabArgs &a, const DevOp *cops, uint32_t nc, uint32_t j, uint32_t meas_off,
+                            uint32_t lane) {
+    for (; j < nc; j++) {
+        const DevOp op = cops[j];
+        const uint32_t opc = op.a >> 24, q = op.a & kQubitMask;
+        const uint32_t pz = ld_u32(a.perm + 2 * q + 1);
+        const uint64_t *x = a.tx + (uint64_t)pz * a.nw, *z = a.tz + (uint64_t)pz * a.nw;
+        int64_t pivot = -1;
+        for (uint32_t base = 0; base < a.nw && pivot < 0; base += 32) {
+            const uint32_t w = base + lane;
+            const uint64_t v = w < a.nw ? ld_u64(x + w) : 0;
+            const uint32_t bal = __ballot_sync(0xffffffffu, v != 0);
+            if (bal) {
+                const uint32_t src = __ffs(bal) - 1;
+                const uint64_t vv = __shfl_sync(0xffffffffu, v, src);
+                pivot = (int64_t)(base + src) * 64 + (__ffsll((long long)vv) - 1);
+            }
+        }
+        if (pivot < 0) {
+            if (lane == 0) {
+                const uint32_t s = ld_u32(a.sign + pz);
+                write_outcome(a, opc, op.b + meas_off, s, 1);
+                if (opc != OP_M) __stcg(a.sign + pz, 0u);
+            }
+            __syncwarp();
+            continue;
+        }
+        const uint32_t p = (uint32_t)pivot;
+        const uint32_t pw = p >> 6;
+        const uint64_t pb = 1ull << (p & 63);
+        uint32_t cnt = 0, m = 0;
+        for (uint32_t base = 0; base < a.nw; base += 32) {
+            const uint32_t w = base + lane;
+            uint64_t xv = w < a.nw ? ld_u64(x + w) : 0;
+            const uint64_t zv = w < a.nw ? ld_u64(z + w) : 0;
+            if (w == pw) xv &= ~pb;
+            if (w < a.nw) __stcg(a.kmask + w, xv);
+            const uint32_t c = __popcll(xv);
+            uint32_t incl = c;
+            for (int d = 1; d < 32; d <<= 1) {
+                const uint32_t t = __shfl_up_sync(0xffffffffu, incl, d);
+                if (lane >= (uint32_t)d) incl += t;
+            }
+            uint32_t off = cnt + incl - c;
+            uint64_t rest = xv;
+            while (rest) {
+                const uint32_t bpos = __ffsll((long long)rest) - 1;
+                __stcg(a.klist + off, w * 64 + bpos);
+                off++;
+                rest &= rest - 1;
+            }
+            cnt += __shfl_sync(0xffffffffu, incl, 31);
+            uint32_t mz = __popcll(xv & zv);
+            for (int d = 16; d > 0; d >>= 1) mz += __shfl_xor_sync(0xffffffffu, mz, d);
+            m += mz;
+        }
+        if (lane == 0) {
+            const uint32_t zp = (uint32_t)((ld_u64(z + pw) & pb) != 0);
+            // column Z_q after the CNOT chain: sign flips floor(m/2) (z_p = 0) or ceil(m/2) (z_p = 1)
+            const uint32_t flips = zp ? ((m + 1) >> 1) : (m >> 1);
+            const uint32_t s_new = ld_u32(a.sign + pz) ^ (flips & 1u);
+            a.ctl->pivot = p;
+            a.ctl->nk = cnt;
+            a.ctl->pivot_is_y = zp ^ (m & 1u);
+            a.ctl->fix_x = s_new;                 // outcome 0: append X on the pivot if the sign is -
+            a.ctl->use_mask = cnt > kListLimit ? 1u : 0u;
+            a.ctl->next_j = j;
+            a.ctl->has_random = 1u;
+            // outcome 0 and not deterministic: nothing to set in ref / detflag
+        }
+        __syncwarp();
+        return;
+    }
+    if (lane == 0) {
+        a.ctl->next_j = nc;
+        a.ctl->has_random = 0u;
+    }
+    __syncwarp();
+}
+
+// Pivot collapse on bits (xp, zp) of one column: optional S, then H, then X fix.
+__device__ __forceinline__ void pivot_ops(uint32_t &xp, uint32_t &zp, uint32_t &s, uint32_t py, uint32_t fx) {
+    if (py) {            // S: X -> -Y, Y -> X
+        s ^= xp & (zp ^ 1u);
+        zp ^= xp;
+    }
+    s ^= xp & zp;        // H: Y -> -Y, X <-> Z
+    const uint32_t t = xp;
+    xp = zp;
+    zp = t;
+    if (fx) s ^= zp;     // X: Z -> -Z, Y -> -Y
+}
+
+__device__ __forceinline__ void set_bit(uint64_t *w, uint64_t b, uint32_t v) {
+    const uint64_t old = ld_u64(w);
+    __stcg(w, v ? (old | b) : (old & ~b));
+}
+
+// Apply the random measurement's appends to every column (list form: one thread per column).
+__device__ void column_pass_list(const TabArgs &a, uint32_t p, uint32_t nk, uint32_t py, uint32_t fx,
+                                 uint32_t gtid, uint32_t nthreads) {
+    const uint32_t pw = p >> 6;
+    const uint64_t pb = 1ull << (p & 63);
+    for (uint32_t c = gtid; c < 2 * a.n; c += nthreads) {
+        uint64_t *x = a.tx + (uint64_t)c * a.nw, *z = a.tz + (uint64_t)c * a.nw;
+        uint32_t xp = (ld_u64(x + pw) & pb) != 0;
+        uint32_t zp = (ld_u64(z + pw) & pb) != 0;
+        uint32_t s = ld_u32(a.sign + c);
+        for (uint32_t t = 0; t < nk; t++) {
+            const uint32_t k = ld_u32(a.klist + t);
+            const uint64_t kb = 1ull << (k & 63);
+            const uint32_t zk = (ld_u64(z + (k >> 6)) & kb) != 0;
+            if (xp) {
+                const uint64_t xw = ld_u64(x + (k >> 6));
+                const uint32_t xk = (xw & kb) != 0;
+                s ^= zk & (xk ^ zp ^ 1u);
+                __stcg(x + (k >> 6), xw ^ kb);
+            }
+            zp ^= zk;
+        }
+        pivot_ops(xp, zp, s, py, fx);
+        set_bit(x + pw, pb, xp);
+        set_bit(z + pw, pb, zp);
+        __stcg(a.sign + c, s);
+    }
+}
+
+// Mask form: one warp per column, word-parallel.
+__device__ void column_pass_mask(const TabArgs &a, uint32_t p, uint32_t py, uint32_t fx, uint32_t gwarp,
+                                 uint32_t nwarps, uint32_t lane) {
+    const uint32_t pw = p >> 6;
+    const uint64_t pb = 1ull << (p & 63);
+    for (uint32_t c = gwarp; c < 2 * a.n; c += nwarps) {
+        uint64_t *x = a.tx + (uint64_t)c * a.nw, *z = a.tz + (uint64_t)c * a.nw;
+        const uint32_t xp = (ld_u64(x + pw) & pb) != 0;
+        const uint32_t zp = (ld_u64(z + pw) & pb) != 0;
+        uint32_t cnt_a = 0, cnt_b = 0;
+        for (uint32_t w = lane; w < a.nw; w += 32) {
+            const uint64_t kw = ld_u64(a.kmask + w);
+            const uint64_t zw = ld_u64(z + w);
+            cnt_b += __popcll(zw & kw);
+            if (xp) {
+                const uint64_t xw = ld_u64(x + w);
+                cnt_a += __popcll(zw & (zp ? xw : ~xw) & kw);
+                __stcg(x + w, xw ^ kw);
+            }
+        }
+        for (int d = 16; d > 0; d >>= 1) {
+            cnt_a += __shfl_xor_sync(0xffffffffu, cnt_a, d);
+            cnt_b += __shfl_xor_sync(0xffffffffu, cnt_b, d);
+        }
+        __syncwarp();
+        if (lane == 0) {
+            uint32_t s = ld_u32(a.sign + c);
+            if (xp) {
+                const uint64_t pairs = (uint64_t)cnt_b * (cnt_b - (cnt_b > 0 ? 1u : 0u)) / 2;
+                s ^= (uint32_t)((cnt_a + pairs) & 1u);
+            }
+            uint32_t xn = xp, zn = zp ^ (cnt_b & 1u);
+            pivot_ops(xn, zn, s, py, fx);
+            set_bit(x + pw, pb, xn);
+            set_bit(z + pw, pb, zn);
+            __stcg(a.sign + c, s);
+        }
+        __syncwarp();
+    }
+}
+
+}  // namespace
+
+__global__ void tableau_init_kernel(TabArgs a) {
+    for (uint32_t q = blockIdx.x * blockDim.x + threadIdx.x; q < a.n; q += gridDim.x * blockDim.x) {
+        a.tx[(uint64_t)(2 * q) * a.nw + (q >> 6)] = 1ull << (q & 63);
+        a.tz[(uint64_t)(2 * q + 1) * a.nw + (q >> 6)] = 1ull << (q & 63);
+        a.perm[2 * q] = 2 * q;
+        a.perm[2 * q + 1] = 2 * q + 1;
+    }
+}
+
+__global__ void __launch_bounds__(512) tableau_kernel(TabArgs a) {
+    const uint32_t lane = threadIdx.x & 31;
+    const uint32_t wpb = blockDim.x >> 5;
+    const uint32_t gwarp = blockIdx.x * wpb + (threadIdx.x >> 5);
+    const uint32_t nwarps = gridDim.x * wpb;
+    const uint32_t gtid = blockIdx.x * blockDim.x + threadIdx.x;
+    const uint32_t nthreads = gridDim.x * blockDim.x;
+    const bool leader = blockIdx.x == 0 && threadIdx.x < 32;
+    __shared__ uint32_t s_first;
+
+    uint32_t meas_off = 0;
+    uint32_t loop_pc[kMaxLoopDepth];
+    uint32_t loop_iter[kMaxLoopDepth];
+    int sp = 0;
+    uint32_t pc = 0;
+    while (pc < a.nprog) {
+        const ProgEntry e = a.prog[pc];
+        if (e.kind == ENT_LOOP_BEGIN) {
+            if (sp >= kMaxLoopDepth) {
+                if (gtid == 0) atomicExch(a.status, DEV_BAD_PROGRAM);
+                return;
+            }
+            loop_pc[sp] = pc;
+            loop_iter[sp] = 0;
+            sp++;
+            pc++;
+            continue;
+        }
+        if (e.kind == ENT_LOOP_END) {
+            if (sp <= 0) {
+                if (gtid == 0) atomicExch(a.status, DEV_BAD_PROGRAM);
+                return;
+            }
+            const uint32_t it = ++loop_iter[sp - 1];
+            if (it < e.reps) {
+                meas_off += e.meas_stride;
+                pc = loop_pc[sp - 1] + 1;
+            } else {
+                meas_off -= e.meas_stride * (e.reps - 1);
+                sp--;
+                pc++;
+            }
+            continue;
+        }
+        pc++;
+        const DevOp *ops = a.ops + e.op_begin;
+        if (e.n_gate) {
+            for (uint32_t t = gwarp; t < 2 * e.n_gate; t += nwarps) {
+                const DevOp op = ops[t >> 1];
+                const uint32_t k = t & 1, opc = op.a >> 24;
+                const uint32_t qa = op.a & kQubitMask, qb = op.b & kQubitMask;
+                switch (opc) {
+                    case OP_H:
+                        if (k == 0 && lane == 0) {
+                            const uint32_t u = ld_u32(a.perm + 2 * qa), v = ld_u32(a.perm + 2 * qa + 1);
+                            __stcg(a.perm + 2 * qa, v);
+                            __stcg(a.perm + 2 * qa + 1, u);
+                        }
+                        break;
+                    case OP_S:
+                        if (k == 0) column_product(a, 2 * qa, 2 * qa + 1, 3u, lane);
+                        break;
+                    case OP_CX:
+                        if (k == 0) column_product(a, 2 * qa, 2 * qb, 0u, lane);
+                        else column_product(a, 2 * qb + 1, 2 * qa + 1, 0u, lane);
+                        break;
+                    case OP_CZ:
+                        if (k == 0) column_product(a, 2 * qa, 2 * qb + 1, 0u, lane);
+                        else column_product(a, 2 * qb, 2 * qa + 1, 0u, lane);
+                        break;
+                    default:
+                        break;
+                }
+            }
+            if (!tab_barrier(a)) return;
+        }
+        if (e.n_collapse == 0) continue;
+        const DevOp *cops = ops + e.n_gate + e.n_noise;
+        const uint32_t nc = e.n_collapse;
+        // (A) which collapsing ops are random, checked in parallel
+        for (uint32_t j = gwarp; j < nc; j += nwarps) {
+            const uint32_t q = cops[j].a & kQubitMask;
+            const uint64_t *x = a.tx + (uint64_t)ld_u32(a.perm + 2 * q + 1) * a.nw;
+            uint32_t any = 0;
+            for (uint32_t w = lane; w < a.nw; w += 32) any |= ld_u64(x + w) != 0;
+            any = __any_sync(0xffffffffu, any);
+            if (lane == 0) __stcg(a.rnd + j, any);
+        }
+        if (!tab_barrier(a)) return;
+        // (B) first random op; everything before it is deterministic and independent
+        if (threadIdx.x == 0) s_first = nc;
+        __syncthreads();
+        for (uint32_t j = threadIdx.x; j < nc; j += blockDim.x)
+            if (ld_u32(a.rnd + j)) atomicMin(&s_first, j);
+        __syncthreads();
+        const uint32_t first = s_first;
+        for (uint32_t j = gtid; j < first; j += nthreads) {
+            const DevOp op = cops[j];
+            const uint32_t opc = op.a >> 24, q = op.a & kQubitMask;
+            const uint32_t pz = ld_u32(a.perm + 2 * q + 1);
+            write_outcome(a, opc, op.b + meas_off, ld_u32(a.sign + pz), 1);
+            if (opc != OP_M) __stcg(a.sign + pz, 0u);
+        }
+        if (!tab_barrier(a)) return;
+        if (first >= nc) continue;
+        // (C) sequential from the first random op
+        uint32_t j = first;
+        for (;;) {
+            if (leader) leader_walk(a, cops, nc, j, meas_off, lane);
+            if (!tab_barrier(a)) return;
+            if (!ld_u32(&a.ctl->has_random)) break;
+            j = ld_u32(&a.ctl->next_j);
+            const uint32_t p = ld_u32(&a.ctl->pivot), nk = ld_u32(&a.ctl->nk);
+            const uint32_t py = ld_u32(&a.ctl->pivot_is_y), fx = ld_u32(&a.ctl->fix_x);
+            if (ld_u32(&a.ctl->use_mask)) column_pass_mask(a, p, py, fx, gwarp, nwarps, lane);
+            else column_pass_list(a, p, nk, py, fx, gtid, nthreads);
+            if (!tab_barrier(a)) return;
+            j++;
+        }
+    }
+}
+
+cudaError_t launch_tableau_init(const TabArgs &a, cudaStream_t stream) {
+    const uint32_t threads = 256;
+    uint32_t blocks = (a.n + threads - 1) / threads;
+    if (blocks == 0) blocks = 1;
+    if (blocks > 4096) blocks = 4096;
+    tableau_init_kernel<<<blocks, threads, 0, stream>>>(a);
+    return cudaGetLastError();
+}
+
+int tableau_max_blocks(uint32_t threads, int device) {
+    int per_sm = 0, sms = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, tableau_kernel, (int)threads, 0) != cudaSuccess)
+        return 1;
+    if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, device) != cudaSuccess) return 1;
+    const int b = per_sm * sms;
+    return b > 0 ? b : 1;
+}
+
+cudaError_t launch_tableau(const TabArgs &a, uint32_t blocks, uint32_t threads, cudaStream_t stream) {
+    TabArgs args = a;
+    void *params[] = {&args};
+    return cudaLaunchCooperativeKernel((const void *)tableau_kernel, dim3(blocks), dim3(threads), params, 0,
+                                       stream);
+}
+
+}  // namespace stimgb

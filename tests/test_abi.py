@@ -1,0 +1,146 @@
+"""The C-ABI library loads and exports every function include/stimgb.h
+declares; the host compiler (no GPU needed) agrees with the oracle's counts
+and rejects malformed circuits."""
+import ctypes
+import os
+import re
+
+import pytest
+
+import oracle
+import paper_2103_02202_gb300 as sg
+from paper_2103_02202_gb300 import build as sgbuild
+from paper_2103_02202_gb300 import workloads as W
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+@pytest.fixture(scope="module", autouse=True)
+def built():
+    sgbuild.build()
+    yield
+
+
+def declared_functions():
+    names = []
+    for h in os.listdir(os.path.join(ROOT, "include")):
+        if not h.endswith(".h"):
+            continue
+        txt = open(os.path.join(ROOT, "include", h)).read()
+        txt = re.sub(r"/\*.*?\*/", "", txt, flags=re.S)
+        names += re.findall(r"^\s*(?:int|void)\s+(stim_\w+)\s*\(", txt, flags=re.M)
+    return sorted(set(names))
+
+
+def test_library_exports_every_declared_symbol():
+    lib = ctypes.CDLL(sg.library_path())
+    decl = declared_functions()
+    assert decl, "no declarations found"
+    for name in decl:
+        assert hasattr(lib, name), name
+    assert sorted(sg.EXPORTED_SYMBOLS) == decl
+
+
+def test_binding_fails_loudly_without_library(monkeypatch):
+    monkeypatch.setattr(sg, "_lib", None)
+    monkeypatch.setattr(sg, "_LIB_PATH", "/nonexistent/libstimgb.so")
+    with pytest.raises(RuntimeError):
+        sg.library()
+
+
+CIRCUITS = {
+    "surface_d3": W.surface_code_memory(3, 3, 1e-3),
+    "surface_d5_noiseless": W.surface_code_memory(5, 4, 0.0),
+    "repetition": W.repetition_code(5, 20, 0.01),
+    "random_clifford": W.random_clifford(60, 20, 7),
+    "random_noisy": W.random_clifford(40, 10, 8, p=0.01),
+    "nested": "REPEAT 3 {\n H 0\n REPEAT 2 {\n CX 0 1\n M 1\n }\n DETECTOR rec[-1] rec[-2]\n}\nM 0\n",
+    "empty": "",
+    "comments": "# only a comment\n\n   \n",
+}
+
+
+@pytest.mark.parametrize("name", sorted(CIRCUITS))
+def test_counts_match_oracle(name):
+    text = CIRCUITS[name]
+    h = sg.stim_compile(text)
+    try:
+        info = sg.stim_info_get(h)
+    finally:
+        sg.stim_free(h)
+    o = oracle.Circuit(text)
+    assert info["num_qubits"] == o.num_qubits
+    assert info["num_measurements"] == o.num_measurements
+    assert info["num_detectors"] == o.num_detectors
+    assert info["num_gate_targets"] == o.num_gate_targets
+    assert info["num_noise_targets"] == o.num_noise_targets
+    assert info["num_instructions"] == o.num_instructions
+
+
+def test_surface_code_layers_are_fused():
+    d, r = 5, 5
+    h = sg.stim_compile(W.surface_code_memory(d, r, 1e-3))
+    info = sg.stim_info_get(h)
+    sg.stim_free(h)
+    # per round: H, 4 CX steps, H, MR (+ noise folded into neighbouring layers)
+    assert info["num_layers"] <= r * 16 + 8
+    assert info["num_program_layers"] < info["num_layers"]
+
+
+BAD = [
+    ("FOO 0\n", sg.STIM_E_PARSE),
+    ("H -1\n", sg.STIM_E_PARSE),
+    ("H 1.5\n", sg.STIM_E_PARSE),
+    ("CX 0 1 2\n", sg.STIM_E_PARSE),
+    ("CX 3 3\n", sg.STIM_E_PARSE),
+    ("CZ 1 1\n", sg.STIM_E_PARSE),
+    ("DEPOLARIZE2(0.1) 4 4\n", sg.STIM_E_PARSE),
+    ("X_ERROR(1.5) 0\n", sg.STIM_E_PARSE),
+    ("X_ERROR(-0.1) 0\n", sg.STIM_E_PARSE),
+    ("X_ERROR 0\n", sg.STIM_E_PARSE),
+    ("X_ERROR(0.1, 0.2) 0\n", sg.STIM_E_PARSE),
+    ("H(0.1) 0\n", sg.STIM_E_PARSE),
+    ("M 0\nDETECTOR rec[-2]\n", sg.STIM_E_PARSE),
+    ("M 0\nDETECTOR rec[-0]\n", sg.STIM_E_PARSE),
+    ("M 0\nDETECTOR rec[1]\n", sg.STIM_E_PARSE),
+    ("REPEAT 2 {\nH 0\n", sg.STIM_E_PARSE),
+    ("H 0\n}\n", sg.STIM_E_PARSE),
+    ("REPEAT 0 {\nH 0\n}\n", sg.STIM_E_PARSE),
+    ("REPEAT x {\nH 0\n}\n", sg.STIM_E_PARSE),
+    ("H 16777216\n", sg.STIM_E_UNSUPPORTED),
+]
+
+
+@pytest.mark.parametrize("text,code", BAD)
+def test_parse_errors(text, code):
+    with pytest.raises(sg.StimError) as ei:
+        sg.stim_compile(text)
+    assert ei.value.code == code
+    assert sg.stim_last_error()
+
+
+def test_parse_error_reports_line():
+    with pytest.raises(sg.StimError) as ei:
+        sg.stim_compile("H 0\nCX 0 1\nBOGUS 2\n")
+    assert "line 3" in str(ei.value)
+
+
+def test_aliases_and_detector_coordinates():
+    h = sg.stim_compile("CNOT 0 1\nM 0 1\nDETECTOR(1, 2.5, 0) rec[-1] rec[-2]\n")
+    info = sg.stim_info_get(h)
+    sg.stim_free(h)
+    assert info["num_detectors"] == 1 and info["num_gate_targets"] == 3
+
+
+def test_invalid_arguments_without_gpu():
+    lib = sg.library()
+    assert lib.stim_reference_sample(None, None, None, 0, None) == sg.STIM_E_INVALID_ARG
+    assert lib.stim_frame_sample(None, 10, 0, None, None, 0, None) == sg.STIM_E_INVALID_ARG
+    h = sg.stim_compile("H 0\nM 0\n")
+    try:
+        rc = lib.stim_frame_sample_ex(h, 10, 0, 3, None, None, 0, None, None)
+        assert rc == sg.STIM_E_INVALID_ARG      # shot_offset not a multiple of 64
+        rc = lib.stim_frame_sample(h, 10, 0, None, None, 0x40, None)
+        assert rc == sg.STIM_E_INVALID_ARG      # unknown flag
+    finally:
+        sg.stim_free(h)
