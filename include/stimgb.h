@@ -153,6 +153,30 @@ int stim_frame_sample_ex(stim_circuit *c, uint64_t num_shots, uint64_t seed,
                          uint64_t shot_offset, uint64_t *meas_out, uint64_t *det_out,
                          int flags, const stim_tile_hint *hint, void *stream);
 
+/*
+ * Kernel timing (measurement support; no counterpart in the paper).
+ *
+ * stim_profile(1) clears the statistics and starts recording a CUDA event
+ * pair around every kernel the library launches, on the stream it launches
+ * it on; stim_profile(0) stops recording. stim_profile_read() waits for the
+ * recorded events, then fills out[k] for kernel ids k < n (STIM_KERNEL_*):
+ * number of launches and summed device milliseconds. Process-wide; not
+ * meant for concurrent use from several threads.
+ */
+#define STIM_KERNEL_FRAME      0
+#define STIM_KERNEL_DETECTORS  1
+#define STIM_KERNEL_TRANSPOSE  2
+#define STIM_KERNEL_TABLEAU    3
+#define STIM_KERNEL_COUNT      4
+
+typedef struct {
+    uint64_t launches;
+    double total_ms;
+} stim_kernel_stat;
+
+int stim_profile(int enable);
+int stim_profile_read(stim_kernel_stat *out, int n);
+
 #ifdef __cplusplus
 }
 #endif

@@ -30,7 +30,7 @@ __all__ = [
     "STIM_MEAS_MAJOR", "STIM_SHOT_MAJOR", "STIM_DEVICE", "STIM_HOST", "STIM_RECOMPUTE",
     "StimError", "library", "library_path", "stim_compile", "stim_info_get", "stim_free",
     "stim_last_error", "stim_reference_sample", "stim_frame_sample", "stim_frame_sample_ex",
-    "Circuit", "EXPORTED_SYMBOLS",
+    "Circuit", "EXPORTED_SYMBOLS", "stim_profile", "stim_profile_read", "KERNEL_NAMES",
 ]
 
 STIM_OK = 0
@@ -72,6 +72,12 @@ class StimTileHint(ctypes.Structure):
                 ("frame_in_global", ctypes.c_uint32)]
 
 
+class StimKernelStat(ctypes.Structure):
+    _fields_ = [("launches", ctypes.c_uint64), ("total_ms", ctypes.c_double)]
+
+
+KERNEL_NAMES = ("frame", "detectors", "transpose", "tableau")
+
 _VP = ctypes.c_void_p
 _U64 = ctypes.c_uint64
 # name -> (restype, argtypes); every entry is declared in include/stimgb.h
@@ -84,6 +90,8 @@ _SIGNATURES = {
     "stim_frame_sample": (ctypes.c_int, [_VP, _U64, _U64, _VP, _VP, ctypes.c_int, _VP]),
     "stim_frame_sample_ex": (ctypes.c_int, [_VP, _U64, _U64, _U64, _VP, _VP, ctypes.c_int,
                                             ctypes.POINTER(StimTileHint), _VP]),
+    "stim_profile": (ctypes.c_int, [ctypes.c_int]),
+    "stim_profile_read": (ctypes.c_int, [ctypes.POINTER(StimKernelStat), ctypes.c_int]),
 }
 EXPORTED_SYMBOLS = tuple(_SIGNATURES)
 
@@ -161,6 +169,19 @@ def stim_frame_sample_ex(handle: int, num_shots: int, seed: int, shot_offset: in
     _check(library().stim_frame_sample_ex(handle, num_shots, seed & (2**64 - 1), shot_offset,
                                           meas_out or None, det_out or None, flags, h,
                                           stream or None))
+
+
+def stim_profile(enable: bool) -> None:
+    """Start (clearing statistics) or stop per-kernel event timing."""
+    _check(library().stim_profile(1 if enable else 0))
+
+
+def stim_profile_read() -> dict:
+    """{kernel name: (launches, total device ms)} since the last stim_profile(True)."""
+    n = len(KERNEL_NAMES)
+    arr = (StimKernelStat * n)()
+    _check(library().stim_profile_read(arr, n))
+    return {KERNEL_NAMES[k]: (int(arr[k].launches), float(arr[k].total_ms)) for k in range(n)}
 
 
 def _words(bits: int) -> int:

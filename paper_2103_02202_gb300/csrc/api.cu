@@ -4,8 +4,10 @@
 #include <algorithm>
 #include <cstdio>
 #include <cstring>
+#include <mutex>
 #include <new>
 #include <string>
+#include <vector>
 
 #include "../../include/stimgb.h"
 #include "internal.h"
@@ -52,6 +54,57 @@ int grow(uint64_t **p, size_t *cap, size_t words, const char *what) {
     STIMGB_CK(cudaMalloc((void **)p, std::max<size_t>(words, 1) * 8), what);
     *cap = words;
     return STIM_OK;
+}
+
+// ---- kernel timing (stim_profile) ----
+std::mutex g_prof_mu;
+bool g_prof_on = false;
+struct ProfRec {
+    int kernel;
+    cudaEvent_t a, b;
+};
+std::vector<ProfRec> g_prof_pending;
+uint64_t g_prof_launches[STIM_KERNEL_COUNT];
+double g_prof_ms[STIM_KERNEL_COUNT];
+
+// Records an event pair around one kernel launch when profiling is on.
+class ProfScope {
+  public:
+    ProfScope(int kernel, cudaStream_t st) : kernel_(kernel), st_(st) {
+        std::lock_guard<std::mutex> lk(g_prof_mu);
+        if (!g_prof_on) return;
+        if (cudaEventCreate(&a_) != cudaSuccess) return;
+        if (cudaEventCreate(&b_) != cudaSuccess) {
+            cudaEventDestroy(a_);
+            return;
+        }
+        active_ = cudaEventRecord(a_, st_) == cudaSuccess;
+    }
+    ~ProfScope() {
+        if (!active_) return;
+        std::lock_guard<std::mutex> lk(g_prof_mu);
+        cudaEventRecord(b_, st_);
+        g_prof_pending.push_back({kernel_, a_, b_});
+    }
+
+  private:
+    int kernel_;
+    cudaStream_t st_;
+    cudaEvent_t a_{}, b_{};
+    bool active_ = false;
+};
+
+void prof_drain_locked() {
+    for (ProfRec &r : g_prof_pending) {
+        float ms = 0;
+        if (cudaEventSynchronize(r.b) == cudaSuccess && cudaEventElapsedTime(&ms, r.a, r.b) == cudaSuccess) {
+            g_prof_launches[r.kernel]++;
+            g_prof_ms[r.kernel] += ms;
+        }
+        cudaEventDestroy(r.a);
+        cudaEventDestroy(r.b);
+    }
+    g_prof_pending.clear();
 }
 
 }  // namespace
@@ -156,6 +209,7 @@ int compute_reference(stim_circuit *c, cudaStream_t st) {
         uint64_t want = (col_words + 16383) / 16384;
         if (want < 1) want = 1;
         uint32_t blocks = (uint32_t)std::min<uint64_t>(want, (uint64_t)maxb);
+        ProfScope ps(STIM_KERNEL_TABLEAU, st);
         e = launch_tableau(a, blocks, threads, st);
     }
     if (e == cudaSuccess) e = cudaStreamSynchronize(st);
@@ -349,6 +403,7 @@ int stim_frame_sample_ex(stim_circuit *c, uint64_t num_shots, uint64_t seed, uin
         a.gframe = gframe;
         a.gstride = gstride;
         a.status = c->d_status;
+        ProfScope ps(STIM_KERNEL_FRAME, st);
         STIMGB_CK(launch_frame(a, W, gmem, (uint32_t)grid, threads, gmem ? 0 : per_word * W, st), "frame kernel");
     }
 
@@ -362,6 +417,7 @@ int stim_frame_sample_ex(stim_circuit *c, uint64_t num_shots, uint64_t seed, uin
             if ((r = grow(&c->d_det, &c->det_cap, D * nwords, "alloc detectors")) != STIM_OK) return r;
             det = c->d_det;
         }
+        ProfScope ps(STIM_KERNEL_DETECTORS, st);
         STIMGB_CK(launch_detectors(rec, nwords, c->d_det_ptr, c->d_det_meas, c->d_ref, D, nwords, last_mask, det,
                                    nwords, st),
                   "detector kernel");
@@ -378,7 +434,10 @@ int stim_frame_sample_ex(stim_circuit *c, uint64_t num_shots, uint64_t seed, uin
                 if (rr != STIM_OK) return rr;
                 tgt = c->d_tr;
             }
-            STIMGB_CK(launch_transpose(src, rows, nwords, num_shots, tgt, out_stride, st), "transpose kernel");
+            {
+                ProfScope ps(STIM_KERNEL_TRANSPOSE, st);
+                STIMGB_CK(launch_transpose(src, rows, nwords, num_shots, tgt, out_stride, st), "transpose kernel");
+            }
             if (host)
                 STIMGB_CK(cudaMemcpyAsync(dst, tgt, num_shots * out_stride * 8, cudaMemcpyDeviceToHost, st), "copy out");
         } else if (host) {
@@ -389,6 +448,30 @@ int stim_frame_sample_ex(stim_circuit *c, uint64_t num_shots, uint64_t seed, uin
     if (meas_out && !meas_direct && (r = emit(rec, M, meas_out)) != STIM_OK) return r;
     if (det_out && !det_direct && (r = emit(det, D, det_out)) != STIM_OK) return r;
     if (host) STIMGB_CK(cudaStreamSynchronize(st), "sync");
+    return STIM_OK;
+}
+
+int stim_profile(int enable) {
+    std::lock_guard<std::mutex> lk(g_prof_mu);
+    if (enable) {
+        prof_drain_locked();
+        for (int k = 0; k < STIM_KERNEL_COUNT; k++) {
+            g_prof_launches[k] = 0;
+            g_prof_ms[k] = 0;
+        }
+    }
+    g_prof_on = enable != 0;
+    return STIM_OK;
+}
+
+int stim_profile_read(stim_kernel_stat *out, int n) {
+    if (!out || n < 0) return fail(STIM_E_INVALID_ARG, "stim_profile_read: bad arguments");
+    std::lock_guard<std::mutex> lk(g_prof_mu);
+    prof_drain_locked();
+    for (int k = 0; k < n && k < STIM_KERNEL_COUNT; k++) {
+        out[k].launches = g_prof_launches[k];
+        out[k].total_ms = g_prof_ms[k];
+    }
     return STIM_OK;
 }
 

@@ -1,0 +1,258 @@
+"""GPU vs oracle parity through the C ABI: reference samples, measurement
+records and detection events must be bit-identical to the CPU oracle on the
+same seeded inputs, for every tile shape, layout and shot split."""
+import numpy as np
+import pytest
+
+import oracle
+import paper_2103_02202_gb300 as sg
+from paper_2103_02202_gb300 import workloads as W
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+
+
+@pytest.fixture(scope="module", autouse=True)
+def gpu():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2103_02202_gb300 import build
+    build.build()
+    torch.cuda.init()
+    yield
+
+
+def words_to_bits(words: np.ndarray, nbits: int) -> np.ndarray:
+    """(R, nwords) uint64 -> (R, nbits) uint8 (LSB-first)."""
+    w = np.ascontiguousarray(words, dtype=np.uint64)
+    b = np.unpackbits(w.view(np.uint8).reshape(w.shape[0], -1), axis=1, bitorder="little")
+    return b[:, :nbits]
+
+
+def to_np(t):
+    return t.cpu().numpy().view(np.uint64)
+
+
+def gpu_sample(text, shots, seed, shot_offset=0, hint=None):
+    c = sg.Circuit(text)
+    m, d = c.sample(shots, seed, shot_offset=shot_offset, hint=hint)
+    torch.cuda.synchronize()
+    M, D = c.num_measurements, c.num_detectors
+    mb = words_to_bits(to_np(m), shots).T if M else np.zeros((shots, 0), np.uint8)
+    db = words_to_bits(to_np(d), shots).T if D else np.zeros((shots, 0), np.uint8)
+    c.close()
+    return mb, db
+
+
+def gpu_reference(text):
+    c = sg.Circuit(text)
+    r, d = c.reference()
+    torch.cuda.synchronize()
+    M = c.num_measurements
+    out = (words_to_bits(to_np(r)[None, :], M)[0], words_to_bits(to_np(d)[None, :], M)[0])
+    c.close()
+    return out
+
+
+def _rand_circuit(rng, n, L, noise=True):
+    lines = []
+    for _ in range(L):
+        g = str(rng.choice(["H", "S", "CX", "CZ", "M", "MR", "R", "BCAST", "NOISE"]))
+        if g == "BCAST":
+            g2 = str(rng.choice(["H", "S", "M", "MR", "R"]))
+            k = int(rng.integers(1, n + 1))
+            lines.append(f"{g2} " + " ".join(map(str, rng.choice(n, k, replace=False))))
+        elif g in ("CX", "CZ"):
+            a, b = rng.choice(n, 2, replace=False)
+            lines.append(f"{g} {a} {b}")
+        elif g == "NOISE":
+            if not noise:
+                continue
+            ch = str(rng.choice(["X_ERROR", "Z_ERROR", "DEPOLARIZE1", "DEPOLARIZE2"]))
+            p = float(rng.choice([0.01, 0.2, 0.5, 1.0]))
+            if ch == "DEPOLARIZE2":
+                a, b = rng.choice(n, 2, replace=False)
+                lines.append(f"{ch}({p}) {a} {b}")
+            else:
+                lines.append(f"{ch}({p}) {rng.integers(n)}")
+        else:
+            lines.append(f"{g} {rng.integers(n)}")
+    lines.append("M " + " ".join(map(str, range(n))))
+    lines.append("DETECTOR rec[-1] rec[-2]")
+    return "\n".join(lines) + "\n"
+
+
+# ---------------------------------------------------------------------------
+# reference sample (inverse tableau)
+# ---------------------------------------------------------------------------
+REF_CIRCUITS = {
+    "surface_d3_r3": W.surface_code_memory(3, 3, 1e-3),
+    "surface_d5_r5": W.surface_code_memory(5, 5, 1e-3),
+    "surface_d25_r25": W.surface_code_memory(25, 25, 1e-3),
+    "repetition": W.repetition_code(5, 20, 0.01),
+    "random_clifford_200": W.random_clifford(200, 60, 3),
+    "random_clifford_700": W.random_clifford(700, 40, 4),
+    "bell": "H 0\nCX 0 1\nM 0 1\n",
+    "reset_after_one": "H 0\nS 0\nS 0\nH 0\nMR 0\nM 0\nR 0\nM 0\n",
+}
+
+
+@pytest.mark.parametrize("name", sorted(REF_CIRCUITS))
+def test_reference_matches_oracle(name):
+    text = REF_CIRCUITS[name]
+    ref, det = gpu_reference(text)
+    oref, odet = oracle.Circuit(text).reference()
+    np.testing.assert_array_equal(ref, oref)
+    np.testing.assert_array_equal(det, odet)
+
+
+def test_reference_random_small_circuits():
+    rng = np.random.default_rng(7)
+    for _ in range(40):
+        n = int(rng.integers(2, 70))
+        text = _rand_circuit(rng, n, int(rng.integers(5, 120)))
+        ref, det = gpu_reference(text)
+        oref, odet = oracle.Circuit(text).reference()
+        np.testing.assert_array_equal(ref, oref, err_msg=text)
+        np.testing.assert_array_equal(det, odet, err_msg=text)
+
+
+def test_reference_recompute_is_stable():
+    c = sg.Circuit(W.random_clifford(300, 30, 9))
+    r1, d1 = c.reference()
+    r2, d2 = c.reference(recompute=True)
+    torch.cuda.synchronize()
+    assert torch.equal(r1, r2) and torch.equal(d1, d2)
+    c.close()
+
+
+# ---------------------------------------------------------------------------
+# frame sampling
+# ---------------------------------------------------------------------------
+def test_surface_d3_full_parity():
+    """The d=3, 3-round, p=1e-3, 1024-shot, seed-0 workload: every shot."""
+    text = W.surface_code_memory(3, 3, 1e-3)
+    mb, db = gpu_sample(text, 1024, 0)
+    om, od = oracle.Circuit(text).sample(np.arange(1024), 0, threads=8)
+    np.testing.assert_array_equal(mb, om)
+    np.testing.assert_array_equal(db, od)
+
+
+@pytest.mark.parametrize("shots", [1, 63, 64, 65, 1000, 3 * 64 * 16 + 5])
+def test_ragged_shot_counts(shots):
+    text = W.surface_code_memory(3, 2, 0.02)
+    mb, db = gpu_sample(text, shots, 12345)
+    om, od = oracle.Circuit(text).sample(np.arange(shots), 12345, threads=8)
+    np.testing.assert_array_equal(mb, om)
+    np.testing.assert_array_equal(db, od)
+
+
+def test_random_circuits_with_all_noise_kinds():
+    rng = np.random.default_rng(11)
+    for _ in range(12):
+        n = int(rng.integers(2, 40))
+        text = _rand_circuit(rng, n, int(rng.integers(10, 80)))
+        shots = int(rng.integers(1, 700))
+        seed = int(rng.integers(0, 2**63))
+        mb, db = gpu_sample(text, shots, seed)
+        om, od = oracle.Circuit(text).sample(np.arange(shots), seed, threads=8)
+        np.testing.assert_array_equal(mb, om, err_msg=text)
+        np.testing.assert_array_equal(db, od, err_msg=text)
+
+
+@pytest.mark.parametrize("hint", [(1, 64, 0), (2, 128, 0), (4, 256, 0), (8, 512, 0), (16, 1024, 0),
+                                  (1, 256, 1), (4, 128, 1), (16, 256, 1)])
+def test_tile_shapes_are_invisible(hint):
+    text = W.surface_code_memory(5, 4, 5e-3)
+    base_m, base_d = gpu_sample(text, 2000, 99)
+    m, d = gpu_sample(text, 2000, 99, hint=hint)
+    np.testing.assert_array_equal(m, base_m)
+    np.testing.assert_array_equal(d, base_d)
+
+
+def test_shot_offset_splits_are_invisible():
+    text = W.surface_code_memory(5, 3, 1e-2)
+    full_m, full_d = gpu_sample(text, 640, 5)
+    a_m, a_d = gpu_sample(text, 192, 5)
+    b_m, b_d = gpu_sample(text, 448, 5, shot_offset=192)
+    np.testing.assert_array_equal(np.concatenate([a_m, b_m]), full_m)
+    np.testing.assert_array_equal(np.concatenate([a_d, b_d]), full_d)
+    om, od = oracle.Circuit(text).sample(np.arange(448), 5, shot_offset=192, threads=8)
+    np.testing.assert_array_equal(b_m, om)
+
+
+def test_layouts_and_host_outputs_agree():
+    text = W.surface_code_memory(3, 3, 0.05)
+    c = sg.Circuit(text)
+    S = 777
+    mm, dm = c.sample(S, 3)
+    ms, ds = c.sample(S, 3, shot_major=True)
+    hm, hd = c.sample_host(S, 3)
+    hs, hds = c.sample_host(S, 3, shot_major=True)
+    torch.cuda.synchronize()
+    M, D = c.num_measurements, c.num_detectors
+    meas = words_to_bits(to_np(mm), S)
+    np.testing.assert_array_equal(words_to_bits(to_np(ms), M), meas.T)
+    np.testing.assert_array_equal(words_to_bits(hm, S), meas)
+    np.testing.assert_array_equal(words_to_bits(hs, M), meas.T)
+    dets = words_to_bits(to_np(dm), S)
+    np.testing.assert_array_equal(words_to_bits(to_np(ds), D), dets.T)
+    np.testing.assert_array_equal(words_to_bits(hd, S), dets)
+    np.testing.assert_array_equal(words_to_bits(hds, D), dets.T)
+    # padding bits are zero in both layouts
+    assert np.all(to_np(mm)[:, -1] >> np.uint64(S % 64) == 0)
+    assert np.all(to_np(ms)[:, -1] >> np.uint64(M % 64) == 0)
+    c.close()
+
+
+def test_noiseless_surface_detectors_vanish_at_scale():
+    text = W.surface_code_memory(15, 15, 0.0)
+    c = sg.Circuit(text)
+    _, d = c.sample(65536, 1, meas=False)
+    torch.cuda.synchronize()
+    assert int(d.count_nonzero()) == 0
+    c.close()
+
+
+def test_surface_d25_bench_size_sampled_parity():
+    """d=25, 25 rounds, p=1e-3, 131072 shots in the default launch: compare the
+    first shot, the last shot, a word boundary and 200 random shots."""
+    text = W.surface_code_memory(25, 25, 1e-3)
+    S = 131072
+    c = sg.Circuit(text)
+    m, d = c.sample(S, 0)
+    torch.cuda.synchronize()
+    rng = np.random.default_rng(0)
+    pick = np.unique(np.concatenate([[0, 63, 64, S - 1], rng.choice(S, 200, replace=False)]))
+    cols = torch.as_tensor(pick // 64, device="cuda")
+    bits = torch.as_tensor(pick % 64, device="cuda")
+    gm = ((m[:, cols] >> bits) & 1).cpu().numpy().astype(np.uint8).T
+    gd = ((d[:, cols] >> bits) & 1).cpu().numpy().astype(np.uint8).T
+    om, od = oracle.Circuit(text).sample(pick, 0, threads=8)
+    np.testing.assert_array_equal(gm, om)
+    np.testing.assert_array_equal(gd, od)
+    c.close()
+
+
+def test_random_clifford_parity():
+    text = W.random_clifford(500, 40, 21)
+    mb, db = gpu_sample(text, 300, 77)
+    om, od = oracle.Circuit(text).sample(np.arange(300), 77, threads=8)
+    np.testing.assert_array_equal(mb, om)
+
+
+def test_edge_cases():
+    # empty circuit, no measurements, zero shots
+    for text in ("", "H 0\nCX 0 1\n", "X_ERROR(0.5) 3\n"):
+        c = sg.Circuit(text)
+        c.sample(100, 1)
+        c.reference()
+        c.close()
+    c = sg.Circuit("H 0\nM 0\n")
+    c.sample(0, 1)
+    c.close()
+    torch.cuda.synchronize()
+    # p = 1 noise flips every shot
+    mb, _ = gpu_sample("X_ERROR(1) 0 1 2\nM 0 1 2\n", 200, 1)
+    assert mb.all()
