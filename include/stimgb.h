@@ -154,6 +154,43 @@ int stim_frame_sample_ex(stim_circuit *c, uint64_t num_shots, uint64_t seed,
                          int flags, const stim_tile_hint *hint, void *stream);
 
 /*
+ * stim_frame_sample_noalloc -- detection events without allocating device
+ * memory. The paper has no counterpart; this is an interface addition.
+ *
+ * Who needs it: callers that cannot call cudaMalloc when they sample, because
+ * all device memory has been handed to another allocator (a framework's
+ * caching allocator, a service that reserves its memory up front), or
+ * because they cannot afford the device-wide synchronization that freeing
+ * device memory implies. stim_frame_sample_ex allocates a record buffer for
+ * detection-event output; this call instead keeps the measurement records in
+ * a fixed array of STIM_NOALLOC_SCRATCH_BYTES (32 MiB) compiled into the
+ * library. Every GPU that loads the library holds that array until the
+ * process exits.
+ *
+ * Same shots, same bits as stim_frame_sample_ex(c, num_shots, seed,
+ * shot_offset, NULL, det_out, STIM_MEAS_MAJOR | STIM_DEVICE, NULL, stream).
+ * det_out: device memory, D rows of ceil(num_shots/64) words (MEAS_MAJOR).
+ * Asynchronous on `stream`.
+ *
+ * Preconditions and limits:
+ *   - stim_reference_sample() must have run for this handle on the current
+ *     device (it uploads the circuit and takes the reference sample, and
+ *     does allocate); otherwise STIM_E_INVALID_ARG.
+ *   - M * ceil(num_shots/64) * 8 bytes must fit the 32 MiB array; larger
+ *     requests fail with STIM_E_UNSUPPORTED -- split them with shot_offset.
+ *   - one 64-shot frame tile (num_qubits * 16 bytes) must fit shared memory;
+ *     otherwise STIM_E_UNSUPPORTED.
+ *   - The first call on each device looks up the array's device address
+ *     (cudaGetSymbolAddress); make that first call before any stream capture.
+ *   - All calls on a device share the one array and each call overwrites it
+ *     before reading it; calls whose work overlaps on the same GPU (other
+ *     streams, other threads) race with each other and must be serialized.
+ */
+#define STIM_NOALLOC_SCRATCH_BYTES (32u << 20)
+int stim_frame_sample_noalloc(stim_circuit *c, uint64_t num_shots, uint64_t seed,
+                              uint64_t shot_offset, uint64_t *det_out, void *stream);
+
+/*
  * Kernel timing (measurement support; no counterpart in the paper).
  *
  * stim_profile(1) clears the statistics and starts recording a CUDA event

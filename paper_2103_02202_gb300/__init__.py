@@ -30,7 +30,7 @@ __all__ = [
     "STIM_MEAS_MAJOR", "STIM_SHOT_MAJOR", "STIM_DEVICE", "STIM_HOST", "STIM_RECOMPUTE",
     "StimError", "library", "library_path", "stim_compile", "stim_info_get", "stim_free",
     "stim_last_error", "stim_reference_sample", "stim_frame_sample", "stim_frame_sample_ex",
-    "Circuit", "EXPORTED_SYMBOLS", "stim_profile", "stim_profile_read", "KERNEL_NAMES",
+    "Circuit", "EXPORTED_SYMBOLS", "stim_frame_sample_noalloc", "stim_profile", "stim_profile_read", "KERNEL_NAMES",
 ]
 
 STIM_OK = 0
@@ -90,6 +90,7 @@ _SIGNATURES = {
     "stim_frame_sample": (ctypes.c_int, [_VP, _U64, _U64, _VP, _VP, ctypes.c_int, _VP]),
     "stim_frame_sample_ex": (ctypes.c_int, [_VP, _U64, _U64, _U64, _VP, _VP, ctypes.c_int,
                                             ctypes.POINTER(StimTileHint), _VP]),
+    "stim_frame_sample_noalloc": (ctypes.c_int, [_VP, _U64, _U64, _U64, _VP, _VP]),
     "stim_profile": (ctypes.c_int, [ctypes.c_int]),
     "stim_profile_read": (ctypes.c_int, [ctypes.POINTER(StimKernelStat), ctypes.c_int]),
 }
@@ -169,6 +170,14 @@ def stim_frame_sample_ex(handle: int, num_shots: int, seed: int, shot_offset: in
     _check(library().stim_frame_sample_ex(handle, num_shots, seed & (2**64 - 1), shot_offset,
                                           meas_out or None, det_out or None, flags, h,
                                           stream or None))
+
+
+def stim_frame_sample_noalloc(handle: int, num_shots: int, seed: int, shot_offset: int = 0,
+                              det_out: int = 0, stream: int = 0) -> None:
+    """Detection events into device memory without any device allocation
+    (records kept in the library's fixed 32 MiB array; see include/stimgb.h)."""
+    _check(library().stim_frame_sample_noalloc(handle, num_shots, seed & (2**64 - 1), shot_offset,
+                                               det_out or None, stream or None))
 
 
 def stim_profile(enable: bool) -> None:

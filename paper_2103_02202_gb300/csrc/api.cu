@@ -11,6 +11,7 @@
 
 #include "../../include/stimgb.h"
 #include "internal.h"
+#include "handle.h"
 #include "kernels.h"
 
 using namespace stimgb;
@@ -109,28 +110,7 @@ void prof_drain_locked() {
 
 }  // namespace
 
-struct stim_circuit {
-    HostProgram hp;
-    int device = -1;
-    ProgEntry *d_prog = nullptr;
-    DevOp *d_ops = nullptr;
-    uint64_t *d_geo = nullptr;
-    uint64_t *d_det_ptr = nullptr;
-    uint32_t *d_det_meas = nullptr;
-    uint64_t *d_ref = nullptr;
-    uint64_t *d_detflag = nullptr;
-    int *d_status = nullptr;
-    bool ref_valid = false;
-    size_t ref_words = 1;
-    uint64_t *d_rec = nullptr;
-    size_t rec_cap = 0;
-    uint64_t *d_det = nullptr;
-    size_t det_cap = 0;
-    uint64_t *d_tr = nullptr;
-    size_t tr_cap = 0;
-    uint64_t *d_gframe = nullptr;
-    size_t gframe_cap = 0;
-};
+
 
 namespace {
 
@@ -226,6 +206,10 @@ int compute_reference(stim_circuit *c, cudaStream_t st) {
 bool valid_flags(int flags, int allowed) { return (flags & ~allowed) == 0; }
 
 }  // namespace
+
+namespace stimgb {
+int report_error(int code, const std::string &msg) { return fail(code, msg); }
+}  // namespace stimgb
 
 extern "C" {
 

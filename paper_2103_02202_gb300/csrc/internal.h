@@ -82,6 +82,9 @@ struct HostProgram {
     uint64_t exec_targets[OP_COUNT] = {0};
 };
 
+// Sets the calling thread's stim_last_error() message; returns code.
+int report_error(int code, const std::string &msg);
+
 // Parse + compile. Returns 0 or a STIM_E_* code with *err filled.
 int compile_circuit(const char *text, size_t len, HostProgram *out, std::string *err);
 
