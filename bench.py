@@ -54,6 +54,8 @@ def parse_args():
     ap.add_argument("--workload", choices=sorted(WORKLOADS), default="surface_d100")
     ap.add_argument("--cpu-shots", type=int, default=0, help="oracle shots per CPU sample (0 = auto)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--shots", type=int, default=0, help="shots per step (0 = the workload's)")
+    ap.add_argument("--tile", default="", help="frame tile hint W,threads,global,cluster (default: library's)")
     return ap.parse_args()
 
 
@@ -234,7 +236,9 @@ def workload_name(wl):
 
 def main():
     args = parse_args()
-    wl = WORKLOADS[args.workload]
+    wl = dict(WORKLOADS[args.workload])
+    if args.shots:
+        wl["shots"] = args.shots
     text = circuit_text(wl)
     if args.impl == "reference":
         run_reference_arm(args, wl, text)
@@ -279,10 +283,12 @@ def main():
 
     det = torch.empty((D, nwords), dtype=torch.int64, device="cuda")
 
+    hint = tuple(int(v) for v in args.tile.split(",")) if args.tile else None
+
     def step(i):
         off = shard_offset(rank, world, i, shots)
         sg.stim_frame_sample_ex(circ.handle, shots, 2021, off, 0, det.data_ptr(), sg.STIM_DEVICE,
-                                None, stream.cuda_stream)
+                                hint, stream.cuda_stream)
 
     for i in range(args.warmup):
         step(i)

@@ -71,9 +71,10 @@ typedef struct {
 
 /* Tile choice for the frame kernel; zero fields mean "let the library pick". */
 typedef struct {
-    uint32_t words_per_cta;    /* 64-shot words held by one CTA: 1, 2, 4, 8 or 16 */
+    uint32_t words_per_cta;    /* 64-shot words per tile: 1, 2, 4 or 8 */
     uint32_t threads;          /* threads per CTA: 32..1024, multiple of 32 */
     uint32_t frame_in_global;  /* 1: keep frames in global memory even if the tile fits shared memory */
+    uint32_t cluster_size;     /* CTAs of a cluster splitting a tile's qubits: 1, 2, 4 or 8 */
 } stim_tile_hint;
 
 /*

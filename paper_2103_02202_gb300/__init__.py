@@ -69,7 +69,7 @@ class StimInfo(ctypes.Structure):
 
 class StimTileHint(ctypes.Structure):
     _fields_ = [("words_per_cta", ctypes.c_uint32), ("threads", ctypes.c_uint32),
-                ("frame_in_global", ctypes.c_uint32)]
+                ("frame_in_global", ctypes.c_uint32), ("cluster_size", ctypes.c_uint32)]
 
 
 class StimKernelStat(ctypes.Structure):
@@ -165,8 +165,8 @@ def stim_frame_sample_ex(handle: int, num_shots: int, seed: int, shot_offset: in
                          stream: int = 0) -> None:
     h = None
     if hint is not None:
-        hint = tuple(hint) + (0,) * (3 - len(hint))
-        h = ctypes.byref(StimTileHint(int(hint[0]), int(hint[1]), int(hint[2])))
+        hint = tuple(hint) + (0,) * (4 - len(hint))
+        h = ctypes.byref(StimTileHint(*(int(v) for v in hint[:4])))
     _check(library().stim_frame_sample_ex(handle, num_shots, seed & (2**64 - 1), shot_offset,
                                           meas_out or None, det_out or None, flags, h,
                                           stream or None))

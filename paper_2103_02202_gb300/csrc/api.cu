@@ -114,6 +114,30 @@ void prof_drain_locked() {
 
 namespace {
 
+int cluster_slot(int C) { return C == 1 ? 0 : C == 2 ? 1 : C == 4 ? 2 : 3; }
+
+// Builds and uploads the frame program for cluster size C (once per handle).
+int frame_program(stim_circuit *c, int C, const DevFrameProgram **out) {
+    DevFrameProgram &d = c->fprog[cluster_slot(C)];
+    if (d.C != C) {
+        FrameProgram fp;
+        try {
+            build_frame_program(c->hp, C, &fp);
+        } catch (const std::bad_alloc &) {
+            return fail(STIM_E_OOM, "out of host memory building the frame program");
+        }
+        int r;
+        if ((r = upload(&d.prog, fp.prog, "upload frame program")) != STIM_OK) return r;
+        if ((r = upload(&d.rank_tab, fp.rank_tab, "upload frame program")) != STIM_OK) return r;
+        if ((r = upload(&d.ops, fp.ops, "upload frame program")) != STIM_OK) return r;
+        d.Q = fp.Q;
+        d.nprog = (uint32_t)fp.prog.size();
+        d.C = C;
+    }
+    *out = &d;
+    return STIM_OK;
+}
+
 int ensure_device(stim_circuit *c) {
     int dev = 0;
     STIMGB_CK(cudaGetDevice(&dev), "cudaGetDevice");
@@ -136,7 +160,8 @@ int ensure_device(stim_circuit *c) {
     STIMGB_CK(cudaMemset(c->d_detflag, 0, c->ref_words * 8), "memset");
     STIMGB_CK(cudaMemset(c->d_status, 0, sizeof(int)), "memset");
     c->device = dev;
-    return STIM_OK;
+    const DevFrameProgram *fp1;
+    return frame_program(c, 1, &fp1);     // the single-CTA program is always resident
 }
 
 int compute_reference(stim_circuit *c, cudaStream_t st) {
@@ -201,6 +226,78 @@ int compute_reference(stim_circuit *c, cudaStream_t st) {
     if (status != 0) return fail(STIM_E_CUDA, "tableau kernel reported a malformed program");
     c->ref_valid = true;
     return rc;
+}
+
+struct TileChoice {
+    int W = 1, C = 1;
+    bool gmem = false;
+    uint32_t threads = 256;
+};
+
+// Tile shape: the smallest cluster whose qubit slice fits shared memory, then
+// the widest word tile that keeps at least two CTAs per SM busy; hints override.
+int choose_tile(uint32_t n, uint64_t nwords, int sms, size_t smem_optin, const stim_tile_hint *hint,
+                TileChoice *out) {
+    TileChoice t;
+    const uint32_t hW = hint ? hint->words_per_cta : 0, hC = hint ? hint->cluster_size : 0;
+    if (hW && hW != 1 && hW != 2 && hW != 4 && hW != 8)
+        return fail(STIM_E_INVALID_ARG, "tile hint: words_per_cta must be 1, 2, 4 or 8");
+    if (hC && hC != 1 && hC != 2 && hC != 4 && hC != 8)
+        return fail(STIM_E_INVALID_ARG, "tile hint: cluster_size must be 1, 2, 4 or 8");
+    if (hint && hint->threads && (hint->threads < 32 || hint->threads > 1024 || hint->threads % 32))
+        return fail(STIM_E_INVALID_ARG, "tile hint: threads must be a multiple of 32 in [32, 1024]");
+    const uint32_t nn = n ? n : 1;
+    auto slice = [&](int C) { return (size_t)((nn + C - 1) / C) * 16; };   // bytes per word of a slice
+    if (hint && hint->frame_in_global) {
+        if (hC > 1) return fail(STIM_E_INVALID_ARG, "tile hint: a global-memory frame uses cluster_size 1");
+        t.gmem = true;
+        t.C = 1;
+    } else if (hC) {
+        t.C = (int)hC;
+        if (slice(t.C) > smem_optin) return fail(STIM_E_INVALID_ARG, "tile hint: slice does not fit shared memory");
+    } else {
+        // smallest cluster whose slice leaves room for two CTAs per SM
+        t.C = 0;
+        for (int C : {1, 2, 4, 8})
+            if (slice(C) * 2 + 2048 <= smem_optin) {
+                t.C = C;
+                break;
+            }
+        if (t.C == 0)
+            for (int C : {1, 2, 4, 8})
+                if (slice(C) <= smem_optin) {
+                    t.C = C;
+                    break;
+                }
+        if (t.C == 0) {
+            t.C = 1;
+            t.gmem = true;
+        }
+    }
+    if (hW) {
+        t.W = (int)hW;
+        if (!t.gmem && slice(t.C) * t.W > smem_optin)
+            return fail(STIM_E_INVALID_ARG, "tile hint: words_per_cta does not fit shared memory");
+    } else {
+        // one 64-shot word per tile: a thread's Philox chains stay independent
+        t.W = t.gmem ? 2 : 1;
+    }
+    if (hint && hint->threads) {
+        t.threads = hint->threads;
+    } else if (t.gmem) {
+        t.threads = 256;
+    } else {
+        const size_t per_cta = slice(t.C) * t.W + 1024;
+        const size_t per_sm = (size_t)smem_optin + 1024;
+        size_t ctas = per_sm / per_cta;
+        if (ctas < 1) ctas = 1;
+        uint32_t th = (uint32_t)(2048 / ctas);
+        if (th > 512) th = 512;
+        if (th < 256) th = 256;
+        t.threads = th;
+    }
+    *out = t;
+    return STIM_OK;
 }
 
 bool valid_flags(int flags, int allowed) { return (flags & ~allowed) == 0; }
@@ -270,6 +367,11 @@ void stim_free(stim_circuit *c) {
         cudaFree(c->d_det);
         cudaFree(c->d_tr);
         cudaFree(c->d_gframe);
+        for (DevFrameProgram &d : c->fprog) {
+            cudaFree(d.prog);
+            cudaFree(d.rank_tab);
+            cudaFree(d.ops);
+        }
         if (cur >= 0 && cur != c->device) cudaSetDevice(cur);
     }
     delete c;
@@ -322,33 +424,14 @@ int stim_frame_sample_ex(stim_circuit *c, uint64_t num_shots, uint64_t seed, uin
     int sms = 0, smem_optin = 0;
     STIMGB_CK(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, c->device), "attr");
     STIMGB_CK(cudaDeviceGetAttribute(&smem_optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, c->device), "attr");
-    int W = 0;
-    uint32_t threads = 256;
-    if (hint && hint->words_per_cta) {
-        W = (int)hint->words_per_cta;
-        if (W != 1 && W != 2 && W != 4 && W != 8 && W != 16)
-            return fail(STIM_E_INVALID_ARG, "tile hint: words_per_cta must be 1, 2, 4, 8 or 16");
-    }
-    if (hint && hint->threads) {
-        threads = hint->threads;
-        if (threads < 32 || threads > 1024 || threads % 32)
-            return fail(STIM_E_INVALID_ARG, "tile hint: threads must be a multiple of 32 in [32, 1024]");
-    }
-    const size_t per_word = (size_t)n * 16;
-    bool gmem = per_word > (size_t)smem_optin || (hint && hint->frame_in_global);
-    if (W == 0) {
-        W = 1;
-        for (int w : {8, 4, 2}) {
-            if (!gmem && per_word * w > (size_t)smem_optin / 2 && w > 1) continue;
-            if ((nwords + w - 1) / w >= (uint64_t)sms * 2) {
-                W = w;
-                break;
-            }
-        }
-    }
-    if (!gmem && per_word * W > (size_t)smem_optin) gmem = true;
-    const uint64_t grid = (nwords + W - 1) / W;
-    if (grid > 0x7FFFFFFFull) return fail(STIM_E_UNSUPPORTED, "too many shots for one call");
+    TileChoice tc;
+    r = choose_tile(n, nwords, sms, (size_t)smem_optin, hint, &tc);
+    if (r != STIM_OK) return r;
+    const int W = tc.W, C = tc.C;
+    const bool gmem = tc.gmem;
+    const uint32_t threads = tc.threads;
+    const uint64_t grid = (nwords + W - 1) / W;     // word tiles (clusters)
+    if (grid * C > 0x7FFFFFFFull) return fail(STIM_E_UNSUPPORTED, "too many shots for one call");
 
     // ---- record buffers ----
     const bool meas_direct = meas_out && !shot_major && !host;
@@ -363,22 +446,24 @@ int stim_frame_sample_ex(stim_circuit *c, uint64_t num_shots, uint64_t seed, uin
         }
     }
     uint64_t *gframe = nullptr;
-    uint64_t gstride = grid * W;
+    const uint64_t gstride = grid * W;
     if (gmem && n > 0) {
         if ((r = grow(&c->d_gframe, &c->gframe_cap, 2 * (size_t)n * gstride, "alloc frame")) != STIM_OK) return r;
         gframe = c->d_gframe;
     }
 
     if (n > 0) {
+        const DevFrameProgram *fp = nullptr;
+        if ((r = frame_program(c, C, &fp)) != STIM_OK) return r;
         FrameArgs a{};
-        a.prog = c->d_prog;
-        a.nprog = (uint32_t)hp.prog.size();
-        a.ops = c->d_ops;
+        a.prog = fp->prog;
+        a.nprog = fp->nprog;
+        a.rank_tab = fp->rank_tab;
+        a.ops = fp->ops;
         a.geo = c->d_geo;
         a.ref = c->d_ref;
         a.n = n;
-        a.k0 = (uint32_t)seed;
-        a.k1 = (uint32_t)(seed >> 32);
+        a.Q = fp->Q;
         a.word0 = shot_offset / 64;
         a.nwords = nwords;
         a.last_mask = last_mask;
@@ -387,8 +472,10 @@ int stim_frame_sample_ex(stim_circuit *c, uint64_t num_shots, uint64_t seed, uin
         a.gframe = gframe;
         a.gstride = gstride;
         a.status = c->d_status;
+        philox_key_schedule(seed, a.rk0, a.rk1);
         ProfScope ps(STIM_KERNEL_FRAME, st);
-        STIMGB_CK(launch_frame(a, W, gmem, (uint32_t)grid, threads, gmem ? 0 : per_word * W, st), "frame kernel");
+        STIMGB_CK(launch_frame(a, W, C, gmem, (uint32_t)grid, threads, gmem ? 0 : (size_t)fp->Q * W * 16, st),
+                  "frame kernel");
     }
 
     // ---- detectors ----

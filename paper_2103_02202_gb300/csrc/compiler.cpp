@@ -476,6 +476,43 @@ void collect_detectors(const Block &b, uint64_t *meas, HostProgram *hp) {
 
 }  // namespace
 
+void build_frame_program(const HostProgram &hp, int C, FrameProgram *out) {
+    FrameProgram fp;
+    fp.C = C;
+    const uint32_t n = hp.num_qubits ? hp.num_qubits : 1;
+    fp.Q = (n + (uint32_t)C - 1) / (uint32_t)C;
+    fp.prog = hp.prog;
+    fp.ops.reserve(hp.ops.size());
+    std::vector<std::vector<DevOp>> bucket((size_t)C);
+    for (ProgEntry &e : fp.prog) {
+        if (e.kind != ENT_LAYER) continue;
+        const uint32_t tot = e.n_gate + e.n_noise + e.n_collapse;
+        for (auto &bk : bucket) bk.clear();
+        for (uint32_t i = 0; i < tot; i++) {
+            DevOp d = hp.ops[e.op_begin + i];
+            const uint32_t opc = d.a >> 24, qa = d.a & kQubitMask;
+            const uint32_t ra = qa / fp.Q;
+            DevOp f = d;
+            f.a = (opc << 24) | (qa - ra * fp.Q);
+            if (opc == OP_CX || opc == OP_CZ || opc == OP_DEP2) {
+                const uint32_t qb = d.b & kQubitMask, rb = qb / fp.Q;
+                f.b = (rb << 24) | (qb - rb * fp.Q);
+                if (opc == OP_DEP2) f.slot = d.slot | ((d.b >> 24) << 24);
+            } else if (op_is_noise(opc)) {
+                f.b = d.b >> 24;
+            }
+            bucket[ra].push_back(f);    // keeps gate / noise / collapse order within a CTA
+        }
+        e.op_begin = (uint32_t)fp.rank_tab.size();
+        for (int r = 0; r < C; r++) {
+            fp.rank_tab.push_back((uint32_t)fp.ops.size());
+            fp.ops.insert(fp.ops.end(), bucket[r].begin(), bucket[r].end());
+        }
+        fp.rank_tab.push_back((uint32_t)fp.ops.size());
+    }
+    *out = std::move(fp);
+}
+
 int compile_circuit(const char *text, size_t len, HostProgram *out, std::string *err) {
     try {
         Parser ps(text, len);

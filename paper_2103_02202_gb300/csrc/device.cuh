@@ -10,17 +10,19 @@ namespace stimgb {
 
 // ---------------------------------------------------------------------------
 // Philox4x32-10 (Salmon, Moraes, Dror, Shaw, SC'11): ten rounds of two 32x32
-// -> 64-bit multiplies with the Weyl-sequence key schedule.
+// -> 64-bit multiplies; the key follows the Weyl sequence
+// (k0, k1) += (0x9E3779B9, 0xBB67AE85) after every round.
 // ---------------------------------------------------------------------------
-__device__ __forceinline__ uint4 philox4x32_10(uint4 c, uint32_t k0, uint32_t k1) {
+// Philox4x32-10 with a precomputed key schedule: rk0[r] = k0 + r * 0x9E3779B9,
+// rk1[r] = k1 + r * 0xBB67AE85 (the kernels receive it as launch parameters,
+// so the key XORs read the constant bank and no key additions remain).
+__device__ __forceinline__ uint4 philox_sched(uint4 c, const uint32_t *rk0, const uint32_t *rk1) {
 #pragma unroll
     for (int r = 0; r < 10; r++) {
         const uint64_t p0 = (uint64_t)0xD2511F53u * c.x;
         const uint64_t p1 = (uint64_t)0xCD9E8D57u * c.z;
-        c = make_uint4((uint32_t)(p1 >> 32) ^ c.y ^ k0, (uint32_t)p1,
-                       (uint32_t)(p0 >> 32) ^ c.w ^ k1, (uint32_t)p0);
-        k0 += 0x9E3779B9u;
-        k1 += 0xBB67AE85u;
+        c = make_uint4((uint32_t)(p1 >> 32) ^ c.y ^ rk0[r], (uint32_t)p1,
+                       (uint32_t)(p0 >> 32) ^ c.w ^ rk1[r], (uint32_t)p0);
     }
     return c;
 }
@@ -32,26 +34,27 @@ constexpr uint32_t kTagInit = 2u << 28;
 
 // 64 fair bits for a collapse (tag COLLAPSE) or the initial frame (tag INIT):
 // draws 0 and 1 of the keyed stream.
-__device__ __forceinline__ uint64_t half_mask(uint32_t k0, uint32_t k1, uint32_t tag_instr,
+__device__ __forceinline__ uint64_t half_mask(const uint32_t *rk0, const uint32_t *rk1, uint32_t tag_instr,
                                               uint32_t slot, uint32_t word) {
-    const uint4 r = philox4x32_10(make_uint4(0u, slot, tag_instr, word), k0, k1);
+    const uint4 r = philox_sched(make_uint4(0u, slot, tag_instr, word), rk0, rk1);
     return (uint64_t)r.x | ((uint64_t)r.y << 32);
 }
 
 // Sequential draws of one keyed stream; block j/4 is generated on demand.
 struct DrawStream {
     uint4 blk;
-    uint32_t j, slot, ti, word, k0, k1;
+    uint32_t j, slot, ti, word;
+    const uint32_t *rk0, *rk1;
 
-    __device__ __forceinline__ DrawStream(uint32_t k0_, uint32_t k1_, uint32_t ti_, uint32_t slot_,
-                                          uint32_t word_)
-        : j(0), slot(slot_), ti(ti_), word(word_), k0(k0_), k1(k1_) {
-        blk = philox4x32_10(make_uint4(0u, slot, ti, word), k0, k1);
+    __device__ __forceinline__ DrawStream(const uint32_t *rk0_, const uint32_t *rk1_, uint32_t ti_,
+                                          uint32_t slot_, uint32_t word_)
+        : j(0), slot(slot_), ti(ti_), word(word_), rk0(rk0_), rk1(rk1_) {
+        blk = philox_sched(make_uint4(0u, slot, ti, word), rk0, rk1);
     }
 
     __device__ __forceinline__ uint32_t next() {
         const uint32_t lane = j & 3u;
-        if (lane == 0u && j != 0u) blk = philox4x32_10(make_uint4(j >> 2, slot, ti, word), k0, k1);
+        if (lane == 0u && j != 0u) blk = philox_sched(make_uint4(j >> 2, slot, ti, word), rk0, rk1);
         j++;
         return lane == 0u ? blk.x : lane == 1u ? blk.y : lane == 2u ? blk.z : blk.w;
     }
@@ -65,10 +68,10 @@ struct DrawStream {
 // the Pauli 1 + floor(3v / 2^32) (1 X, 2 Y, 3 Z); DEPOLARIZE2 on
 // c = 1 + floor(15v / 2^32), first-qubit Pauli c >> 2, second c & 3.
 template <uint32_t OP>
-__device__ __forceinline__ void noise_masks(const uint64_t *__restrict__ G, uint32_t k0, uint32_t k1,
-                                            uint32_t instr, uint32_t slot, uint32_t word,
+__device__ __forceinline__ void noise_masks(const uint64_t *__restrict__ G, const uint32_t *rk0,
+                                            const uint32_t *rk1, uint32_t instr, uint32_t slot, uint32_t word,
                                             uint64_t &xa, uint64_t &za, uint64_t &xb, uint64_t &zb) {
-    DrawStream ds(k0, k1, kTagNoise | instr, slot, word);
+    DrawStream ds(rk0, rk1, kTagNoise | instr, slot, word);
     int pos = -1;
     xa = za = xb = zb = 0;
     for (;;) {

@@ -1,40 +1,78 @@
 // frame.cu -- batched Pauli-frame propagation (Section 3 of the paper).
 //
-// Each CTA owns W 64-shot words of frames for all n qubits. The X and Z
-// planes are kept separately (the paper's "XXXX...ZZZZ" layout, Section 5.1),
-// qubit-major with the CTA's W words contiguous per qubit:
-//     X[q * qstride + w], Z[q * qstride + w]
-// in shared memory for the whole circuit when n * W * 16 bytes fit
-// (qstride = W), otherwise in a global-memory frame of all words of the call
-// (qstride = words of the call). The CTA walks the compiled program: for
-// every fused layer its threads take (op, word) items -- ops of a layer touch
-// disjoint qubits -- and a block barrier separates layers.
+// Work unit: a tile of W 64-shot words for all n qubits, owned by a cluster
+// of C CTAs (C = 1: a single CTA). The qubits are split into C contiguous
+// slices of Q = ceil(n / C); CTA r of the cluster keeps the X and Z planes of
+// its slice -- the paper's separate "XXXX...ZZZZ" planes (Section 5.1) --
+// resident in shared memory for the whole circuit:
+//     X[l * W + w], Z[l * W + w]      l = local qubit, w = word of the tile
+// so a row of W words per qubit is contiguous.
+// (When even one 64-shot word of the largest slice does not fit, a C = 1
+// variant keeps the same rows in a global-memory frame instead.)
 //
-// Per item:
+// The CTA walks the compiled program; for each fused layer (ops on disjoint
+// qubits) its threads take (op, word) items of the CTA's own slice:
 //   H: swap(x, z)   S: z ^= x   CX(c,t): z_c ^= z_t, x_t ^= x_c
 //   CZ(a,b): z_a ^= x_b, z_b ^= x_a
 //   M:  record = ref[m] ^ x, then z ^= collapse coin
 //   MR: record = ref[m] ^ x, then x = 0, z = collapse coin
 //   R:  x = 0, z = collapse coin
 //   noise: keyed geometric masks multiplied into the frame.
-// Frames start as x = 0 and z = a fair coin per qubit (step 2 of the
-// algorithm in Section 3).
+// The second qubit of a two-qubit op may belong to another CTA of the
+// cluster; it is then read and written in that CTA's shared memory through
+// the cluster's distributed shared memory. Layers end with a cluster barrier
+// (a block barrier when C = 1). Frames start as x = 0, z = fair coin (step 2
+// of the algorithm in Section 3).
+#include <cooperative_groups.h>
 #include <cuda_runtime.h>
 
 #include "device.cuh"
 #include "kernels.h"
 
+namespace cg = cooperative_groups;
+
 namespace stimgb {
 
-template <int W>
-__device__ __forceinline__ void frame_apply(const FrameArgs &a, const DevOp op, uint32_t w,
-                                            uint64_t *__restrict__ X, uint64_t *__restrict__ Z,
-                                            uint64_t qstride, uint64_t tile0, uint32_t instr_off,
-                                            uint32_t meas_off) {
+namespace {
+
+constexpr int kPrefetch = 4;
+
+__device__ __forceinline__ DevOp as_op(uint4 v) { return DevOp{v.x, v.y, v.z, v.w}; }
+
+template <int C>
+__device__ __forceinline__ void sync_tile() {
+    if constexpr (C == 1) {
+        __syncthreads();
+    } else {
+        cg::this_cluster().sync();
+    }
+}
+
+// Row pointers of the partner qubit of a two-qubit op (possibly in a peer CTA).
+template <int C>
+__device__ __forceinline__ void partner(uint32_t b, uint32_t my_rank, uint64_t *X, uint64_t *Z, uint64_t qstride,
+                                        uint64_t *&xb, uint64_t *&zb) {
+    const uint32_t rb = b >> 24, lb = b & 0xFFFFFFu;
+    xb = X + (uint64_t)lb * qstride;
+    zb = Z + (uint64_t)lb * qstride;
+    if constexpr (C > 1) {
+        if (rb != my_rank) {
+            cg::cluster_group cl = cg::this_cluster();
+            xb = cl.map_shared_rank(xb, rb);
+            zb = cl.map_shared_rank(zb, rb);
+        }
+    }
+}
+
+// Applies one op to word w of the tile (X, Z point at word 0 of the rows).
+template <int C>
+__device__ __forceinline__ void frame_op_word(const FrameArgs &a, const DevOp op, uint32_t w, uint32_t my_rank,
+                                              uint64_t *X, uint64_t *Z, uint64_t qstride, uint64_t tile0,
+                                              uint32_t instr_off, uint32_t meas_off) {
     const uint32_t opc = op.a >> 24;
-    const uint64_t ia = (uint64_t)(op.a & kQubitMask) * qstride + w;
-    const uint64_t lw = tile0 + w;                       // word index within this call
-    const uint32_t gw = (uint32_t)(a.word0 + lw);        // global 64-shot word (RNG counter)
+    const uint64_t ia = (uint64_t)(op.a & 0xFFFFFFu) * qstride + w;
+    const uint64_t lw = tile0 + w;                    // word index within this call
+    const uint32_t gw = (uint32_t)(a.word0 + lw);     // global 64-shot word (RNG counter)
     switch (opc) {
         case OP_H: {
             const uint64_t t = X[ia];
@@ -45,28 +83,31 @@ __device__ __forceinline__ void frame_apply(const FrameArgs &a, const DevOp op, 
         case OP_S:
             Z[ia] ^= X[ia];
             break;
-        case OP_CX: {
-            const uint64_t ib = (uint64_t)(op.b & kQubitMask) * qstride + w;
-            Z[ia] ^= Z[ib];
-            X[ib] ^= X[ia];
-            break;
-        }
+        case OP_CX:
         case OP_CZ: {
-            const uint64_t ib = (uint64_t)(op.b & kQubitMask) * qstride + w;
-            Z[ia] ^= X[ib];
-            Z[ib] ^= X[ia];
+            uint64_t *xb, *zb;
+            partner<C>(op.b, my_rank, X + w, Z + w, qstride, xb, zb);
+            if (opc == OP_CX) {
+                Z[ia] ^= *zb;
+                *xb ^= X[ia];
+            } else {
+                const uint64_t xa = X[ia];
+                Z[ia] ^= *xb;
+                *zb ^= xa;
+            }
             break;
         }
         case OP_M:
-        case OP_MR: {
-            const uint32_t m = op.b + meas_off;
-            if (a.rec != nullptr && lw < a.nwords) {
+        case OP_MR:
+        case OP_R: {
+            if (opc != OP_R && a.rec != nullptr && lw < a.nwords) {
+                const uint32_t m = op.b + meas_off;
                 const uint64_t refm = 0ull - ((__ldg(a.ref + (m >> 6)) >> (m & 63)) & 1ull);
                 uint64_t v = X[ia] ^ refm;
                 if (lw == a.nwords - 1) v &= a.last_mask;
                 a.rec[(uint64_t)m * a.rec_stride + lw] = v;
             }
-            const uint64_t coin = half_mask(a.k0, a.k1, kTagCollapse | (op.instr + instr_off), op.slot, gw);
+            const uint64_t coin = half_mask(a.rk0, a.rk1, kTagCollapse | (op.instr + instr_off), op.slot, gw);
             if (opc == OP_M) {
                 Z[ia] ^= coin;
             } else {
@@ -75,42 +116,31 @@ __device__ __forceinline__ void frame_apply(const FrameArgs &a, const DevOp op, 
             }
             break;
         }
-        case OP_R: {
-            X[ia] = 0;
-            Z[ia] = half_mask(a.k0, a.k1, kTagCollapse | (op.instr + instr_off), op.slot, gw);
-            break;
-        }
-        case OP_XERR: {
-            uint64_t xa, za, xb, zb;
-            noise_masks<OP_XERR>(a.geo + 64u * (op.b >> 24), a.k0, a.k1, op.instr + instr_off, op.slot, gw,
-                                 xa, za, xb, zb);
-            X[ia] ^= xa;
-            break;
-        }
-        case OP_ZERR: {
-            uint64_t xa, za, xb, zb;
-            noise_masks<OP_ZERR>(a.geo + 64u * (op.b >> 24), a.k0, a.k1, op.instr + instr_off, op.slot, gw,
-                                 xa, za, xb, zb);
-            Z[ia] ^= za;
-            break;
-        }
+        case OP_XERR:
+        case OP_ZERR:
         case OP_DEP1: {
-            uint64_t xa, za, xb, zb;
-            noise_masks<OP_DEP1>(a.geo + 64u * (op.b >> 24), a.k0, a.k1, op.instr + instr_off, op.slot, gw,
-                                 xa, za, xb, zb);
-            X[ia] ^= xa;
-            Z[ia] ^= za;
+            uint64_t mx, mz, u1, u2;
+            const uint64_t *G = a.geo + 64u * op.b;
+            const uint32_t instr = op.instr + instr_off;
+            if (opc == OP_XERR) noise_masks<OP_XERR>(G, a.rk0, a.rk1, instr, op.slot, gw, mx, mz, u1, u2);
+            else if (opc == OP_ZERR) noise_masks<OP_ZERR>(G, a.rk0, a.rk1, instr, op.slot, gw, mx, mz, u1, u2);
+            else noise_masks<OP_DEP1>(G, a.rk0, a.rk1, instr, op.slot, gw, mx, mz, u1, u2);
+            if (mx) X[ia] ^= mx;
+            if (mz) Z[ia] ^= mz;
             break;
         }
         case OP_DEP2: {
-            uint64_t xa, za, xb, zb;
-            noise_masks<OP_DEP2>(a.geo + 64u * (op.b >> 24), a.k0, a.k1, op.instr + instr_off, op.slot, gw,
-                                 xa, za, xb, zb);
-            const uint64_t ib = (uint64_t)(op.b & kQubitMask) * qstride + w;
-            X[ia] ^= xa;
-            Z[ia] ^= za;
-            X[ib] ^= xb;
-            Z[ib] ^= zb;
+            uint64_t m0x, m0z, m1x, m1z;
+            noise_masks<OP_DEP2>(a.geo + 64u * (op.slot >> 24), a.rk0, a.rk1, op.instr + instr_off,
+                                 op.slot & 0xFFFFFFu, gw, m0x, m0z, m1x, m1z);
+            if (m0x | m0z | m1x | m1z) {
+                uint64_t *xb, *zb;
+                partner<C>(op.b, my_rank, X + w, Z + w, qstride, xb, zb);
+                X[ia] ^= m0x;
+                Z[ia] ^= m0z;
+                *xb ^= m1x;
+                *zb ^= m1z;
+            }
             break;
         }
         default:
@@ -118,28 +148,32 @@ __device__ __forceinline__ void frame_apply(const FrameArgs &a, const DevOp op, 
     }
 }
 
-template <int W, bool GMEM>
-__global__ void __launch_bounds__(1024) frame_kernel(FrameArgs a) {
+}  // namespace
+
+template <int W, int C, bool GMEM>
+__global__ void __launch_bounds__(1024, 1) frame_kernel(const __grid_constant__ FrameArgs a) {
     extern __shared__ __align__(16) uint64_t smem[];
-    const uint32_t n = a.n;
-    const uint64_t tile0 = (uint64_t)blockIdx.x * W;
+    const uint32_t rank = C > 1 ? (uint32_t)(blockIdx.x % C) : 0u;
+    const uint64_t tile0 = (uint64_t)(blockIdx.x / C) * W;
+    const uint32_t qlo = rank * a.Q;
+    const uint32_t nq = a.n > qlo ? min(a.Q, a.n - qlo) : 0u;
     uint64_t *X, *Z;
     uint64_t qstride;
     if (GMEM) {
         X = a.gframe + tile0;
-        Z = a.gframe + (uint64_t)n * a.gstride + tile0;
+        Z = a.gframe + (uint64_t)a.n * a.gstride + tile0;
         qstride = a.gstride;
     } else {
         X = smem;
-        Z = smem + (uint64_t)n * W;
+        Z = smem + (uint64_t)a.Q * W;
         qstride = W;
     }
-    for (uint32_t i = threadIdx.x; i < n * W; i += blockDim.x) {
-        const uint32_t q = i / W, w = i % W;
-        X[(uint64_t)q * qstride + w] = 0;
-        Z[(uint64_t)q * qstride + w] = half_mask(a.k0, a.k1, kTagInit, q, (uint32_t)(a.word0 + tile0 + w));
+    for (uint32_t i = threadIdx.x; i < nq * W; i += blockDim.x) {
+        const uint32_t l = i / W, w = i % W;
+        X[(uint64_t)l * qstride + w] = 0;
+        Z[(uint64_t)l * qstride + w] = half_mask(a.rk0, a.rk1, kTagInit, qlo + l, (uint32_t)(a.word0 + tile0 + w));
     }
-    __syncthreads();
+    sync_tile<C>();
 
     uint32_t instr_off = 0, meas_off = 0;
     uint32_t loop_pc[kMaxLoopDepth];
@@ -149,11 +183,27 @@ __global__ void __launch_bounds__(1024) frame_kernel(FrameArgs a) {
     while (pc < a.nprog) {
         const ProgEntry e = a.prog[pc];
         if (e.kind == ENT_LAYER) {
-            const uint32_t items = (e.n_gate + e.n_noise + e.n_collapse) * W;
-            const DevOp *ops = a.ops + e.op_begin;
-            for (uint32_t i = threadIdx.x; i < items; i += blockDim.x)
-                frame_apply<W>(a, ops[i / W], i % W, X, Z, qstride, tile0, instr_off, meas_off);
-            __syncthreads();
+            const uint32_t b = __ldg(a.rank_tab + e.op_begin + rank);
+            const uint32_t en = __ldg(a.rank_tab + e.op_begin + rank + 1);
+            // Items are (op, word) pairs with the W words of an op on adjacent
+            // threads (one op fetch serves W lanes). A thread fetches up to
+            // kPrefetch of its ops before applying any, so their latencies overlap.
+            const uint32_t items = (en - b) * W;
+            for (uint32_t base = threadIdx.x; base < items; base += kPrefetch * blockDim.x) {
+                DevOp op[kPrefetch];
+#pragma unroll
+                for (int k = 0; k < kPrefetch; k++) {
+                    const uint32_t it = base + k * blockDim.x;
+                    if (it < items) op[k] = as_op(__ldg(reinterpret_cast<const uint4 *>(a.ops) + b + it / W));
+                }
+#pragma unroll
+                for (int k = 0; k < kPrefetch; k++) {
+                    const uint32_t it = base + k * blockDim.x;
+                    if (it < items)
+                        frame_op_word<C>(a, op[k], it % W, rank, X, Z, qstride, tile0, instr_off, meas_off);
+                }
+            }
+            sync_tile<C>();
             pc++;
         } else if (e.kind == ENT_LOOP_BEGIN) {
             if (sp >= kMaxLoopDepth) {
@@ -184,34 +234,61 @@ __global__ void __launch_bounds__(1024) frame_kernel(FrameArgs a) {
     }
 }
 
-template <int W, bool GMEM>
-static cudaError_t launch_frame_t(const FrameArgs &a, uint32_t grid, uint32_t threads, size_t smem,
+template <int W, int C, bool GMEM>
+static cudaError_t launch_frame_t(const FrameArgs &a, uint32_t tiles, uint32_t threads, size_t smem,
                                   cudaStream_t stream) {
-    auto kern = frame_kernel<W, GMEM>;
+    auto kern = frame_kernel<W, C, GMEM>;
     if (!GMEM && smem > 48 * 1024) {
         cudaError_t err = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         if (err != cudaSuccess) return err;
     }
-    kern<<<grid, threads, GMEM ? 0 : smem, stream>>>(a);
-    return cudaGetLastError();
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3(tiles * C);
+    cfg.blockDim = dim3(threads);
+    cfg.dynamicSmemBytes = GMEM ? 0 : smem;
+    cfg.stream = stream;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeClusterDimension;
+    attr[0].val.clusterDim.x = C;
+    attr[0].val.clusterDim.y = 1;
+    attr[0].val.clusterDim.z = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = C > 1 ? 1 : 0;
+    return cudaLaunchKernelEx(&cfg, kern, a);
 }
 
-cudaError_t launch_frame(const FrameArgs &a, int W, bool gmem, uint32_t grid, uint32_t threads, size_t smem,
-                         cudaStream_t stream) {
-#define STIMGB_CASE(w)                                                             \
-    case w:                                                                        \
-        return gmem ? launch_frame_t<w, true>(a, grid, threads, smem, stream)      \
-                    : launch_frame_t<w, false>(a, grid, threads, smem, stream);
+template <int C, bool GMEM>
+static cudaError_t launch_frame_w(const FrameArgs &a, int W, uint32_t tiles, uint32_t threads, size_t smem,
+                                  cudaStream_t stream) {
     switch (W) {
-        STIMGB_CASE(1)
-        STIMGB_CASE(2)
-        STIMGB_CASE(4)
-        STIMGB_CASE(8)
-        STIMGB_CASE(16)
-        default:
-            return cudaErrorInvalidValue;
+        case 1: return launch_frame_t<1, C, GMEM>(a, tiles, threads, smem, stream);
+        case 2: return launch_frame_t<2, C, GMEM>(a, tiles, threads, smem, stream);
+        case 4: return launch_frame_t<4, C, GMEM>(a, tiles, threads, smem, stream);
+        case 8: return launch_frame_t<8, C, GMEM>(a, tiles, threads, smem, stream);
+        default: return cudaErrorInvalidValue;
     }
-#undef STIMGB_CASE
+}
+
+cudaError_t launch_frame(const FrameArgs &a, int W, int C, bool gmem, uint32_t tiles, uint32_t threads, size_t smem,
+                         cudaStream_t stream) {
+    if (gmem) return C == 1 ? launch_frame_w<1, true>(a, W, tiles, threads, smem, stream) : cudaErrorInvalidValue;
+    switch (C) {
+        case 1: return launch_frame_w<1, false>(a, W, tiles, threads, smem, stream);
+        case 2: return launch_frame_w<2, false>(a, W, tiles, threads, smem, stream);
+        case 4: return launch_frame_w<4, false>(a, W, tiles, threads, smem, stream);
+        case 8: return launch_frame_w<8, false>(a, W, tiles, threads, smem, stream);
+        default: return cudaErrorInvalidValue;
+    }
+}
+
+void philox_key_schedule(uint64_t seed, uint32_t rk0[10], uint32_t rk1[10]) {
+    uint32_t k0 = (uint32_t)seed, k1 = (uint32_t)(seed >> 32);
+    for (int r = 0; r < 10; r++) {
+        rk0[r] = k0;
+        rk1[r] = k1;
+        k0 += 0x9E3779B9u;
+        k1 += 0xBB67AE85u;
+    }
 }
 
 }  // namespace stimgb

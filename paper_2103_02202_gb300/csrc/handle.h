@@ -6,6 +6,16 @@
 
 #include "internal.h"
 
+// Device copy of a FrameProgram for one cluster size.
+struct DevFrameProgram {
+    int C = 0;                          // 0: not built
+    uint32_t Q = 0;
+    uint32_t nprog = 0;
+    stimgb::ProgEntry *prog = nullptr;
+    uint32_t *rank_tab = nullptr;
+    stimgb::DevOp *ops = nullptr;
+};
+
 struct stim_circuit {
     stimgb::HostProgram hp;
     int device = -1;
@@ -27,4 +37,5 @@ struct stim_circuit {
     size_t tr_cap = 0;
     uint64_t *d_gframe = nullptr;
     size_t gframe_cap = 0;
+    DevFrameProgram fprog[4];           // cluster sizes 1, 2, 4, 8
 };

@@ -82,6 +82,27 @@ struct HostProgram {
     uint64_t exec_targets[OP_COUNT] = {0};
 };
 
+// Frame-kernel program for a cluster of C CTAs that split the qubits into
+// contiguous slices of Q = ceil(n / C): qubit q lives in CTA q / Q at local
+// index q % Q. Entries mirror HostProgram::prog one for one; a LAYER's
+// op_begin indexes rank_tab, whose C + 1 values bound each CTA's ops.
+// Op encoding (local addresses):
+//   a:     opcode << 24 | local index of qubit a (in the owning CTA)
+//   b:     two-qubit ops: rank of qubit b << 24 | local index of qubit b
+//          M, MR: measurement index of the first loop iteration
+//          one-qubit noise: table index
+//   instr: flattened instruction ordinal of the first loop iteration
+//   slot:  target slot; DEPOLARIZE2 keeps its table index in bits 24..31
+struct FrameProgram {
+    int C = 1;
+    uint32_t Q = 0;
+    std::vector<ProgEntry> prog;
+    std::vector<uint32_t> rank_tab;
+    std::vector<DevOp> ops;
+};
+
+void build_frame_program(const HostProgram &hp, int C, FrameProgram *out);
+
 // Sets the calling thread's stim_last_error() message; returns code.
 int report_error(int code, const std::string &msg);
 

@@ -10,13 +10,14 @@
 namespace stimgb {
 
 struct FrameArgs {
-    const ProgEntry *prog;
+    const ProgEntry *prog;     // FrameProgram::prog (LAYER.op_begin indexes rank_tab)
     uint32_t nprog;
-    const DevOp *ops;
+    const uint32_t *rank_tab;  // per layer: C + 1 op offsets
+    const DevOp *ops;          // FrameProgram::ops (local qubit addresses)
     const uint64_t *geo;       // [tables][64]
     const uint64_t *ref;       // packed reference sample (ceil(M/64) words)
     uint32_t n;                // qubits
-    uint32_t k0, k1;           // Philox key = (seed lo, seed hi)
+    uint32_t Q;                // qubits per CTA slice
     uint64_t word0;            // global 64-shot word of this call's word 0
     uint64_t nwords;           // words written by this call
     uint64_t last_mask;        // valid bits of the last word
@@ -25,9 +26,13 @@ struct FrameArgs {
     uint64_t *gframe;          // global frame [2][n][gstride] when the tile is not in smem
     uint64_t gstride;
     int *status;
+    uint32_t rk0[10], rk1[10]; // Philox key schedule of the seed
 };
 
-cudaError_t launch_frame(const FrameArgs &a, int W, bool gmem, uint32_t grid, uint32_t threads, size_t smem,
+void philox_key_schedule(uint64_t seed, uint32_t rk0[10], uint32_t rk1[10]);
+
+// tiles = word tiles (clusters); the grid has tiles * C CTAs.
+cudaError_t launch_frame(const FrameArgs &a, int W, int C, bool gmem, uint32_t tiles, uint32_t threads, size_t smem,
                          cudaStream_t stream);
 
 struct TabCtl {

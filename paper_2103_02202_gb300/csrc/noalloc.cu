@@ -101,15 +101,18 @@ extern "C" int stim_frame_sample_noalloc(stim_circuit *c, uint64_t num_shots, ui
                 break;
             }
         }
+        const DevFrameProgram &fp = c->fprog[0];    // single-CTA program, uploaded with the circuit
+        if (fp.C != 1) return fail(STIM_E_INVALID_ARG, "stim_frame_sample_noalloc: circuit not uploaded");
         FrameArgs a{};
-        a.prog = c->d_prog;
-        a.nprog = (uint32_t)hp.prog.size();
-        a.ops = c->d_ops;
+        a.prog = fp.prog;
+        a.nprog = fp.nprog;
+        a.rank_tab = fp.rank_tab;
+        a.ops = fp.ops;
         a.geo = c->d_geo;
         a.ref = c->d_ref;
         a.n = n;
-        a.k0 = (uint32_t)seed;
-        a.k1 = (uint32_t)(seed >> 32);
+        a.Q = fp.Q;
+        philox_key_schedule(seed, a.rk0, a.rk1);
         a.word0 = shot_offset / 64;
         a.nwords = nwords;
         a.last_mask = (num_shots % 64) ? ((1ull << (num_shots % 64)) - 1) : ~0ull;
@@ -117,7 +120,7 @@ extern "C" int stim_frame_sample_noalloc(stim_circuit *c, uint64_t num_shots, ui
         a.rec_stride = nwords;
         a.status = c->d_status;
         const uint64_t grid = (nwords + W - 1) / W;
-        e = launch_frame(a, W, false, (uint32_t)grid, 256, per_word * W, st);
+        e = launch_frame(a, W, 1, false, (uint32_t)grid, 256, per_word * W, st);
         if (e != cudaSuccess) return fail(STIM_E_CUDA, std::string("frame kernel: ") + cudaGetErrorString(e));
     }
     if (det_out && D > 0) {

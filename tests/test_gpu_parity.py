@@ -161,8 +161,10 @@ def test_random_circuits_with_all_noise_kinds():
         np.testing.assert_array_equal(db, od, err_msg=text)
 
 
-@pytest.mark.parametrize("hint", [(1, 64, 0), (2, 128, 0), (4, 256, 0), (8, 512, 0), (16, 1024, 0),
-                                  (1, 256, 1), (4, 128, 1), (16, 256, 1)])
+@pytest.mark.parametrize("hint", [(1, 64, 0, 1), (2, 128, 0, 1), (4, 256, 0, 1), (8, 512, 0, 1),
+                                  (1, 256, 1, 1), (4, 128, 1, 1), (8, 256, 1, 1),
+                                  (1, 128, 0, 2), (2, 256, 0, 4), (4, 512, 0, 8), (8, 512, 0, 8),
+                                  (1, 32, 0, 8)])
 def test_tile_shapes_are_invisible(hint):
     text = W.surface_code_memory(5, 4, 5e-3)
     base_m, base_d = gpu_sample(text, 2000, 99)
@@ -233,6 +235,21 @@ def test_surface_d25_bench_size_sampled_parity():
     np.testing.assert_array_equal(gm, om)
     np.testing.assert_array_equal(gd, od)
     c.close()
+
+
+@pytest.mark.parametrize("cluster", [2, 4, 8])
+def test_cluster_partitions_random_circuits(cluster):
+    """Qubit slices split over a cluster: two-qubit gates and DEPOLARIZE2 that
+    cross slices go through distributed shared memory."""
+    rng = np.random.default_rng(100 + cluster)
+    for _ in range(4):
+        n = int(rng.integers(cluster, 60))
+        text = _rand_circuit(rng, n, 60)
+        shots = int(rng.integers(1, 900))
+        mb, db = gpu_sample(text, shots, 3, hint=(int(rng.choice([1, 2, 4])), 128, 0, cluster))
+        om, od = oracle.Circuit(text).sample(np.arange(shots), 3, threads=8)
+        np.testing.assert_array_equal(mb, om, err_msg=text)
+        np.testing.assert_array_equal(db, od, err_msg=text)
 
 
 def test_random_clifford_parity():
