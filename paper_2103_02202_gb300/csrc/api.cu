@@ -129,6 +129,7 @@ int frame_program(stim_circuit *c, int C, const DevFrameProgram **out) {
         int r;
         if ((r = upload(&d.prog, fp.prog, "upload frame program")) != STIM_OK) return r;
         if ((r = upload(&d.rank_tab, fp.rank_tab, "upload frame program")) != STIM_OK) return r;
+        if ((r = upload(&d.segs, fp.segs, "upload frame program")) != STIM_OK) return r;
         if ((r = upload(&d.ops, fp.ops, "upload frame program")) != STIM_OK) return r;
         d.Q = fp.Q;
         d.nprog = (uint32_t)fp.prog.size();
@@ -370,6 +371,7 @@ void stim_free(stim_circuit *c) {
         for (DevFrameProgram &d : c->fprog) {
             cudaFree(d.prog);
             cudaFree(d.rank_tab);
+            cudaFree(d.segs);
             cudaFree(d.ops);
         }
         if (cur >= 0 && cur != c->device) cudaSetDevice(cur);
@@ -459,6 +461,7 @@ int stim_frame_sample_ex(stim_circuit *c, uint64_t num_shots, uint64_t seed, uin
         a.prog = fp->prog;
         a.nprog = fp->nprog;
         a.rank_tab = fp->rank_tab;
+        a.segs = fp->segs;
         a.ops = fp->ops;
         a.geo = c->d_geo;
         a.ref = c->d_ref;

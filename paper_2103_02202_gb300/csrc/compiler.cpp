@@ -476,40 +476,171 @@ void collect_detectors(const Block &b, uint64_t *meas, HostProgram *hp) {
 
 }  // namespace
 
+namespace {
+
+struct Chain {
+    uint32_t q0, q1;            // footprint (q1 == q0 for one qubit)
+    std::vector<DevOp> ops;     // global encoding (as in HostProgram::ops)
+};
+
+inline uint32_t op_q0(const DevOp &d) { return d.a & kQubitMask; }
+inline uint32_t op_q1(const DevOp &d) {
+    const uint32_t opc = d.a >> 24;
+    return op_is_pair(opc) ? (d.b & kQubitMask) : op_q0(d);
+}
+
+class FrameBuilder {
+  public:
+    FrameBuilder(const HostProgram &hp, int C, FrameProgram *fp) : hp_(hp), C_(C), fp_(fp), owner_(hp.num_qubits + 1, -1) {}
+
+    // Folds the layers [first, last) (consecutive LAYER entries of hp.prog)
+    // into merged layers; returns the number of merged layers emitted.
+    uint32_t run(size_t first, size_t last) {
+        uint32_t emitted = 0;
+        for (size_t k = first; k < last; k++) {
+            const ProgEntry &e = hp_.prog[k];
+            const uint32_t tot = e.n_gate + e.n_noise + e.n_collapse;
+            const DevOp *ops = hp_.ops.data() + e.op_begin;
+            bool fold = !chains_.empty();
+            if (fold) {
+                for (uint32_t i = 0; i < tot && fold; i++) {
+                    const int c0 = owner_[op_q0(ops[i])], c1 = owner_[op_q1(ops[i])];
+                    fold = c0 >= 0 && c0 == c1;
+                }
+            }
+            if (!fold) {
+                if (!chains_.empty()) emitted += emit();
+                for (uint32_t i = 0; i < tot; i++) {
+                    Chain ch{op_q0(ops[i]), op_q1(ops[i]), {ops[i]}};
+                    owner_[ch.q0] = owner_[ch.q1] = (int)chains_.size();
+                    chains_.push_back(std::move(ch));
+                }
+            } else {
+                for (uint32_t i = 0; i < tot; i++) chains_[owner_[op_q0(ops[i])]].ops.push_back(ops[i]);
+            }
+        }
+        if (!chains_.empty()) emitted += emit();
+        return emitted;
+    }
+
+  private:
+    const HostProgram &hp_;
+    int C_;
+    FrameProgram *fp_;
+    std::vector<int> owner_;       // qubit -> chain of the open merged layer
+    std::vector<Chain> chains_;
+
+    uint32_t ref(uint32_t q) const { return ((q / fp_->Q) << 24) | (q % fp_->Q); }
+
+    DevOp encode(const DevOp &d) const {
+        const uint32_t opc = d.a >> 24;
+        DevOp f = d;
+        f.a = (opc << 28) | ref(op_q0(d));
+        if (op_is_pair(opc)) {
+            f.b = ref(d.b & kQubitMask);
+            if (opc == OP_DEP2) f.slot = d.slot | ((d.b >> 24) << 24);
+        } else if (op_is_noise(opc)) {
+            f.b = d.b >> 24;
+        }
+        return f;
+    }
+
+    uint32_t emit() {
+        ProgEntry e{};
+        e.kind = ENT_LAYER;
+        e.op_begin = (uint32_t)fp_->rank_tab.size();
+        uint32_t ng = 0, nn = 0, nc = 0;
+        // per rank: chains sorted by opcode signature
+        std::vector<std::vector<uint32_t>> by_rank((size_t)C_);
+        for (uint32_t i = 0; i < chains_.size(); i++) by_rank[chains_[i].q0 / fp_->Q].push_back(i);
+        for (int r = 0; r < C_; r++) {
+            fp_->rank_tab.push_back((uint32_t)fp_->segs.size());
+            auto sig_less = [&](uint32_t x, uint32_t y) {
+                const auto &a = chains_[x].ops, &b = chains_[y].ops;
+                if (a.size() != b.size()) return a.size() < b.size();
+                for (size_t j = 0; j < a.size(); j++)
+                    if ((a[j].a >> 24) != (b[j].a >> 24)) return (a[j].a >> 24) < (b[j].a >> 24);
+                return false;
+            };
+            std::stable_sort(by_rank[r].begin(), by_rank[r].end(), sig_less);
+            size_t i = 0;
+            while (i < by_rank[r].size()) {
+                size_t j = i + 1;
+                while (j < by_rank[r].size() && !sig_less(by_rank[r][i], by_rank[r][j]) &&
+                       !sig_less(by_rank[r][j], by_rank[r][i]))
+                    j++;
+                FrameSeg sg{};
+                sg.len = (uint32_t)chains_[by_rank[r][i]].ops.size();
+                sg.op_begin = (uint32_t)fp_->ops.size();
+                sg.count = (uint32_t)(j - i);
+                for (size_t k = i; k < j; k++)
+                    for (const DevOp &d : chains_[by_rank[r][k]].ops) {
+                        fp_->ops.push_back(encode(d));
+                        const uint32_t opc = d.a >> 24;
+                        if (op_is_gate(opc)) ng++;
+                        else if (op_is_noise(opc)) nn++;
+                        else nc++;
+                    }
+                fp_->segs.push_back(sg);
+                i = j;
+            }
+        }
+        fp_->rank_tab.push_back((uint32_t)fp_->segs.size());
+        e.n_gate = ng;
+        e.n_noise = nn;
+        e.n_collapse = nc;
+        fp_->prog.push_back(e);
+        for (const Chain &ch : chains_) owner_[ch.q0] = owner_[ch.q1] = -1;
+        chains_.clear();
+        return 1;
+    }
+};
+
+}  // namespace
+
 void build_frame_program(const HostProgram &hp, int C, FrameProgram *out) {
     FrameProgram fp;
     fp.C = C;
     const uint32_t n = hp.num_qubits ? hp.num_qubits : 1;
     fp.Q = (n + (uint32_t)C - 1) / (uint32_t)C;
-    fp.prog = hp.prog;
     fp.ops.reserve(hp.ops.size());
-    std::vector<std::vector<DevOp>> bucket((size_t)C);
-    for (ProgEntry &e : fp.prog) {
-        if (e.kind != ENT_LAYER) continue;
-        const uint32_t tot = e.n_gate + e.n_noise + e.n_collapse;
-        for (auto &bk : bucket) bk.clear();
-        for (uint32_t i = 0; i < tot; i++) {
-            DevOp d = hp.ops[e.op_begin + i];
-            const uint32_t opc = d.a >> 24, qa = d.a & kQubitMask;
-            const uint32_t ra = qa / fp.Q;
-            DevOp f = d;
-            f.a = (opc << 24) | (qa - ra * fp.Q);
-            if (opc == OP_CX || opc == OP_CZ || opc == OP_DEP2) {
-                const uint32_t qb = d.b & kQubitMask, rb = qb / fp.Q;
-                f.b = (rb << 24) | (qb - rb * fp.Q);
-                if (opc == OP_DEP2) f.slot = d.slot | ((d.b >> 24) << 24);
-            } else if (op_is_noise(opc)) {
-                f.b = d.b >> 24;
-            }
-            bucket[ra].push_back(f);    // keeps gate / noise / collapse order within a CTA
+    FrameBuilder fb(hp, C, &fp);
+    // Walk the program; runs of consecutive LAYER entries are folded, loop
+    // markers are copied (their cross references are rewritten).
+    std::vector<size_t> open;            // indices (in fp.prog) of open LOOP_BEGINs
+    std::vector<uint64_t> layer_count;   // merged layers emitted inside each open loop
+    uint64_t top_layers = 0;
+    size_t k = 0;
+    while (k < hp.prog.size()) {
+        const ProgEntry &e = hp.prog[k];
+        if (e.kind == ENT_LAYER) {
+            size_t j = k;
+            while (j < hp.prog.size() && hp.prog[j].kind == ENT_LAYER) j++;
+            const uint32_t m = fb.run(k, j);
+            if (layer_count.empty()) top_layers += m;
+            else layer_count.back() += m;
+            k = j;
+            continue;
         }
-        e.op_begin = (uint32_t)fp.rank_tab.size();
-        for (int r = 0; r < C; r++) {
-            fp.rank_tab.push_back((uint32_t)fp.ops.size());
-            fp.ops.insert(fp.ops.end(), bucket[r].begin(), bucket[r].end());
+        if (e.kind == ENT_LOOP_BEGIN) {
+            open.push_back(fp.prog.size());
+            layer_count.push_back(0);
+            fp.prog.push_back(e);
+        } else {
+            const size_t b = open.back();
+            open.pop_back();
+            ProgEntry f = e;
+            f.op_begin = (uint32_t)b;
+            fp.prog[b].op_begin = (uint32_t)fp.prog.size();
+            fp.prog.push_back(f);
+            const uint64_t inner = layer_count.back() * e.reps;
+            layer_count.pop_back();
+            if (layer_count.empty()) top_layers += inner;
+            else layer_count.back() += inner;
         }
-        fp.rank_tab.push_back((uint32_t)fp.ops.size());
+        k++;
     }
+    fp.merged_layers_exec = top_layers;
     *out = std::move(fp);
 }
 

@@ -47,10 +47,8 @@ struct DrawStream {
     const uint32_t *rk0, *rk1;
 
     __device__ __forceinline__ DrawStream(const uint32_t *rk0_, const uint32_t *rk1_, uint32_t ti_,
-                                          uint32_t slot_, uint32_t word_)
-        : j(0), slot(slot_), ti(ti_), word(word_), rk0(rk0_), rk1(rk1_) {
-        blk = philox_sched(make_uint4(0u, slot, ti, word), rk0, rk1);
-    }
+                                          uint32_t slot_, uint32_t word_, uint4 blk0)
+        : blk(blk0), j(0), slot(slot_), ti(ti_), word(word_), rk0(rk0_), rk1(rk1_) {}
 
     __device__ __forceinline__ uint32_t next() {
         const uint32_t lane = j & 3u;
@@ -60,18 +58,17 @@ struct DrawStream {
     }
 };
 
-// Error masks of one noise slot over the 64 shots of one word, by exact
-// geometric gaps: with G the threshold table of p, a draw u gives the gap
-// min{k : u < G[k]} to the next error. The first test asks whether the next
-// error falls beyond bit 63 (u >= G[remaining - 1]); only otherwise is the gap
-// located by binary search. DEPOLARIZE1 spends one more draw v per error on
-// the Pauli 1 + floor(3v / 2^32) (1 X, 2 Y, 3 Z); DEPOLARIZE2 on
-// c = 1 + floor(15v / 2^32), first-qubit Pauli c >> 2, second c & 3.
+// General procedure: exact geometric gaps. With G the threshold table of p, a
+// draw u gives the gap min{k : u < G[k]} to the next error. The first test
+// asks whether the next error falls beyond bit 63 (u >= G[remaining - 1]);
+// only otherwise is the gap located by binary search. DEPOLARIZE1 spends one
+// more draw v per error on the Pauli 1 + floor(3v / 2^32) (1 X, 2 Y, 3 Z);
+// DEPOLARIZE2 on c = 1 + floor(15v / 2^32), first-qubit Pauli c >> 2, second c & 3.
 template <uint32_t OP>
-__device__ __forceinline__ void noise_masks(const uint64_t *__restrict__ G, const uint32_t *rk0,
-                                            const uint32_t *rk1, uint32_t instr, uint32_t slot, uint32_t word,
-                                            uint64_t &xa, uint64_t &za, uint64_t &xb, uint64_t &zb) {
-    DrawStream ds(rk0, rk1, kTagNoise | instr, slot, word);
+__device__ __forceinline__ void noise_masks_slow(const uint64_t *__restrict__ G, const uint32_t *rk0,
+                                              const uint32_t *rk1, uint32_t instr, uint32_t slot, uint32_t word,
+                                              uint4 blk0, uint64_t &xa, uint64_t &za, uint64_t &xb, uint64_t &zb) {
+    DrawStream ds(rk0, rk1, kTagNoise | instr, slot, word, blk0);
     int pos = -1;
     xa = za = xb = zb = 0;
     for (;;) {
@@ -104,6 +101,19 @@ __device__ __forceinline__ void noise_masks(const uint64_t *__restrict__ G, cons
             if (pb >= 2u) zb |= bit;
         }
     }
+}
+
+// Error masks of one noise slot over the 64 shots of one word. The first draw
+// alone decides the common case: no error in the word exactly when
+// u0 >= G[63]. Only then is the general procedure run (out of line).
+template <uint32_t OP>
+__device__ __forceinline__ bool noise_masks(const uint64_t *__restrict__ G, const uint32_t *rk0, const uint32_t *rk1,
+                                            uint32_t instr, uint32_t slot, uint32_t word, uint64_t &xa,
+                                            uint64_t &za, uint64_t &xb, uint64_t &zb) {
+    const uint4 blk0 = philox_sched(make_uint4(0u, slot, kTagNoise | instr, word), rk0, rk1);
+    if ((uint64_t)blk0.x >= __ldg(G + 63)) return false;
+    noise_masks_slow<OP>(G, rk0, rk1, instr, slot, word, blk0, xa, za, xb, zb);
+    return true;
 }
 
 __device__ __forceinline__ uint64_t globaltimer_ns() {

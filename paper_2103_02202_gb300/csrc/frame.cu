@@ -10,8 +10,10 @@
 // (When even one 64-shot word of the largest slice does not fit, a C = 1
 // variant keeps the same rows in a global-memory frame instead.)
 //
-// The CTA walks the compiled program; for each fused layer (ops on disjoint
-// qubits) its threads take (op, word) items of the CTA's own slice:
+// The CTA walks the compiled program. Consecutive fused layers are folded
+// into chains (an op that acts only on qubits of one earlier op runs right
+// after it on the same thread); for each merged layer the threads take
+// (chain, word) items of the CTA's own chains and apply each chain's ops:
 //   H: swap(x, z)   S: z ^= x   CX(c,t): z_c ^= z_t, x_t ^= x_c
 //   CZ(a,b): z_a ^= x_b, z_b ^= x_a
 //   M:  record = ref[m] ^ x, then z ^= collapse coin
@@ -35,8 +37,6 @@ namespace stimgb {
 
 namespace {
 
-constexpr int kPrefetch = 4;
-
 __device__ __forceinline__ DevOp as_op(uint4 v) { return DevOp{v.x, v.y, v.z, v.w}; }
 
 template <int C>
@@ -48,53 +48,85 @@ __device__ __forceinline__ void sync_tile() {
     }
 }
 
-// Row pointers of the partner qubit of a two-qubit op (possibly in a peer CTA).
-template <int C>
-__device__ __forceinline__ void partner(uint32_t b, uint32_t my_rank, uint64_t *X, uint64_t *Z, uint64_t qstride,
-                                        uint64_t *&xb, uint64_t *&zb) {
-    const uint32_t rb = b >> 24, lb = b & 0xFFFFFFu;
-    xb = X + (uint64_t)lb * qstride;
-    zb = Z + (uint64_t)lb * qstride;
-    if constexpr (C > 1) {
-        if (rb != my_rank) {
-            cg::cluster_group cl = cg::this_cluster();
-            xb = cl.map_shared_rank(xb, rb);
-            zb = cl.map_shared_rank(zb, rb);
-        }
-    }
+// Word of a peer CTA's shared memory (same offset, CTA `rank` of the cluster).
+__device__ __forceinline__ uint64_t ld_peer(const uint64_t *p, uint32_t rank) {
+    const uint32_t sa = (uint32_t)__cvta_generic_to_shared(p);
+    uint32_t ra;
+    uint64_t v;
+    asm volatile("mapa.shared::cluster.u32 %0, %1, %2;" : "=r"(ra) : "r"(sa), "r"(rank));
+    asm volatile("ld.shared::cluster.u64 %0, [%1];" : "=l"(v) : "r"(ra) : "memory");
+    return v;
 }
 
-// Applies one op to word w of the tile (X, Z point at word 0 of the rows).
-template <int C>
-__device__ __forceinline__ void frame_op_word(const FrameArgs &a, const DevOp op, uint32_t w, uint32_t my_rank,
-                                              uint64_t *X, uint64_t *Z, uint64_t qstride, uint64_t tile0,
-                                              uint32_t instr_off, uint32_t meas_off) {
-    const uint32_t opc = op.a >> 24;
-    const uint64_t ia = (uint64_t)(op.a & 0xFFFFFFu) * qstride + w;
-    const uint64_t lw = tile0 + w;                    // word index within this call
+__device__ __forceinline__ void st_peer(uint64_t *p, uint32_t rank, uint64_t v) {
+    const uint32_t sa = (uint32_t)__cvta_generic_to_shared(p);
+    uint32_t ra;
+    asm volatile("mapa.shared::cluster.u32 %0, %1, %2;" : "=r"(ra) : "r"(sa), "r"(rank));
+    asm volatile("st.shared::cluster.u64 [%0], %1;" ::"r"(ra), "l"(v) : "memory");
+}
+
+// The X and Z planes of one tile as seen from one CTA. A qubit reference is
+// (rank << 24 | local index); references to other CTAs of the cluster go
+// through distributed shared memory.
+template <int C, bool GMEM>
+struct Tile {
+    uint64_t *X, *Z;
+    uint64_t qstride;
+    uint32_t rank;
+
+    __device__ __forceinline__ uint64_t *at(uint64_t *P, uint32_t ref, uint32_t w) const {
+        return P + (uint64_t)(ref & 0xFFFFFFu) * qstride + w;
+    }
+    __device__ __forceinline__ uint64_t ld(uint64_t *P, uint32_t ref, uint32_t w) const {
+        uint64_t *p = at(P, ref, w);
+        if constexpr (C > 1) {
+            if ((ref >> 24) != rank) return ld_peer(p, ref >> 24);
+        }
+        return *p;
+    }
+    __device__ __forceinline__ void st(uint64_t *P, uint32_t ref, uint32_t w, uint64_t v) const {
+        uint64_t *p = at(P, ref, w);
+        if constexpr (C > 1) {
+            if ((ref >> 24) != rank) {
+                st_peer(p, ref >> 24, v);
+                return;
+            }
+        }
+        *p = v;
+    }
+};
+
+// Applies one op to word w of the tile.
+template <int C, bool GMEM>
+__device__ __forceinline__ void frame_op(const FrameArgs &a, const Tile<C, GMEM> &t, const DevOp op, uint32_t w,
+                                         uint64_t lw, uint32_t instr_off, uint32_t meas_off) {
+    const uint32_t opc = op.a >> 28;
+    const uint32_t ra = op.a & 0x0FFFFFFFu;
     const uint32_t gw = (uint32_t)(a.word0 + lw);     // global 64-shot word (RNG counter)
     switch (opc) {
         case OP_H: {
-            const uint64_t t = X[ia];
-            X[ia] = Z[ia];
-            Z[ia] = t;
+            const uint64_t x = t.ld(t.X, ra, w), z = t.ld(t.Z, ra, w);
+            t.st(t.X, ra, w, z);
+            t.st(t.Z, ra, w, x);
             break;
         }
         case OP_S:
-            Z[ia] ^= X[ia];
+            t.st(t.Z, ra, w, t.ld(t.Z, ra, w) ^ t.ld(t.X, ra, w));
             break;
-        case OP_CX:
+        case OP_CX: {
+            const uint32_t rb = op.b;
+            const uint64_t xa = t.ld(t.X, ra, w), za = t.ld(t.Z, ra, w);
+            const uint64_t xb = t.ld(t.X, rb, w), zb = t.ld(t.Z, rb, w);
+            t.st(t.Z, ra, w, za ^ zb);
+            t.st(t.X, rb, w, xb ^ xa);
+            break;
+        }
         case OP_CZ: {
-            uint64_t *xb, *zb;
-            partner<C>(op.b, my_rank, X + w, Z + w, qstride, xb, zb);
-            if (opc == OP_CX) {
-                Z[ia] ^= *zb;
-                *xb ^= X[ia];
-            } else {
-                const uint64_t xa = X[ia];
-                Z[ia] ^= *xb;
-                *zb ^= xa;
-            }
+            const uint32_t rb = op.b;
+            const uint64_t xa = t.ld(t.X, ra, w), za = t.ld(t.Z, ra, w);
+            const uint64_t xb = t.ld(t.X, rb, w), zb = t.ld(t.Z, rb, w);
+            t.st(t.Z, ra, w, za ^ xb);
+            t.st(t.Z, rb, w, zb ^ xa);
             break;
         }
         case OP_M:
@@ -103,16 +135,16 @@ __device__ __forceinline__ void frame_op_word(const FrameArgs &a, const DevOp op
             if (opc != OP_R && a.rec != nullptr && lw < a.nwords) {
                 const uint32_t m = op.b + meas_off;
                 const uint64_t refm = 0ull - ((__ldg(a.ref + (m >> 6)) >> (m & 63)) & 1ull);
-                uint64_t v = X[ia] ^ refm;
+                uint64_t v = t.ld(t.X, ra, w) ^ refm;
                 if (lw == a.nwords - 1) v &= a.last_mask;
                 a.rec[(uint64_t)m * a.rec_stride + lw] = v;
             }
             const uint64_t coin = half_mask(a.rk0, a.rk1, kTagCollapse | (op.instr + instr_off), op.slot, gw);
             if (opc == OP_M) {
-                Z[ia] ^= coin;
+                t.st(t.Z, ra, w, t.ld(t.Z, ra, w) ^ coin);
             } else {
-                X[ia] = 0;
-                Z[ia] = coin;
+                t.st(t.X, ra, w, 0);
+                t.st(t.Z, ra, w, coin);
             }
             break;
         }
@@ -122,24 +154,25 @@ __device__ __forceinline__ void frame_op_word(const FrameArgs &a, const DevOp op
             uint64_t mx, mz, u1, u2;
             const uint64_t *G = a.geo + 64u * op.b;
             const uint32_t instr = op.instr + instr_off;
-            if (opc == OP_XERR) noise_masks<OP_XERR>(G, a.rk0, a.rk1, instr, op.slot, gw, mx, mz, u1, u2);
-            else if (opc == OP_ZERR) noise_masks<OP_ZERR>(G, a.rk0, a.rk1, instr, op.slot, gw, mx, mz, u1, u2);
-            else noise_masks<OP_DEP1>(G, a.rk0, a.rk1, instr, op.slot, gw, mx, mz, u1, u2);
-            if (mx) X[ia] ^= mx;
-            if (mz) Z[ia] ^= mz;
+            bool hit;
+            if (opc == OP_XERR) hit = noise_masks<OP_XERR>(G, a.rk0, a.rk1, instr, op.slot, gw, mx, mz, u1, u2);
+            else if (opc == OP_ZERR) hit = noise_masks<OP_ZERR>(G, a.rk0, a.rk1, instr, op.slot, gw, mx, mz, u1, u2);
+            else hit = noise_masks<OP_DEP1>(G, a.rk0, a.rk1, instr, op.slot, gw, mx, mz, u1, u2);
+            if (hit) {
+                if (mx) t.st(t.X, ra, w, t.ld(t.X, ra, w) ^ mx);
+                if (mz) t.st(t.Z, ra, w, t.ld(t.Z, ra, w) ^ mz);
+            }
             break;
         }
         case OP_DEP2: {
             uint64_t m0x, m0z, m1x, m1z;
-            noise_masks<OP_DEP2>(a.geo + 64u * (op.slot >> 24), a.rk0, a.rk1, op.instr + instr_off,
-                                 op.slot & 0xFFFFFFu, gw, m0x, m0z, m1x, m1z);
-            if (m0x | m0z | m1x | m1z) {
-                uint64_t *xb, *zb;
-                partner<C>(op.b, my_rank, X + w, Z + w, qstride, xb, zb);
-                X[ia] ^= m0x;
-                Z[ia] ^= m0z;
-                *xb ^= m1x;
-                *zb ^= m1z;
+            if (noise_masks<OP_DEP2>(a.geo + 64u * (op.slot >> 24), a.rk0, a.rk1, op.instr + instr_off,
+                                     op.slot & 0xFFFFFFu, gw, m0x, m0z, m1x, m1z)) {
+                const uint32_t rb = op.b;
+                t.st(t.X, ra, w, t.ld(t.X, ra, w) ^ m0x);
+                t.st(t.Z, ra, w, t.ld(t.Z, ra, w) ^ m0z);
+                t.st(t.X, rb, w, t.ld(t.X, rb, w) ^ m1x);
+                t.st(t.Z, rb, w, t.ld(t.Z, rb, w) ^ m1z);
             }
             break;
         }
@@ -157,21 +190,22 @@ __global__ void __launch_bounds__(1024, 1) frame_kernel(const __grid_constant__ 
     const uint64_t tile0 = (uint64_t)(blockIdx.x / C) * W;
     const uint32_t qlo = rank * a.Q;
     const uint32_t nq = a.n > qlo ? min(a.Q, a.n - qlo) : 0u;
-    uint64_t *X, *Z;
-    uint64_t qstride;
+    Tile<C, GMEM> t;
+    t.rank = rank;
     if (GMEM) {
-        X = a.gframe + tile0;
-        Z = a.gframe + (uint64_t)a.n * a.gstride + tile0;
-        qstride = a.gstride;
+        t.X = a.gframe + tile0;
+        t.Z = a.gframe + (uint64_t)a.n * a.gstride + tile0;
+        t.qstride = a.gstride;
     } else {
-        X = smem;
-        Z = smem + (uint64_t)a.Q * W;
-        qstride = W;
+        t.X = smem;
+        t.Z = smem + (uint64_t)a.Q * W;
+        t.qstride = W;
     }
     for (uint32_t i = threadIdx.x; i < nq * W; i += blockDim.x) {
         const uint32_t l = i / W, w = i % W;
-        X[(uint64_t)l * qstride + w] = 0;
-        Z[(uint64_t)l * qstride + w] = half_mask(a.rk0, a.rk1, kTagInit, qlo + l, (uint32_t)(a.word0 + tile0 + w));
+        t.X[(uint64_t)l * t.qstride + w] = 0;
+        t.Z[(uint64_t)l * t.qstride + w] =
+            half_mask(a.rk0, a.rk1, kTagInit, qlo + l, (uint32_t)(a.word0 + tile0 + w));
     }
     sync_tile<C>();
 
@@ -183,25 +217,23 @@ __global__ void __launch_bounds__(1024, 1) frame_kernel(const __grid_constant__ 
     while (pc < a.nprog) {
         const ProgEntry e = a.prog[pc];
         if (e.kind == ENT_LAYER) {
-            const uint32_t b = __ldg(a.rank_tab + e.op_begin + rank);
-            const uint32_t en = __ldg(a.rank_tab + e.op_begin + rank + 1);
-            // Items are (op, word) pairs with the W words of an op on adjacent
-            // threads (one op fetch serves W lanes). A thread fetches up to
-            // kPrefetch of its ops before applying any, so their latencies overlap.
-            const uint32_t items = (en - b) * W;
-            for (uint32_t base = threadIdx.x; base < items; base += kPrefetch * blockDim.x) {
-                DevOp op[kPrefetch];
-#pragma unroll
-                for (int k = 0; k < kPrefetch; k++) {
-                    const uint32_t it = base + k * blockDim.x;
-                    if (it < items) op[k] = as_op(__ldg(reinterpret_cast<const uint4 *>(a.ops) + b + it / W));
+            // Items are (chain, word) pairs, numbered across this CTA's
+            // segments of the merged layer; the W words of a chain sit on
+            // adjacent threads, which share its op fetches.
+            const uint32_t sb = __ldg(a.rank_tab + e.op_begin + rank);
+            const uint32_t se = __ldg(a.rank_tab + e.op_begin + rank + 1);
+            uint32_t g = threadIdx.x, seg_start = 0;
+            for (uint32_t s = sb; s < se; s++) {
+                const uint4 sv = __ldg(reinterpret_cast<const uint4 *>(a.segs) + s);
+                const uint32_t len = sv.x, op0 = sv.y, items = sv.z * W;
+                for (; g < seg_start + items; g += blockDim.x) {
+                    const uint32_t it = g - seg_start;
+                    const uint32_t w = it % W;
+                    const uint4 *cp = reinterpret_cast<const uint4 *>(a.ops) + op0 + (it / W) * len;
+                    for (uint32_t j = 0; j < len; j++)
+                        frame_op<C, GMEM>(a, t, as_op(__ldg(cp + j)), w, tile0 + w, instr_off, meas_off);
                 }
-#pragma unroll
-                for (int k = 0; k < kPrefetch; k++) {
-                    const uint32_t it = base + k * blockDim.x;
-                    if (it < items)
-                        frame_op_word<C>(a, op[k], it % W, rank, X, Z, qstride, tile0, instr_off, meas_off);
-                }
+                seg_start += items;
             }
             sync_tile<C>();
             pc++;

@@ -13,6 +13,7 @@ struct DevFrameProgram {
     uint32_t nprog = 0;
     stimgb::ProgEntry *prog = nullptr;
     uint32_t *rank_tab = nullptr;
+    stimgb::FrameSeg *segs = nullptr;
     stimgb::DevOp *ops = nullptr;
 };
 

@@ -84,20 +84,40 @@ struct HostProgram {
 
 // Frame-kernel program for a cluster of C CTAs that split the qubits into
 // contiguous slices of Q = ceil(n / C): qubit q lives in CTA q / Q at local
-// index q % Q. Entries mirror HostProgram::prog one for one; a LAYER's
-// op_begin indexes rank_tab, whose C + 1 values bound each CTA's ops.
-// Op encoding (local addresses):
-//   a:     opcode << 24 | local index of qubit a (in the owning CTA)
-//   b:     two-qubit ops: rank of qubit b << 24 | local index of qubit b
+// index q % Q.
+//
+// Consecutive layers are folded into chains: an op joins the chain of the
+// previous merged layer whose first op covers all of its qubits, and runs
+// right after it on the same thread. Chains of one merged layer have disjoint
+// qubit footprints. A CTA owns the chains whose first op's first qubit is in
+// its slice; its chains of a merged layer are grouped into segments of equal
+// opcode signature (so warps run uniform code).
+//
+// Entries mirror HostProgram::prog except that folded LAYER entries are
+// removed; a LAYER's op_begin indexes rank_tab, whose C + 1 values bound
+// each CTA's segments in segs.
+// Qubit references are (rank << 24 | local index).
+// Op encoding:
+//   a:     opcode << 28 | reference of qubit a
+//   b:     two-qubit ops: reference of qubit b
 //          M, MR: measurement index of the first loop iteration
 //          one-qubit noise: table index
 //   instr: flattened instruction ordinal of the first loop iteration
 //   slot:  target slot; DEPOLARIZE2 keeps its table index in bits 24..31
+struct FrameSeg {
+    uint32_t len;       // ops per chain
+    uint32_t op_begin;  // first op of the first chain
+    uint32_t count;     // chains
+    uint32_t pad;
+};
+
 struct FrameProgram {
     int C = 1;
     uint32_t Q = 0;
+    uint64_t merged_layers_exec = 0;
     std::vector<ProgEntry> prog;
     std::vector<uint32_t> rank_tab;
+    std::vector<FrameSeg> segs;
     std::vector<DevOp> ops;
 };
 

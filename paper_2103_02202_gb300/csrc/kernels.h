@@ -12,8 +12,9 @@ namespace stimgb {
 struct FrameArgs {
     const ProgEntry *prog;     // FrameProgram::prog (LAYER.op_begin indexes rank_tab)
     uint32_t nprog;
-    const uint32_t *rank_tab;  // per layer: C + 1 op offsets
-    const DevOp *ops;          // FrameProgram::ops (local qubit addresses)
+    const uint32_t *rank_tab;  // per merged layer: C + 1 segment offsets
+    const FrameSeg *segs;      // FrameProgram::segs
+    const DevOp *ops;          // FrameProgram::ops (qubit references)
     const uint64_t *geo;       // [tables][64]
     const uint64_t *ref;       // packed reference sample (ceil(M/64) words)
     uint32_t n;                // qubits

@@ -107,6 +107,7 @@ extern "C" int stim_frame_sample_noalloc(stim_circuit *c, uint64_t num_shots, ui
         a.prog = fp.prog;
         a.nprog = fp.nprog;
         a.rank_tab = fp.rank_tab;
+        a.segs = fp.segs;
         a.ops = fp.ops;
         a.geo = c->d_geo;
         a.ref = c->d_ref;
