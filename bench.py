@@ -51,7 +51,9 @@ def parse_args():
     ap.add_argument("--steps", type=int, default=64)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
-    ap.add_argument("--workload", choices=sorted(WORKLOADS), default="surface_d100")
+    ap.add_argument("--workload", choices=sorted(WORKLOADS) + ["batch"], default="surface_d100")
+    ap.add_argument("--batch-per-launch", type=int, default=8,
+                    help="batches of the workload per persistent batched launch (0 = skip)")
     ap.add_argument("--cpu-shots", type=int, default=0, help="oracle shots per CPU sample (0 = auto)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--shots", type=int, default=0, help="shots per step (0 = the workload's)")
@@ -234,8 +236,81 @@ def workload_name(wl):
             % (wl["d"], wl["rounds"], wl["p"], wl["shots"]))
 
 
+def run_batch_workload(args):
+    """64 heterogeneous circuits: one persistent batched launch vs a plain
+    launch per circuit, same shots, same outputs."""
+    import torch
+    import paper_2103_02202_gb300 as sg
+    from paper_2103_02202_gb300 import build as sgbuild
+    from paper_2103_02202_gb300 import workloads as W
+    torch.cuda.set_device(0)
+    sgbuild.build()
+    spec = W.batch_circuits()
+    t0 = time.perf_counter()
+    cs = [sg.Circuit(e["text"]) for e in spec]
+    compile_s = time.perf_counter() - t0
+    t0 = time.perf_counter()
+    for c in cs:
+        c.reference()
+    torch.cuda.synchronize()
+    ref_s = time.perf_counter() - t0
+    shots = [e["shots"] for e in spec]
+    seeds = [e["seed"] for e in spec]
+    stream = torch.cuda.current_stream()
+    outs = []
+    for c, S in zip(cs, shots):
+        w = (S + 63) // 64
+        if c.num_detectors:
+            outs.append((None, torch.empty((c.num_detectors, w), dtype=torch.int64, device="cuda")))
+        else:
+            outs.append((torch.empty((c.num_measurements, w), dtype=torch.int64, device="cuda"), None))
+    gate_shots = sum(c.info["num_gate_targets"] * S for c, S in zip(cs, shots))
+
+    def plain_step():
+        for c, S, sd, (m, d) in zip(cs, shots, seeds, outs):
+            sg.stim_frame_sample_ex(c.handle, S, sd, 0, m.data_ptr() if m is not None else 0,
+                                    d.data_ptr() if d is not None else 0, 0, None, stream.cuda_stream)
+
+    plan = sg.stim_batch_create([c.handle for c in cs], shots, None, stream.cuda_stream)
+
+    def batch_step():
+        sg.stim_batch_sample(plan, seeds, None, [m.data_ptr() if m is not None else 0 for m, _ in outs],
+                             [d.data_ptr() if d is not None else 0 for _, d in outs], stream.cuda_stream)
+
+    res = {}
+    for name, fn in (("plain", plain_step), ("batched", batch_step)):
+        for _ in range(max(args.warmup, 1)):
+            fn()
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(args.steps):
+            fn()
+        e1.record(stream)
+        torch.cuda.synchronize()
+        res[name] = e0.elapsed_time(e1) / args.steps
+    line = {
+        "metric": METRIC, "value": gate_shots / (res["batched"] / 1000.0), "unit": "shot-gates/s",
+        "n_gpus": 1, "steps": args.steps, "warmup": args.warmup, "ms_per_step": res["batched"],
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "u64", "data": "synthetic",
+        "config": {"workload": "64 circuits: 32 rotated surface codes d in 3..31, rounds d..2d, p log-uniform "
+                               "[1e-4, 1e-2]; 32 random Clifford n in [50, 2000], depth [100, 1000]; shots "
+                               "log-uniform [1e3, 1e6] (seeded)", "total_shots": sum(shots),
+                   "tile": sg.stim_batch_info(plan)},
+        "plain": {"value": gate_shots / (res["plain"] / 1000.0), "unit": "shot-gates/s",
+                  "ms_per_step": res["plain"], "launches_per_step": 2 * len(cs)},
+        "shots_per_s": sum(shots) / (res["batched"] / 1000.0),
+        "compile_s": compile_s, "reference_samples_s": ref_s,
+    }
+    print(json.dumps(line), flush=True)
+    sg.stim_batch_free(plan)
+
+
 def main():
     args = parse_args()
+    if args.workload == "batch":
+        run_batch_workload(args)
+        return
     wl = dict(WORKLOADS[args.workload])
     if args.shots:
         wl["shots"] = args.shots
@@ -320,6 +395,41 @@ def main():
     total_shots = shots * args.steps * world
     value = total_shots * gate_targets / sec
 
+    # ---- batched: the same shots, several batches per persistent launch ----
+    batched = None
+    B = args.batch_per_launch
+    if B > 0 and args.steps % B == 0:
+        plan = sg.stim_batch_create([circ.handle] * B, [shots] * B, None, stream.cuda_stream)
+        dets_b = [torch.empty((D, nwords), dtype=torch.int64, device="cuda") for _ in range(B)]
+
+        def bstep(j):
+            offs = [shard_offset(rank, world, j * B + i, shots) for i in range(B)]
+            sg.stim_batch_sample(plan, [2021] * B, offs, None, [t.data_ptr() for t in dets_b], stream.cuda_stream)
+
+        for j in range(max(1, args.warmup // B + 1)):
+            bstep(j)
+        torch.cuda.synchronize()
+        if dist:
+            dist.barrier()
+        b0 = torch.cuda.Event(enable_timing=True)
+        b1 = torch.cuda.Event(enable_timing=True)
+        b0.record(stream)
+        for j in range(args.steps // B):
+            bstep(args.warmup // B + 1 + j)
+        b1.record(stream)
+        torch.cuda.synchronize()
+        bms = b0.elapsed_time(b1)
+        if dist:
+            t = torch.tensor([bms], device="cuda")
+            dist.all_reduce(t, op=dist.ReduceOp.MAX)
+            bms = float(t.item())
+        binfo = sg.stim_batch_info(plan)
+        batched = {"value": total_shots * gate_targets / (bms / 1000.0), "unit": "shot-gates/s",
+                   "ms_per_step": bms / args.steps, "batches_per_launch": B,
+                   "launches": args.steps // B, "tile": binfo}
+        sg.stim_batch_free(plan)
+        del dets_b
+
     # ---- end to end: same steps through the public API with host output ----
     host_det = torch.empty((D, nwords), dtype=torch.int64, pin_memory=True)
     e2e_steps = max(1, min(args.steps, 16))
@@ -398,6 +508,7 @@ def main():
             "kernel": "frame", "peak_source": peak_src,
             "algorithmic_bytes_per_launch": frame_bytes,
         },
+        "batched": batched,
         "e2e": {"value": e2e_value, "unit": "shot-gates/s", "h2d_bytes_per_step": 0,
                 "d2h_bytes_per_step": D * nwords * 8, "steps": e2e_steps},
         "gpu_launches": int(f_launch + d_launch),

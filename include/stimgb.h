@@ -155,6 +155,43 @@ int stim_frame_sample_ex(stim_circuit *c, uint64_t num_shots, uint64_t seed,
                          int flags, const stim_tile_hint *hint, void *stream);
 
 /*
+ * Batched sampling: many compiled circuits in one persistent launch.
+ *
+ * stim_batch_create plans the work of k circuits sampling num_shots[i] shots
+ * each: every circuit gets its reference sample (computed if missing) and its
+ * frame program; the (circuit, 64-shot-word tile) work items are ordered most
+ * expensive circuit first; one persistent kernel (clusters of CTAs when a
+ * circuit's qubits need them) pulls items from an atomic counter, followed
+ * by one batched detector kernel. hint may fix words_per_cta / threads /
+ * cluster_size; otherwise the first stim_batch_sample times candidate tile
+ * shapes on a prefix of the work list and keeps the fastest (remembered per
+ * batch shape for the process, and in the file named by the environment
+ * variable STIMGB_TUNE_CACHE if set). Errors: STIM_E_INVALID_ARG,
+ * STIM_E_UNSUPPORTED (a circuit too wide even for 8-CTA clusters), STIM_E_OOM,
+ * STIM_E_CUDA, STIM_E_TIMEOUT.
+ *
+ * stim_batch_sample runs the plan on `stream`: circuit i samples its
+ * num_shots[i] shots with global shot indices shot_offsets[i] + 0.. (offsets
+ * may be NULL = all 0; multiples of 64) under seeds[i]. meas_out[i] and
+ * det_out[i] are device memory in MEAS_MAJOR layout (M or D rows of
+ * ceil(num_shots[i]/64) words); either array or entry may be NULL. Results
+ * equal stim_frame_sample_ex bit for bit. The work is captured in a CUDA
+ * graph on the first call for a given set of non-NULL outputs and replayed
+ * afterwards; a call waits for the plan's previous launch before reusing its
+ * pinned descriptor buffer.
+ */
+typedef struct stim_batch stim_batch;
+
+int stim_batch_create(stim_circuit *const *circuits, const uint64_t *num_shots, size_t k,
+                      const stim_tile_hint *hint, void *stream, stim_batch **out);
+int stim_batch_sample(stim_batch *b, const uint64_t *seeds, const uint64_t *shot_offsets,
+                      uint64_t *const *meas_out, uint64_t *const *det_out, void *stream);
+/* Tile shape chosen for the plan and its size (any pointer may be NULL). */
+int stim_batch_info(const stim_batch *b, uint32_t *words_per_tile, uint32_t *threads,
+                    uint32_t *cluster_size, uint32_t *ctas, uint64_t *work_items);
+void stim_batch_free(stim_batch *b);
+
+/*
  * stim_frame_sample_noalloc -- detection events without allocating device
  * memory. The paper has no counterpart; this is an interface addition.
  *

@@ -30,7 +30,8 @@ __all__ = [
     "STIM_MEAS_MAJOR", "STIM_SHOT_MAJOR", "STIM_DEVICE", "STIM_HOST", "STIM_RECOMPUTE",
     "StimError", "library", "library_path", "stim_compile", "stim_info_get", "stim_free",
     "stim_last_error", "stim_reference_sample", "stim_frame_sample", "stim_frame_sample_ex",
-    "Circuit", "EXPORTED_SYMBOLS", "stim_frame_sample_noalloc", "stim_profile", "stim_profile_read", "KERNEL_NAMES",
+    "Circuit", "EXPORTED_SYMBOLS", "stim_frame_sample_noalloc", "stim_batch_create", "stim_batch_sample",
+    "stim_batch_info", "stim_batch_free", "Batch", "stim_profile", "stim_profile_read", "KERNEL_NAMES",
 ]
 
 STIM_OK = 0
@@ -91,6 +92,14 @@ _SIGNATURES = {
     "stim_frame_sample_ex": (ctypes.c_int, [_VP, _U64, _U64, _U64, _VP, _VP, ctypes.c_int,
                                             ctypes.POINTER(StimTileHint), _VP]),
     "stim_frame_sample_noalloc": (ctypes.c_int, [_VP, _U64, _U64, _U64, _VP, _VP]),
+    "stim_batch_create": (ctypes.c_int, [ctypes.POINTER(_VP), ctypes.POINTER(_U64), ctypes.c_size_t,
+                                         ctypes.POINTER(StimTileHint), _VP, ctypes.POINTER(_VP)]),
+    "stim_batch_sample": (ctypes.c_int, [_VP, ctypes.POINTER(_U64), ctypes.POINTER(_U64),
+                                         ctypes.POINTER(_VP), ctypes.POINTER(_VP), _VP]),
+    "stim_batch_info": (ctypes.c_int, [_VP, ctypes.POINTER(ctypes.c_uint32), ctypes.POINTER(ctypes.c_uint32),
+                                       ctypes.POINTER(ctypes.c_uint32), ctypes.POINTER(ctypes.c_uint32),
+                                       ctypes.POINTER(_U64)]),
+    "stim_batch_free": (None, [_VP]),
     "stim_profile": (ctypes.c_int, [ctypes.c_int]),
     "stim_profile_read": (ctypes.c_int, [ctypes.POINTER(StimKernelStat), ctypes.c_int]),
 }
@@ -180,6 +189,46 @@ def stim_frame_sample_noalloc(handle: int, num_shots: int, seed: int, shot_offse
                                                det_out or None, stream or None))
 
 
+def _hint(hint):
+    if hint is None:
+        return None
+    hint = tuple(hint) + (0,) * (4 - len(hint))
+    return ctypes.byref(StimTileHint(*(int(v) for v in hint[:4])))
+
+
+def stim_batch_create(handles, num_shots, hint=None, stream: int = 0) -> int:
+    """Plan one persistent launch over circuits `handles` sampling num_shots[i] each."""
+    k = len(handles)
+    hs = (_VP * k)(*handles)
+    ns = (_U64 * k)(*[int(x) for x in num_shots])
+    out = _VP()
+    _check(library().stim_batch_create(hs, ns, k, _hint(hint), stream or None, ctypes.byref(out)))
+    return out.value
+
+
+def stim_batch_sample(plan: int, seeds, shot_offsets=None, meas_out=None, det_out=None, stream: int = 0) -> None:
+    k = len(seeds)
+    sd = (_U64 * k)(*[int(x) & (2**64 - 1) for x in seeds])
+    off = (_U64 * k)(*[int(x) for x in shot_offsets]) if shot_offsets is not None else None
+    mo = (_VP * k)(*[p or None for p in meas_out]) if meas_out is not None else None
+    do = (_VP * k)(*[p or None for p in det_out]) if det_out is not None else None
+    _check(library().stim_batch_sample(plan, sd, off, mo, do, stream or None))
+
+
+def stim_batch_info(plan: int) -> dict:
+    w, t, c, ctas = (ctypes.c_uint32() for _ in range(4))
+    items = _U64()
+    _check(library().stim_batch_info(plan, ctypes.byref(w), ctypes.byref(t), ctypes.byref(c), ctypes.byref(ctas),
+                                     ctypes.byref(items)))
+    return dict(words_per_tile=w.value, threads=t.value, cluster_size=c.value, ctas=ctas.value,
+                work_items=items.value)
+
+
+def stim_batch_free(plan: int) -> None:
+    if plan:
+        library().stim_batch_free(plan)
+
+
 def stim_profile(enable: bool) -> None:
     """Start (clearing statistics) or stop per-kernel event timing."""
     _check(library().stim_profile(1 if enable else 0))
@@ -266,3 +315,46 @@ class Circuit:
                              ma.ctypes.data if ma is not None and ma.size else 0,
                              da.ctypes.data if da is not None and da.size else 0, flags, hint, 0)
         return ma, da
+
+
+class Batch:
+    """A persistent batched launch over several Circuit objects (device
+    MEAS_MAJOR outputs as int64 tensors)."""
+
+    def __init__(self, circuits, num_shots, hint=None, stream=None):
+        import torch
+        self.circuits = list(circuits)
+        self.num_shots = [int(x) for x in num_shots]
+        s = stream if stream is not None else torch.cuda.current_stream()
+        self.plan = stim_batch_create([c.handle for c in self.circuits], self.num_shots, hint, s.cuda_stream)
+
+    def info(self):
+        return stim_batch_info(self.plan)
+
+    def sample(self, seeds, shot_offsets=None, meas=True, dets=True, stream=None, out=None):
+        import torch
+        s = stream if stream is not None else torch.cuda.current_stream()
+        if out is None:
+            out = []
+            for c, S in zip(self.circuits, self.num_shots):
+                w = _words(S)
+                m = torch.empty((c.num_measurements, w), dtype=torch.int64, device="cuda") \
+                    if meas and c.num_measurements else None
+                d = torch.empty((c.num_detectors, w), dtype=torch.int64, device="cuda") \
+                    if dets and c.num_detectors else None
+                out.append((m, d))
+        stim_batch_sample(self.plan, seeds, shot_offsets,
+                          [m.data_ptr() if m is not None else 0 for m, _ in out],
+                          [d.data_ptr() if d is not None else 0 for _, d in out], s.cuda_stream)
+        return out
+
+    def close(self):
+        if getattr(self, "plan", None):
+            stim_batch_free(self.plan)
+            self.plan = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

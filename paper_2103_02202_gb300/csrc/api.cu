@@ -305,6 +305,20 @@ bool valid_flags(int flags, int allowed) { return (flags & ~allowed) == 0; }
 
 }  // namespace
 
+// Used by the batched launch (batch.cu).
+int stimgb_frame_program(stim_circuit *c, int C, const DevFrameProgram **out) {
+    int r = ensure_device(c);
+    if (r != STIM_OK) return r;
+    return frame_program(c, C, out);
+}
+
+int stimgb_ensure_reference(stim_circuit *c, cudaStream_t st) {
+    int r = ensure_device(c);
+    if (r != STIM_OK) return r;
+    if (!c->ref_valid) return compute_reference(c, st);
+    return STIM_OK;
+}
+
 namespace stimgb {
 int report_error(int code, const std::string &msg) { return fail(code, msg); }
 }  // namespace stimgb
@@ -475,7 +489,7 @@ int stim_frame_sample_ex(stim_circuit *c, uint64_t num_shots, uint64_t seed, uin
         a.gframe = gframe;
         a.gstride = gstride;
         a.status = c->d_status;
-        philox_key_schedule(seed, a.rk0, a.rk1);
+        a.seed = seed;
         ProfScope ps(STIM_KERNEL_FRAME, st);
         STIMGB_CK(launch_frame(a, W, C, gmem, (uint32_t)grid, threads, gmem ? 0 : (size_t)fp->Q * W * 16, st),
                   "frame kernel");

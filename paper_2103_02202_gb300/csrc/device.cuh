@@ -13,16 +13,20 @@ namespace stimgb {
 // -> 64-bit multiplies; the key follows the Weyl sequence
 // (k0, k1) += (0x9E3779B9, 0xBB67AE85) after every round.
 // ---------------------------------------------------------------------------
-// Philox4x32-10 with a precomputed key schedule: rk0[r] = k0 + r * 0x9E3779B9,
-// rk1[r] = k1 + r * 0xBB67AE85 (the kernels receive it as launch parameters,
-// so the key XORs read the constant bank and no key additions remain).
-__device__ __forceinline__ uint4 philox_sched(uint4 c, const uint32_t *rk0, const uint32_t *rk1) {
+// The key of round r is (k0 + r * 0x9E3779B9, k1 + r * 0xBB67AE85): each is
+// one add of a compile-time constant to the seed words, off the dependency
+// chain of the rounds.
+struct Key {
+    uint32_t k0, k1;
+};
+
+__device__ __forceinline__ uint4 philox_sched(uint4 c, Key k) {
 #pragma unroll
     for (int r = 0; r < 10; r++) {
         const uint64_t p0 = (uint64_t)0xD2511F53u * c.x;
         const uint64_t p1 = (uint64_t)0xCD9E8D57u * c.z;
-        c = make_uint4((uint32_t)(p1 >> 32) ^ c.y ^ rk0[r], (uint32_t)p1,
-                       (uint32_t)(p0 >> 32) ^ c.w ^ rk1[r], (uint32_t)p0);
+        c = make_uint4((uint32_t)(p1 >> 32) ^ c.y ^ (k.k0 + (uint32_t)r * 0x9E3779B9u), (uint32_t)p1,
+                       (uint32_t)(p0 >> 32) ^ c.w ^ (k.k1 + (uint32_t)r * 0xBB67AE85u), (uint32_t)p0);
     }
     return c;
 }
@@ -34,9 +38,8 @@ constexpr uint32_t kTagInit = 2u << 28;
 
 // 64 fair bits for a collapse (tag COLLAPSE) or the initial frame (tag INIT):
 // draws 0 and 1 of the keyed stream.
-__device__ __forceinline__ uint64_t half_mask(const uint32_t *rk0, const uint32_t *rk1, uint32_t tag_instr,
-                                              uint32_t slot, uint32_t word) {
-    const uint4 r = philox_sched(make_uint4(0u, slot, tag_instr, word), rk0, rk1);
+__device__ __forceinline__ uint64_t half_mask(Key key, uint32_t tag_instr, uint32_t slot, uint32_t word) {
+    const uint4 r = philox_sched(make_uint4(0u, slot, tag_instr, word), key);
     return (uint64_t)r.x | ((uint64_t)r.y << 32);
 }
 
@@ -44,15 +47,14 @@ __device__ __forceinline__ uint64_t half_mask(const uint32_t *rk0, const uint32_
 struct DrawStream {
     uint4 blk;
     uint32_t j, slot, ti, word;
-    const uint32_t *rk0, *rk1;
+    Key key;
 
-    __device__ __forceinline__ DrawStream(const uint32_t *rk0_, const uint32_t *rk1_, uint32_t ti_,
-                                          uint32_t slot_, uint32_t word_, uint4 blk0)
-        : blk(blk0), j(0), slot(slot_), ti(ti_), word(word_), rk0(rk0_), rk1(rk1_) {}
+    __device__ __forceinline__ DrawStream(Key key_, uint32_t ti_, uint32_t slot_, uint32_t word_, uint4 blk0)
+        : blk(blk0), j(0), slot(slot_), ti(ti_), word(word_), key(key_) {}
 
     __device__ __forceinline__ uint32_t next() {
         const uint32_t lane = j & 3u;
-        if (lane == 0u && j != 0u) blk = philox_sched(make_uint4(j >> 2, slot, ti, word), rk0, rk1);
+        if (lane == 0u && j != 0u) blk = philox_sched(make_uint4(j >> 2, slot, ti, word), key);
         j++;
         return lane == 0u ? blk.x : lane == 1u ? blk.y : lane == 2u ? blk.z : blk.w;
     }
@@ -65,10 +67,10 @@ struct DrawStream {
 // more draw v per error on the Pauli 1 + floor(3v / 2^32) (1 X, 2 Y, 3 Z);
 // DEPOLARIZE2 on c = 1 + floor(15v / 2^32), first-qubit Pauli c >> 2, second c & 3.
 template <uint32_t OP>
-__device__ __forceinline__ void noise_masks_slow(const uint64_t *__restrict__ G, const uint32_t *rk0,
-                                              const uint32_t *rk1, uint32_t instr, uint32_t slot, uint32_t word,
-                                              uint4 blk0, uint64_t &xa, uint64_t &za, uint64_t &xb, uint64_t &zb) {
-    DrawStream ds(rk0, rk1, kTagNoise | instr, slot, word, blk0);
+__device__ __forceinline__ void noise_masks_slow(const uint64_t *__restrict__ G, Key key, uint32_t instr,
+                                                 uint32_t slot, uint32_t word, uint4 blk0, uint64_t &xa,
+                                                 uint64_t &za, uint64_t &xb, uint64_t &zb) {
+    DrawStream ds(key, kTagNoise | instr, slot, word, blk0);
     int pos = -1;
     xa = za = xb = zb = 0;
     for (;;) {
@@ -107,12 +109,12 @@ __device__ __forceinline__ void noise_masks_slow(const uint64_t *__restrict__ G,
 // alone decides the common case: no error in the word exactly when
 // u0 >= G[63]. Only then is the general procedure run (out of line).
 template <uint32_t OP>
-__device__ __forceinline__ bool noise_masks(const uint64_t *__restrict__ G, const uint32_t *rk0, const uint32_t *rk1,
-                                            uint32_t instr, uint32_t slot, uint32_t word, uint64_t &xa,
-                                            uint64_t &za, uint64_t &xb, uint64_t &zb) {
-    const uint4 blk0 = philox_sched(make_uint4(0u, slot, kTagNoise | instr, word), rk0, rk1);
+__device__ __forceinline__ bool noise_masks(const uint64_t *__restrict__ G, Key key, uint32_t instr, uint32_t slot,
+                                            uint32_t word, uint64_t &xa, uint64_t &za, uint64_t &xb,
+                                            uint64_t &zb) {
+    const uint4 blk0 = philox_sched(make_uint4(0u, slot, kTagNoise | instr, word), key);
     if ((uint64_t)blk0.x >= __ldg(G + 63)) return false;
-    noise_masks_slow<OP>(G, rk0, rk1, instr, slot, word, blk0, xa, za, xb, zb);
+    noise_masks_slow<OP>(G, key, instr, slot, word, blk0, xa, za, xb, zb);
     return true;
 }
 

@@ -27,10 +27,8 @@ struct FrameArgs {
     uint64_t *gframe;          // global frame [2][n][gstride] when the tile is not in smem
     uint64_t gstride;
     int *status;
-    uint32_t rk0[10], rk1[10]; // Philox key schedule of the seed
+    uint64_t seed;             // Philox key = (seed lo, seed hi)
 };
-
-void philox_key_schedule(uint64_t seed, uint32_t rk0[10], uint32_t rk1[10]);
 
 // tiles = word tiles (clusters); the grid has tiles * C CTAs.
 cudaError_t launch_frame(const FrameArgs &a, int W, int C, bool gmem, uint32_t tiles, uint32_t threads, size_t smem,

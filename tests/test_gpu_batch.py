@@ -1,0 +1,93 @@
+"""Batched persistent launch: every circuit of a heterogeneous batch returns
+exactly what the single-circuit entry point returns for the same shots."""
+import numpy as np
+import pytest
+
+import oracle
+import paper_2103_02202_gb300 as sg
+from paper_2103_02202_gb300 import workloads as W
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+
+
+@pytest.fixture(scope="module", autouse=True)
+def gpu():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2103_02202_gb300 import build
+    build.build()
+    yield
+
+
+TEXTS = [
+    W.surface_code_memory(3, 3, 1e-3),
+    W.surface_code_memory(5, 7, 5e-3),
+    W.random_clifford(120, 40, 1),
+    W.repetition_code(5, 20, 0.02),
+    W.random_clifford(300, 25, 2, p=0.01),
+    W.surface_code_memory(7, 3, 0.02),
+]
+SHOTS = [1024, 777, 4096, 65, 2000, 1]
+
+
+def plain(c, shots, seed, offset=0):
+    m, d = c.sample(shots, seed, shot_offset=offset)
+    return m, d
+
+
+@pytest.mark.parametrize("hint", [None, (1, 256, 0, 1), (2, 512, 0, 1), (4, 256, 0, 2), (1, 128, 0, 4)])
+def test_batch_equals_plain(hint):
+    cs = [sg.Circuit(t) for t in TEXTS]
+    b = sg.Batch(cs, SHOTS, hint=hint)
+    seeds = [11 * i + 3 for i in range(len(cs))]
+    offs = [64 * i for i in range(len(cs))]
+    out = b.sample(seeds, offs)
+    torch.cuda.synchronize()
+    for c, S, sd, off, (m, d) in zip(cs, SHOTS, seeds, offs, out):
+        pm, pd = plain(c, S, sd, off)
+        torch.cuda.synchronize()
+        if m is not None:
+            assert torch.equal(m, pm)
+        if d is not None:
+            assert torch.equal(d, pd)
+    info = b.info()
+    assert info["work_items"] >= len(cs)
+    b.close()
+
+
+def test_batch_replay_new_seeds_and_outputs():
+    cs = [sg.Circuit(t) for t in TEXTS[:4]]
+    b = sg.Batch(cs, SHOTS[:4])
+    for rep in range(3):
+        seeds = [rep * 1000 + i for i in range(4)]
+        out = b.sample(seeds, dets=(rep != 1), meas=(rep != 2))
+        torch.cuda.synchronize()
+        for c, S, sd, (m, d) in zip(cs, SHOTS[:4], seeds, out):
+            pm, pd = plain(c, S, sd)
+            torch.cuda.synchronize()
+            if m is not None:
+                assert torch.equal(m, pm)
+            if d is not None:
+                assert torch.equal(d, pd)
+    b.close()
+
+
+def test_batch_matches_oracle_on_sampled_shots():
+    text = W.surface_code_memory(5, 5, 0.01)
+    c = sg.Circuit(text)
+    b = sg.Batch([c, c], [3000, 3000])
+    (m0, d0), (m1, d1) = b.sample([5, 5], [0, 3008])
+    torch.cuda.synchronize()
+    o = oracle.Circuit(text)
+    pick = np.array([0, 1, 63, 64, 2999])
+    for m, d, off in ((m0, d0, 0), (m1, d1, 3008)):
+        cols = torch.as_tensor(pick // 64, device="cuda")
+        bits = torch.as_tensor(pick % 64, device="cuda")
+        gm = ((m[:, cols] >> bits) & 1).cpu().numpy().astype(np.uint8).T
+        gd = ((d[:, cols] >> bits) & 1).cpu().numpy().astype(np.uint8).T
+        om, od = o.sample(pick, 5, shot_offset=off, threads=4)
+        np.testing.assert_array_equal(gm, om)
+        np.testing.assert_array_equal(gd, od)
+    b.close()
