@@ -51,7 +51,8 @@ def parse_args():
     ap.add_argument("--steps", type=int, default=64)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
-    ap.add_argument("--workload", choices=sorted(WORKLOADS) + ["batch"], default="surface_d100")
+    ap.add_argument("--workload", choices=sorted(WORKLOADS) + ["batch", "serve"], default="surface_d100")
+    ap.add_argument("--requests", type=int, default=10000, help="serve workload: number of requests")
     ap.add_argument("--batch-per-launch", type=int, default=8,
                     help="batches of the workload per persistent batched launch (0 = skip)")
     ap.add_argument("--cpu-shots", type=int, default=0, help="oracle shots per CPU sample (0 = auto)")
@@ -306,10 +307,103 @@ def run_batch_workload(args):
     sg.stim_batch_free(plan)
 
 
+def run_serve_workload(args):
+    """Poisson stream of sampling requests through the continuous-batching
+    server (150 GB budget); rate set to 80% of the measured capacity."""
+    import threading
+    import torch
+    import paper_2103_02202_gb300 as sg
+    from paper_2103_02202_gb300 import build as sgbuild
+    from paper_2103_02202_gb300 import workloads as W
+    torch.cuda.set_device(0)
+    sgbuild.build()
+    catalogue, _ = W.serve_requests(count=1)
+    t0 = time.perf_counter()
+    cs = [sg.Circuit(W.catalogue_text(e)) for e in catalogue]
+    compile_s = time.perf_counter() - t0
+    t0 = time.perf_counter()
+    for c in cs:
+        c.reference()
+    torch.cuda.synchronize()
+    ref_s = time.perf_counter() - t0
+    srv = sg.Server(150 << 30, streams=16)
+
+    def outputs(c):
+        return sg.STIM_OUT_DET if c.num_detectors else sg.STIM_OUT_MEAS
+
+    # capacity: a burst of requests drawn like the stream, all submitted at once
+    _, probe = W.serve_requests(seed=99, count=min(600, args.requests))
+    for r in probe[:50]:
+        rid = srv.submit(cs[r["circuit"]], r["shots"], r["seed"], 0, outputs(cs[r["circuit"]]))
+        srv.wait(rid, 600)
+        srv.release(rid)
+    t0 = time.perf_counter()
+    ids = [srv.submit(cs[r["circuit"]], r["shots"], r["seed"], 0, outputs(cs[r["circuit"]])) for r in probe]
+    for rid in ids:
+        srv.wait(rid, 600)
+        srv.release(rid)
+    burst_s = time.perf_counter() - t0
+    capacity = len(probe) / burst_s
+    rate = 0.8 * capacity
+    srv.close()
+
+    srv = sg.Server(150 << 30, streams=16)
+    _, reqs = W.serve_requests(seed=5, count=args.requests, rate_hz=rate)
+    done_ids = []
+    lock = threading.Lock()
+
+    def feeder():
+        start = time.perf_counter()
+        for r in reqs:
+            delay = r["t"] - (time.perf_counter() - start)
+            if delay > 0:
+                time.sleep(delay)
+            c = cs[r["circuit"]]
+            rid = srv.submit(c, r["shots"], r["seed"], 0, outputs(c))
+            with lock:
+                done_ids.append(rid)
+
+    th = threading.Thread(target=feeder)
+    t0 = time.perf_counter()
+    th.start()
+    k = 0
+    while k < len(reqs):
+        with lock:
+            avail = len(done_ids)
+        if k >= avail:
+            time.sleep(0.0005)
+            continue
+        rid = done_ids[k]
+        srv.wait(rid, 600)
+        srv.release(rid)
+        k += 1
+    th.join()
+    wall = time.perf_counter() - t0
+    st = srv.stats()
+    srv.close()
+    line = {
+        "metric": METRIC, "value": st["gate_shots"] / st["wall_s"], "unit": "shot-gates/s",
+        "n_gpus": 1, "steps": 1, "warmup": 0, "ms_per_step": 1000 * wall, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "u64", "data": "synthetic",
+        "config": {"workload": "serving: %d Poisson requests over %d resident circuits (rotated surface codes "
+                               "d=3..51 x p in {1e-4,1e-3,1e-2}, 8 random Clifford), shots log-uniform "
+                               "[1e3, 1e5], HBM budget 150 GB, 16 streams" % (len(reqs), len(cs)),
+                   "arrival_rate_hz": rate, "capacity_hz": capacity},
+        "shots_per_s": st["shots"] / st["wall_s"], "requests": st["completed"], "failed": st["failed"],
+        "p50_latency_s": st["p50_latency_s"], "p99_latency_s": st["p99_latency_s"],
+        "max_latency_s": st["max_latency_s"], "peak_hbm_bytes": st["peak_bytes_in_use"],
+        "compile_s": compile_s, "reference_samples_s": ref_s,
+    }
+    print(json.dumps(line), flush=True)
+
+
 def main():
     args = parse_args()
     if args.workload == "batch":
         run_batch_workload(args)
+        return
+    if args.workload == "serve":
+        run_serve_workload(args)
         return
     wl = dict(WORKLOADS[args.workload])
     if args.shots:

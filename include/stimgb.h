@@ -192,6 +192,74 @@ int stim_batch_info(const stim_batch *b, uint32_t *words_per_tile, uint32_t *thr
 void stim_batch_free(stim_batch *b);
 
 /*
+ * Sampling server: continuous batching under an HBM budget.
+ *
+ * stim_server_create reserves hbm_budget_bytes of device memory on the
+ * current device (the arena all request buffers come from) and starts one
+ * dispatcher thread with `streams` CUDA streams (0 = 8). Requests queue in
+ * arrival order; whenever a stream is free and the arena can hold the next
+ * request's outputs and scratch, that request is admitted and launched, so
+ * requests that arrive while others run start at once and overlap on the GPU.
+ * Circuits stay compiled and their reference samples resident across
+ * requests (a circuit without a reference sample gets one when its first
+ * request is admitted; call stim_reference_sample beforehand to keep that out
+ * of request latency). The caller keeps circuit handles alive until their
+ * requests are released and must not sample them directly meanwhile.
+ *
+ * stim_server_submit: num_shots shots with global indices shot_offset + 0..
+ *   (shot_offset a multiple of 64) under seed; outputs = STIM_OUT_MEAS and/or
+ *   STIM_OUT_DET. Results are bit-identical to stim_frame_sample_ex.
+ * stim_server_poll: STIM_OK when done, STIM_E_BUSY while queued or running,
+ *   the request's error code if it failed; fills *out.
+ * stim_server_wait: blocks up to timeout_ns; STIM_E_TIMEOUT if still running.
+ * Result buffers (device, MEAS_MAJOR, words_per_row words per row) live in
+ * the arena until stim_server_release(id); releasing frees them for queued
+ * requests. stim_server_cancel removes a request that has not started.
+ * stim_server_stats reports completed requests, latency percentiles (from
+ * submission to completion) and arena use. stim_server_destroy finishes the
+ * queued work, then frees everything.
+ */
+#define STIM_OUT_MEAS 0x1
+#define STIM_OUT_DET  0x2
+
+typedef struct stim_server stim_server;
+typedef uint64_t stim_request_id;
+
+typedef struct {
+    int status;               /* STIM_OK, STIM_E_BUSY (not finished) or the failure code */
+    uint64_t num_shots;
+    uint64_t words_per_row;   /* ceil(num_shots / 64) */
+    uint64_t *meas;           /* M rows, device memory (NULL if not requested) */
+    uint64_t *det;            /* D rows, device memory (NULL if not requested) */
+    double queue_s;           /* submission to admission */
+    double latency_s;         /* submission to completion */
+} stim_result;
+
+typedef struct {
+    uint64_t completed, failed, queued, running;
+    uint64_t shots;           /* shots of completed requests */
+    double gate_shots;        /* shots x gate targets of completed requests */
+    size_t budget_bytes, bytes_in_use, peak_bytes_in_use;
+    double p50_latency_s, p99_latency_s, max_latency_s;
+    double wall_s;            /* first submission to last completion */
+} stim_server_statistics;
+
+int stim_server_create(size_t hbm_budget_bytes, int streams, stim_server **out);
+int stim_server_submit(stim_server *s, stim_circuit *c, uint64_t num_shots, uint64_t seed,
+                       uint64_t shot_offset, int outputs, stim_request_id *id);
+int stim_server_poll(stim_server *s, stim_request_id id, stim_result *out);
+int stim_server_wait(stim_server *s, stim_request_id id, uint64_t timeout_ns, stim_result *out);
+int stim_server_cancel(stim_server *s, stim_request_id id);
+int stim_server_release(stim_server *s, stim_request_id id);
+/* Copies a finished request's outputs into caller buffers (either may be
+ * NULL): flags STIM_HOST or STIM_DEVICE; MEAS_MAJOR layout. Host copies return
+ * when done; device copies are asynchronous on `stream`. */
+int stim_server_copy_result(stim_server *s, stim_request_id id, uint64_t *meas_dst, uint64_t *det_dst,
+                            int flags, void *stream);
+int stim_server_stats(stim_server *s, stim_server_statistics *out);
+void stim_server_destroy(stim_server *s);
+
+/*
  * stim_frame_sample_noalloc -- detection events without allocating device
  * memory. The paper has no counterpart; this is an interface addition.
  *

@@ -31,7 +31,7 @@ __all__ = [
     "StimError", "library", "library_path", "stim_compile", "stim_info_get", "stim_free",
     "stim_last_error", "stim_reference_sample", "stim_frame_sample", "stim_frame_sample_ex",
     "Circuit", "EXPORTED_SYMBOLS", "stim_frame_sample_noalloc", "stim_batch_create", "stim_batch_sample",
-    "stim_batch_info", "stim_batch_free", "Batch", "stim_profile", "stim_profile_read", "KERNEL_NAMES",
+    "stim_batch_info", "stim_batch_free", "Batch", "Server", "STIM_OUT_MEAS", "STIM_OUT_DET", "stim_profile", "stim_profile_read", "KERNEL_NAMES",
 ]
 
 STIM_OK = 0
@@ -79,6 +79,24 @@ class StimKernelStat(ctypes.Structure):
 
 KERNEL_NAMES = ("frame", "detectors", "transpose", "tableau")
 
+class StimResult(ctypes.Structure):
+    _fields_ = [("status", ctypes.c_int), ("num_shots", ctypes.c_uint64), ("words_per_row", ctypes.c_uint64),
+                ("meas", ctypes.c_void_p), ("det", ctypes.c_void_p), ("queue_s", ctypes.c_double),
+                ("latency_s", ctypes.c_double)]
+
+
+class StimServerStatistics(ctypes.Structure):
+    _fields_ = [("completed", ctypes.c_uint64), ("failed", ctypes.c_uint64), ("queued", ctypes.c_uint64),
+                ("running", ctypes.c_uint64), ("shots", ctypes.c_uint64), ("gate_shots", ctypes.c_double),
+                ("budget_bytes", ctypes.c_size_t), ("bytes_in_use", ctypes.c_size_t),
+                ("peak_bytes_in_use", ctypes.c_size_t), ("p50_latency_s", ctypes.c_double),
+                ("p99_latency_s", ctypes.c_double), ("max_latency_s", ctypes.c_double),
+                ("wall_s", ctypes.c_double)]
+
+
+STIM_OUT_MEAS = 0x1
+STIM_OUT_DET = 0x2
+
 _VP = ctypes.c_void_p
 _U64 = ctypes.c_uint64
 # name -> (restype, argtypes); every entry is declared in include/stimgb.h
@@ -100,6 +118,15 @@ _SIGNATURES = {
                                        ctypes.POINTER(ctypes.c_uint32), ctypes.POINTER(ctypes.c_uint32),
                                        ctypes.POINTER(_U64)]),
     "stim_batch_free": (None, [_VP]),
+    "stim_server_create": (ctypes.c_int, [ctypes.c_size_t, ctypes.c_int, ctypes.POINTER(_VP)]),
+    "stim_server_submit": (ctypes.c_int, [_VP, _VP, _U64, _U64, _U64, ctypes.c_int, ctypes.POINTER(_U64)]),
+    "stim_server_poll": (ctypes.c_int, [_VP, _U64, ctypes.POINTER(StimResult)]),
+    "stim_server_wait": (ctypes.c_int, [_VP, _U64, _U64, ctypes.POINTER(StimResult)]),
+    "stim_server_cancel": (ctypes.c_int, [_VP, _U64]),
+    "stim_server_release": (ctypes.c_int, [_VP, _U64]),
+    "stim_server_copy_result": (ctypes.c_int, [_VP, _U64, _VP, _VP, ctypes.c_int, _VP]),
+    "stim_server_stats": (ctypes.c_int, [_VP, ctypes.POINTER(StimServerStatistics)]),
+    "stim_server_destroy": (None, [_VP]),
     "stim_profile": (ctypes.c_int, [ctypes.c_int]),
     "stim_profile_read": (ctypes.c_int, [ctypes.POINTER(StimKernelStat), ctypes.c_int]),
 }
@@ -352,6 +379,67 @@ class Batch:
         if getattr(self, "plan", None):
             stim_batch_free(self.plan)
             self.plan = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+class Server:
+    """Continuous-batching sampling server (see include/stimgb.h)."""
+
+    def __init__(self, hbm_budget_bytes: int, streams: int = 0):
+        out = _VP()
+        _check(library().stim_server_create(int(hbm_budget_bytes), int(streams), ctypes.byref(out)))
+        self.handle = out.value
+
+    def submit(self, circuit, num_shots: int, seed: int, shot_offset: int = 0,
+               outputs: int = STIM_OUT_MEAS | STIM_OUT_DET) -> int:
+        rid = _U64()
+        _check(library().stim_server_submit(self.handle, circuit.handle, int(num_shots), int(seed) & (2**64 - 1),
+                                            int(shot_offset), int(outputs), ctypes.byref(rid)))
+        return rid.value
+
+    def poll(self, rid: int):
+        r = StimResult()
+        rc = library().stim_server_poll(self.handle, rid, ctypes.byref(r))
+        return rc, r
+
+    def wait(self, rid: int, timeout_s: float = 60.0):
+        r = StimResult()
+        rc = library().stim_server_wait(self.handle, rid, int(timeout_s * 1e9), ctypes.byref(r))
+        if rc != STIM_OK:
+            raise StimError(rc, stim_last_error())
+        return r
+
+    def fetch(self, circuit, rid: int, num_shots: int):
+        """Copy a finished request's outputs into new device int64 tensors."""
+        import torch
+        w = _words(num_shots)
+        m = torch.empty((circuit.num_measurements, w), dtype=torch.int64, device="cuda")
+        d = torch.empty((circuit.num_detectors, w), dtype=torch.int64, device="cuda")
+        s = torch.cuda.current_stream()
+        _check(library().stim_server_copy_result(self.handle, rid, m.data_ptr() if m.numel() else None,
+                                                 d.data_ptr() if d.numel() else None, STIM_DEVICE, s.cuda_stream))
+        return m, d
+
+    def cancel(self, rid: int) -> int:
+        return library().stim_server_cancel(self.handle, rid)
+
+    def release(self, rid: int) -> None:
+        _check(library().stim_server_release(self.handle, rid))
+
+    def stats(self) -> dict:
+        st = StimServerStatistics()
+        _check(library().stim_server_stats(self.handle, ctypes.byref(st)))
+        return {k: getattr(st, k) for k, _ in StimServerStatistics._fields_}
+
+    def close(self):
+        if getattr(self, "handle", None):
+            library().stim_server_destroy(self.handle)
+            self.handle = None
 
     def __del__(self):
         try:

@@ -229,12 +229,6 @@ int compute_reference(stim_circuit *c, cudaStream_t st) {
     return rc;
 }
 
-struct TileChoice {
-    int W = 1, C = 1;
-    bool gmem = false;
-    uint32_t threads = 256;
-};
-
 // Tile shape: the smallest cluster whose qubit slice fits shared memory, then
 // the widest word tile that keeps at least two CTAs per SM busy; hints override.
 int choose_tile(uint32_t n, uint64_t nwords, int sms, size_t smem_optin, const stim_tile_hint *hint,
@@ -301,6 +295,56 @@ int choose_tile(uint32_t n, uint64_t nwords, int sms, size_t smem_optin, const s
     return STIM_OK;
 }
 
+// Frame kernel (records into rec, may be null) and detector kernel (events
+// into det, may be null) for one call, with caller-provided buffers.
+int launch_sampling(stim_circuit *c, uint64_t num_shots, uint64_t seed, uint64_t shot_offset, const TileChoice &tc,
+                    uint64_t *rec, uint64_t *det, uint64_t *gframe, cudaStream_t st) {
+    const HostProgram &hp = c->hp;
+    const uint32_t n = hp.num_qubits;
+    const uint64_t D = hp.num_det;
+    const uint64_t nwords = (num_shots + 63) / 64;
+    const uint64_t last_mask = (num_shots % 64) ? ((1ull << (num_shots % 64)) - 1) : ~0ull;
+    const int W = tc.W, C = tc.C;
+    const bool gmem = tc.gmem;
+    const uint32_t threads = tc.threads;
+    const uint64_t grid = (nwords + W - 1) / W;
+    const uint64_t gstride = grid * W;
+    int r;
+    if (n > 0) {
+        const DevFrameProgram *fp = nullptr;
+        if ((r = frame_program(c, C, &fp)) != STIM_OK) return r;
+        FrameArgs a{};
+        a.prog = fp->prog;
+        a.nprog = fp->nprog;
+        a.rank_tab = fp->rank_tab;
+        a.segs = fp->segs;
+        a.ops = fp->ops;
+        a.geo = c->d_geo;
+        a.ref = c->d_ref;
+        a.n = n;
+        a.Q = fp->Q;
+        a.word0 = shot_offset / 64;
+        a.nwords = nwords;
+        a.last_mask = last_mask;
+        a.rec = hp.num_meas ? rec : nullptr;
+        a.rec_stride = nwords;
+        a.gframe = gframe;
+        a.gstride = gstride;
+        a.status = c->d_status;
+        a.seed = seed;
+        ProfScope ps(STIM_KERNEL_FRAME, st);
+        STIMGB_CK(launch_frame(a, W, C, gmem, (uint32_t)grid, threads, gmem ? 0 : (size_t)fp->Q * W * 16, st),
+                  "frame kernel");
+    }
+    if (det && D > 0) {
+        ProfScope ps(STIM_KERNEL_DETECTORS, st);
+        STIMGB_CK(launch_detectors(rec, nwords, c->d_det_ptr, c->d_det_meas, c->d_ref, D, nwords, last_mask, det,
+                                   nwords, st),
+                  "detector kernel");
+    }
+    return STIM_OK;
+}
+
 bool valid_flags(int flags, int allowed) { return (flags & ~allowed) == 0; }
 
 }  // namespace
@@ -310,6 +354,26 @@ int stimgb_frame_program(stim_circuit *c, int C, const DevFrameProgram **out) {
     int r = ensure_device(c);
     if (r != STIM_OK) return r;
     return frame_program(c, C, out);
+}
+
+int stimgb_sampling_layout(stim_circuit *c, uint64_t num_shots, TileChoice *tc, size_t *gframe_words) {
+    int r = ensure_device(c);
+    if (r != STIM_OK) return r;
+    int sms = 0, smem_optin = 0;
+    STIMGB_CK(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, c->device), "attr");
+    STIMGB_CK(cudaDeviceGetAttribute(&smem_optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, c->device), "attr");
+    const uint64_t nwords = (num_shots + 63) / 64;
+    r = choose_tile(c->hp.num_qubits, nwords, sms, (size_t)smem_optin, nullptr, tc);
+    if (r != STIM_OK) return r;
+    const uint64_t grid = (nwords + tc->W - 1) / tc->W;
+    *gframe_words = tc->gmem ? 2 * (size_t)c->hp.num_qubits * grid * tc->W : 0;
+    const DevFrameProgram *fp;
+    return frame_program(c, tc->C, &fp);
+}
+
+int stimgb_sample_into(stim_circuit *c, uint64_t num_shots, uint64_t seed, uint64_t shot_offset, const TileChoice &tc,
+                       uint64_t *rec, uint64_t *det, uint64_t *gframe, cudaStream_t st) {
+    return launch_sampling(c, num_shots, seed, shot_offset, tc, rec, det, gframe, st);
 }
 
 int stimgb_ensure_reference(stim_circuit *c, cudaStream_t st) {
@@ -468,34 +532,6 @@ int stim_frame_sample_ex(stim_circuit *c, uint64_t num_shots, uint64_t seed, uin
         gframe = c->d_gframe;
     }
 
-    if (n > 0) {
-        const DevFrameProgram *fp = nullptr;
-        if ((r = frame_program(c, C, &fp)) != STIM_OK) return r;
-        FrameArgs a{};
-        a.prog = fp->prog;
-        a.nprog = fp->nprog;
-        a.rank_tab = fp->rank_tab;
-        a.segs = fp->segs;
-        a.ops = fp->ops;
-        a.geo = c->d_geo;
-        a.ref = c->d_ref;
-        a.n = n;
-        a.Q = fp->Q;
-        a.word0 = shot_offset / 64;
-        a.nwords = nwords;
-        a.last_mask = last_mask;
-        a.rec = rec;
-        a.rec_stride = nwords;
-        a.gframe = gframe;
-        a.gstride = gstride;
-        a.status = c->d_status;
-        a.seed = seed;
-        ProfScope ps(STIM_KERNEL_FRAME, st);
-        STIMGB_CK(launch_frame(a, W, C, gmem, (uint32_t)grid, threads, gmem ? 0 : (size_t)fp->Q * W * 16, st),
-                  "frame kernel");
-    }
-
-    // ---- detectors ----
     uint64_t *det = nullptr;
     const bool det_direct = det_out && !shot_major && !host;
     if (det_out && D > 0) {
@@ -505,11 +541,8 @@ int stim_frame_sample_ex(stim_circuit *c, uint64_t num_shots, uint64_t seed, uin
             if ((r = grow(&c->d_det, &c->det_cap, D * nwords, "alloc detectors")) != STIM_OK) return r;
             det = c->d_det;
         }
-        ProfScope ps(STIM_KERNEL_DETECTORS, st);
-        STIMGB_CK(launch_detectors(rec, nwords, c->d_det_ptr, c->d_det_meas, c->d_ref, D, nwords, last_mask, det,
-                                   nwords, st),
-                  "detector kernel");
     }
+    if ((r = launch_sampling(c, num_shots, seed, shot_offset, tc, rec, det, gframe, st)) != STIM_OK) return r;
 
     // ---- output layouts ----
     auto emit = [&](uint64_t *src, uint64_t rows, uint64_t *dst) -> int {

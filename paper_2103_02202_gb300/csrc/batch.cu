@@ -287,10 +287,6 @@ size_t batch_smem(const stim_batch *b, int W, int C) {
 
 }  // namespace
 
-// Defined in api.cu.
-int stimgb_frame_program(stim_circuit *c, int C, const DevFrameProgram **out);
-int stimgb_ensure_reference(stim_circuit *c, cudaStream_t st);
-
 namespace {
 
 int fill_descs(stim_batch *b, const uint64_t *seeds, const uint64_t *offsets, uint64_t *const *meas_out,

@@ -4,6 +4,8 @@
 #include <cstddef>
 #include <cstdint>
 
+#include <cuda_runtime.h>
+
 #include "internal.h"
 
 // Device copy of a FrameProgram for one cluster size.
@@ -40,3 +42,20 @@ struct stim_circuit {
     size_t gframe_cap = 0;
     DevFrameProgram fprog[4];           // cluster sizes 1, 2, 4, 8
 };
+
+// Frame-kernel launch shape.
+struct TileChoice {
+    int W = 1, C = 1;
+    bool gmem = false;
+    uint32_t threads = 256;
+};
+
+// Library-internal entry points shared by the batched and serving paths.
+int stimgb_frame_program(stim_circuit *c, int C, const DevFrameProgram **out);
+int stimgb_ensure_reference(stim_circuit *c, cudaStream_t st);
+// Tile shape for num_shots shots and the global-frame scratch it needs (words).
+int stimgb_sampling_layout(stim_circuit *c, uint64_t num_shots, TileChoice *tc, size_t *gframe_words);
+// Frame and detector launches into caller-provided buffers (rec: M rows of
+// ceil(num_shots/64) words, required when det is given; any may be null).
+int stimgb_sample_into(stim_circuit *c, uint64_t num_shots, uint64_t seed, uint64_t shot_offset, const TileChoice &tc,
+                       uint64_t *rec, uint64_t *det, uint64_t *gframe, cudaStream_t st);
