@@ -133,6 +133,7 @@ int frame_program(stim_circuit *c, int C, const DevFrameProgram **out) {
         if ((r = upload(&d.ops, fp.ops, "upload frame program")) != STIM_OK) return r;
         d.Q = fp.Q;
         d.nprog = (uint32_t)fp.prog.size();
+        d.max_rank_ops = fp.max_rank_ops;
         d.C = C;
     }
     *out = &d;
@@ -249,7 +250,7 @@ int choose_tile(uint32_t n, uint64_t nwords, int sms, size_t smem_optin, const s
         t.C = 1;
     } else if (hC) {
         t.C = (int)hC;
-        if (slice(t.C) > smem_optin) return fail(STIM_E_INVALID_ARG, "tile hint: slice does not fit shared memory");
+        if (slice(t.C) + kTileHeaderBytes > smem_optin) return fail(STIM_E_INVALID_ARG, "tile hint: slice does not fit shared memory");
     } else {
         // smallest cluster whose slice leaves room for two CTAs per SM
         t.C = 0;
@@ -260,7 +261,7 @@ int choose_tile(uint32_t n, uint64_t nwords, int sms, size_t smem_optin, const s
             }
         if (t.C == 0)
             for (int C : {1, 2, 4, 8})
-                if (slice(C) <= smem_optin) {
+                if (slice(C) + kTileHeaderBytes <= smem_optin) {
                     t.C = C;
                     break;
                 }
@@ -271,7 +272,7 @@ int choose_tile(uint32_t n, uint64_t nwords, int sms, size_t smem_optin, const s
     }
     if (hW) {
         t.W = (int)hW;
-        if (!t.gmem && slice(t.C) * t.W > smem_optin)
+        if (!t.gmem && slice(t.C) * t.W + kTileHeaderBytes > smem_optin)
             return fail(STIM_E_INVALID_ARG, "tile hint: words_per_cta does not fit shared memory");
     } else {
         // one 64-shot word per tile: a thread's Philox chains stay independent
@@ -332,8 +333,12 @@ int launch_sampling(stim_circuit *c, uint64_t num_shots, uint64_t seed, uint64_t
         a.gstride = gstride;
         a.status = c->d_status;
         a.seed = seed;
+        int smem_optin = 0;
+        STIMGB_CK(cudaDeviceGetAttribute(&smem_optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, c->device), "attr");
+        const size_t frame_bytes = gmem ? 0 : (size_t)fp->Q * W * 16;
+        a.op_cap = stage_capacity(fp->max_rank_ops, frame_bytes, (size_t)smem_optin);
         ProfScope ps(STIM_KERNEL_FRAME, st);
-        STIMGB_CK(launch_frame(a, W, C, gmem, (uint32_t)grid, threads, gmem ? 0 : (size_t)fp->Q * W * 16, st),
+        STIMGB_CK(launch_frame(a, W, C, gmem, (uint32_t)grid, threads, tile_smem_bytes(fp->Q, W, a.op_cap, gmem), st),
                   "frame kernel");
     }
     if (det && D > 0) {

@@ -56,10 +56,10 @@ template <int W, int C>
 __global__ void __launch_bounds__(1024, 1) batch_frame_kernel(const FrameArgs *__restrict__ descs,
                                                               const BatchItem *__restrict__ items, uint32_t nitems,
                                                               uint32_t *counter) {
-    extern __shared__ __align__(16) uint64_t smem[];
+    extern __shared__ __align__(128) unsigned char smem[];
     __shared__ uint32_t s_item;
     FrameArgs *sa = reinterpret_cast<FrameArgs *>(smem);
-    uint64_t *frame = smem + kDescBytes / 8;
+    unsigned char *tile_dyn = smem + kDescBytes;
     const uint32_t rank = C > 1 ? (uint32_t)(blockIdx.x % C) : 0u;
     for (;;) {
         if (rank == 0 && threadIdx.x == 0) s_item = atomicAdd(counter, 1u);
@@ -81,7 +81,7 @@ __global__ void __launch_bounds__(1024, 1) batch_frame_kernel(const FrameArgs *_
         for (uint32_t i = threadIdx.x; i < sizeof(FrameArgs) / 4; i += blockDim.x)
             reinterpret_cast<uint32_t *>(sa)[i] = __ldg(src + i);
         __syncthreads();
-        frame_detail::run_tile<W, C, false>(*sa, frame, rank, it.tile);
+        frame_detail::run_tile<W, C, false>(*sa, tile_dyn, rank, it.tile);
         __syncthreads();
     }
 }
@@ -208,6 +208,7 @@ struct stim_batch {
     bool tuned = false;
     std::string tune_key;
     bool hinted = false;
+    uint32_t op_cap = 0;
     std::vector<uint8_t> out_sig;          // which outputs the captured graph serves
 };
 
@@ -275,14 +276,19 @@ int upload_items(stim_batch *b) {
     return STIM_OK;
 }
 
-// Shared-memory bytes and the largest slice of any circuit in the batch.
-size_t batch_smem(const stim_batch *b, int W, int C) {
+// Largest qubit slice of any circuit in the batch.
+uint32_t batch_max_slice(const stim_batch *b, int C) {
     uint32_t maxq = 1;
     for (stim_circuit *c : b->cs) {
         const uint32_t n = c->hp.num_qubits ? c->hp.num_qubits : 1;
         maxq = std::max(maxq, (n + (uint32_t)C - 1) / (uint32_t)C);
     }
-    return kDescBytes + (size_t)maxq * W * 16;
+    return maxq;
+}
+
+// Dynamic shared memory of the persistent kernel: descriptor + tile region.
+size_t batch_smem(const stim_batch *b, int W, int C, uint32_t op_cap) {
+    return kDescBytes + tile_smem_bytes(batch_max_slice(b, C), W, op_cap, false);
 }
 
 }  // namespace
@@ -332,6 +338,7 @@ int fill_descs(stim_batch *b, const uint64_t *seeds, const uint64_t *offsets, ui
         a.rec_stride = nwords;
         a.status = c->d_status;
         a.seed = seeds[i];
+        a.op_cap = b->op_cap;
         b->h_descs[i] = a;
         DetDesc d{};
         d.rec = rec;
@@ -374,7 +381,20 @@ int configure(stim_batch *b, int W, uint32_t threads) {
     STIMGB_BCK(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, b->device), "attr");
     b->W = W;
     b->threads = threads;
-    b->smem = batch_smem(b, W, b->C);
+    int smem_optin = 0;
+    STIMGB_BCK(cudaDeviceGetAttribute(&smem_optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, b->device), "attr");
+    uint32_t max_ops = 0;
+    for (stim_circuit *c : b->cs) {
+        const DevFrameProgram *fp;
+        int r = stimgb_frame_program(c, b->C, &fp);
+        if (r != STIM_OK) return r;
+        max_ops = std::max(max_ops, fp->max_rank_ops);
+    }
+    const size_t frame_bytes = (size_t)batch_max_slice(b, b->C) * W * 16 + kDescBytes;
+    b->op_cap = stage_capacity(max_ops, frame_bytes, (size_t)smem_optin);
+    b->smem = batch_smem(b, W, b->C, b->op_cap);
+    // descriptors must never promise more staged ops than this shape's shared memory holds
+    for (size_t i = 0; i < b->k; i++) b->h_descs[i].op_cap = b->op_cap;
     const int ctas = max_resident_ctas(W, b->C, threads, b->smem, sms);
     if (ctas <= 0) return bfail(STIM_E_UNSUPPORTED, "batch: tile shape does not fit an SM");
     b->blocks = (uint32_t)ctas;
@@ -401,7 +421,7 @@ int autotune(stim_batch *b, cudaStream_t st) {
     STIMGB_BCK(cudaEventCreate(&e0), "event");
     STIMGB_BCK(cudaEventCreate(&e1), "event");
     for (int w : cand_w) {
-        if (batch_smem(b, w, b->C) > (size_t)smem_optin) continue;
+        if (batch_smem(b, w, b->C, 0) > (size_t)smem_optin) continue;
         for (uint32_t t : cand_t) {
             if (configure(b, w, t) != STIM_OK) continue;
             const uint32_t lim = std::min<uint32_t>(b->nitems, std::max<uint32_t>(4 * b->blocks / b->C, 1));
@@ -470,7 +490,7 @@ int stim_batch_create(stim_circuit *const *circuits, const uint64_t *num_shots, 
         // smallest cluster whose largest slice fits with two tiles per SM
         b->C = 0;
         for (int C : {1, 2, 4, 8})
-            if ((size_t)((maxn + C - 1) / C) * 16 * 2 + 2 * kDescBytes <= (size_t)smem_optin) {
+            if ((size_t)((maxn + C - 1) / C) * 16 * 2 + 2 * (kDescBytes + kTileHeaderBytes) <= (size_t)smem_optin) {
                 b->C = C;
                 break;
             }

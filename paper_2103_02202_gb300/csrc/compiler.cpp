@@ -555,6 +555,7 @@ class FrameBuilder {
         for (uint32_t i = 0; i < chains_.size(); i++) by_rank[chains_[i].q0 / fp_->Q].push_back(i);
         for (int r = 0; r < C_; r++) {
             fp_->rank_tab.push_back((uint32_t)fp_->segs.size());
+            const size_t rank_op0 = fp_->ops.size();
             auto sig_less = [&](uint32_t x, uint32_t y) {
                 const auto &a = chains_[x].ops, &b = chains_[y].ops;
                 if (a.size() != b.size()) return a.size() < b.size();
@@ -584,6 +585,7 @@ class FrameBuilder {
                 fp_->segs.push_back(sg);
                 i = j;
             }
+            fp_->max_rank_ops = std::max<uint32_t>(fp_->max_rank_ops, (uint32_t)(fp_->ops.size() - rank_op0));
         }
         fp_->rank_tab.push_back((uint32_t)fp_->segs.size());
         e.n_gate = ng;

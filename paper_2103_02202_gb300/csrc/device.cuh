@@ -13,22 +13,86 @@ namespace stimgb {
 // -> 64-bit multiplies; the key follows the Weyl sequence
 // (k0, k1) += (0x9E3779B9, 0xBB67AE85) after every round.
 // ---------------------------------------------------------------------------
-// The key of round r is (k0 + r * 0x9E3779B9, k1 + r * 0xBB67AE85): each is
-// one add of a compile-time constant to the seed words, off the dependency
-// chain of the rounds.
+// The key of round r is (k0 + r * 0x9E3779B9, k1 + r * 0xBB67AE85).
 struct Key {
     uint32_t k0, k1;
 };
 
-__device__ __forceinline__ uint4 philox_sched(uint4 c, Key k) {
+// ---- shared-memory helpers (32-bit shared-window addresses) ----
+__device__ __forceinline__ uint32_t smem_addr(const void *p) { return (uint32_t)__cvta_generic_to_shared(p); }
+
+__device__ __forceinline__ uint64_t lds64(uint32_t a) {
+    uint64_t v;
+    asm volatile("ld.shared.u64 %0, [%1];" : "=l"(v) : "r"(a) : "memory");
+    return v;
+}
+__device__ __forceinline__ void sts64(uint32_t a, uint64_t v) {
+    asm volatile("st.shared.u64 [%0], %1;" ::"r"(a), "l"(v) : "memory");
+}
+__device__ __forceinline__ uint4 lds128(uint32_t a) {
+    uint4 v;
+    asm volatile("ld.shared.v4.u32 {%0, %1, %2, %3}, [%4];" : "=r"(v.x), "=r"(v.y), "=r"(v.z), "=r"(v.w) : "r"(a));
+    return v;
+}
+
+// Round keys precomputed once per CTA in shared memory: 10 rounds as 5
+// 16-byte vectors (k0_2i, k1_2i, k0_2i+1, k1_2i+1).
+struct SmemKeys {
+    uint32_t sa;
+    __device__ __forceinline__ uint4 pair(int i) const { return lds128(sa + 16u * (uint32_t)i); }
+};
+
+__device__ __forceinline__ void write_round_keys(uint32_t *dst, Key k) {
+    // called by threads 0..9 of a CTA: dst[2r] = k0 + r W0, dst[2r + 1] = k1 + r W1
+    const uint32_t r = threadIdx.x;
+    if (r < 10) {
+        dst[2 * r] = k.k0 + r * 0x9E3779B9u;
+        dst[2 * r + 1] = k.k1 + r * 0xBB67AE85u;
+    }
+}
+
+__device__ __forceinline__ uint4 philox_round(uint4 c, uint32_t k0, uint32_t k1) {
+    const uint64_t p0 = (uint64_t)0xD2511F53u * c.x;
+    const uint64_t p1 = (uint64_t)0xCD9E8D57u * c.z;
+    return make_uint4((uint32_t)(p1 >> 32) ^ c.y ^ k0, (uint32_t)p1, (uint32_t)(p0 >> 32) ^ c.w ^ k1,
+                      (uint32_t)p0);
+}
+
+__device__ __forceinline__ uint4 philox_sched(uint4 c, SmemKeys k) {
 #pragma unroll
-    for (int r = 0; r < 10; r++) {
-        const uint64_t p0 = (uint64_t)0xD2511F53u * c.x;
-        const uint64_t p1 = (uint64_t)0xCD9E8D57u * c.z;
-        c = make_uint4((uint32_t)(p1 >> 32) ^ c.y ^ (k.k0 + (uint32_t)r * 0x9E3779B9u), (uint32_t)p1,
-                       (uint32_t)(p0 >> 32) ^ c.w ^ (k.k1 + (uint32_t)r * 0xBB67AE85u), (uint32_t)p0);
+    for (int i = 0; i < 5; i++) {
+        const uint4 kk = k.pair(i);
+        c = philox_round(c, kk.x, kk.y);
+        c = philox_round(c, kk.z, kk.w);
     }
     return c;
+}
+
+// ---- mbarrier / bulk async copy (TMA engine, 1-D) ----
+__device__ __forceinline__ void mbar_init(uint32_t mb, uint32_t count) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(mb), "r"(count) : "memory");
+}
+__device__ __forceinline__ void mbar_arrive_expect_tx(uint32_t mb, uint32_t bytes) {
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(mb), "r"(bytes) : "memory");
+}
+__device__ __forceinline__ bool mbar_try_wait(uint32_t mb, uint32_t parity) {
+    uint32_t ok;
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+        "selp.u32 %0, 1, 0, p;\n\t}"
+        : "=r"(ok)
+        : "r"(mb), "r"(parity)
+        : "memory");
+    return ok != 0;
+}
+__device__ __forceinline__ void fence_proxy_async_smem() { asm volatile("fence.proxy.async.shared::cta;" ::: "memory"); }
+// Copies `bytes` (multiple of 16, both addresses 16-byte aligned) from global
+// memory into this CTA's shared memory; completion is signalled on mbarrier mb.
+__device__ __forceinline__ void bulk_g2s(uint32_t dst, const void *src, uint32_t bytes, uint32_t mb) {
+    asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(dst),
+                 "l"(src), "r"(bytes), "r"(mb)
+                 : "memory");
 }
 
 // Counter layout: (draw block, slot, tag << 28 | instruction ordinal, 64-shot word).
@@ -38,84 +102,67 @@ constexpr uint32_t kTagInit = 2u << 28;
 
 // 64 fair bits for a collapse (tag COLLAPSE) or the initial frame (tag INIT):
 // draws 0 and 1 of the keyed stream.
-__device__ __forceinline__ uint64_t half_mask(Key key, uint32_t tag_instr, uint32_t slot, uint32_t word) {
+template <class K>
+__device__ __forceinline__ uint64_t half_mask(K key, uint32_t tag_instr, uint32_t slot, uint32_t word) {
     const uint4 r = philox_sched(make_uint4(0u, slot, tag_instr, word), key);
     return (uint64_t)r.x | ((uint64_t)r.y << 32);
 }
 
-// Sequential draws of one keyed stream; block j/4 is generated on demand.
-struct DrawStream {
-    uint4 blk;
-    uint32_t j, slot, ti, word;
-    Key key;
-
-    __device__ __forceinline__ DrawStream(Key key_, uint32_t ti_, uint32_t slot_, uint32_t word_, uint4 blk0)
-        : blk(blk0), j(0), slot(slot_), ti(ti_), word(word_), key(key_) {}
-
-    __device__ __forceinline__ uint32_t next() {
-        const uint32_t lane = j & 3u;
-        if (lane == 0u && j != 0u) blk = philox_sched(make_uint4(j >> 2, slot, ti, word), key);
-        j++;
-        return lane == 0u ? blk.x : lane == 1u ? blk.y : lane == 2u ? blk.z : blk.w;
-    }
-};
+// Gap to the next error for a draw u with u < G[63]: min{k : u < G[k]}, by a
+// branch-free binary search over the 64 monotone thresholds.
+__device__ __forceinline__ int geo_gap(const uint64_t *__restrict__ G, uint32_t u) {
+    int k = 0;
+#pragma unroll
+    for (int step = 32; step >= 1; step >>= 1)
+        if ((uint64_t)u >= __ldg(G + k + step - 1)) k += step;
+    return k;
+}
 
 // General procedure: exact geometric gaps. With G the threshold table of p, a
-// draw u gives the gap min{k : u < G[k]} to the next error. The first test
-// asks whether the next error falls beyond bit 63 (u >= G[remaining - 1]);
-// only otherwise is the gap located by binary search. DEPOLARIZE1 spends one
-// more draw v per error on the Pauli 1 + floor(3v / 2^32) (1 X, 2 Y, 3 Z);
-// DEPOLARIZE2 on c = 1 + floor(15v / 2^32), first-qubit Pauli c >> 2, second c & 3.
-template <uint32_t OP>
-__device__ __forceinline__ void noise_masks_slow(const uint64_t *__restrict__ G, Key key, uint32_t instr,
+// draw u gives the gap min{k : u < G[k]} to the next error; the error process
+// stops at the first draw with u >= G[remaining - 1] (next error beyond bit
+// 63). The caller has drawn block 0 and found an error: its first word, draw
+// 0, satisfies blk0.x < G[63]. DEPOLARIZE1 spends one more draw v per error
+// on the Pauli 1 + floor(3v / 2^32) (1 X, 2 Y, 3 Z); DEPOLARIZE2 on
+// c = 1 + floor(15v / 2^32), first-qubit Pauli c >> 2, second c & 3.
+template <uint32_t OP, class K>
+__device__ __forceinline__ void noise_masks_slow(const uint64_t *__restrict__ G, K key, uint32_t instr,
                                                  uint32_t slot, uint32_t word, uint4 blk0, uint64_t &xa,
                                                  uint64_t &za, uint64_t &xb, uint64_t &zb) {
-    DrawStream ds(key, kTagNoise | instr, slot, word, blk0);
-    int pos = -1;
+    uint4 blk = blk0;
+    uint32_t j = 1;                       // index of the next draw
+    auto next = [&]() -> uint32_t {
+        const uint32_t l = j & 3u;
+        if (l == 0u) blk = philox_sched(make_uint4(j >> 2, slot, kTagNoise | instr, word), key);
+        j++;
+        return l == 0u ? blk.x : l == 1u ? blk.y : l == 2u ? blk.z : blk.w;
+    };
     xa = za = xb = zb = 0;
+    uint32_t u = blk0.x;
+    int pos = -1;
     for (;;) {
-        const int remaining = 63 - pos;
-        if (remaining <= 0) break;
-        const uint32_t u = ds.next();
-        if ((uint64_t)u >= __ldg(G + remaining - 1)) break;
-        int lo = 0, hi = remaining - 1;
-        while (lo < hi) {
-            const int mid = (lo + hi) >> 1;
-            if ((uint64_t)u < __ldg(G + mid)) hi = mid;
-            else lo = mid + 1;
-        }
-        pos += lo + 1;
+        pos += geo_gap(G, u) + 1;
         const uint64_t bit = 1ull << pos;
         if (OP == OP_XERR) {
             xa |= bit;
         } else if (OP == OP_ZERR) {
             za |= bit;
         } else if (OP == OP_DEP1) {
-            const uint32_t pa = 1u + (uint32_t)((3ull * ds.next()) >> 32);
+            const uint32_t pa = 1u + (uint32_t)((3ull * next()) >> 32);
             if (pa <= 2u) xa |= bit;
             if (pa >= 2u) za |= bit;
         } else {
-            const uint32_t c = 1u + (uint32_t)((15ull * ds.next()) >> 32);
+            const uint32_t c = 1u + (uint32_t)((15ull * next()) >> 32);
             const uint32_t pa = c >> 2, pb = c & 3u;
             if (pa == 1u || pa == 2u) xa |= bit;
             if (pa >= 2u) za |= bit;
             if (pb == 1u || pb == 2u) xb |= bit;
             if (pb >= 2u) zb |= bit;
         }
+        if (pos >= 63) break;
+        u = next();
+        if ((uint64_t)u >= __ldg(G + (62 - pos))) break;    // G[remaining - 1], remaining = 63 - pos
     }
-}
-
-// Error masks of one noise slot over the 64 shots of one word. The first draw
-// alone decides the common case: no error in the word exactly when
-// u0 >= G[63]. Only then is the general procedure run (out of line).
-template <uint32_t OP>
-__device__ __forceinline__ bool noise_masks(const uint64_t *__restrict__ G, Key key, uint32_t instr, uint32_t slot,
-                                            uint32_t word, uint64_t &xa, uint64_t &za, uint64_t &xb,
-                                            uint64_t &zb) {
-    const uint4 blk0 = philox_sched(make_uint4(0u, slot, kTagNoise | instr, word), key);
-    if ((uint64_t)blk0.x >= __ldg(G + 63)) return false;
-    noise_masks_slow<OP>(G, key, instr, slot, word, blk0, xa, za, xb, zb);
-    return true;
 }
 
 __device__ __forceinline__ uint64_t globaltimer_ns() {

@@ -33,23 +33,23 @@ namespace stimgb {
 
 template <int W, int C, bool GMEM>
 __global__ void __launch_bounds__(1024, 1) frame_kernel(const __grid_constant__ FrameArgs a) {
-    extern __shared__ __align__(16) uint64_t smem[];
+    extern __shared__ __align__(128) unsigned char dyn_smem[];
     const uint32_t rank = C > 1 ? (uint32_t)(blockIdx.x % C) : 0u;
-    frame_detail::run_tile<W, C, GMEM>(a, smem, rank, blockIdx.x / C);
+    frame_detail::run_tile<W, C, GMEM>(a, dyn_smem, rank, blockIdx.x / C);
 }
 
 template <int W, int C, bool GMEM>
 static cudaError_t launch_frame_t(const FrameArgs &a, uint32_t tiles, uint32_t threads, size_t smem,
                                   cudaStream_t stream) {
     auto kern = frame_kernel<W, C, GMEM>;
-    if (!GMEM && smem > 48 * 1024) {
+    if (smem > 48 * 1024) {
         cudaError_t err = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         if (err != cudaSuccess) return err;
     }
     cudaLaunchConfig_t cfg = {};
     cfg.gridDim = dim3(tiles * C);
     cfg.blockDim = dim3(threads);
-    cfg.dynamicSmemBytes = GMEM ? 0 : smem;
+    cfg.dynamicSmemBytes = smem;
     cfg.stream = stream;
     cudaLaunchAttribute attr[1];
     attr[0].id = cudaLaunchAttributeClusterDimension;

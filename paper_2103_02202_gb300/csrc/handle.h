@@ -6,6 +6,8 @@
 
 #include <cuda_runtime.h>
 
+#include <algorithm>
+
 #include "internal.h"
 
 // Device copy of a FrameProgram for one cluster size.
@@ -13,6 +15,7 @@ struct DevFrameProgram {
     int C = 0;                          // 0: not built
     uint32_t Q = 0;
     uint32_t nprog = 0;
+    uint32_t max_rank_ops = 0;
     stimgb::ProgEntry *prog = nullptr;
     uint32_t *rank_tab = nullptr;
     stimgb::FrameSeg *segs = nullptr;
@@ -49,6 +52,19 @@ struct TileChoice {
     bool gmem = false;
     uint32_t threads = 256;
 };
+
+// Ops of one layer staged in shared memory for a tile whose frame takes
+// frame_bytes: as many as the program's largest per-CTA layer needs, within
+// what leaves room for two CTAs per SM when the frame allows it.
+inline uint32_t stage_capacity(uint32_t max_rank_ops, size_t frame_bytes, size_t smem_optin) {
+    // 1 KB of margin per CTA leaves room for the kernels' static shared memory
+    const size_t half = smem_optin / 2 > 2048 ? smem_optin / 2 - 1024 : 0;
+    const size_t full = smem_optin > 1024 ? smem_optin - 1024 : 0;
+    const size_t target = frame_bytes + 256 + 16 * 64 <= half ? half : full;
+    if (target <= frame_bytes + 256) return 0;
+    const size_t cap = (target - frame_bytes - 256) / 16;
+    return (uint32_t)std::min<size_t>(cap, max_rank_ops);
+}
 
 // Library-internal entry points shared by the batched and serving paths.
 int stimgb_frame_program(stim_circuit *c, int C, const DevFrameProgram **out);

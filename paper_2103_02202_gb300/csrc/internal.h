@@ -115,6 +115,7 @@ struct FrameProgram {
     int C = 1;
     uint32_t Q = 0;
     uint64_t merged_layers_exec = 0;
+    uint32_t max_rank_ops = 0;          // largest op range of one CTA in one merged layer
     std::vector<ProgEntry> prog;
     std::vector<uint32_t> rank_tab;
     std::vector<FrameSeg> segs;

@@ -28,7 +28,16 @@ struct FrameArgs {
     uint64_t gstride;
     int *status;
     uint64_t seed;             // Philox key = (seed lo, seed hi)
+    uint32_t op_cap;           // ops of one layer staged in shared memory (rest read from global)
 };
+
+// Dynamic shared memory of a frame tile: a 256-byte header (round keys,
+// staging mbarrier), op_cap staged ops of 16 bytes, then (shared layout) the
+// frame rows of Q qubits x 2W words.
+constexpr uint32_t kTileHeaderBytes = 256;
+inline size_t tile_smem_bytes(uint32_t Q, int W, uint32_t op_cap, bool gmem) {
+    return kTileHeaderBytes + 16 * (size_t)op_cap + (gmem ? 0 : (size_t)Q * 2 * W * 8);
+}
 
 // tiles = word tiles (clusters); the grid has tiles * C CTAs.
 cudaError_t launch_frame(const FrameArgs &a, int W, int C, bool gmem, uint32_t tiles, uint32_t threads, size_t smem,

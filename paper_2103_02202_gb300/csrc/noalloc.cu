@@ -84,7 +84,7 @@ extern "C" int stim_frame_sample_noalloc(stim_circuit *c, uint64_t num_shots, ui
     if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
     if (e != cudaSuccess) return fail(STIM_E_CUDA, std::string("attribute: ") + cudaGetErrorString(e));
     const size_t per_word = (size_t)n * 16;
-    if (per_word > (size_t)smem_optin)
+    if (per_word + kTileHeaderBytes > (size_t)smem_optin)
         return fail(STIM_E_UNSUPPORTED,
                     "stim_frame_sample_noalloc: one 64-shot frame tile does not fit shared memory");
     uint64_t *rec = nullptr;
@@ -96,7 +96,7 @@ extern "C" int stim_frame_sample_noalloc(stim_circuit *c, uint64_t num_shots, ui
     if (n > 0 && M > 0) {
         int W = 1;
         for (int w : {8, 4, 2}) {
-            if (per_word * w <= (size_t)smem_optin / 2 && (nwords + w - 1) / w >= (uint64_t)sms * 2) {
+            if (per_word * w + 256 <= (size_t)smem_optin / 2 && (nwords + w - 1) / w >= (uint64_t)sms * 2) {
                 W = w;
                 break;
             }
@@ -121,7 +121,8 @@ extern "C" int stim_frame_sample_noalloc(stim_circuit *c, uint64_t num_shots, ui
         a.rec_stride = nwords;
         a.status = c->d_status;
         const uint64_t grid = (nwords + W - 1) / W;
-        e = launch_frame(a, W, 1, false, (uint32_t)grid, 256, per_word * W, st);
+        a.op_cap = stage_capacity(fp.max_rank_ops, per_word * W, (size_t)smem_optin);
+        e = launch_frame(a, W, 1, false, (uint32_t)grid, 256, tile_smem_bytes(fp.Q, W, a.op_cap, false), st);
         if (e != cudaSuccess) return fail(STIM_E_CUDA, std::string("frame kernel: ") + cudaGetErrorString(e));
     }
     if (det_out && D > 0) {

@@ -273,3 +273,28 @@ def test_edge_cases():
     # p = 1 noise flips every shot
     mb, _ = gpu_sample("X_ERROR(1) 0 1 2\nM 0 1 2\n", 200, 1)
     assert mb.all()
+
+
+@pytest.mark.slow
+def test_surface_d100_bench_configuration_sampled_parity():
+    """d=100, 100 rounds, p=1e-3, 16384 shots at shot offset 16384 (step 1
+    of the benchmark), default launch (thread-block clusters): sampled shots
+    vs the oracle, and the full reference sample vs the oracle's tableau."""
+    text = W.surface_code_memory(100, 100, 1e-3)
+    S, off = 16384, 16384
+    c = sg.Circuit(text)
+    ref, det = c.reference()
+    _, d = c.sample(S, 2021, shot_offset=off, meas=False)
+    torch.cuda.synchronize()
+    o = oracle.Circuit(text)
+    oref, odet = o.reference()
+    M = c.num_measurements
+    np.testing.assert_array_equal(words_to_bits(to_np(ref)[None, :], M)[0], oref)
+    np.testing.assert_array_equal(words_to_bits(to_np(det)[None, :], M)[0], odet)
+    pick = np.array([0, 1, 63, 64, 8191, S - 1] + list(np.random.default_rng(3).choice(S, 10, replace=False)))
+    cols = torch.as_tensor(pick // 64, device="cuda")
+    bits = torch.as_tensor(pick % 64, device="cuda")
+    gd = ((d[:, cols] >> bits) & 1).cpu().numpy().astype(np.uint8).T
+    _, od = o.sample(pick, 2021, shot_offset=off, threads=16, ref=oref)
+    np.testing.assert_array_equal(gd, od)
+    c.close()
