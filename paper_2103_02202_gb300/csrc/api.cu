@@ -126,6 +126,9 @@ int frame_program(stim_circuit *c, int C, const DevFrameProgram **out) {
         } catch (const std::bad_alloc &) {
             return fail(STIM_E_OOM, "out of host memory building the frame program");
         }
+        // deferred noise hits name their op by a 29-bit index within the CTA's layer
+        if (fp.max_rank_ops >= (1u << 29))
+            return fail(STIM_E_UNSUPPORTED, "a layer holds 2^29 or more ops for one CTA");
         int r;
         if ((r = upload(&d.prog, fp.prog, "upload frame program")) != STIM_OK) return r;
         if ((r = upload(&d.rank_tab, fp.rank_tab, "upload frame program")) != STIM_OK) return r;
@@ -279,6 +282,8 @@ int choose_tile(uint32_t n, uint64_t nwords, int sms, size_t smem_optin, const s
         t.W = t.gmem ? 2 : 1;
     }
     if (hint && hint->threads) {
+        if ((int)hint->threads > frame_max_threads(t.W))
+            return fail(STIM_E_INVALID_ARG, "tile hint: too many threads per CTA for this many words per tile (768 for 2, 512 for 4 or 8)");
         t.threads = hint->threads;
     } else if (t.gmem) {
         t.threads = 256;

@@ -53,7 +53,7 @@ constexpr uint32_t kDescBytes = 256;   // FrameArgs copy at the start of dynamic
 static_assert(sizeof(FrameArgs) <= kDescBytes, "descriptor does not fit its slot");
 
 template <int W, int C>
-__global__ void __launch_bounds__(1024, 1) batch_frame_kernel(const FrameArgs *__restrict__ descs,
+__global__ void __launch_bounds__(frame_max_threads(W), 1) batch_frame_kernel(const FrameArgs *__restrict__ descs,
                                                               const BatchItem *__restrict__ items, uint32_t nitems,
                                                               uint32_t *counter) {
     extern __shared__ __align__(128) unsigned char smem[];
@@ -379,6 +379,8 @@ int enqueue(stim_batch *b, cudaStream_t st, uint32_t nitems_limit) {
 int configure(stim_batch *b, int W, uint32_t threads) {
     int sms = 0;
     STIMGB_BCK(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, b->device), "attr");
+    if ((int)threads > frame_max_threads(W))
+        return bfail(STIM_E_INVALID_ARG, "batch: too many threads per CTA for this many words per tile (768 for 2, 512 for 4 or 8)");
     b->W = W;
     b->threads = threads;
     int smem_optin = 0;

@@ -574,6 +574,14 @@ class FrameBuilder {
                 sg.len = (uint32_t)chains_[by_rank[r][i]].ops.size();
                 sg.op_begin = (uint32_t)fp_->ops.size();
                 sg.count = (uint32_t)(j - i);
+                // first chain step from which only noise ops follow: their
+                // error masks commute, so they may be applied after the chain
+                {
+                    const auto &c0 = chains_[by_rank[r][i]].ops;
+                    uint32_t d = (uint32_t)c0.size();
+                    while (d > 0 && op_is_noise(c0[d - 1].a >> 24)) d--;
+                    sg.defer_from = d;
+                }
                 for (size_t k = i; k < j; k++)
                     for (const DevOp &d : chains_[by_rank[r][k]].ops) {
                         fp_->ops.push_back(encode(d));

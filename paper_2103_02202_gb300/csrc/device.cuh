@@ -125,8 +125,8 @@ __device__ __forceinline__ int geo_gap(const uint64_t *__restrict__ G, uint32_t 
 // 0, satisfies blk0.x < G[63]. DEPOLARIZE1 spends one more draw v per error
 // on the Pauli 1 + floor(3v / 2^32) (1 X, 2 Y, 3 Z); DEPOLARIZE2 on
 // c = 1 + floor(15v / 2^32), first-qubit Pauli c >> 2, second c & 3.
-template <uint32_t OP, class K>
-__device__ __forceinline__ void noise_masks_slow(const uint64_t *__restrict__ G, K key, uint32_t instr,
+template <class K>
+__device__ __forceinline__ void noise_masks_slow(uint32_t opc, const uint64_t *__restrict__ G, K key, uint32_t instr,
                                                  uint32_t slot, uint32_t word, uint4 blk0, uint64_t &xa,
                                                  uint64_t &za, uint64_t &xb, uint64_t &zb) {
     uint4 blk = blk0;
@@ -143,11 +143,11 @@ __device__ __forceinline__ void noise_masks_slow(const uint64_t *__restrict__ G,
     for (;;) {
         pos += geo_gap(G, u) + 1;
         const uint64_t bit = 1ull << pos;
-        if (OP == OP_XERR) {
+        if (opc == OP_XERR) {
             xa |= bit;
-        } else if (OP == OP_ZERR) {
+        } else if (opc == OP_ZERR) {
             za |= bit;
-        } else if (OP == OP_DEP1) {
+        } else if (opc == OP_DEP1) {
             const uint32_t pa = 1u + (uint32_t)((3ull * next()) >> 32);
             if (pa <= 2u) xa |= bit;
             if (pa >= 2u) za |= bit;

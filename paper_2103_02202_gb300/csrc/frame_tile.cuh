@@ -2,13 +2,15 @@
 // the per-circuit kernel (frame.cu) and the batched persistent kernel
 // (batch.cu).
 //
-// Dynamic shared memory of one tile (byte offsets from the region start):
+// Dynamic shared memory of one tile (byte offsets from the region start;
+// H = kTileHeaderBytes):
 //   [0, 80)                  Philox round keys of the seed
 //   [128, 136)               mbarrier of the op-staging copy
-//   [256, 256 + 16 op_cap)   the current layer's ops of this CTA, copied in
+//   [256, H)                 per-warp queues of deferred noise hits
+//   [H, H + 16 op_cap)       the current layer's ops of this CTA, copied in
 //                            by the TMA engine (cp.async.bulk) at the start of
 //                            the layer
-//   [256 + 16 op_cap, ...)   frame rows (shared-memory layout)
+//   [H + 16 op_cap, ...)     frame rows (shared-memory layout)
 // Frame layout (W 64-shot words per tile): each qubit owns a row of 2W words,
 // its X words then its Z words,
 //     shared memory:  row(q) = q * 2W;  X = row[w], Z = row[W + w]
@@ -31,28 +33,19 @@ constexpr uint64_t kStageTimeoutNs = 2000000000ull;   // bounded wait for a stag
 
 __device__ __forceinline__ DevOp as_op(uint4 v) { return DevOp{v.x, v.y, v.z, v.w}; }
 
+// Layer barrier of the tile, split in two halves: arrive when this thread's
+// frame writes of the layer are done, wait before the next layer touches the
+// frame. The next layer's op copy is issued in between, so the staging latency
+// overlaps the cluster barrier. The CTA barrier in the arrive half also frees
+// the staging buffer for that copy.
 template <int C>
-__device__ __forceinline__ void sync_tile() {
-    if constexpr (C == 1) {
-        __syncthreads();
-    } else {
-        cg::this_cluster().sync();
-    }
+__device__ __forceinline__ void tile_arrive() {
+    __syncthreads();
+    if constexpr (C > 1) asm volatile("barrier.cluster.arrive.release.aligned;" ::: "memory");
 }
-
-// Word of a peer CTA's shared memory (same offset, CTA `rank` of the cluster).
-__device__ __forceinline__ uint64_t ld_peer(uint32_t sa, uint32_t rank) {
-    uint32_t ra;
-    uint64_t v;
-    asm volatile("mapa.shared::cluster.u32 %0, %1, %2;" : "=r"(ra) : "r"(sa), "r"(rank));
-    asm volatile("ld.shared::cluster.u64 %0, [%1];" : "=l"(v) : "r"(ra) : "memory");
-    return v;
-}
-
-__device__ __forceinline__ void st_peer(uint32_t sa, uint32_t rank, uint64_t v) {
-    uint32_t ra;
-    asm volatile("mapa.shared::cluster.u32 %0, %1, %2;" : "=r"(ra) : "r"(sa), "r"(rank));
-    asm volatile("st.shared::cluster.u64 [%0], %1;" ::"r"(ra), "l"(v) : "memory");
+template <int C>
+__device__ __forceinline__ void tile_wait() {
+    if constexpr (C > 1) asm volatile("barrier.cluster.wait.acquire.aligned;" ::: "memory");
 }
 
 // The tile as seen from one CTA of the cluster.
@@ -64,7 +57,48 @@ struct Tile {
     uint32_t rank;
 };
 
-// One qubit's X and Z words at word w of the tile; a qubit reference is
+// Words per thread: a thread applies each op to V consecutive words of the
+// tile (W / V threads share a chain when W > V).
+template <int W>
+struct VecWidth {
+    static constexpr int V = W < 4 ? W : 4;
+};
+
+// 16-byte shared-memory accesses: this CTA (shared::cta window) or a peer
+// CTA of the cluster (shared::cluster window, address from mapa).
+__device__ __forceinline__ void lds_v2(uint32_t a, uint64_t &v0, uint64_t &v1) {
+    asm volatile("ld.shared.v2.u64 {%0, %1}, [%2];" : "=l"(v0), "=l"(v1) : "r"(a) : "memory");
+}
+__device__ __forceinline__ void sts_v2(uint32_t a, uint64_t v0, uint64_t v1) {
+    asm volatile("st.shared.v2.u64 [%0], {%1, %2};" ::"r"(a), "l"(v0), "l"(v1) : "memory");
+}
+__device__ __forceinline__ void ldc_v2(uint32_t a, uint64_t &v0, uint64_t &v1) {
+    asm volatile("ld.shared::cluster.v2.u64 {%0, %1}, [%2];" : "=l"(v0), "=l"(v1) : "r"(a) : "memory");
+}
+__device__ __forceinline__ void stc_v2(uint32_t a, uint64_t v0, uint64_t v1) {
+    asm volatile("st.shared::cluster.v2.u64 [%0], {%1, %2};" ::"r"(a), "l"(v0), "l"(v1) : "memory");
+}
+__device__ __forceinline__ uint64_t ldc64(uint32_t a) {
+    uint64_t v;
+    asm volatile("ld.shared::cluster.u64 %0, [%1];" : "=l"(v) : "r"(a) : "memory");
+    return v;
+}
+__device__ __forceinline__ void stc64(uint32_t a, uint64_t v) {
+    asm volatile("st.shared::cluster.u64 [%0], %1;" ::"r"(a), "l"(v) : "memory");
+}
+__device__ __forceinline__ uint32_t mapa_rank(uint32_t sa, uint32_t rank) {
+    uint32_t ra;
+    asm volatile("mapa.shared::cluster.u32 %0, %1, %2;" : "=r"(ra) : "r"(sa), "r"(rank));
+    return ra;
+}
+
+// V words of one qubit's X and Z planes.
+template <int V>
+struct Planes {
+    uint64_t x[V], z[V];
+};
+
+// One qubit's V words at word offset wo of the tile; a qubit reference is
 // (rank << 24 | local index), other ranks are reached through distributed
 // shared memory.
 template <int W, int C, bool GMEM>
@@ -72,141 +106,330 @@ struct Qubit;
 
 template <int W, int C>
 struct Qubit<W, C, false> {
-    uint32_t sa;         // shared address of the X word
-    uint32_t peer;       // owning CTA when remote, else 0xFFFFFFFF
+    static constexpr int V = VecWidth<W>::V;
+    uint32_t sa;         // X word wo of the qubit (shared::cta, or shared::cluster when remote)
+    bool remote;
 
-    __device__ __forceinline__ Qubit(const Tile<W, C, false> &t, uint32_t ref, uint32_t w) {
-        sa = t.fsa + ((ref & 0xFFFFFFu) * (2u * W) + w) * 8u;
-        peer = 0xFFFFFFFFu;
+    __device__ __forceinline__ Qubit(const Tile<W, C, false> &t, uint32_t ref, uint32_t wo) {
+        sa = t.fsa + ((ref & 0xFFFFFFu) * (2u * W) + wo) * 8u;
+        remote = false;
         if constexpr (C > 1) {
-            if ((ref >> 24) != t.rank) peer = ref >> 24;
-        }
-    }
-    __device__ __forceinline__ uint64_t get(uint32_t off) const {
-        if constexpr (C > 1) {
-            if (peer != 0xFFFFFFFFu) return ld_peer(sa + off, peer);
-        }
-        return lds64(sa + off);
-    }
-    __device__ __forceinline__ void put(uint32_t off, uint64_t v) const {
-        if constexpr (C > 1) {
-            if (peer != 0xFFFFFFFFu) {
-                st_peer(sa + off, peer, v);
-                return;
+            if ((ref >> 24) != t.rank) {
+                remote = true;
+                sa = mapa_rank(sa, ref >> 24);
             }
         }
-        sts64(sa + off, v);
     }
-    __device__ __forceinline__ uint64_t x(const Tile<W, C, false> &) const { return get(0); }
-    __device__ __forceinline__ uint64_t z(const Tile<W, C, false> &) const { return get(8u * W); }
-    __device__ __forceinline__ void set_x(const Tile<W, C, false> &, uint64_t v) const { put(0, v); }
-    __device__ __forceinline__ void set_z(const Tile<W, C, false> &, uint64_t v) const { put(8u * W, v); }
+    __device__ __forceinline__ void ld(uint32_t off, uint64_t (&v)[V]) const {
+        if constexpr (V == 1) {
+            v[0] = (C > 1 && remote) ? ldc64(sa + off) : lds64(sa + off);
+        } else {
+#pragma unroll
+            for (int i = 0; i < V / 2; i++) {
+                if (C > 1 && remote) ldc_v2(sa + off + 16u * i, v[2 * i], v[2 * i + 1]);
+                else lds_v2(sa + off + 16u * i, v[2 * i], v[2 * i + 1]);
+            }
+        }
+    }
+    __device__ __forceinline__ void st(uint32_t off, const uint64_t (&v)[V]) const {
+        if constexpr (V == 1) {
+            if (C > 1 && remote) stc64(sa + off, v[0]);
+            else sts64(sa + off, v[0]);
+        } else {
+#pragma unroll
+            for (int i = 0; i < V / 2; i++) {
+                if (C > 1 && remote) stc_v2(sa + off + 16u * i, v[2 * i], v[2 * i + 1]);
+                else sts_v2(sa + off + 16u * i, v[2 * i], v[2 * i + 1]);
+            }
+        }
+    }
+    __device__ __forceinline__ void load(const Tile<W, C, false> &, Planes<V> &p) const {
+        if constexpr (W == 1) {      // X and Z of the word are adjacent: one 16-byte access
+            if (C > 1 && remote) ldc_v2(sa, p.x[0], p.z[0]);
+            else lds_v2(sa, p.x[0], p.z[0]);
+        } else {
+            ld(0, p.x);
+            ld(8u * W, p.z);
+        }
+    }
+    __device__ __forceinline__ void store(const Tile<W, C, false> &, const Planes<V> &p) const {
+        if constexpr (W == 1) {
+            if (C > 1 && remote) stc_v2(sa, p.x[0], p.z[0]);
+            else sts_v2(sa, p.x[0], p.z[0]);
+        } else {
+            st(0, p.x);
+            st(8u * W, p.z);
+        }
+    }
+    __device__ __forceinline__ void store_x(const Tile<W, C, false> &, const uint64_t (&x)[V]) const { st(0, x); }
+    __device__ __forceinline__ void store_z(const Tile<W, C, false> &, const uint64_t (&z)[V]) const {
+        st(8u * W, z);
+    }
 };
 
 template <int W, int C>
 struct Qubit<W, C, true> {
+    static constexpr int V = VecWidth<W>::V;
     uint64_t *p;
 
-    __device__ __forceinline__ Qubit(const Tile<W, C, true> &t, uint32_t ref, uint32_t w) {
-        p = t.base + (uint64_t)(ref & 0xFFFFFFu) * (2 * t.gstride) + w;
+    __device__ __forceinline__ Qubit(const Tile<W, C, true> &t, uint32_t ref, uint32_t wo) {
+        p = t.base + (uint64_t)(ref & 0xFFFFFFu) * (2 * t.gstride) + wo;
     }
-    __device__ __forceinline__ uint64_t x(const Tile<W, C, true> &) const { return *p; }
-    __device__ __forceinline__ uint64_t z(const Tile<W, C, true> &t) const { return p[t.gstride]; }
-    __device__ __forceinline__ void set_x(const Tile<W, C, true> &, uint64_t v) const { *p = v; }
-    __device__ __forceinline__ void set_z(const Tile<W, C, true> &t, uint64_t v) const { p[t.gstride] = v; }
+    __device__ __forceinline__ void load(const Tile<W, C, true> &t, Planes<V> &q) const {
+#pragma unroll
+        for (int i = 0; i < V; i++) {
+            q.x[i] = p[i];
+            q.z[i] = p[t.gstride + i];
+        }
+    }
+    __device__ __forceinline__ void store(const Tile<W, C, true> &t, const Planes<V> &q) const {
+#pragma unroll
+        for (int i = 0; i < V; i++) {
+            p[i] = q.x[i];
+            p[t.gstride + i] = q.z[i];
+        }
+    }
+    __device__ __forceinline__ void store_x(const Tile<W, C, true> &, const uint64_t (&x)[V]) const {
+#pragma unroll
+        for (int i = 0; i < V; i++) p[i] = x[i];
+    }
+    __device__ __forceinline__ void store_z(const Tile<W, C, true> &t, const uint64_t (&z)[V]) const {
+#pragma unroll
+        for (int i = 0; i < V; i++) p[t.gstride + i] = z[i];
+    }
 };
 
-// One noise op on word w. Every lane draws block 0 of its stream; only when
-// its first draw shows an error in the 64 shots (probability about 64p) does
-// it run the general gap procedure.
+// One noise op on V words. Every word draws block 0 of its stream; only a
+// word whose first draw shows an error in its 64 shots (probability about
+// 64p) runs the general gap procedure, one word at a time.
 template <int W, int C, bool GMEM>
 __device__ __forceinline__ void noise_op(const FrameArgs &a, const SmemKeys key, const Tile<W, C, GMEM> &t,
-                                         const DevOp op, uint32_t w, uint32_t gw, uint32_t instr_off) {
+                                         const DevOp op, uint32_t wo, uint32_t gw0, uint32_t instr_off) {
+    constexpr int V = VecWidth<W>::V;
     const uint32_t opc = op.a >> 28;
     const bool pair = opc == OP_DEP2;
     const uint32_t tbl = pair ? (op.slot >> 24) : op.b;
     const uint32_t slot = pair ? (op.slot & 0xFFFFFFu) : op.slot;
-    const uint32_t ti = kTagNoise | (op.instr + instr_off);
+    const uint32_t instr = op.instr + instr_off;
     const uint64_t *G = a.geo + 64u * tbl;
-    const uint4 blk0 = philox_sched(make_uint4(0u, slot, ti, gw), key);
-    if ((uint64_t)blk0.x < __ldg(G + 63)) {
-        uint64_t xa, za, xb, zb;
-        const uint32_t instr = op.instr + instr_off;
-        if (opc == OP_XERR) noise_masks_slow<OP_XERR>(G, key, instr, slot, gw, blk0, xa, za, xb, zb);
-        else if (opc == OP_ZERR) noise_masks_slow<OP_ZERR>(G, key, instr, slot, gw, blk0, xa, za, xb, zb);
-        else if (opc == OP_DEP1) noise_masks_slow<OP_DEP1>(G, key, instr, slot, gw, blk0, xa, za, xb, zb);
-        else noise_masks_slow<OP_DEP2>(G, key, instr, slot, gw, blk0, xa, za, xb, zb);
-        const Qubit<W, C, GMEM> qa(t, op.a & 0x0FFFFFFFu, w);
-        if (xa) qa.set_x(t, qa.x(t) ^ xa);
-        if (za) qa.set_z(t, qa.z(t) ^ za);
-        if (pair) {
-            const Qubit<W, C, GMEM> qb(t, op.b, w);
-            if (xb) qb.set_x(t, qb.x(t) ^ xb);
-            if (zb) qb.set_z(t, qb.z(t) ^ zb);
+    const uint64_t g63 = __ldg(G + 63);
+    uint4 blk[V];
+    uint32_t hits = 0;
+#pragma unroll
+    for (int i = 0; i < V; i++) {
+        blk[i] = philox_sched(make_uint4(0u, slot, kTagNoise | instr, gw0 + i), key);
+        if ((uint64_t)blk[i].x < g63) hits |= 1u << i;
+    }
+    if (!hits) return;
+    const Qubit<W, C, GMEM> qa(t, op.a & 0x0FFFFFFFu, wo);
+    Planes<V> pa, pb;
+    qa.load(t, pa);
+    if (pair) {
+        const Qubit<W, C, GMEM> qb(t, op.b, wo);
+        qb.load(t, pb);
+    }
+    while (hits) {
+        const int w = __ffs((int)hits) - 1;
+        hits &= hits - 1u;
+        uint4 b0 = blk[0];
+#pragma unroll
+        for (int i = 1; i < V; i++)
+            if (w == i) b0 = blk[i];
+        uint64_t mxa, mza, mxb, mzb;
+        noise_masks_slow(opc, G, key, instr, slot, gw0 + (uint32_t)w, b0, mxa, mza, mxb, mzb);
+#pragma unroll
+        for (int i = 0; i < V; i++) {
+            if (w == i) {
+                pa.x[i] ^= mxa;
+                pa.z[i] ^= mza;
+                pb.x[i] ^= mxb;
+                pb.z[i] ^= mzb;
+            }
         }
+    }
+    qa.store(t, pa);
+    if (pair) {
+        const Qubit<W, C, GMEM> qb(t, op.b, wo);
+        qb.store(t, pb);
     }
 }
 
-// Applies one op to word w of the tile; lw = word within the call. Padding
-// lanes (act false) do nothing.
+// Applies one op to the V words at word offset wo of the tile (word tile0 + wo
+// of the call).
 template <int W, int C, bool GMEM>
 __device__ __forceinline__ void frame_op(const FrameArgs &a, const SmemKeys key, const Tile<W, C, GMEM> &t,
-                                         const DevOp op, uint32_t w, uint32_t lw, uint32_t instr_off,
-                                         uint32_t meas_off, bool act) {
-    if (!act) return;
+                                         const DevOp op, uint32_t wo, uint32_t tile0, uint32_t instr_off,
+                                         uint32_t meas_off) {
+    constexpr int V = VecWidth<W>::V;
     const uint32_t opc = op.a >> 28;
-    const uint32_t gw = (uint32_t)a.word0 + lw;       // global 64-shot word (RNG counter)
+    const uint32_t lw0 = tile0 + wo;                   // first word within the call
+    const uint32_t gw0 = (uint32_t)a.word0 + lw0;      // first global 64-shot word (RNG counter)
     if (opc >= OP_XERR) {
-        noise_op<W, C, GMEM>(a, key, t, op, w, gw, instr_off);
+        noise_op<W, C, GMEM>(a, key, t, op, wo, gw0, instr_off);
         return;
     }
-    const Qubit<W, C, GMEM> qa(t, op.a & 0x0FFFFFFFu, w);
+    const Qubit<W, C, GMEM> qa(t, op.a & 0x0FFFFFFFu, wo);
+    Planes<V> pa;
     switch (opc) {
         case OP_H: {
-            const uint64_t x = qa.x(t), z = qa.z(t);
-            qa.set_x(t, z);
-            qa.set_z(t, x);
+            qa.load(t, pa);
+            Planes<V> sw;
+#pragma unroll
+            for (int i = 0; i < V; i++) {
+                sw.x[i] = pa.z[i];
+                sw.z[i] = pa.x[i];
+            }
+            qa.store(t, sw);
             break;
         }
-        case OP_S:
-            qa.set_z(t, qa.z(t) ^ qa.x(t));
+        case OP_S: {
+            qa.load(t, pa);
+#pragma unroll
+            for (int i = 0; i < V; i++) pa.z[i] ^= pa.x[i];
+            qa.store_z(t, pa.z);
             break;
+        }
         case OP_CX: {
-            const Qubit<W, C, GMEM> qb(t, op.b, w);
-            const uint64_t xa = qa.x(t), za = qa.z(t), xb = qb.x(t), zb = qb.z(t);
-            qa.set_z(t, za ^ zb);
-            qb.set_x(t, xb ^ xa);
+            const Qubit<W, C, GMEM> qb(t, op.b, wo);
+            Planes<V> pb;
+            qa.load(t, pa);
+            qb.load(t, pb);
+#pragma unroll
+            for (int i = 0; i < V; i++) {
+                pa.z[i] ^= pb.z[i];
+                pb.x[i] ^= pa.x[i];
+            }
+            qa.store_z(t, pa.z);
+            qb.store_x(t, pb.x);
             break;
         }
         case OP_CZ: {
-            const Qubit<W, C, GMEM> qb(t, op.b, w);
-            const uint64_t xa = qa.x(t), za = qa.z(t), xb = qb.x(t), zb = qb.z(t);
-            qa.set_z(t, za ^ xb);
-            qb.set_z(t, zb ^ xa);
+            const Qubit<W, C, GMEM> qb(t, op.b, wo);
+            Planes<V> pb;
+            qa.load(t, pa);
+            qb.load(t, pb);
+#pragma unroll
+            for (int i = 0; i < V; i++) {
+                pa.z[i] ^= pb.x[i];
+                pb.z[i] ^= pa.x[i];
+            }
+            qa.store_z(t, pa.z);
+            qb.store_z(t, pb.z);
             break;
         }
         case OP_M:
         case OP_MR:
         case OP_R: {
-            if (opc != OP_R && a.rec != nullptr && lw < a.nwords) {
+            if (opc != OP_R) qa.load(t, pa);
+            if (opc != OP_R && a.rec != nullptr) {
                 const uint32_t m = op.b + meas_off;
                 const uint64_t refm = 0ull - ((__ldg(a.ref + (m >> 6)) >> (m & 63)) & 1ull);
-                uint64_t v = qa.x(t) ^ refm;
-                if (lw == a.nwords - 1) v &= a.last_mask;
-                a.rec[(uint64_t)m * a.rec_stride + lw] = v;
+                uint64_t *row = a.rec + (uint64_t)m * a.rec_stride;
+#pragma unroll
+                for (int i = 0; i < V; i++) {
+                    const uint32_t lw = lw0 + i;
+                    if (lw < a.nwords) {
+                        uint64_t v = pa.x[i] ^ refm;
+                        if (lw == a.nwords - 1) v &= a.last_mask;
+                        row[lw] = v;
+                    }
+                }
             }
-            const uint64_t coin = half_mask(key, kTagCollapse | (op.instr + instr_off), op.slot, gw);
+            const uint32_t ti = kTagCollapse | (op.instr + instr_off);
             if (opc == OP_M) {
-                qa.set_z(t, qa.z(t) ^ coin);
+#pragma unroll
+                for (int i = 0; i < V; i++) pa.z[i] ^= half_mask(key, ti, op.slot, gw0 + i);
+                qa.store_z(t, pa.z);
             } else {
-                qa.set_x(t, 0);
-                qa.set_z(t, coin);
+#pragma unroll
+                for (int i = 0; i < V; i++) {
+                    pa.x[i] = 0;
+                    pa.z[i] = half_mask(key, ti, op.slot, gw0 + i);
+                }
+                qa.store(t, pa);
             }
             break;
         }
         default:
             break;
     }
+}
+
+__device__ __forceinline__ uint32_t lds32(uint32_t a) {
+    uint32_t v;
+    asm volatile("ld.shared.u32 %0, [%1];" : "=r"(v) : "r"(a) : "memory");
+    return v;
+}
+__device__ __forceinline__ void sts32(uint32_t a, uint32_t v) {
+    asm volatile("st.shared.u32 [%0], %1;" ::"r"(a), "r"(v) : "memory");
+}
+__device__ __forceinline__ void red_xor_smem(uint32_t a, uint64_t v) {
+    asm volatile("red.shared.xor.b64 [%0], %1;" ::"r"(a), "l"(v) : "memory");
+}
+__device__ __forceinline__ void red_xor_cluster(uint32_t a, uint64_t v) {
+    asm volatile("red.shared::cluster.xor.b64 [%0], %1;" ::"r"(a), "l"(v) : "memory");
+}
+
+// XORs error masks into word w of one qubit. Atomic: two deferred hits of one
+// chain (say DEPOLARIZE2 then X_ERROR on a shared qubit) may meet in one word.
+template <int W, int C, bool GMEM>
+__device__ __forceinline__ void xor_qubit_word(const Tile<W, C, GMEM> &t, uint32_t ref, uint32_t w, uint64_t mx,
+                                               uint64_t mz) {
+    if constexpr (GMEM) {
+        uint64_t *p = t.base + (uint64_t)(ref & 0xFFFFFFu) * (2 * t.gstride) + w;
+        if (mx) atomicXor(reinterpret_cast<unsigned long long *>(p), (unsigned long long)mx);
+        if (mz) atomicXor(reinterpret_cast<unsigned long long *>(p + t.gstride), (unsigned long long)mz);
+    } else {
+        uint32_t sa = t.fsa + ((ref & 0xFFFFFFu) * (2u * W) + w) * 8u;
+        if (C > 1 && (ref >> 24) != t.rank) {
+            sa = mapa_rank(sa, ref >> 24);
+            if (mx) red_xor_cluster(sa, mx);
+            if (mz) red_xor_cluster(sa + 8u * W, mz);
+        } else {
+            if (mx) red_xor_smem(sa, mx);
+            if (mz) red_xor_smem(sa + 8u * W, mz);
+        }
+    }
+}
+
+// First draws of a noise op on V words: bit i set when word i has an error.
+template <int V>
+__device__ __forceinline__ uint32_t noise_hits(const FrameArgs &a, const SmemKeys key, const DevOp op, uint32_t gw0,
+                                               uint32_t instr_off) {
+    const uint32_t opc = op.a >> 28;
+    const bool pair = opc == OP_DEP2;
+    const uint32_t tbl = pair ? (op.slot >> 24) : op.b;
+    const uint32_t slot = pair ? (op.slot & 0xFFFFFFu) : op.slot;
+    const uint32_t ti = kTagNoise | (op.instr + instr_off);
+    const uint64_t g63 = __ldg(a.geo + 64u * tbl + 63u);
+    uint32_t hits = 0;
+#pragma unroll
+    for (int i = 0; i < V; i++) {
+        const uint4 blk = philox_sched(make_uint4(0u, slot, ti, gw0 + (uint32_t)i), key);
+        if ((uint64_t)blk.x < g63) hits |= 1u << i;
+    }
+    return hits;
+}
+
+// A deferred hit: entry = (op index within the CTA's layer) << 3 | word of the
+// tile. Redraws block 0, runs the general procedure and XORs the masks in.
+template <int W, int C, bool GMEM>
+__device__ __forceinline__ void deferred_hit(const FrameArgs &a, const SmemKeys key, const Tile<W, C, GMEM> &t,
+                                             uint32_t e, uint32_t opbuf, uint32_t staged, uint32_t first,
+                                             uint32_t tile0, uint32_t instr_off) {
+    const uint32_t oi = e >> 3, w = e & 7u;
+    const uint4 ov = oi < staged ? lds128(opbuf + oi * 16u) : __ldg(reinterpret_cast<const uint4 *>(a.ops) + first + oi);
+    const uint32_t opc = ov.x >> 28;
+    const bool pair = opc == OP_DEP2;
+    const uint32_t tbl = pair ? (ov.w >> 24) : ov.y;
+    const uint32_t slot = pair ? (ov.w & 0xFFFFFFu) : ov.w;
+    const uint32_t instr = ov.z + instr_off;
+    const uint32_t gw = (uint32_t)a.word0 + tile0 + w;
+    const uint4 blk0 = philox_sched(make_uint4(0u, slot, kTagNoise | instr, gw), key);
+    uint64_t mxa, mza, mxb, mzb;
+    noise_masks_slow(opc, a.geo + 64u * tbl, key, instr, slot, gw, blk0, mxa, mza, mxb, mzb);
+    xor_qubit_word<W, C, GMEM>(t, ov.x & 0x0FFFFFFFu, w, mxa, mza);
+    if (pair) xor_qubit_word<W, C, GMEM>(t, ov.y, w, mxb, mzb);
 }
 
 __device__ __forceinline__ uint64_t to_global(const void *p) {
@@ -220,10 +443,13 @@ __device__ __forceinline__ uint64_t to_global(const void *p) {
 // above). Returns false on a malformed program or a staging timeout.
 template <int W, int C, bool GMEM>
 __device__ __forceinline__ bool run_tile(const FrameArgs &a, unsigned char *dyn, uint32_t rank, uint64_t tile) {
+    constexpr int V = VecWidth<W>::V;
     const uint32_t tile0 = (uint32_t)(tile * W);
     const uint32_t sbase = smem_addr(dyn);
     const SmemKeys key{sbase};
     const uint32_t mb = sbase + 128u;
+    const uint32_t lane = threadIdx.x & 31u;
+    const uint32_t qsa = sbase + kHitQueueOffset + (threadIdx.x >> 5) * (4u * kHitQueueCap);   // this warp's queue
     const uint32_t opbuf = sbase + kTileHeaderBytes;
     const uint32_t op_cap = a.op_cap;
     const uint32_t qlo = rank * a.Q;
@@ -252,7 +478,8 @@ __device__ __forceinline__ bool run_tile(const FrameArgs &a, unsigned char *dyn,
             sts64(sa + 8u * W, coin);
         }
     }
-    sync_tile<C>();
+    tile_arrive<C>();
+    bool waiting = true;      // an arrive of this thread awaits its wait
 
     const uint64_t ops_g = to_global(a.ops);
     uint32_t phase = 0;
@@ -274,51 +501,95 @@ __device__ __forceinline__ bool run_tile(const FrameArgs &a, unsigned char *dyn,
                 const uint32_t first = s0.y;
                 const uint32_t nops = s1.y + s1.z * s1.x - first;
                 const uint32_t staged = nops < op_cap ? nops : op_cap;
+                if (staged && threadIdx.x == 0) {
+                    fence_proxy_async_smem();
+                    mbar_arrive_expect_tx(mb, staged * 16u);
+                    bulk_g2s(opbuf, reinterpret_cast<const void *>(ops_g + (uint64_t)first * 16u), staged * 16u, mb);
+                }
+                if (waiting) {      // the previous layer is complete in every CTA of the cluster
+                    tile_wait<C>();
+                    waiting = false;
+                }
                 if (staged) {
-                    if (threadIdx.x == 0) {
-                        fence_proxy_async_smem();
-                        mbar_arrive_expect_tx(mb, staged * 16u);
-                        bulk_g2s(opbuf, reinterpret_cast<const void *>(ops_g + (uint64_t)first * 16u), staged * 16u,
-                                 mb);
-                    }
                     const uint64_t t0 = globaltimer_ns();
+                    bool timed_out = false;
                     while (!mbar_try_wait(mb, phase)) {
                         if (globaltimer_ns() - t0 > kStageTimeoutNs) {
-                            ok = false;
-                            pending = true;        // the copy may still land: wait for it before leaving
-                            atomicExch(a.status, DEV_TIMEOUT);
+                            timed_out = true;
                             break;
                         }
                     }
-                    if (!pending) phase ^= 1u;
+                    // warp-uniform outcome: the item loop below uses warp collectives
+                    if (__any_sync(0xFFFFFFFFu, timed_out)) {
+                        ok = false;
+                        pending = true;        // the copy may still land: wait for it before leaving
+                        if (lane == 0) atomicExch(a.status, DEV_TIMEOUT);
+                    } else {
+                        phase ^= 1u;
+                    }
                 }
                 if (ok) {
-                    // Items are (chain, word) pairs, numbered across this CTA's
-                    // segments of the merged layer; the W words of a chain sit
-                    // on adjacent threads.
-                    // Each segment's items are padded to whole warps, so a warp
-                    // stays inside one segment: its lanes run the same opcode at
-                    // every chain step (padding lanes replay chain 0, inactive).
+                    // Items are (chain, V-word group) pairs, numbered across this
+                    // CTA's segments of the merged layer. Each segment's items are
+                    // padded to whole warps, so a warp stays inside one segment and
+                    // all its lanes run the same chain step together (padding
+                    // lanes replay chain 0 without effect). Noise steps in a
+                    // chain's deferrable tail only take the first draw; hits are
+                    // queued per warp and resolved 32 at a time, one per lane.
+                    uint32_t qn = 0;
+                    auto flush = [&](uint32_t n) {
+                        __syncwarp();
+                        if (lane < n)
+                            deferred_hit<W, C, GMEM>(a, key, t, lds32(qsa + 4u * lane), opbuf, staged, first, tile0,
+                                                     instr_off);
+                        __syncwarp();
+                    };
                     uint32_t g = threadIdx.x, seg_start = 0;
                     for (uint32_t s = sb; s < se; s++) {
                         const uint4 sv = __ldg(reinterpret_cast<const uint4 *>(a.segs) + s);
-                        const uint32_t len = sv.x, items = sv.z * W, span = (items + 31u) & ~31u;
+                        const uint32_t len = sv.x, items = sv.z * (W / V), span = (items + 31u) & ~31u;
+                        const uint32_t dfrom = sv.w;
                         for (; g < seg_start + span; g += blockDim.x) {
                             const uint32_t it = g - seg_start;
                             const bool act = it < items;
-                            const uint32_t w = it % W;
-                            uint32_t oi = sv.y + (act ? it / W : 0u) * len - first;     // index within the layer
+                            const uint32_t wo = act ? (it % (W / V)) * V : 0u;
+                            uint32_t oi = sv.y + (act ? it / (W / V) : 0u) * len - first;     // index within the layer
                             for (uint32_t j = 0; j < len; j++, oi++) {
                                 const uint4 ov = oi < staged ? lds128(opbuf + oi * 16u)
                                                              : __ldg(reinterpret_cast<const uint4 *>(a.ops) + first + oi);
-                                frame_op<W, C, GMEM>(a, key, t, as_op(ov), w, tile0 + w, instr_off, meas_off, act);
+                                if (j < dfrom) {
+                                    if (act) frame_op<W, C, GMEM>(a, key, t, as_op(ov), wo, tile0, instr_off, meas_off);
+                                } else {
+                                    const uint32_t hits =
+                                        act ? noise_hits<V>(a, key, as_op(ov), (uint32_t)a.word0 + tile0 + wo, instr_off)
+                                            : 0u;
+#pragma unroll
+                                    for (int i = 0; i < V; i++) {
+                                        const bool h = (hits >> i) & 1u;
+                                        const uint32_t m = __ballot_sync(0xFFFFFFFFu, h);
+                                        if (m) {
+                                            const uint32_t cnt = __popc(m);
+                                            if (qn + cnt > kHitQueueCap) {
+                                                flush(qn);
+                                                qn = 0;
+                                            }
+                                            if (h)
+                                                sts32(qsa + 4u * (qn + __popc(m & ((1u << lane) - 1u))),
+                                                      (oi << 3) | (wo + (uint32_t)i));
+                                            qn += cnt;
+                                        }
+                                    }
+                                }
                             }
                         }
                         seg_start += span;
                     }
+                    if (qn) flush(qn);
                 }
             }
-            sync_tile<C>();
+            if (waiting) tile_wait<C>();
+            tile_arrive<C>();
+            waiting = true;
             pc++;
         } else if (e.kind == ENT_LOOP_BEGIN) {
             if (sp >= kMaxLoopDepth) {
@@ -349,6 +620,7 @@ __device__ __forceinline__ bool run_tile(const FrameArgs &a, unsigned char *dyn,
             }
         }
     }
+    if (waiting) tile_wait<C>();
     if (pending) {
         const uint64_t t0 = globaltimer_ns();
         while (!mbar_try_wait(mb, phase) && globaltimer_ns() - t0 < kStageTimeoutNs) {

@@ -9,6 +9,7 @@
 #include <algorithm>
 
 #include "internal.h"
+#include "kernels.h"
 
 // Device copy of a FrameProgram for one cluster size.
 struct DevFrameProgram {
@@ -60,9 +61,10 @@ inline uint32_t stage_capacity(uint32_t max_rank_ops, size_t frame_bytes, size_t
     // 1 KB of margin per CTA leaves room for the kernels' static shared memory
     const size_t half = smem_optin / 2 > 2048 ? smem_optin / 2 - 1024 : 0;
     const size_t full = smem_optin > 1024 ? smem_optin - 1024 : 0;
-    const size_t target = frame_bytes + 256 + 16 * 64 <= half ? half : full;
-    if (target <= frame_bytes + 256) return 0;
-    const size_t cap = (target - frame_bytes - 256) / 16;
+    const size_t hdr = stimgb::kTileHeaderBytes;
+    const size_t target = frame_bytes + hdr + 16 * 64 <= half ? half : full;
+    if (target <= frame_bytes + hdr) return 0;
+    const size_t cap = (target - frame_bytes - hdr) / 16;
     return (uint32_t)std::min<size_t>(cap, max_rank_ops);
 }
 

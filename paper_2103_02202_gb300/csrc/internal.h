@@ -91,7 +91,9 @@ struct HostProgram {
 // right after it on the same thread. Chains of one merged layer have disjoint
 // qubit footprints. A CTA owns the chains whose first op's first qubit is in
 // its slice; its chains of a merged layer are grouped into segments of equal
-// opcode signature (so warps run uniform code).
+// opcode signature (so warps run uniform code). Noise ops at the end of a
+// chain (defer_from onwards) touch nothing the chain reads later, and their
+// error masks commute, so the kernel may apply them after the chain.
 //
 // Entries mirror HostProgram::prog except that folded LAYER entries are
 // removed; a LAYER's op_begin indexes rank_tab, whose C + 1 values bound
@@ -105,10 +107,10 @@ struct HostProgram {
 //   instr: flattened instruction ordinal of the first loop iteration
 //   slot:  target slot; DEPOLARIZE2 keeps its table index in bits 24..31
 struct FrameSeg {
-    uint32_t len;       // ops per chain
-    uint32_t op_begin;  // first op of the first chain
-    uint32_t count;     // chains
-    uint32_t pad;
+    uint32_t len;         // ops per chain
+    uint32_t op_begin;    // first op of the first chain
+    uint32_t count;       // chains
+    uint32_t defer_from;  // chain steps >= defer_from are all noise ops
 };
 
 struct FrameProgram {

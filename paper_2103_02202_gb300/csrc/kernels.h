@@ -31,10 +31,17 @@ struct FrameArgs {
     uint32_t op_cap;           // ops of one layer staged in shared memory (rest read from global)
 };
 
-// Dynamic shared memory of a frame tile: a 256-byte header (round keys,
-// staging mbarrier), op_cap staged ops of 16 bytes, then (shared layout) the
-// frame rows of Q qubits x 2W words.
-constexpr uint32_t kTileHeaderBytes = 256;
+// Dynamic shared memory of a frame tile: a header (round keys, staging
+// mbarrier, then 32 queues of 32 deferred noise hits, one per warp), op_cap
+// staged ops of 16 bytes, then (shared layout) the frame rows of Q qubits x
+// 2W words.
+constexpr uint32_t kHitQueueOffset = 256;
+constexpr uint32_t kHitQueueCap = 32;          // entries per warp
+constexpr uint32_t kTileHeaderBytes = kHitQueueOffset + 32 * kHitQueueCap * 4;
+
+// Largest CTA of a frame kernel with W words per tile: threads that apply ops
+// to two or four words at once need more registers.
+constexpr int frame_max_threads(int W) { return W >= 4 ? 512 : W == 2 ? 768 : 1024; }
 inline size_t tile_smem_bytes(uint32_t Q, int W, uint32_t op_cap, bool gmem) {
     return kTileHeaderBytes + 16 * (size_t)op_cap + (gmem ? 0 : (size_t)Q * 2 * W * 8);
 }
