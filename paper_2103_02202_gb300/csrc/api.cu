@@ -130,9 +130,22 @@ int frame_program(stim_circuit *c, int C, const DevFrameProgram **out) {
         if (fp.max_rank_ops >= (1u << 29))
             return fail(STIM_E_UNSUPPORTED, "a layer holds 2^29 or more ops for one CTA");
         int r;
-        if ((r = upload(&d.prog, fp.prog, "upload frame program")) != STIM_OK) return r;
-        if ((r = upload(&d.rank_tab, fp.rank_tab, "upload frame program")) != STIM_OK) return r;
-        if ((r = upload(&d.segs, fp.segs, "upload frame program")) != STIM_OK) return r;
+        // prog | rank_tab | segs, each starting on a 16-byte boundary
+        auto pad16 = [](size_t x) { return (x + 15) & ~(size_t)15; };
+        const size_t off_rt = pad16(fp.prog.size() * sizeof(ProgEntry));
+        const size_t off_sg = off_rt + pad16(fp.rank_tab.size() * sizeof(uint32_t));
+        const size_t total = off_sg + pad16(fp.segs.size() * sizeof(FrameSeg));
+        if (total >= (1ull << 32)) return fail(STIM_E_UNSUPPORTED, "frame program metadata above 4 GiB");
+        std::vector<unsigned char> meta(std::max<size_t>(total, 16), 0);
+        if (!fp.prog.empty()) std::memcpy(meta.data(), fp.prog.data(), fp.prog.size() * sizeof(ProgEntry));
+        if (!fp.rank_tab.empty())
+            std::memcpy(meta.data() + off_rt, fp.rank_tab.data(), fp.rank_tab.size() * sizeof(uint32_t));
+        if (!fp.segs.empty()) std::memcpy(meta.data() + off_sg, fp.segs.data(), fp.segs.size() * sizeof(FrameSeg));
+        if ((r = upload(&d.meta, meta, "upload frame program")) != STIM_OK) return r;
+        d.meta_bytes = (uint32_t)meta.size();
+        d.prog = reinterpret_cast<ProgEntry *>(d.meta);
+        d.rank_tab = reinterpret_cast<uint32_t *>(d.meta + off_rt);
+        d.segs = reinterpret_cast<FrameSeg *>(d.meta + off_sg);
         if ((r = upload(&d.ops, fp.ops, "upload frame program")) != STIM_OK) return r;
         d.Q = fp.Q;
         d.nprog = (uint32_t)fp.prog.size();
@@ -277,6 +290,11 @@ int choose_tile(uint32_t n, uint64_t nwords, int sms, size_t smem_optin, const s
         t.W = (int)hW;
         if (!t.gmem && slice(t.C) * t.W + kTileHeaderBytes > smem_optin)
             return fail(STIM_E_INVALID_ARG, "tile hint: words_per_cta does not fit shared memory");
+    } else if (t.C == 1 && !t.gmem && n >= 1024 && nwords >= (uint64_t)8 * sms &&
+               slice(1) * 8 + kTileHeaderBytes + kMetaCap + 1024 <= smem_optin) {
+        // a large circuit whose 8-word tile fits one CTA: threads apply each op
+        // to 4 words (independent Philox streams in flight), two per chain
+        t.W = 8;
     } else {
         // one 64-shot word per tile: a thread's Philox chains stay independent
         t.W = t.gmem ? 2 : 1;
@@ -287,6 +305,8 @@ int choose_tile(uint32_t n, uint64_t nwords, int sms, size_t smem_optin, const s
         t.threads = hint->threads;
     } else if (t.gmem) {
         t.threads = 256;
+    } else if (t.W >= 4) {
+        t.threads = 512;
     } else {
         const size_t per_cta = slice(t.C) * t.W + 1024;
         const size_t per_sm = (size_t)smem_optin + 1024;
@@ -341,9 +361,11 @@ int launch_sampling(stim_circuit *c, uint64_t num_shots, uint64_t seed, uint64_t
         int smem_optin = 0;
         STIMGB_CK(cudaDeviceGetAttribute(&smem_optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, c->device), "attr");
         const size_t frame_bytes = gmem ? 0 : (size_t)fp->Q * W * 16;
-        a.op_cap = stage_capacity(fp->max_rank_ops, frame_bytes, (size_t)smem_optin);
+        a.meta_bytes = fp->meta_bytes;
+        a.meta_region = meta_region_for(fp->meta_bytes);
+        a.op_cap = stage_capacity(fp->max_rank_ops, frame_bytes + a.meta_region, (size_t)smem_optin);
         ProfScope ps(STIM_KERNEL_FRAME, st);
-        STIMGB_CK(launch_frame(a, W, C, gmem, (uint32_t)grid, threads, tile_smem_bytes(fp->Q, W, a.op_cap, gmem), st),
+        STIMGB_CK(launch_frame(a, W, C, gmem, (uint32_t)grid, threads, tile_smem_bytes(fp->Q, W, a.op_cap, gmem, a.meta_region), st),
                   "frame kernel");
     }
     if (det && D > 0) {
@@ -457,9 +479,7 @@ void stim_free(stim_circuit *c) {
         cudaFree(c->d_tr);
         cudaFree(c->d_gframe);
         for (DevFrameProgram &d : c->fprog) {
-            cudaFree(d.prog);
-            cudaFree(d.rank_tab);
-            cudaFree(d.segs);
+            cudaFree(d.meta);
             cudaFree(d.ops);
         }
         if (cur >= 0 && cur != c->device) cudaSetDevice(cur);

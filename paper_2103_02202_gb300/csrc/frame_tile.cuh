@@ -7,10 +7,12 @@
 //   [0, 80)                  Philox round keys of the seed
 //   [128, 136)               mbarrier of the op-staging copy
 //   [256, H)                 per-warp queues of deferred noise hits
-//   [H, H + 16 op_cap)       the current layer's ops of this CTA, copied in
+//   [H, H + R)               program metadata (prog | rank_tab | segs) when it
+//                            fits the R = meta_region bytes reserved for it
+//   [H + R, + 16 op_cap)     the current layer's ops of this CTA, copied in
 //                            by the TMA engine (cp.async.bulk) at the start of
 //                            the layer
-//   [H + 16 op_cap, ...)     frame rows (shared-memory layout)
+//   [.., ...)                frame rows (shared-memory layout)
 // Frame layout (W 64-shot words per tile): each qubit owns a row of 2W words,
 // its X words then its Z words,
 //     shared memory:  row(q) = q * 2W;  X = row[w], Z = row[W + w]
@@ -450,7 +452,7 @@ __device__ __forceinline__ bool run_tile(const FrameArgs &a, unsigned char *dyn,
     const uint32_t mb = sbase + 128u;
     const uint32_t lane = threadIdx.x & 31u;
     const uint32_t qsa = sbase + kHitQueueOffset + (threadIdx.x >> 5) * (4u * kHitQueueCap);   // this warp's queue
-    const uint32_t opbuf = sbase + kTileHeaderBytes;
+    const uint32_t opbuf = sbase + kTileHeaderBytes + a.meta_region;
     const uint32_t op_cap = a.op_cap;
     const uint32_t qlo = rank * a.Q;
     const uint32_t nq = a.n > qlo ? min(a.Q, a.n - qlo) : 0u;
@@ -460,6 +462,18 @@ __device__ __forceinline__ bool run_tile(const FrameArgs &a, unsigned char *dyn,
     t.fsa = opbuf + 16u * op_cap;
     t.base = a.gframe + tile0;
     write_round_keys(reinterpret_cast<uint32_t *>(dyn), Key{(uint32_t)a.seed, (uint32_t)(a.seed >> 32)});
+    // program metadata (prog | rank_tab | segs): a shared copy when it fits
+    const unsigned char *meta_g = reinterpret_cast<const unsigned char *>(a.prog);
+    const bool meta_shared = a.meta_bytes != 0 && a.meta_bytes <= a.meta_region;
+    const unsigned char *meta = meta_shared ? dyn + kTileHeaderBytes : meta_g;
+    if (meta_shared) {
+        for (uint32_t i = threadIdx.x; i < a.meta_bytes / 16u; i += blockDim.x)
+            reinterpret_cast<uint4 *>(dyn + kTileHeaderBytes)[i] = __ldg(reinterpret_cast<const uint4 *>(meta_g) + i);
+    }
+    const ProgEntry *prog = reinterpret_cast<const ProgEntry *>(meta);
+    const uint32_t *rank_tab =
+        reinterpret_cast<const uint32_t *>(meta + (reinterpret_cast<const unsigned char *>(a.rank_tab) - meta_g));
+    const uint4 *segs = reinterpret_cast<const uint4 *>(meta + (reinterpret_cast<const unsigned char *>(a.segs) - meta_g));
     if (threadIdx.x == 0) {
         mbar_init(mb, 1);
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
@@ -490,14 +504,14 @@ __device__ __forceinline__ bool run_tile(const FrameArgs &a, unsigned char *dyn,
     int sp = 0;
     uint32_t pc = 0;
     while (pc < a.nprog) {
-        const ProgEntry e = a.prog[pc];
+        const ProgEntry e = prog[pc];
         if (e.kind == ENT_LAYER) {
-            const uint32_t sb = __ldg(a.rank_tab + e.op_begin + rank);
-            const uint32_t se = __ldg(a.rank_tab + e.op_begin + rank + 1);
+            const uint32_t sb = rank_tab[e.op_begin + rank];
+            const uint32_t se = rank_tab[e.op_begin + rank + 1];
             if (sb < se && ok) {
                 // this CTA's ops of the layer are contiguous: stage them in shared memory
-                const uint4 s0 = __ldg(reinterpret_cast<const uint4 *>(a.segs) + sb);
-                const uint4 s1 = __ldg(reinterpret_cast<const uint4 *>(a.segs) + se - 1);
+                const uint4 s0 = segs[sb];
+                const uint4 s1 = segs[se - 1];
                 const uint32_t first = s0.y;
                 const uint32_t nops = s1.y + s1.z * s1.x - first;
                 const uint32_t staged = nops < op_cap ? nops : op_cap;
@@ -546,7 +560,7 @@ __device__ __forceinline__ bool run_tile(const FrameArgs &a, unsigned char *dyn,
                     };
                     uint32_t g = threadIdx.x, seg_start = 0;
                     for (uint32_t s = sb; s < se; s++) {
-                        const uint4 sv = __ldg(reinterpret_cast<const uint4 *>(a.segs) + s);
+                        const uint4 sv = segs[s];
                         const uint32_t len = sv.x, items = sv.z * (W / V), span = (items + 31u) & ~31u;
                         const uint32_t dfrom = sv.w;
                         for (; g < seg_start + span; g += blockDim.x) {

@@ -17,6 +17,10 @@ struct DevFrameProgram {
     uint32_t Q = 0;
     uint32_t nprog = 0;
     uint32_t max_rank_ops = 0;
+    // prog, rank_tab and segs live in one allocation (meta, meta_bytes, a
+    // multiple of 16) that kernels copy into shared memory when it is small
+    unsigned char *meta = nullptr;
+    uint32_t meta_bytes = 0;
     stimgb::ProgEntry *prog = nullptr;
     uint32_t *rank_tab = nullptr;
     stimgb::FrameSeg *segs = nullptr;
