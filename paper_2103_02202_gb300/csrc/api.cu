@@ -358,14 +358,10 @@ int launch_sampling(stim_circuit *c, uint64_t num_shots, uint64_t seed, uint64_t
         a.gstride = gstride;
         a.status = c->d_status;
         a.seed = seed;
-        int smem_optin = 0;
-        STIMGB_CK(cudaDeviceGetAttribute(&smem_optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, c->device), "attr");
-        const size_t frame_bytes = gmem ? 0 : (size_t)fp->Q * W * 16;
         a.meta_bytes = fp->meta_bytes;
         a.meta_region = meta_region_for(fp->meta_bytes);
-        a.op_cap = stage_capacity(fp->max_rank_ops, frame_bytes + a.meta_region, (size_t)smem_optin);
         ProfScope ps(STIM_KERNEL_FRAME, st);
-        STIMGB_CK(launch_frame(a, W, C, gmem, (uint32_t)grid, threads, tile_smem_bytes(fp->Q, W, a.op_cap, gmem, a.meta_region), st),
+        STIMGB_CK(launch_frame(a, W, C, gmem, (uint32_t)grid, threads, tile_smem_bytes(fp->Q, W, gmem, a.meta_region), st),
                   "frame kernel");
     }
     if (det && D > 0) {

@@ -208,7 +208,6 @@ struct stim_batch {
     bool tuned = false;
     std::string tune_key;
     bool hinted = false;
-    uint32_t op_cap = 0;
     uint32_t meta_region = 0;              // shared bytes for the largest program metadata that fits
     std::vector<uint8_t> out_sig;          // which outputs the captured graph serves
 };
@@ -288,8 +287,8 @@ uint32_t batch_max_slice(const stim_batch *b, int C) {
 }
 
 // Dynamic shared memory of the persistent kernel: descriptor + tile region.
-size_t batch_smem(const stim_batch *b, int W, int C, uint32_t op_cap, uint32_t meta_region) {
-    return kDescBytes + tile_smem_bytes(batch_max_slice(b, C), W, op_cap, false, meta_region);
+size_t batch_smem(const stim_batch *b, int W, int C, uint32_t meta_region) {
+    return kDescBytes + tile_smem_bytes(batch_max_slice(b, C), W, false, meta_region);
 }
 
 }  // namespace
@@ -339,7 +338,6 @@ int fill_descs(stim_batch *b, const uint64_t *seeds, const uint64_t *offsets, ui
         a.rec_stride = nwords;
         a.status = c->d_status;
         a.seed = seeds[i];
-        a.op_cap = b->op_cap;
         a.meta_bytes = fp->meta_bytes;
         a.meta_region = b->meta_region;
         b->h_descs[i] = a;
@@ -388,24 +386,19 @@ int configure(stim_batch *b, int W, uint32_t threads) {
     b->threads = threads;
     int smem_optin = 0;
     STIMGB_BCK(cudaDeviceGetAttribute(&smem_optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, b->device), "attr");
-    uint32_t max_ops = 0, meta_region = 0;
+    uint32_t meta_region = 0;
     for (stim_circuit *c : b->cs) {
         const DevFrameProgram *fp;
         int r = stimgb_frame_program(c, b->C, &fp);
         if (r != STIM_OK) return r;
-        max_ops = std::max(max_ops, fp->max_rank_ops);
         meta_region = std::max(meta_region, meta_region_for(fp->meta_bytes));
     }
+    // the metadata region is part of this shape's shared memory: a circuit
+    // larger than it reads its metadata from global memory
+    if (batch_smem(b, W, b->C, meta_region) > (size_t)smem_optin) meta_region = 0;
     b->meta_region = meta_region;
-    const size_t frame_bytes = (size_t)batch_max_slice(b, b->C) * W * 16 + kDescBytes + meta_region;
-    b->op_cap = stage_capacity(max_ops, frame_bytes, (size_t)smem_optin);
-    b->smem = batch_smem(b, W, b->C, b->op_cap, meta_region);
-    // descriptors must never promise more staged ops (or metadata) than this
-    // shape's shared memory holds
-    for (size_t i = 0; i < b->k; i++) {
-        b->h_descs[i].op_cap = b->op_cap;
-        b->h_descs[i].meta_region = meta_region;
-    }
+    b->smem = batch_smem(b, W, b->C, meta_region);
+    for (size_t i = 0; i < b->k; i++) b->h_descs[i].meta_region = meta_region;
     const int ctas = max_resident_ctas(W, b->C, threads, b->smem, sms);
     if (ctas <= 0) return bfail(STIM_E_UNSUPPORTED, "batch: tile shape does not fit an SM");
     b->blocks = (uint32_t)ctas;
@@ -432,7 +425,7 @@ int autotune(stim_batch *b, cudaStream_t st) {
     STIMGB_BCK(cudaEventCreate(&e0), "event");
     STIMGB_BCK(cudaEventCreate(&e1), "event");
     for (int w : cand_w) {
-        if (batch_smem(b, w, b->C, 0, 0) > (size_t)smem_optin) continue;
+        if (batch_smem(b, w, b->C, 0) > (size_t)smem_optin) continue;
         for (uint32_t t : cand_t) {
             if (configure(b, w, t) != STIM_OK) continue;
             const uint32_t lim = std::min<uint32_t>(b->nitems, std::max<uint32_t>(4 * b->blocks / b->C, 1));

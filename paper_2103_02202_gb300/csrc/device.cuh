@@ -68,33 +68,6 @@ __device__ __forceinline__ uint4 philox_sched(uint4 c, SmemKeys k) {
     return c;
 }
 
-// ---- mbarrier / bulk async copy (TMA engine, 1-D) ----
-__device__ __forceinline__ void mbar_init(uint32_t mb, uint32_t count) {
-    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(mb), "r"(count) : "memory");
-}
-__device__ __forceinline__ void mbar_arrive_expect_tx(uint32_t mb, uint32_t bytes) {
-    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(mb), "r"(bytes) : "memory");
-}
-__device__ __forceinline__ bool mbar_try_wait(uint32_t mb, uint32_t parity) {
-    uint32_t ok;
-    asm volatile(
-        "{\n\t.reg .pred p;\n\t"
-        "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
-        "selp.u32 %0, 1, 0, p;\n\t}"
-        : "=r"(ok)
-        : "r"(mb), "r"(parity)
-        : "memory");
-    return ok != 0;
-}
-__device__ __forceinline__ void fence_proxy_async_smem() { asm volatile("fence.proxy.async.shared::cta;" ::: "memory"); }
-// Copies `bytes` (multiple of 16, both addresses 16-byte aligned) from global
-// memory into this CTA's shared memory; completion is signalled on mbarrier mb.
-__device__ __forceinline__ void bulk_g2s(uint32_t dst, const void *src, uint32_t bytes, uint32_t mb) {
-    asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(dst),
-                 "l"(src), "r"(bytes), "r"(mb)
-                 : "memory");
-}
-
 // Counter layout: (draw block, slot, tag << 28 | instruction ordinal, 64-shot word).
 constexpr uint32_t kTagNoise = 0u << 28;
 constexpr uint32_t kTagCollapse = 1u << 28;

@@ -5,14 +5,10 @@
 // Dynamic shared memory of one tile (byte offsets from the region start;
 // H = kTileHeaderBytes):
 //   [0, 80)                  Philox round keys of the seed
-//   [128, 136)               mbarrier of the op-staging copy
 //   [256, H)                 per-warp queues of deferred noise hits
 //   [H, H + R)               program metadata (prog | rank_tab | segs) when it
 //                            fits the R = meta_region bytes reserved for it
-//   [H + R, + 16 op_cap)     the current layer's ops of this CTA, copied in
-//                            by the TMA engine (cp.async.bulk) at the start of
-//                            the layer
-//   [.., ...)                frame rows (shared-memory layout)
+//   [H + R, ...)             frame rows (shared-memory layout)
 // Frame layout (W 64-shot words per tile): each qubit owns a row of 2W words,
 // its X words then its Z words,
 //     shared memory:  row(q) = q * 2W;  X = row[w], Z = row[W + w]
@@ -31,15 +27,12 @@ namespace cg = cooperative_groups;
 namespace stimgb {
 namespace frame_detail {
 
-constexpr uint64_t kStageTimeoutNs = 2000000000ull;   // bounded wait for a staging copy
 
 __device__ __forceinline__ DevOp as_op(uint4 v) { return DevOp{v.x, v.y, v.z, v.w}; }
 
 // Layer barrier of the tile, split in two halves: arrive when this thread's
 // frame writes of the layer are done, wait before the next layer touches the
-// frame. The next layer's op copy is issued in between, so the staging latency
-// overlaps the cluster barrier. The CTA barrier in the arrive half also frees
-// the staging buffer for that copy.
+// frame. The loads of the next layer's first ops are issued in between.
 template <int C>
 __device__ __forceinline__ void tile_arrive() {
     __syncthreads();
@@ -109,45 +102,41 @@ struct Qubit;
 template <int W, int C>
 struct Qubit<W, C, false> {
     static constexpr int V = VecWidth<W>::V;
-    uint32_t sa;         // X word wo of the qubit (shared::cta, or shared::cluster when remote)
-    bool remote;
+    // X word wo of the qubit: a shared::cta address (C == 1) or, in a
+    // cluster, the shared::cluster address of the owning CTA's copy (mapa),
+    // so local and remote qubits take the same path
+    uint32_t sa;
 
     __device__ __forceinline__ Qubit(const Tile<W, C, false> &t, uint32_t ref, uint32_t wo) {
         sa = t.fsa + ((ref & 0xFFFFFFu) * (2u * W) + wo) * 8u;
-        remote = false;
-        if constexpr (C > 1) {
-            if ((ref >> 24) != t.rank) {
-                remote = true;
-                sa = mapa_rank(sa, ref >> 24);
-            }
-        }
+        if constexpr (C > 1) sa = mapa_rank(sa, ref >> 24);
     }
     __device__ __forceinline__ void ld(uint32_t off, uint64_t (&v)[V]) const {
         if constexpr (V == 1) {
-            v[0] = (C > 1 && remote) ? ldc64(sa + off) : lds64(sa + off);
+            v[0] = C > 1 ? ldc64(sa + off) : lds64(sa + off);
         } else {
 #pragma unroll
             for (int i = 0; i < V / 2; i++) {
-                if (C > 1 && remote) ldc_v2(sa + off + 16u * i, v[2 * i], v[2 * i + 1]);
+                if constexpr (C > 1) ldc_v2(sa + off + 16u * i, v[2 * i], v[2 * i + 1]);
                 else lds_v2(sa + off + 16u * i, v[2 * i], v[2 * i + 1]);
             }
         }
     }
     __device__ __forceinline__ void st(uint32_t off, const uint64_t (&v)[V]) const {
         if constexpr (V == 1) {
-            if (C > 1 && remote) stc64(sa + off, v[0]);
+            if constexpr (C > 1) stc64(sa + off, v[0]);
             else sts64(sa + off, v[0]);
         } else {
 #pragma unroll
             for (int i = 0; i < V / 2; i++) {
-                if (C > 1 && remote) stc_v2(sa + off + 16u * i, v[2 * i], v[2 * i + 1]);
+                if constexpr (C > 1) stc_v2(sa + off + 16u * i, v[2 * i], v[2 * i + 1]);
                 else sts_v2(sa + off + 16u * i, v[2 * i], v[2 * i + 1]);
             }
         }
     }
     __device__ __forceinline__ void load(const Tile<W, C, false> &, Planes<V> &p) const {
         if constexpr (W == 1) {      // X and Z of the word are adjacent: one 16-byte access
-            if (C > 1 && remote) ldc_v2(sa, p.x[0], p.z[0]);
+            if constexpr (C > 1) ldc_v2(sa, p.x[0], p.z[0]);
             else lds_v2(sa, p.x[0], p.z[0]);
         } else {
             ld(0, p.x);
@@ -156,7 +145,7 @@ struct Qubit<W, C, false> {
     }
     __device__ __forceinline__ void store(const Tile<W, C, false> &, const Planes<V> &p) const {
         if constexpr (W == 1) {
-            if (C > 1 && remote) stc_v2(sa, p.x[0], p.z[0]);
+            if constexpr (C > 1) stc_v2(sa, p.x[0], p.z[0]);
             else sts_v2(sa, p.x[0], p.z[0]);
         } else {
             st(0, p.x);
@@ -383,7 +372,7 @@ __device__ __forceinline__ void xor_qubit_word(const Tile<W, C, GMEM> &t, uint32
         if (mz) atomicXor(reinterpret_cast<unsigned long long *>(p + t.gstride), (unsigned long long)mz);
     } else {
         uint32_t sa = t.fsa + ((ref & 0xFFFFFFu) * (2u * W) + w) * 8u;
-        if (C > 1 && (ref >> 24) != t.rank) {
+        if constexpr (C > 1) {
             sa = mapa_rank(sa, ref >> 24);
             if (mx) red_xor_cluster(sa, mx);
             if (mz) red_xor_cluster(sa + 8u * W, mz);
@@ -417,11 +406,11 @@ __device__ __forceinline__ uint32_t noise_hits(const FrameArgs &a, const SmemKey
 // tile. Redraws block 0, runs the general procedure and XORs the masks in.
 template <int W, int C, bool GMEM>
 __device__ __forceinline__ void deferred_hit(const FrameArgs &a, const SmemKeys key, const Tile<W, C, GMEM> &t,
-                                             uint32_t e, uint32_t opbuf, uint32_t staged, uint32_t first,
-                                             uint32_t tile0, uint32_t instr_off) {
+                                             uint32_t e, uint32_t first, uint32_t tile0, uint32_t instr_off) {
     const uint32_t oi = e >> 3, w = e & 7u;
-    const uint4 ov = oi < staged ? lds128(opbuf + oi * 16u) : __ldg(reinterpret_cast<const uint4 *>(a.ops) + first + oi);
+    const uint4 ov = __ldg(reinterpret_cast<const uint4 *>(a.ops) + first + oi);
     const uint32_t opc = ov.x >> 28;
+    if (opc < OP_XERR) return;      // only noise ops are queued
     const bool pair = opc == OP_DEP2;
     const uint32_t tbl = pair ? (ov.w >> 24) : ov.y;
     const uint32_t slot = pair ? (ov.w & 0xFFFFFFu) : ov.w;
@@ -442,24 +431,21 @@ __device__ __forceinline__ uint64_t to_global(const void *p) {
 
 // Propagates the frames of one tile (W words, this CTA's qubit slice) through
 // the whole program. dyn = start of the tile's dynamic shared memory (layout
-// above). Returns false on a malformed program or a staging timeout.
+// above). Returns false on a malformed program.
 template <int W, int C, bool GMEM>
 __device__ __forceinline__ bool run_tile(const FrameArgs &a, unsigned char *dyn, uint32_t rank, uint64_t tile) {
     constexpr int V = VecWidth<W>::V;
     const uint32_t tile0 = (uint32_t)(tile * W);
     const uint32_t sbase = smem_addr(dyn);
     const SmemKeys key{sbase};
-    const uint32_t mb = sbase + 128u;
     const uint32_t lane = threadIdx.x & 31u;
     const uint32_t qsa = sbase + kHitQueueOffset + (threadIdx.x >> 5) * (4u * kHitQueueCap);   // this warp's queue
-    const uint32_t opbuf = sbase + kTileHeaderBytes + a.meta_region;
-    const uint32_t op_cap = a.op_cap;
     const uint32_t qlo = rank * a.Q;
     const uint32_t nq = a.n > qlo ? min(a.Q, a.n - qlo) : 0u;
     Tile<W, C, GMEM> t;
     t.rank = rank;
     t.gstride = a.gstride;
-    t.fsa = opbuf + 16u * op_cap;
+    t.fsa = sbase + kTileHeaderBytes + a.meta_region;
     t.base = a.gframe + tile0;
     write_round_keys(reinterpret_cast<uint32_t *>(dyn), Key{(uint32_t)a.seed, (uint32_t)(a.seed >> 32)});
     // program metadata (prog | rank_tab | segs): a shared copy when it fits
@@ -474,11 +460,7 @@ __device__ __forceinline__ bool run_tile(const FrameArgs &a, unsigned char *dyn,
     const uint32_t *rank_tab =
         reinterpret_cast<const uint32_t *>(meta + (reinterpret_cast<const unsigned char *>(a.rank_tab) - meta_g));
     const uint4 *segs = reinterpret_cast<const uint4 *>(meta + (reinterpret_cast<const unsigned char *>(a.segs) - meta_g));
-    if (threadIdx.x == 0) {
-        mbar_init(mb, 1);
-        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
-    }
-    __syncthreads();   // round keys visible before the first draw
+    __syncthreads();   // round keys and metadata visible before use
     for (uint32_t i = threadIdx.x; i < nq * W; i += blockDim.x) {
         const uint32_t l = i / W, w = i % W;
         const uint64_t coin = half_mask(key, kTagInit, qlo + l, (uint32_t)a.word0 + tile0 + w);
@@ -493,11 +475,9 @@ __device__ __forceinline__ bool run_tile(const FrameArgs &a, unsigned char *dyn,
         }
     }
     tile_arrive<C>();
-    bool waiting = true;      // an arrive of this thread awaits its wait
 
-    const uint64_t ops_g = to_global(a.ops);
-    uint32_t phase = 0;
-    bool ok = true, pending = false;
+    const uint4 *ops = reinterpret_cast<const uint4 *>(a.ops);
+    bool ok = true;
     uint32_t instr_off = 0, meas_off = 0;
     uint32_t loop_pc[kMaxLoopDepth];
     uint32_t loop_iter[kMaxLoopDepth];
@@ -508,102 +488,67 @@ __device__ __forceinline__ bool run_tile(const FrameArgs &a, unsigned char *dyn,
         if (e.kind == ENT_LAYER) {
             const uint32_t sb = rank_tab[e.op_begin + rank];
             const uint32_t se = rank_tab[e.op_begin + rank + 1];
+            tile_wait<C>();      // the previous layer is complete in every CTA of the cluster
             if (sb < se && ok) {
-                // this CTA's ops of the layer are contiguous: stage them in shared memory
-                const uint4 s0 = segs[sb];
-                const uint4 s1 = segs[se - 1];
-                const uint32_t first = s0.y;
-                const uint32_t nops = s1.y + s1.z * s1.x - first;
-                const uint32_t staged = nops < op_cap ? nops : op_cap;
-                if (staged && threadIdx.x == 0) {
-                    fence_proxy_async_smem();
-                    mbar_arrive_expect_tx(mb, staged * 16u);
-                    bulk_g2s(opbuf, reinterpret_cast<const void *>(ops_g + (uint64_t)first * 16u), staged * 16u, mb);
-                }
-                if (waiting) {      // the previous layer is complete in every CTA of the cluster
-                    tile_wait<C>();
-                    waiting = false;
-                }
-                if (staged) {
-                    const uint64_t t0 = globaltimer_ns();
-                    bool timed_out = false;
-                    while (!mbar_try_wait(mb, phase)) {
-                        if (globaltimer_ns() - t0 > kStageTimeoutNs) {
-                            timed_out = true;
-                            break;
-                        }
-                    }
-                    // warp-uniform outcome: the item loop below uses warp collectives
-                    if (__any_sync(0xFFFFFFFFu, timed_out)) {
-                        ok = false;
-                        pending = true;        // the copy may still land: wait for it before leaving
-                        if (lane == 0) atomicExch(a.status, DEV_TIMEOUT);
-                    } else {
-                        phase ^= 1u;
-                    }
-                }
-                if (ok) {
-                    // Items are (chain, V-word group) pairs, numbered across this
-                    // CTA's segments of the merged layer. Each segment's items are
-                    // padded to whole warps, so a warp stays inside one segment and
-                    // all its lanes run the same chain step together (padding
-                    // lanes replay chain 0 without effect). Noise steps in a
-                    // chain's deferrable tail only take the first draw; hits are
-                    // queued per warp and resolved 32 at a time, one per lane.
-                    uint32_t qn = 0;
-                    auto flush = [&](uint32_t n) {
-                        __syncwarp();
-                        if (lane < n)
-                            deferred_hit<W, C, GMEM>(a, key, t, lds32(qsa + 4u * lane), opbuf, staged, first, tile0,
-                                                     instr_off);
-                        __syncwarp();
-                    };
-                    uint32_t g = threadIdx.x, seg_start = 0;
-                    for (uint32_t s = sb; s < se; s++) {
-                        const uint4 sv = segs[s];
-                        const uint32_t len = sv.x, items = sv.z * (W / V), span = (items + 31u) & ~31u;
-                        const uint32_t dfrom = sv.w;
-                        for (; g < seg_start + span; g += blockDim.x) {
-                            const uint32_t it = g - seg_start;
-                            const bool act = it < items;
-                            const uint32_t wo = act ? (it % (W / V)) * V : 0u;
-                            uint32_t oi = sv.y + (act ? it / (W / V) : 0u) * len - first;     // index within the layer
-                            for (uint32_t j = 0; j < len; j++, oi++) {
-                                const uint4 ov = oi < staged ? lds128(opbuf + oi * 16u)
-                                                             : __ldg(reinterpret_cast<const uint4 *>(a.ops) + first + oi);
-                                if (j < dfrom) {
-                                    if (act) frame_op<W, C, GMEM>(a, key, t, as_op(ov), wo, tile0, instr_off, meas_off);
-                                } else {
-                                    const uint32_t hits =
-                                        act ? noise_hits<V>(a, key, as_op(ov), (uint32_t)a.word0 + tile0 + wo, instr_off)
-                                            : 0u;
+                // Items are (chain, V-word group) pairs, numbered across this
+                // CTA's segments of the merged layer. Each segment's items are
+                // padded to whole warps, so a warp stays inside one segment and
+                // all its lanes run the same chain step together (padding lanes
+                // replay chain 0 without effect). Noise steps in a chain's
+                // deferrable tail only take the first draw; hits are queued per
+                // warp and resolved 32 at a time, one per lane.
+                const uint32_t first = segs[sb].y;
+                uint32_t qn = 0;
+                auto flush = [&](uint32_t n) {
+                    __syncwarp();
+                    if (lane < n) deferred_hit<W, C, GMEM>(a, key, t, lds32(qsa + 4u * lane), first, tile0, instr_off);
+                    __syncwarp();
+                };
+                uint32_t g = threadIdx.x, seg_start = 0;
+                for (uint32_t s = sb; s < se; s++) {
+                    const uint4 sv = segs[s];
+                    const uint32_t len = sv.x, items = sv.z * (W / V), span = (items + 31u) & ~31u;
+                    const uint32_t dfrom = sv.w;
+                    for (; g < seg_start + span; g += blockDim.x) {
+                        const uint32_t it = g - seg_start;
+                        const bool act = it < items;
+                        const uint32_t wo = act ? (it % (W / V)) * V : 0u;
+                        const uint32_t op0 = sv.y + (act ? it / (W / V) : 0u) * len;
+                        uint4 nxt = __ldg(ops + op0);
+                        for (uint32_t j = 0; j < len; j++) {
+                            const uint4 ov = nxt;
+                            if (j + 1 < len) nxt = __ldg(ops + op0 + j + 1);     // one op ahead
+                            if (j < dfrom) {
+                                if (act) frame_op<W, C, GMEM>(a, key, t, as_op(ov), wo, tile0, instr_off, meas_off);
+                            } else {
+                                const uint32_t hits =
+                                    act ? noise_hits<V>(a, key, as_op(ov), (uint32_t)a.word0 + tile0 + wo, instr_off)
+                                        : 0u;
+                                const uint32_t oi = op0 + j - first;       // index within the CTA's layer
 #pragma unroll
-                                    for (int i = 0; i < V; i++) {
-                                        const bool h = (hits >> i) & 1u;
-                                        const uint32_t m = __ballot_sync(0xFFFFFFFFu, h);
-                                        if (m) {
-                                            const uint32_t cnt = __popc(m);
-                                            if (qn + cnt > kHitQueueCap) {
-                                                flush(qn);
-                                                qn = 0;
-                                            }
-                                            if (h)
-                                                sts32(qsa + 4u * (qn + __popc(m & ((1u << lane) - 1u))),
-                                                      (oi << 3) | (wo + (uint32_t)i));
-                                            qn += cnt;
+                                for (int i = 0; i < V; i++) {
+                                    const bool h = (hits >> i) & 1u;
+                                    const uint32_t m = __ballot_sync(0xFFFFFFFFu, h);
+                                    if (m) {
+                                        const uint32_t cnt = __popc(m);
+                                        if (qn + cnt > kHitQueueCap) {
+                                            flush(qn);
+                                            qn = 0;
                                         }
+                                        if (h)
+                                            sts32(qsa + 4u * (qn + __popc(m & ((1u << lane) - 1u))),
+                                                  (oi << 3) | (wo + (uint32_t)i));
+                                        qn += cnt;
                                     }
                                 }
                             }
                         }
-                        seg_start += span;
                     }
-                    if (qn) flush(qn);
+                    seg_start += span;
                 }
+                if (qn) flush(qn);
             }
-            if (waiting) tile_wait<C>();
             tile_arrive<C>();
-            waiting = true;
             pc++;
         } else if (e.kind == ENT_LOOP_BEGIN) {
             if (sp >= kMaxLoopDepth) {
@@ -634,15 +579,7 @@ __device__ __forceinline__ bool run_tile(const FrameArgs &a, unsigned char *dyn,
             }
         }
     }
-    if (waiting) tile_wait<C>();
-    if (pending) {
-        const uint64_t t0 = globaltimer_ns();
-        while (!mbar_try_wait(mb, phase) && globaltimer_ns() - t0 < kStageTimeoutNs) {
-        }
-    }
-    __syncthreads();
-    if (threadIdx.x == 0) asm volatile("mbarrier.inval.shared::cta.b64 [%0];" ::"r"(mb) : "memory");
-    __syncthreads();
+    tile_wait<C>();
     return ok;
 }
 

@@ -58,19 +58,6 @@ struct TileChoice {
     uint32_t threads = 256;
 };
 
-// Ops of one layer staged in shared memory for a tile whose frame takes
-// frame_bytes: as many as the program's largest per-CTA layer needs, within
-// what leaves room for two CTAs per SM when the frame allows it.
-inline uint32_t stage_capacity(uint32_t max_rank_ops, size_t frame_bytes, size_t smem_optin) {
-    // 1 KB of margin per CTA leaves room for the kernels' static shared memory
-    const size_t half = smem_optin / 2 > 2048 ? smem_optin / 2 - 1024 : 0;
-    const size_t full = smem_optin > 1024 ? smem_optin - 1024 : 0;
-    const size_t hdr = stimgb::kTileHeaderBytes;
-    const size_t target = frame_bytes + hdr + 16 * 64 <= half ? half : full;
-    if (target <= frame_bytes + hdr) return 0;
-    const size_t cap = (target - frame_bytes - hdr) / 16;
-    return (uint32_t)std::min<size_t>(cap, max_rank_ops);
-}
 
 // Library-internal entry points shared by the batched and serving paths.
 int stimgb_frame_program(stim_circuit *c, int C, const DevFrameProgram **out);

@@ -123,9 +123,7 @@ extern "C" int stim_frame_sample_noalloc(stim_circuit *c, uint64_t num_shots, ui
         const uint64_t grid = (nwords + W - 1) / W;
         a.meta_bytes = fp.meta_bytes;
         a.meta_region = meta_region_for(fp.meta_bytes);
-        a.op_cap = stage_capacity(fp.max_rank_ops, per_word * W + a.meta_region, (size_t)smem_optin);
-        e = launch_frame(a, W, 1, false, (uint32_t)grid, 256, tile_smem_bytes(fp.Q, W, a.op_cap, false, a.meta_region),
-                         st);
+        e = launch_frame(a, W, 1, false, (uint32_t)grid, 256, tile_smem_bytes(fp.Q, W, false, a.meta_region), st);
         if (e != cudaSuccess) return fail(STIM_E_CUDA, std::string("frame kernel: ") + cudaGetErrorString(e));
     }
     if (det_out && D > 0) {
