@@ -11,7 +11,8 @@
 //   [H + R, ...)             frame rows (shared-memory layout)
 // Frame layout (W 64-shot words per tile): each qubit owns a row of 2W words,
 // its X words then its Z words,
-//     shared memory:  row(q) = q * 2W;  X = row[w], Z = row[W + w]
+//     shared memory:  row(q) = q * 2W;  X = word w, Z = word W + w of the row,
+//                     16-byte chunks XOR-swizzled by q (row_word)
 //     global memory:  row(q) = gframe + q * 2G + tile0;  Z = row[G + w]
 // (G = words of the call), so one offset addresses both planes of a qubit.
 #pragma once
@@ -87,6 +88,16 @@ __device__ __forceinline__ uint32_t mapa_rank(uint32_t sa, uint32_t rank) {
     return ra;
 }
 
+// Shared-layout address of word widx (0..2W-1: X words, then Z words) of the
+// row of local qubit q. The row's 16-byte chunks are XOR-swizzled by the low
+// bits of q, so lanes reading the same word of different qubits spread over
+// the banks instead of all starting on the same bank.
+template <int W>
+__device__ __forceinline__ uint32_t row_word(uint32_t fsa, uint32_t q, uint32_t widx) {
+    const uint32_t chunk = (widx >> 1) ^ (q & (uint32_t)(W - 1));
+    return fsa + q * (16u * W) + chunk * 16u + (widx & 1u) * 8u;
+}
+
 // V words of one qubit's X and Z planes.
 template <int V>
 struct Planes {
@@ -102,60 +113,67 @@ struct Qubit;
 template <int W, int C>
 struct Qubit<W, C, false> {
     static constexpr int V = VecWidth<W>::V;
-    // X word wo of the qubit: a shared::cta address (C == 1) or, in a
-    // cluster, the shared::cluster address of the owning CTA's copy (mapa),
-    // so local and remote qubits take the same path
-    uint32_t sa;
+    // shared::cta (C == 1) or shared::cluster (mapa to the owning CTA) address
+    // of the qubit's row, its local index q and the first word wo of the group
+    uint32_t row, q, wo;
 
-    __device__ __forceinline__ Qubit(const Tile<W, C, false> &t, uint32_t ref, uint32_t wo) {
-        sa = t.fsa + ((ref & 0xFFFFFFu) * (2u * W) + wo) * 8u;
-        if constexpr (C > 1) sa = mapa_rank(sa, ref >> 24);
+    __device__ __forceinline__ Qubit(const Tile<W, C, false> &t, uint32_t ref, uint32_t wo_) {
+        q = ref & 0xFFFFFFu;
+        wo = wo_;
+        row = t.fsa + q * (16u * W);
+        if constexpr (C > 1) row = mapa_rank(row, ref >> 24);
     }
-    __device__ __forceinline__ void ld(uint32_t off, uint64_t (&v)[V]) const {
+    // address of word widx of the row (same swizzle as row_word)
+    __device__ __forceinline__ uint32_t at(uint32_t widx) const {
+        return row + (((widx >> 1) ^ (q & (uint32_t)(W - 1))) * 16u) + (widx & 1u) * 8u;
+    }
+    __device__ __forceinline__ void ld(uint32_t plane, uint64_t (&v)[V]) const {
         if constexpr (V == 1) {
-            v[0] = C > 1 ? ldc64(sa + off) : lds64(sa + off);
+            const uint32_t a = at(plane * W + wo);
+            v[0] = C > 1 ? ldc64(a) : lds64(a);
         } else {
 #pragma unroll
             for (int i = 0; i < V / 2; i++) {
-                if constexpr (C > 1) ldc_v2(sa + off + 16u * i, v[2 * i], v[2 * i + 1]);
-                else lds_v2(sa + off + 16u * i, v[2 * i], v[2 * i + 1]);
+                const uint32_t a = at(plane * W + wo + 2u * i);
+                if constexpr (C > 1) ldc_v2(a, v[2 * i], v[2 * i + 1]);
+                else lds_v2(a, v[2 * i], v[2 * i + 1]);
             }
         }
     }
-    __device__ __forceinline__ void st(uint32_t off, const uint64_t (&v)[V]) const {
+    __device__ __forceinline__ void st(uint32_t plane, const uint64_t (&v)[V]) const {
         if constexpr (V == 1) {
-            if constexpr (C > 1) stc64(sa + off, v[0]);
-            else sts64(sa + off, v[0]);
+            const uint32_t a = at(plane * W + wo);
+            if constexpr (C > 1) stc64(a, v[0]);
+            else sts64(a, v[0]);
         } else {
 #pragma unroll
             for (int i = 0; i < V / 2; i++) {
-                if constexpr (C > 1) stc_v2(sa + off + 16u * i, v[2 * i], v[2 * i + 1]);
-                else sts_v2(sa + off + 16u * i, v[2 * i], v[2 * i + 1]);
+                const uint32_t a = at(plane * W + wo + 2u * i);
+                if constexpr (C > 1) stc_v2(a, v[2 * i], v[2 * i + 1]);
+                else sts_v2(a, v[2 * i], v[2 * i + 1]);
             }
         }
     }
     __device__ __forceinline__ void load(const Tile<W, C, false> &, Planes<V> &p) const {
-        if constexpr (W == 1) {      // X and Z of the word are adjacent: one 16-byte access
-            if constexpr (C > 1) ldc_v2(sa, p.x[0], p.z[0]);
-            else lds_v2(sa, p.x[0], p.z[0]);
+        if constexpr (W == 1) {      // X and Z of the word share one 16-byte chunk
+            if constexpr (C > 1) ldc_v2(row, p.x[0], p.z[0]);
+            else lds_v2(row, p.x[0], p.z[0]);
         } else {
             ld(0, p.x);
-            ld(8u * W, p.z);
+            ld(1, p.z);
         }
     }
     __device__ __forceinline__ void store(const Tile<W, C, false> &, const Planes<V> &p) const {
         if constexpr (W == 1) {
-            if constexpr (C > 1) stc_v2(sa, p.x[0], p.z[0]);
-            else sts_v2(sa, p.x[0], p.z[0]);
+            if constexpr (C > 1) stc_v2(row, p.x[0], p.z[0]);
+            else sts_v2(row, p.x[0], p.z[0]);
         } else {
             st(0, p.x);
-            st(8u * W, p.z);
+            st(1, p.z);
         }
     }
     __device__ __forceinline__ void store_x(const Tile<W, C, false> &, const uint64_t (&x)[V]) const { st(0, x); }
-    __device__ __forceinline__ void store_z(const Tile<W, C, false> &, const uint64_t (&z)[V]) const {
-        st(8u * W, z);
-    }
+    __device__ __forceinline__ void store_z(const Tile<W, C, false> &, const uint64_t (&z)[V]) const { st(1, z); }
 };
 
 template <int W, int C>
@@ -371,14 +389,16 @@ __device__ __forceinline__ void xor_qubit_word(const Tile<W, C, GMEM> &t, uint32
         if (mx) atomicXor(reinterpret_cast<unsigned long long *>(p), (unsigned long long)mx);
         if (mz) atomicXor(reinterpret_cast<unsigned long long *>(p + t.gstride), (unsigned long long)mz);
     } else {
-        uint32_t sa = t.fsa + ((ref & 0xFFFFFFu) * (2u * W) + w) * 8u;
+        const uint32_t q = ref & 0xFFFFFFu;
+        uint32_t ax = row_word<W>(t.fsa, q, w), az = row_word<W>(t.fsa, q, W + w);
         if constexpr (C > 1) {
-            sa = mapa_rank(sa, ref >> 24);
-            if (mx) red_xor_cluster(sa, mx);
-            if (mz) red_xor_cluster(sa + 8u * W, mz);
+            ax = mapa_rank(ax, ref >> 24);
+            az = mapa_rank(az, ref >> 24);
+            if (mx) red_xor_cluster(ax, mx);
+            if (mz) red_xor_cluster(az, mz);
         } else {
-            if (mx) red_xor_smem(sa, mx);
-            if (mz) red_xor_smem(sa + 8u * W, mz);
+            if (mx) red_xor_smem(ax, mx);
+            if (mz) red_xor_smem(az, mz);
         }
     }
 }
@@ -469,9 +489,8 @@ __device__ __forceinline__ bool run_tile(const FrameArgs &a, unsigned char *dyn,
             p[0] = 0;
             p[a.gstride] = coin;
         } else {
-            const uint32_t sa = t.fsa + (l * (2u * W) + w) * 8u;
-            sts64(sa, 0);
-            sts64(sa + 8u * W, coin);
+            sts64(row_word<W>(t.fsa, l, w), 0);
+            sts64(row_word<W>(t.fsa, l, W + w), coin);
         }
     }
     tile_arrive<C>();
