@@ -55,6 +55,8 @@ extern "C" {
 #define STIM_DEVICE       0x0  /* output pointers are device memory */
 #define STIM_HOST         0x2  /* output pointers are host memory */
 #define STIM_RECOMPUTE    0x4  /* stim_reference_sample: ignore the cached sample */
+#define STIM_ASYNC        0x8  /* stim_frame_sample(_ex): return once the work and the host
+                                  copies are enqueued on the stream; see stim_frame_sample_ex */
 
 typedef struct stim_circuit stim_circuit;
 
@@ -149,6 +151,15 @@ int stim_frame_sample(stim_circuit *c, uint64_t num_shots, uint64_t seed,
  * shot_offset .. shot_offset+num_shots-1. shot_offset must be a multiple of
  * 64 (it selects 64-shot RNG words); the outputs hold the num_shots shots
  * starting at row/bit 0. hint may be NULL.
+ *
+ * Host outputs (STIM_HOST) are staged in device memory owned by the handle and
+ * copied out on `stream`. Without STIM_ASYNC the call returns after the copy.
+ * With STIM_ASYNC it returns once the kernels and copies are enqueued: the
+ * host buffers must stay valid and unread until `stream` is synchronized.
+ * Asynchronous calls alternate between two staging sets, so the copies of one
+ * call overlap the kernels of the next when the two run on different streams;
+ * a call that reuses a set waits on the GPU for that set's previous copies.
+ * Calls on one handle must still come from one host thread at a time.
  */
 int stim_frame_sample_ex(stim_circuit *c, uint64_t num_shots, uint64_t seed,
                          uint64_t shot_offset, uint64_t *meas_out, uint64_t *det_out,

@@ -48,6 +48,7 @@ STIM_SHOT_MAJOR = 0x1
 STIM_DEVICE = 0x0
 STIM_HOST = 0x2
 STIM_RECOMPUTE = 0x4
+STIM_ASYNC = 0x8
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
 _LIB_PATH = os.path.join(_HERE, "_build", "libstimgb.so")
@@ -96,6 +97,14 @@ class StimServerStatistics(ctypes.Structure):
 
 STIM_OUT_MEAS = 0x1
 STIM_OUT_DET = 0x2
+
+STIM_NOALLOC_SCRATCH_BYTES = 32 << 20
+
+STIM_KERNEL_FRAME = 0
+STIM_KERNEL_DETECTORS = 1
+STIM_KERNEL_TRANSPOSE = 2
+STIM_KERNEL_TABLEAU = 3
+STIM_KERNEL_COUNT = 4
 
 _VP = ctypes.c_void_p
 _U64 = ctypes.c_uint64

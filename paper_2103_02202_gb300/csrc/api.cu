@@ -470,10 +470,13 @@ void stim_free(stim_circuit *c) {
         cudaFree(c->d_ref);
         cudaFree(c->d_detflag);
         cudaFree(c->d_status);
-        cudaFree(c->d_rec);
-        cudaFree(c->d_det);
-        cudaFree(c->d_tr);
-        cudaFree(c->d_gframe);
+        for (auto &sc : c->scratch) {
+            cudaFree(sc.rec);
+            cudaFree(sc.det);
+            cudaFree(sc.tr);
+            cudaFree(sc.gframe);
+            if (sc.done) cudaEventDestroy(sc.done);
+        }
         for (DevFrameProgram &d : c->fprog) {
             cudaFree(d.meta);
             cudaFree(d.ops);
@@ -506,7 +509,7 @@ int stim_frame_sample_ex(stim_circuit *c, uint64_t num_shots, uint64_t seed, uin
                          uint64_t *meas_out, uint64_t *det_out, int flags, const stim_tile_hint *hint,
                          void *stream) {
     if (!c) return fail(STIM_E_INVALID_ARG, "stim_frame_sample: null handle");
-    if (!valid_flags(flags, STIM_HOST | STIM_SHOT_MAJOR))
+    if (!valid_flags(flags, STIM_HOST | STIM_SHOT_MAJOR | STIM_ASYNC))
         return fail(STIM_E_INVALID_ARG, "stim_frame_sample: unknown flags");
     if (shot_offset % 64) return fail(STIM_E_INVALID_ARG, "stim_frame_sample: shot_offset must be a multiple of 64");
     if ((shot_offset + num_shots + 63) / 64 > (1ull << 32))
@@ -539,6 +542,12 @@ int stim_frame_sample_ex(stim_circuit *c, uint64_t num_shots, uint64_t seed, uin
     const uint64_t grid = (nwords + W - 1) / W;     // word tiles (clusters)
     if (grid * C > 0x7FFFFFFFull) return fail(STIM_E_UNSUPPORTED, "too many shots for one call");
 
+    // ---- staging set (two alternate under STIM_ASYNC) ----
+    const bool async = (flags & STIM_ASYNC) != 0;
+    stim_circuit::Scratch &sc = c->scratch[async ? (c->next_scratch++ & 1u) : 0u];
+    if (!sc.done) STIMGB_CK(cudaEventCreateWithFlags(&sc.done, cudaEventDisableTiming), "event");
+    if (sc.used) STIMGB_CK(cudaStreamWaitEvent(st, sc.done, 0), "wait for staging");
+
     // ---- record buffers ----
     const bool meas_direct = meas_out && !shot_major && !host;
     const bool need_rec = (meas_out || det_out) && M > 0;
@@ -547,15 +556,15 @@ int stim_frame_sample_ex(stim_circuit *c, uint64_t num_shots, uint64_t seed, uin
         if (meas_direct) {
             rec = meas_out;
         } else {
-            if ((r = grow(&c->d_rec, &c->rec_cap, M * nwords, "alloc records")) != STIM_OK) return r;
-            rec = c->d_rec;
+            if ((r = grow(&sc.rec, &sc.rec_cap, M * nwords, "alloc records")) != STIM_OK) return r;
+            rec = sc.rec;
         }
     }
     uint64_t *gframe = nullptr;
     const uint64_t gstride = grid * W;
     if (gmem && n > 0) {
-        if ((r = grow(&c->d_gframe, &c->gframe_cap, 2 * (size_t)n * gstride, "alloc frame")) != STIM_OK) return r;
-        gframe = c->d_gframe;
+        if ((r = grow(&sc.gframe, &sc.gframe_cap, 2 * (size_t)n * gstride, "alloc frame")) != STIM_OK) return r;
+        gframe = sc.gframe;
     }
 
     uint64_t *det = nullptr;
@@ -564,8 +573,8 @@ int stim_frame_sample_ex(stim_circuit *c, uint64_t num_shots, uint64_t seed, uin
         if (det_direct) {
             det = det_out;
         } else {
-            if ((r = grow(&c->d_det, &c->det_cap, D * nwords, "alloc detectors")) != STIM_OK) return r;
-            det = c->d_det;
+            if ((r = grow(&sc.det, &sc.det_cap, D * nwords, "alloc detectors")) != STIM_OK) return r;
+            det = sc.det;
         }
     }
     if ((r = launch_sampling(c, num_shots, seed, shot_offset, tc, rec, det, gframe, st)) != STIM_OK) return r;
@@ -577,9 +586,9 @@ int stim_frame_sample_ex(stim_circuit *c, uint64_t num_shots, uint64_t seed, uin
             const uint64_t out_stride = (rows + 63) / 64;
             uint64_t *tgt = dst;
             if (host) {
-                int rr = grow(&c->d_tr, &c->tr_cap, num_shots * out_stride, "alloc transpose");
+                int rr = grow(&sc.tr, &sc.tr_cap, num_shots * out_stride, "alloc transpose");
                 if (rr != STIM_OK) return rr;
-                tgt = c->d_tr;
+                tgt = sc.tr;
             }
             {
                 ProfScope ps(STIM_KERNEL_TRANSPOSE, st);
@@ -594,7 +603,9 @@ int stim_frame_sample_ex(stim_circuit *c, uint64_t num_shots, uint64_t seed, uin
     };
     if (meas_out && !meas_direct && (r = emit(rec, M, meas_out)) != STIM_OK) return r;
     if (det_out && !det_direct && (r = emit(det, D, det_out)) != STIM_OK) return r;
-    if (host) STIMGB_CK(cudaStreamSynchronize(st), "sync");
+    STIMGB_CK(cudaEventRecord(sc.done, st), "record staging");
+    sc.used = true;
+    if (host && !async) STIMGB_CK(cudaStreamSynchronize(st), "sync");
     return STIM_OK;
 }
 

@@ -40,14 +40,23 @@ struct stim_circuit {
     int *d_status = nullptr;
     bool ref_valid = false;
     size_t ref_words = 1;
-    uint64_t *d_rec = nullptr;
-    size_t rec_cap = 0;
-    uint64_t *d_det = nullptr;
-    size_t det_cap = 0;
-    uint64_t *d_tr = nullptr;
-    size_t tr_cap = 0;
-    uint64_t *d_gframe = nullptr;
-    size_t gframe_cap = 0;
+    // Device staging of stim_frame_sample_ex (records, detection events,
+    // transposes, spilled frames). Calls with STIM_ASYNC alternate between the
+    // two sets so one call's copies overlap the next call's kernels; every call
+    // waits on the GPU for the previous user of its set (done event).
+    struct Scratch {
+        uint64_t *rec = nullptr;
+        size_t rec_cap = 0;
+        uint64_t *det = nullptr;
+        size_t det_cap = 0;
+        uint64_t *tr = nullptr;
+        size_t tr_cap = 0;
+        uint64_t *gframe = nullptr;
+        size_t gframe_cap = 0;
+        cudaEvent_t done = nullptr;
+        bool used = false;
+    } scratch[2];
+    unsigned next_scratch = 0;
     DevFrameProgram fprog[4];           // cluster sizes 1, 2, 4, 8
 };
 

@@ -41,6 +41,17 @@ def test_library_exports_every_declared_symbol():
     assert sorted(sg.EXPORTED_SYMBOLS) == decl
 
 
+def test_binding_constants_match_header():
+    """Every STIM_* integer #define of the header has the same value in the binding."""
+    txt = open(os.path.join(ROOT, "include", "stimgb.h")).read()
+    defs = re.findall(r"^#define\s+(STIM_\w+)\s+\(?(-?(?:0x[0-9a-fA-F]+|\d+))u?(?:\s*<<\s*(\d+))?\)?", txt, flags=re.M)
+    assert defs
+    for name, val, shift in defs:
+        v = int(val, 0) << (int(shift) if shift else 0)
+        assert hasattr(sg, name), name
+        assert getattr(sg, name) == v, name
+
+
 def test_binding_fails_loudly_without_library(monkeypatch):
     monkeypatch.setattr(sg, "_lib", None)
     monkeypatch.setattr(sg, "_LIB_PATH", "/nonexistent/libstimgb.so")

@@ -208,6 +208,31 @@ def test_layouts_and_host_outputs_agree():
     c.close()
 
 
+def test_async_host_outputs_on_two_streams_agree():
+    """STIM_ASYNC host copies from alternating streams (double-buffered staging)
+    equal synchronous device outputs, call for call."""
+    text = W.surface_code_memory(5, 5, 0.02)
+    c = sg.Circuit(text)
+    S = 4000
+    M, D = c.num_measurements, c.num_detectors
+    nw = (S + 63) // 64
+    streams = [torch.cuda.Stream(), torch.cuda.Stream()]
+    calls = 6
+    host_m = [torch.empty((M, nw), dtype=torch.int64, pin_memory=True) for _ in range(calls)]
+    host_d = [torch.empty((D, nw), dtype=torch.int64, pin_memory=True) for _ in range(calls)]
+    for i in range(calls):
+        st = streams[i % 2]
+        sg.stim_frame_sample_ex(c.handle, S, 11 + i, 64 * i, host_m[i].data_ptr(), host_d[i].data_ptr(),
+                                sg.STIM_HOST | sg.STIM_ASYNC, None, st.cuda_stream)
+    torch.cuda.synchronize()
+    for i in range(calls):
+        mm, dm = c.sample(S, 11 + i, shot_offset=64 * i)
+        torch.cuda.synchronize()
+        np.testing.assert_array_equal(host_m[i].numpy().view(np.uint64), to_np(mm))
+        np.testing.assert_array_equal(host_d[i].numpy().view(np.uint64), to_np(dm))
+    c.close()
+
+
 def test_noiseless_surface_detectors_vanish_at_scale():
     text = W.surface_code_memory(15, 15, 0.0)
     c = sg.Circuit(text)
