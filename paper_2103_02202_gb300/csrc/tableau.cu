@@ -75,31 +75,48 @@ __device__ __forceinline__ bool tab_barrier(const TabArgs &a) {
     return *(volatile int *)&a.ctl->abort == 0;
 }
 
-__device__ __forceinline__ uint32_t ld_u32(const uint32_t *p) { return __ldcg(p); }
-__device__ __forceinline__ uint64_t ld_u64(const uint64_t *p) { return __ldcg(p); }
+// Tableau accesses. With several CTAs the data is shared through L2 (cache-
+// global loads and stores, ordered by the grid barrier); a single CTA (L1)
+// keeps it in its own L1, ordered by __syncthreads.
+template <bool L1>
+__device__ __forceinline__ uint32_t ld_u32(const uint32_t *p) {
+    if constexpr (L1) return *p;
+    else return __ldcg(p);
+}
+template <bool L1>
+__device__ __forceinline__ uint64_t ld_u64(const uint64_t *p) {
+    if constexpr (L1) return *p;
+    else return __ldcg(p);
+}
+template <bool L1, class T>
+__device__ __forceinline__ void st_tab(T *p, T v) {
+    if constexpr (L1) *p = v;
+    else __stcg(p, v);
+}
 
 // dst column := dst * src (logical columns); extra = additional power of i.
+template <bool L1>
 __device__ void column_product(const TabArgs &a, uint32_t dst, uint32_t src, uint32_t extra, uint32_t lane) {
-    const uint32_t pd = ld_u32(a.perm + dst), ps = ld_u32(a.perm + src);
+    const uint32_t pd = ld_u32<L1>(a.perm + dst), ps = ld_u32<L1>(a.perm + src);
     uint64_t *dx = a.tx + (uint64_t)pd * a.nw, *dz = a.tz + (uint64_t)pd * a.nw;
     const uint64_t *sx = a.tx + (uint64_t)ps * a.nw, *sz = a.tz + (uint64_t)ps * a.nw;
     uint64_t c1 = 0, c2 = 0;   // per-bit two-bit counters of the phase exponent
     for (uint32_t w = lane; w < a.nw; w += 32) {
-        const uint64_t x1 = ld_u64(dx + w), z1 = ld_u64(dz + w);
-        const uint64_t x2 = ld_u64(sx + w), z2 = ld_u64(sz + w);
+        const uint64_t x1 = ld_u64<L1>(dx + w), z1 = ld_u64<L1>(dz + w);
+        const uint64_t x2 = ld_u64<L1>(sx + w), z2 = ld_u64<L1>(sz + w);
         const uint64_t nx = x1 ^ x2, nz = z1 ^ z2;
         const uint64_t x1z2 = x1 & z2;
         const uint64_t anti = (x2 & z1) ^ x1z2;            // positions that anticommute
         c2 ^= (c1 ^ nx ^ nz ^ x1z2) & anti;               // +1 or -1 per anticommuting position
         c1 ^= anti;
-        __stcg(dx + w, nx);
-        __stcg(dz + w, nz);
+        st_tab<L1>(dx + w, nx);
+        st_tab<L1>(dz + w, nz);
     }
     uint32_t ph = (uint32_t)(__popcll(c1) + 2 * __popcll(c2));
     for (int d = 16; d > 0; d >>= 1) ph += __shfl_xor_sync(0xffffffffu, ph, d);
     if (lane == 0) {
-        const uint32_t tot = (ph + extra + 2u * ld_u32(a.sign + pd) + 2u * ld_u32(a.sign + ps)) & 3u;
-        __stcg(a.sign + pd, tot >> 1);   // tot is even: the product of the images is Hermitian
+        const uint32_t tot = (ph + extra + 2u * ld_u32<L1>(a.sign + pd) + 2u * ld_u32<L1>(a.sign + ps)) & 3u;
+        st_tab<L1>(a.sign + pd, tot >> 1);   // tot is even: the product of the images is Hermitian
     }
 }
 
@@ -114,17 +131,18 @@ __device__ __forceinline__ void write_outcome(const TabArgs &a, uint32_t opc, ui
 // Leader warp: walk collapsing ops from j in source order. Deterministic ones
 // are resolved here; at the first random one the elimination data is
 // published for the grid. Returns nothing; results go to a.ctl.
+template <bool L1>
 __device__ void leader_walk(const TabArgs &a, const DevOp *cops, uint32_t nc, uint32_t j, uint32_t meas_off,
                             uint32_t lane) {
     for (; j < nc; j++) {
         const DevOp op = cops[j];
         const uint32_t opc = op.a >> 24, q = op.a & kQubitMask;
-        const uint32_t pz = ld_u32(a.perm + 2 * q + 1);
+        const uint32_t pz = ld_u32<L1>(a.perm + 2 * q + 1);
         const uint64_t *x = a.tx + (uint64_t)pz * a.nw, *z = a.tz + (uint64_t)pz * a.nw;
         int64_t pivot = -1;
         for (uint32_t base = 0; base < a.nw && pivot < 0; base += 32) {
             const uint32_t w = base + lane;
-            const uint64_t v = w < a.nw ? ld_u64(x + w) : 0;
+            const uint64_t v = w < a.nw ? ld_u64<L1>(x + w) : 0;
             const uint32_t bal = __ballot_sync(0xffffffffu, v != 0);
             if (bal) {
                 const uint32_t src = __ffs(bal) - 1;
@@ -134,9 +152,9 @@ __device__ void leader_walk(const TabArgs &a, const DevOp *cops, uint32_t nc, ui
         }
         if (pivot < 0) {
             if (lane == 0) {
-                const uint32_t s = ld_u32(a.sign + pz);
+                const uint32_t s = ld_u32<L1>(a.sign + pz);
                 write_outcome(a, opc, op.b + meas_off, s, 1);
-                if (opc != OP_M) __stcg(a.sign + pz, 0u);
+                if (opc != OP_M) st_tab<L1>(a.sign + pz, 0u);
             }
             __syncwarp();
             continue;
@@ -147,10 +165,10 @@ __device__ void leader_walk(const TabArgs &a, const DevOp *cops, uint32_t nc, ui
         uint32_t cnt = 0, m = 0;
         for (uint32_t base = 0; base < a.nw; base += 32) {
             const uint32_t w = base + lane;
-            uint64_t xv = w < a.nw ? ld_u64(x + w) : 0;
-            const uint64_t zv = w < a.nw ? ld_u64(z + w) : 0;
+            uint64_t xv = w < a.nw ? ld_u64<L1>(x + w) : 0;
+            const uint64_t zv = w < a.nw ? ld_u64<L1>(z + w) : 0;
             if (w == pw) xv &= ~pb;
-            if (w < a.nw) __stcg(a.kmask + w, xv);
+            if (w < a.nw) st_tab<L1>(a.kmask + w, xv);
             const uint32_t c = __popcll(xv);
             uint32_t incl = c;
             for (int d = 1; d < 32; d <<= 1) {
@@ -161,7 +179,7 @@ __device__ void leader_walk(const TabArgs &a, const DevOp *cops, uint32_t nc, ui
             uint64_t rest = xv;
             while (rest) {
                 const uint32_t bpos = __ffsll((long long)rest) - 1;
-                __stcg(a.klist + off, w * 64 + bpos);
+                st_tab<L1>(a.klist + off, w * 64 + bpos);
                 off++;
                 rest &= rest - 1;
             }
@@ -171,10 +189,10 @@ __device__ void leader_walk(const TabArgs &a, const DevOp *cops, uint32_t nc, ui
             m += mz;
         }
         if (lane == 0) {
-            const uint32_t zp = (uint32_t)((ld_u64(z + pw) & pb) != 0);
+            const uint32_t zp = (uint32_t)((ld_u64<L1>(z + pw) & pb) != 0);
             // column Z_q after the CNOT chain: sign flips floor(m/2) (z_p = 0) or ceil(m/2) (z_p = 1)
             const uint32_t flips = zp ? ((m + 1) >> 1) : (m >> 1);
-            const uint32_t s_new = ld_u32(a.sign + pz) ^ (flips & 1u);
+            const uint32_t s_new = ld_u32<L1>(a.sign + pz) ^ (flips & 1u);
             a.ctl->pivot = p;
             a.ctl->nk = cnt;
             a.ctl->pivot_is_y = zp ^ (m & 1u);
@@ -207,58 +225,61 @@ __device__ __forceinline__ void pivot_ops(uint32_t &xp, uint32_t &zp, uint32_t &
     if (fx) s ^= zp;     // X: Z -> -Z, Y -> -Y
 }
 
+template <bool L1>
 __device__ __forceinline__ void set_bit(uint64_t *w, uint64_t b, uint32_t v) {
-    const uint64_t old = ld_u64(w);
-    __stcg(w, v ? (old | b) : (old & ~b));
+    const uint64_t old = ld_u64<L1>(w);
+    st_tab<L1>(w, v ? (old | b) : (old & ~b));
 }
 
 // Apply the random measurement's appends to every column (list form: one thread per column).
+template <bool L1>
 __device__ void column_pass_list(const TabArgs &a, uint32_t p, uint32_t nk, uint32_t py, uint32_t fx,
                                  uint32_t gtid, uint32_t nthreads) {
     const uint32_t pw = p >> 6;
     const uint64_t pb = 1ull << (p & 63);
     for (uint32_t c = gtid; c < 2 * a.n; c += nthreads) {
         uint64_t *x = a.tx + (uint64_t)c * a.nw, *z = a.tz + (uint64_t)c * a.nw;
-        uint32_t xp = (ld_u64(x + pw) & pb) != 0;
-        uint32_t zp = (ld_u64(z + pw) & pb) != 0;
-        uint32_t s = ld_u32(a.sign + c);
+        uint32_t xp = (ld_u64<L1>(x + pw) & pb) != 0;
+        uint32_t zp = (ld_u64<L1>(z + pw) & pb) != 0;
+        uint32_t s = ld_u32<L1>(a.sign + c);
         for (uint32_t t = 0; t < nk; t++) {
-            const uint32_t k = ld_u32(a.klist + t);
+            const uint32_t k = ld_u32<L1>(a.klist + t);
             const uint64_t kb = 1ull << (k & 63);
-            const uint32_t zk = (ld_u64(z + (k >> 6)) & kb) != 0;
+            const uint32_t zk = (ld_u64<L1>(z + (k >> 6)) & kb) != 0;
             if (xp) {
-                const uint64_t xw = ld_u64(x + (k >> 6));
+                const uint64_t xw = ld_u64<L1>(x + (k >> 6));
                 const uint32_t xk = (xw & kb) != 0;
                 s ^= zk & (xk ^ zp ^ 1u);
-                __stcg(x + (k >> 6), xw ^ kb);
+                st_tab<L1>(x + (k >> 6), xw ^ kb);
             }
             zp ^= zk;
         }
         pivot_ops(xp, zp, s, py, fx);
-        set_bit(x + pw, pb, xp);
-        set_bit(z + pw, pb, zp);
-        __stcg(a.sign + c, s);
+        set_bit<L1>(x + pw, pb, xp);
+        set_bit<L1>(z + pw, pb, zp);
+        st_tab<L1>(a.sign + c, s);
     }
 }
 
 // Mask form: one warp per column, word-parallel.
+template <bool L1>
 __device__ void column_pass_mask(const TabArgs &a, uint32_t p, uint32_t py, uint32_t fx, uint32_t gwarp,
                                  uint32_t nwarps, uint32_t lane) {
     const uint32_t pw = p >> 6;
     const uint64_t pb = 1ull << (p & 63);
     for (uint32_t c = gwarp; c < 2 * a.n; c += nwarps) {
         uint64_t *x = a.tx + (uint64_t)c * a.nw, *z = a.tz + (uint64_t)c * a.nw;
-        const uint32_t xp = (ld_u64(x + pw) & pb) != 0;
-        const uint32_t zp = (ld_u64(z + pw) & pb) != 0;
+        const uint32_t xp = (ld_u64<L1>(x + pw) & pb) != 0;
+        const uint32_t zp = (ld_u64<L1>(z + pw) & pb) != 0;
         uint32_t cnt_a = 0, cnt_b = 0;
         for (uint32_t w = lane; w < a.nw; w += 32) {
-            const uint64_t kw = ld_u64(a.kmask + w);
-            const uint64_t zw = ld_u64(z + w);
+            const uint64_t kw = ld_u64<L1>(a.kmask + w);
+            const uint64_t zw = ld_u64<L1>(z + w);
             cnt_b += __popcll(zw & kw);
             if (xp) {
-                const uint64_t xw = ld_u64(x + w);
+                const uint64_t xw = ld_u64<L1>(x + w);
                 cnt_a += __popcll(zw & (zp ? xw : ~xw) & kw);
-                __stcg(x + w, xw ^ kw);
+                st_tab<L1>(x + w, xw ^ kw);
             }
         }
         for (int d = 16; d > 0; d >>= 1) {
@@ -267,16 +288,16 @@ __device__ void column_pass_mask(const TabArgs &a, uint32_t p, uint32_t py, uint
         }
         __syncwarp();
         if (lane == 0) {
-            uint32_t s = ld_u32(a.sign + c);
+            uint32_t s = ld_u32<L1>(a.sign + c);
             if (xp) {
                 const uint64_t pairs = (uint64_t)cnt_b * (cnt_b - (cnt_b > 0 ? 1u : 0u)) / 2;
                 s ^= (uint32_t)((cnt_a + pairs) & 1u);
             }
             uint32_t xn = xp, zn = zp ^ (cnt_b & 1u);
             pivot_ops(xn, zn, s, py, fx);
-            set_bit(x + pw, pb, xn);
-            set_bit(z + pw, pb, zn);
-            __stcg(a.sign + c, s);
+            set_bit<L1>(x + pw, pb, xn);
+            set_bit<L1>(z + pw, pb, zn);
+            st_tab<L1>(a.sign + c, s);
         }
         __syncwarp();
     }
@@ -293,6 +314,7 @@ __global__ void tableau_init_kernel(TabArgs a) {
     }
 }
 
+template <bool L1>
 __global__ void __launch_bounds__(512) tableau_kernel(TabArgs a) {
     const uint32_t lane = threadIdx.x & 31;
     const uint32_t wpb = blockDim.x >> 5;
@@ -347,21 +369,21 @@ __global__ void __launch_bounds__(512) tableau_kernel(TabArgs a) {
                 switch (opc) {
                     case OP_H:
                         if (k == 0 && lane == 0) {
-                            const uint32_t u = ld_u32(a.perm + 2 * qa), v = ld_u32(a.perm + 2 * qa + 1);
-                            __stcg(a.perm + 2 * qa, v);
-                            __stcg(a.perm + 2 * qa + 1, u);
+                            const uint32_t u = ld_u32<L1>(a.perm + 2 * qa), v = ld_u32<L1>(a.perm + 2 * qa + 1);
+                            st_tab<L1>(a.perm + 2 * qa, v);
+                            st_tab<L1>(a.perm + 2 * qa + 1, u);
                         }
                         break;
                     case OP_S:
-                        if (k == 0) column_product(a, 2 * qa, 2 * qa + 1, 3u, lane);
+                        if (k == 0) column_product<L1>(a, 2 * qa, 2 * qa + 1, 3u, lane);
                         break;
                     case OP_CX:
-                        if (k == 0) column_product(a, 2 * qa, 2 * qb, 0u, lane);
-                        else column_product(a, 2 * qb + 1, 2 * qa + 1, 0u, lane);
+                        if (k == 0) column_product<L1>(a, 2 * qa, 2 * qb, 0u, lane);
+                        else column_product<L1>(a, 2 * qb + 1, 2 * qa + 1, 0u, lane);
                         break;
                     case OP_CZ:
-                        if (k == 0) column_product(a, 2 * qa, 2 * qb + 1, 0u, lane);
-                        else column_product(a, 2 * qb, 2 * qa + 1, 0u, lane);
+                        if (k == 0) column_product<L1>(a, 2 * qa, 2 * qb + 1, 0u, lane);
+                        else column_product<L1>(a, 2 * qb, 2 * qa + 1, 0u, lane);
                         break;
                     default:
                         break;
@@ -375,40 +397,40 @@ __global__ void __launch_bounds__(512) tableau_kernel(TabArgs a) {
         // (A) which collapsing ops are random, checked in parallel
         for (uint32_t j = gwarp; j < nc; j += nwarps) {
             const uint32_t q = cops[j].a & kQubitMask;
-            const uint64_t *x = a.tx + (uint64_t)ld_u32(a.perm + 2 * q + 1) * a.nw;
+            const uint64_t *x = a.tx + (uint64_t)ld_u32<L1>(a.perm + 2 * q + 1) * a.nw;
             uint32_t any = 0;
-            for (uint32_t w = lane; w < a.nw; w += 32) any |= ld_u64(x + w) != 0;
+            for (uint32_t w = lane; w < a.nw; w += 32) any |= ld_u64<L1>(x + w) != 0;
             any = __any_sync(0xffffffffu, any);
-            if (lane == 0) __stcg(a.rnd + j, any);
+            if (lane == 0) st_tab<L1>(a.rnd + j, any);
         }
         if (!tab_barrier(a)) return;
         // (B) first random op; everything before it is deterministic and independent
         if (threadIdx.x == 0) s_first = nc;
         __syncthreads();
         for (uint32_t j = threadIdx.x; j < nc; j += blockDim.x)
-            if (ld_u32(a.rnd + j)) atomicMin(&s_first, j);
+            if (ld_u32<L1>(a.rnd + j)) atomicMin(&s_first, j);
         __syncthreads();
         const uint32_t first = s_first;
         for (uint32_t j = gtid; j < first; j += nthreads) {
             const DevOp op = cops[j];
             const uint32_t opc = op.a >> 24, q = op.a & kQubitMask;
-            const uint32_t pz = ld_u32(a.perm + 2 * q + 1);
-            write_outcome(a, opc, op.b + meas_off, ld_u32(a.sign + pz), 1);
-            if (opc != OP_M) __stcg(a.sign + pz, 0u);
+            const uint32_t pz = ld_u32<L1>(a.perm + 2 * q + 1);
+            write_outcome(a, opc, op.b + meas_off, ld_u32<L1>(a.sign + pz), 1);
+            if (opc != OP_M) st_tab<L1>(a.sign + pz, 0u);
         }
         if (!tab_barrier(a)) return;
         if (first >= nc) continue;
         // (C) sequential from the first random op
         uint32_t j = first;
         for (;;) {
-            if (leader) leader_walk(a, cops, nc, j, meas_off, lane);
+            if (leader) leader_walk<L1>(a, cops, nc, j, meas_off, lane);
             if (!tab_barrier(a)) return;
-            if (!ld_u32(&a.ctl->has_random)) break;
-            j = ld_u32(&a.ctl->next_j);
-            const uint32_t p = ld_u32(&a.ctl->pivot), nk = ld_u32(&a.ctl->nk);
-            const uint32_t py = ld_u32(&a.ctl->pivot_is_y), fx = ld_u32(&a.ctl->fix_x);
-            if (ld_u32(&a.ctl->use_mask)) column_pass_mask(a, p, py, fx, gwarp, nwarps, lane);
-            else column_pass_list(a, p, nk, py, fx, gtid, nthreads);
+            if (!ld_u32<L1>(&a.ctl->has_random)) break;
+            j = ld_u32<L1>(&a.ctl->next_j);
+            const uint32_t p = ld_u32<L1>(&a.ctl->pivot), nk = ld_u32<L1>(&a.ctl->nk);
+            const uint32_t py = ld_u32<L1>(&a.ctl->pivot_is_y), fx = ld_u32<L1>(&a.ctl->fix_x);
+            if (ld_u32<L1>(&a.ctl->use_mask)) column_pass_mask<L1>(a, p, py, fx, gwarp, nwarps, lane);
+            else column_pass_list<L1>(a, p, nk, py, fx, gtid, nthreads);
             if (!tab_barrier(a)) return;
             j++;
         }
@@ -426,7 +448,8 @@ cudaError_t launch_tableau_init(const TabArgs &a, cudaStream_t stream) {
 
 int tableau_max_blocks(uint32_t threads, int device) {
     int per_sm = 0, sms = 0;
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, tableau_kernel, (int)threads, 0) != cudaSuccess)
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, tableau_kernel<false>, (int)threads, 0) !=
+        cudaSuccess)
         return 1;
     if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, device) != cudaSuccess) return 1;
     const int b = per_sm * sms;
@@ -436,7 +459,10 @@ int tableau_max_blocks(uint32_t threads, int device) {
 cudaError_t launch_tableau(const TabArgs &a, uint32_t blocks, uint32_t threads, cudaStream_t stream) {
     TabArgs args = a;
     void *params[] = {&args};
-    return cudaLaunchCooperativeKernel((const void *)tableau_kernel, dim3(blocks), dim3(threads), params, 0,
+    if (blocks == 1)    // one CTA: the tableau stays in its L1, no grid barrier
+        return cudaLaunchCooperativeKernel((const void *)tableau_kernel<true>, dim3(1), dim3(threads), params, 0,
+                                           stream);
+    return cudaLaunchCooperativeKernel((const void *)tableau_kernel<false>, dim3(blocks), dim3(threads), params, 0,
                                        stream);
 }
 
