@@ -316,7 +316,7 @@ int choose_tile(uint32_t n, uint64_t nwords, int sms, size_t smem_optin, const s
         uint32_t th = (uint32_t)(2048 / ctas);
         if (th > 512) th = 512;
         if (th < 256) th = 256;
-        t.threads = th;
+        t.threads = th & ~31u;      // whole warps: the kernel's warp collectives name all 32 lanes
     }
     *out = t;
     return STIM_OK;

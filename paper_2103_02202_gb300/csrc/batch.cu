@@ -169,6 +169,8 @@ static int max_resident_ctas_t(uint32_t threads, size_t smem, int sms) {
 
 static cudaError_t launch_batch(int W, int C, const FrameArgs *descs, const BatchItem *items, uint32_t nitems,
                                 uint32_t *counter, uint32_t blocks, uint32_t threads, size_t smem, cudaStream_t st) {
+    // the kernel's warp collectives (hit-queue ballots) name all 32 lanes of every warp
+    if (threads == 0 || threads % 32 != 0) return cudaErrorInvalidValue;
     STIMGB_BATCH_DISPATCH(launch_batch_t, descs, items, nitems, counter, blocks, threads, smem, st)
     return cudaErrorInvalidValue;
 }
@@ -380,6 +382,8 @@ int enqueue(stim_batch *b, cudaStream_t st, uint32_t nitems_limit) {
 int configure(stim_batch *b, int W, uint32_t threads) {
     int sms = 0;
     STIMGB_BCK(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, b->device), "attr");
+    if (threads == 0 || threads % 32 != 0)
+        return bfail(STIM_E_INVALID_ARG, "batch: threads per CTA must be a multiple of 32");
     if ((int)threads > frame_max_threads(W))
         return bfail(STIM_E_INVALID_ARG, "batch: too many threads per CTA for this many words per tile (768 for 2, 512 for 4 or 8)");
     b->W = W;

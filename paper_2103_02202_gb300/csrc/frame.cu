@@ -75,6 +75,8 @@ static cudaError_t launch_frame_w(const FrameArgs &a, int W, uint32_t tiles, uin
 
 cudaError_t launch_frame(const FrameArgs &a, int W, int C, bool gmem, uint32_t tiles, uint32_t threads, size_t smem,
                          cudaStream_t stream) {
+    // the kernel's warp collectives (hit-queue ballots) name all 32 lanes of every warp
+    if (threads == 0 || threads % 32 != 0) return cudaErrorInvalidValue;
     if (gmem) return C == 1 ? launch_frame_w<1, true>(a, W, tiles, threads, smem, stream) : cudaErrorInvalidValue;
     switch (C) {
         case 1: return launch_frame_w<1, false>(a, W, tiles, threads, smem, stream);

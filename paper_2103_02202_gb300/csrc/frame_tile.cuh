@@ -455,6 +455,10 @@ __device__ __forceinline__ uint64_t to_global(const void *p) {
 template <int W, int C, bool GMEM>
 __device__ __forceinline__ bool run_tile(const FrameArgs &a, unsigned char *dyn, uint32_t rank, uint64_t tile) {
     constexpr int V = VecWidth<W>::V;
+    if (blockDim.x % 32u != 0u) {       // partial warps would stall the hit-queue ballots
+        if (threadIdx.x == 0) atomicExch(a.status, DEV_BAD_PROGRAM);
+        return false;
+    }
     const uint32_t tile0 = (uint32_t)(tile * W);
     const uint32_t sbase = smem_addr(dyn);
     const SmemKeys key{sbase};

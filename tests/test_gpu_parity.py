@@ -139,6 +139,17 @@ def test_surface_d3_full_parity():
     np.testing.assert_array_equal(db, od)
 
 
+@pytest.mark.parametrize("d", [23, 27, 31, 37])
+def test_default_tiles_of_mid_size_circuits(d):
+    """Default tile shapes for 1,000-2,700-qubit circuits (the library sizes
+    the CTA from the qubits' shared memory; every CTA must be whole warps)."""
+    text = W.surface_code_memory(d, 2, 0.01)
+    mb, db = gpu_sample(text, 640, 9)
+    om, od = oracle.Circuit(text).sample(np.arange(640), 9, threads=8)
+    np.testing.assert_array_equal(mb, om)
+    np.testing.assert_array_equal(db, od)
+
+
 @pytest.mark.parametrize("shots", [1, 63, 64, 65, 1000, 3 * 64 * 16 + 5])
 def test_ragged_shot_counts(shots):
     text = W.surface_code_memory(3, 2, 0.02)
