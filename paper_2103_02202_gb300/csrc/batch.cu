@@ -410,7 +410,7 @@ int configure(stim_batch *b, int W, uint32_t threads) {
     return upload_items(b);
 }
 
-// Times candidate tile shapes on a prefix of the work list; keeps the fastest.
+// Times candidate tile shapes on the whole work list; keeps the fastest.
 int autotune(stim_batch *b, cudaStream_t st) {
     {
         std::lock_guard<std::mutex> lk(g_tune_mu);
@@ -420,8 +420,12 @@ int autotune(stim_batch *b, cudaStream_t st) {
     }
     int smem_optin = 0;
     STIMGB_BCK(cudaDeviceGetAttribute(&smem_optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, b->device), "attr");
-    const int cand_w[3] = {1, 2, 4};
+    // Each candidate shape runs the whole batch once (after one warm-up run of
+    // the first shape): prefixes of the largest-first queue misjudge mixes of
+    // large and small circuits.
+    const int cand_w[4] = {1, 2, 4, 8};
     const uint32_t cand_t[2] = {256, 512};
+    bool warm = false;
     double best = -1;
     int bw = 1;
     uint32_t bt = 256;
@@ -432,17 +436,17 @@ int autotune(stim_batch *b, cudaStream_t st) {
         if (batch_smem(b, w, b->C, 0) > (size_t)smem_optin) continue;
         for (uint32_t t : cand_t) {
             if (configure(b, w, t) != STIM_OK) continue;
-            const uint32_t lim = std::min<uint32_t>(b->nitems, std::max<uint32_t>(4 * b->blocks / b->C, 1));
-            uint64_t words = 0;
-            for (uint32_t i = 0; i < lim; i++) words += w;
-            if (enqueue(b, st, lim) != STIM_OK) continue;       // warm-up
+            if (!warm) {
+                if (enqueue(b, st, b->nitems) != STIM_OK) continue;
+                warm = true;
+            }
             cudaEventRecord(e0, st);
-            if (enqueue(b, st, lim) != STIM_OK) continue;
+            if (enqueue(b, st, b->nitems) != STIM_OK) continue;
             cudaEventRecord(e1, st);
             if (cudaEventSynchronize(e1) != cudaSuccess) continue;
             float ms = 0;
             cudaEventElapsedTime(&ms, e0, e1);
-            const double rate = ms > 0 ? (double)words / ms : 0;
+            const double rate = ms > 0 ? 1.0 / ms : 0;
             if (rate > best) {
                 best = rate;
                 bw = w;
