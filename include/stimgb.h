@@ -48,6 +48,7 @@ extern "C" {
 #define STIM_E_TIMEOUT      (-5)  /* a bounded device wait ran out */
 #define STIM_E_BUSY         (-6)  /* resource in use (server admission) */
 #define STIM_E_UNSUPPORTED  (-7)  /* circuit exceeds a documented limit */
+#define STIM_E_CAPACITY     (-8)  /* output capacity too small (the needed size is reported) */
 
 /* ---- flags --------------------------------------------------------------- */
 #define STIM_MEAS_MAJOR   0x0  /* row r = measurement/detector r; bit s = shot s */
@@ -164,6 +165,27 @@ int stim_frame_sample(stim_circuit *c, uint64_t num_shots, uint64_t seed,
 int stim_frame_sample_ex(stim_circuit *c, uint64_t num_shots, uint64_t seed,
                          uint64_t shot_offset, uint64_t *meas_out, uint64_t *det_out,
                          int flags, const stim_tile_hint *hint, void *stream);
+
+/*
+ * stim_frame_sample_detections -- detection events of shots shot_offset ..
+ * shot_offset+num_shots-1 (as stim_frame_sample_ex) as per-shot lists of the
+ * fired detectors, the "hits" form of the paper's output formats (Section
+ * 5.6): detectors[shot_begin[s] .. shot_begin[s+1]) are the indices of the
+ * detectors that fired in shot s (0-based within the call), ascending.
+ *
+ * shot_begin: num_shots + 1 offsets (uint64), may be NULL.
+ * detectors: uint32 detector indices, room for `capacity` entries; may be NULL
+ *   (then only the count and offsets are produced).
+ * count: host pointer, receives the total number of events.
+ * flags: STIM_HOST (both outputs are host memory) or STIM_DEVICE. The call
+ *   synchronizes `stream` (the count decides the copy size).
+ * Errors: as stim_frame_sample_ex; STIM_E_CAPACITY when the events do not fit
+ *   `capacity` (*count holds the number needed; the first `capacity` entries
+ *   and all offsets are written).
+ */
+int stim_frame_sample_detections(stim_circuit *c, uint64_t num_shots, uint64_t seed, uint64_t shot_offset,
+                                 uint64_t *shot_begin, uint32_t *detectors, uint64_t capacity, uint64_t *count,
+                                 int flags, void *stream);
 
 /*
  * Batched sampling: many compiled circuits in one persistent launch.

@@ -26,7 +26,8 @@ from . import workloads  # noqa: F401  (seeded input generators)
 
 __all__ = [
     "STIM_OK", "STIM_E_PARSE", "STIM_E_INVALID_ARG", "STIM_E_OOM", "STIM_E_CUDA",
-    "STIM_E_TIMEOUT", "STIM_E_BUSY", "STIM_E_UNSUPPORTED",
+    "STIM_E_TIMEOUT", "STIM_E_BUSY", "STIM_E_UNSUPPORTED", "STIM_E_CAPACITY", "STIM_ASYNC",
+    "stim_frame_sample_detections",
     "STIM_MEAS_MAJOR", "STIM_SHOT_MAJOR", "STIM_DEVICE", "STIM_HOST", "STIM_RECOMPUTE",
     "StimError", "library", "library_path", "stim_compile", "stim_info_get", "stim_free",
     "stim_last_error", "stim_reference_sample", "stim_frame_sample", "stim_frame_sample_ex",
@@ -42,6 +43,7 @@ STIM_E_CUDA = -4
 STIM_E_TIMEOUT = -5
 STIM_E_BUSY = -6
 STIM_E_UNSUPPORTED = -7
+STIM_E_CAPACITY = -8
 
 STIM_MEAS_MAJOR = 0x0
 STIM_SHOT_MAJOR = 0x1
@@ -119,6 +121,8 @@ _SIGNATURES = {
     "stim_frame_sample_ex": (ctypes.c_int, [_VP, _U64, _U64, _U64, _VP, _VP, ctypes.c_int,
                                             ctypes.POINTER(StimTileHint), _VP]),
     "stim_frame_sample_noalloc": (ctypes.c_int, [_VP, _U64, _U64, _U64, _VP, _VP]),
+    "stim_frame_sample_detections": (ctypes.c_int, [_VP, _U64, _U64, _U64, _VP, _VP, _U64,
+                                                    ctypes.POINTER(_U64), ctypes.c_int, _VP]),
     "stim_batch_create": (ctypes.c_int, [ctypes.POINTER(_VP), ctypes.POINTER(_U64), ctypes.c_size_t,
                                          ctypes.POINTER(StimTileHint), _VP, ctypes.POINTER(_VP)]),
     "stim_batch_sample": (ctypes.c_int, [_VP, ctypes.POINTER(_U64), ctypes.POINTER(_U64),
@@ -203,6 +207,19 @@ def stim_frame_sample(handle: int, num_shots: int, seed: int, meas_out: int = 0,
                       flags: int = 0, stream: int = 0) -> None:
     _check(library().stim_frame_sample(handle, num_shots, seed & (2**64 - 1), meas_out or None,
                                        det_out or None, flags, stream or None))
+
+
+def stim_frame_sample_detections(handle: int, num_shots: int, seed: int, shot_offset: int = 0,
+                                 shot_begin: int = 0, detectors: int = 0, capacity: int = 0, flags: int = 0,
+                                 stream: int = 0) -> int:
+    """Per-shot lists of fired detectors; returns the total number of events.
+    Raises StimError(STIM_E_CAPACITY) when `capacity` is too small."""
+    cnt = _U64(0)
+    rc = library().stim_frame_sample_detections(handle, num_shots, seed & (2**64 - 1), shot_offset,
+                                                shot_begin or None, detectors or None, capacity,
+                                                ctypes.byref(cnt), flags, stream or None)
+    _check(rc)
+    return int(cnt.value)
 
 
 def stim_frame_sample_ex(handle: int, num_shots: int, seed: int, shot_offset: int = 0,
@@ -351,6 +368,19 @@ class Circuit:
                              ma.ctypes.data if ma is not None and ma.size else 0,
                              da.ctypes.data if da is not None and da.size else 0, flags, hint, 0)
         return ma, da
+
+
+    def sample_detections(self, num_shots: int, seed: int, *, shot_offset: int = 0, capacity: int = 0):
+        """Per-shot lists of fired detectors in host memory: returns
+        (shot_begin uint64[num_shots + 1], detectors uint32[count]). With
+        capacity 0 the count is taken first and the lists fetched second."""
+        begin = np.zeros(num_shots + 1, np.uint64)
+        if capacity <= 0:
+            capacity = stim_frame_sample_detections(self.handle, num_shots, seed, shot_offset, 0, 0, 0, STIM_HOST, 0)
+        dets = np.zeros(max(capacity, 1), np.uint32)
+        n = stim_frame_sample_detections(self.handle, num_shots, seed, shot_offset, begin.ctypes.data,
+                                         dets.ctypes.data, capacity, STIM_HOST, 0)
+        return begin, dets[:n]
 
 
 class Batch:

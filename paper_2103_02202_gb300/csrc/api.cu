@@ -476,6 +476,8 @@ void stim_free(stim_circuit *c) {
             cudaFree(sc.det);
             cudaFree(sc.tr);
             cudaFree(sc.gframe);
+            cudaFree(sc.hits);
+            cudaFree(sc.hits_out);
             if (sc.done) cudaEventDestroy(sc.done);
         }
         for (DevFrameProgram &d : c->fprog) {
@@ -607,6 +609,74 @@ int stim_frame_sample_ex(stim_circuit *c, uint64_t num_shots, uint64_t seed, uin
     STIMGB_CK(cudaEventRecord(sc.done, st), "record staging");
     sc.used = true;
     if (host && !async) STIMGB_CK(cudaStreamSynchronize(st), "sync");
+    return STIM_OK;
+}
+
+int stim_frame_sample_detections(stim_circuit *c, uint64_t num_shots, uint64_t seed, uint64_t shot_offset,
+                                 uint64_t *shot_begin, uint32_t *detectors, uint64_t capacity, uint64_t *count,
+                                 int flags, void *stream) {
+    if (!c || !count) return fail(STIM_E_INVALID_ARG, "stim_frame_sample_detections: null argument");
+    if (!valid_flags(flags, STIM_HOST))
+        return fail(STIM_E_INVALID_ARG, "stim_frame_sample_detections: unknown flags");
+    *count = 0;
+    cudaStream_t st = (cudaStream_t)stream;
+    int r = ensure_device(c);
+    if (r != STIM_OK) return r;
+    const bool host = (flags & STIM_HOST) != 0;
+    const uint64_t D = c->hp.num_det;
+    const uint64_t S = num_shots, nwords = (S + 63) / 64, dw = (D + 63) / 64;
+    stim_circuit::Scratch &sc = c->scratch[0];
+    if (!sc.done) STIMGB_CK(cudaEventCreateWithFlags(&sc.done, cudaEventDisableTiming), "event");
+    if (sc.used) STIMGB_CK(cudaStreamWaitEvent(st, sc.done, 0), "wait for staging");
+    // dense events [D][nwords] -> shot-major rows [S][dw] -> per-shot lists
+    if (D > 0 && S > 0 && (r = grow(&sc.det, &sc.det_cap, D * nwords, "alloc detectors")) != STIM_OK) return r;
+    if (D > 0 && S > 0 && (r = grow(&sc.tr, &sc.tr_cap, S * dw, "alloc transpose")) != STIM_OK) return r;
+    const uint64_t nblocks = (S + 1023) / 1024;
+    const size_t w_counts = (S + 1) / 2, w_part = S, w_tot = nblocks + 1;
+    const bool begin_here = host || !shot_begin;     // offsets staged in the pool
+    if ((r = grow(&sc.hits, &sc.hits_cap, w_counts + w_part + w_tot + (begin_here ? S + 1 : 0) + 1,
+                  "alloc event lists")) != STIM_OK)
+        return r;
+    uint32_t *counts = reinterpret_cast<uint32_t *>(sc.hits);
+    uint64_t *part = sc.hits + w_counts, *tot = part + w_part;
+    uint64_t *begin = begin_here ? tot + w_tot : shot_begin;
+    if (D > 0 && S > 0) {
+        r = stim_frame_sample_ex(c, S, seed, shot_offset, nullptr, sc.det, STIM_MEAS_MAJOR | STIM_DEVICE, nullptr,
+                                 stream);
+        if (r != STIM_OK) return r;
+        {
+            ProfScope ps(STIM_KERNEL_TRANSPOSE, st);
+            STIMGB_CK(launch_transpose(sc.det, D, nwords, S, sc.tr, dw, st), "transpose kernel");
+        }
+        STIMGB_CK(launch_hits(sc.tr, S, dw, counts, part, tot, begin, st), "event list kernels");
+    } else {
+        if (shot_offset % 64) return fail(STIM_E_INVALID_ARG, "stim_frame_sample: shot_offset must be a multiple of 64");
+        STIMGB_CK(cudaMemsetAsync(begin, 0, (S + 1) * sizeof(uint64_t), st), "event list offsets");
+    }
+    uint64_t total = 0;
+    STIMGB_CK(cudaMemcpyAsync(&total, begin + S, sizeof(uint64_t), cudaMemcpyDeviceToHost, st), "copy count");
+    STIMGB_CK(cudaStreamSynchronize(st), "sync");
+    *count = total;
+    const uint64_t keep = std::min<uint64_t>(total, detectors ? capacity : 0);
+    if (detectors && keep > 0) {
+        uint32_t *dst = detectors;
+        if (host) {      // a separate buffer: growing sc.hits would drop the offsets
+            if ((r = grow(&sc.hits_out, &sc.hits_out_cap, (keep + 1) / 2, "alloc event lists")) != STIM_OK) return r;
+            dst = reinterpret_cast<uint32_t *>(sc.hits_out);
+        }
+        STIMGB_CK(launch_hits_write(sc.tr, S, dw, begin, dst, keep, st), "event list kernel");
+        if (host) STIMGB_CK(cudaMemcpyAsync(detectors, dst, keep * sizeof(uint32_t), cudaMemcpyDeviceToHost, st),
+                            "copy events");
+    }
+    if (host && shot_begin)
+        STIMGB_CK(cudaMemcpyAsync(shot_begin, begin, (S + 1) * sizeof(uint64_t), cudaMemcpyDeviceToHost, st),
+                  "copy offsets");
+    STIMGB_CK(cudaEventRecord(sc.done, st), "record staging");
+    sc.used = true;
+    if (host) STIMGB_CK(cudaStreamSynchronize(st), "sync");
+    if (detectors && total > capacity)
+        return fail(STIM_E_CAPACITY, "stim_frame_sample_detections: " + std::to_string(total) +
+                                         " events exceed the capacity of " + std::to_string(capacity));
     return STIM_OK;
 }
 

@@ -53,6 +53,10 @@ struct stim_circuit {
         size_t tr_cap = 0;
         uint64_t *gframe = nullptr;
         size_t gframe_cap = 0;
+        uint64_t *hits = nullptr;         // per-shot event lists: counts, scans, offsets
+        size_t hits_cap = 0;
+        uint64_t *hits_out = nullptr;     // per-shot event lists: host-bound detector indices
+        size_t hits_out_cap = 0;
         cudaEvent_t done = nullptr;
         bool used = false;
     } scratch[2];

@@ -100,4 +100,14 @@ cudaError_t launch_detectors(const uint64_t *rec, uint64_t rec_stride, const uin
 cudaError_t launch_transpose(const uint64_t *in, uint64_t rows, uint64_t in_stride, uint64_t cols,
                              uint64_t *out, uint64_t out_stride, cudaStream_t stream);
 
+// Per-row lists of set bits (CSR): begin[0] = 0, begin[r + 1] = begin[r] +
+// popcount(row r), for nrows rows of `stride` words. Scratch: counts[nrows],
+// part[nrows], tot[ceil(nrows / 1024)]. launch_hits_write then stores the bit
+// indices of row r at out[begin[r] ...] in ascending order, skipping entries at
+// or beyond capacity.
+cudaError_t launch_hits(const uint64_t *rows, uint64_t nrows, uint64_t stride, uint32_t *counts, uint64_t *part,
+                        uint64_t *tot, uint64_t *begin, cudaStream_t stream);
+cudaError_t launch_hits_write(const uint64_t *rows, uint64_t nrows, uint64_t stride, const uint64_t *begin,
+                              uint32_t *out, uint64_t capacity, cudaStream_t stream);
+
 }  // namespace stimgb

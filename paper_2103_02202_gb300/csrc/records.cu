@@ -88,6 +88,100 @@ __global__ void __launch_bounds__(256) transpose_kernel(const uint64_t *__restri
     }
 }
 
+// ---- per-shot lists of fired detectors (CSR) from shot-major event rows ----
+
+// counts[s] = number of set bits of row s (one warp per row).
+__global__ void __launch_bounds__(256) hits_count_kernel(const uint64_t *__restrict__ rows, uint64_t nrows,
+                                                         uint64_t stride, uint32_t *__restrict__ counts) {
+    const uint32_t lane = threadIdx.x & 31;
+    const uint64_t warps = (uint64_t)gridDim.x * (blockDim.x >> 5);
+    for (uint64_t r = (uint64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5); r < nrows; r += warps) {
+        const uint64_t *row = rows + r * stride;
+        uint32_t c = 0;
+        for (uint64_t w = lane; w < stride; w += 32) c += __popcll(__ldg(row + w));
+        for (int d = 16; d > 0; d >>= 1) c += __shfl_xor_sync(0xffffffffu, c, d);
+        if (lane == 0) counts[r] = c;
+    }
+}
+
+// Inclusive scan of counts inside blocks of 1024: part[s], block totals tot[b].
+__global__ void __launch_bounds__(1024) hits_scan_kernel(const uint32_t *__restrict__ counts, uint64_t n,
+                                                         uint64_t *__restrict__ part, uint64_t *__restrict__ tot) {
+    __shared__ uint64_t warp_sum[32];
+    const uint32_t lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const uint64_t i = (uint64_t)blockIdx.x * 1024 + threadIdx.x;
+    uint64_t v = i < n ? counts[i] : 0;
+    for (int d = 1; d < 32; d <<= 1) {
+        const uint64_t u = __shfl_up_sync(0xffffffffu, v, d);
+        if (lane >= (uint32_t)d) v += u;
+    }
+    if (lane == 31) warp_sum[warp] = v;
+    __syncthreads();
+    if (warp == 0) {
+        uint64_t w = warp_sum[lane];
+        for (int d = 1; d < 32; d <<= 1) {
+            const uint64_t u = __shfl_up_sync(0xffffffffu, w, d);
+            if (lane >= (uint32_t)d) w += u;
+        }
+        warp_sum[lane] = w;     // inclusive over warps
+    }
+    __syncthreads();
+    if (warp > 0) v += warp_sum[warp - 1];
+    if (i < n) part[i] = v;
+    if (threadIdx.x == 1023) tot[blockIdx.x] = v;
+}
+
+// Exclusive scan of the block totals, in place (one thread: a few thousand
+// blocks at most per call), then begin[0] = 0 and begin[s + 1] = part[s] +
+// the exclusive total of s's block.
+__global__ void hits_block_offsets_kernel(uint64_t *tot, uint64_t nblocks) {
+    if (blockIdx.x != 0 || threadIdx.x != 0) return;
+    uint64_t run = 0;
+    for (uint64_t b = 0; b < nblocks; b++) {
+        const uint64_t t = tot[b];
+        tot[b] = run;
+        run += t;
+    }
+}
+
+__global__ void hits_begin_kernel(const uint64_t *__restrict__ part, const uint64_t *__restrict__ off, uint64_t n,
+                                  uint64_t *__restrict__ begin) {
+    for (uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; i <= n; i += (uint64_t)gridDim.x * blockDim.x)
+        begin[i] = i == 0 ? 0 : part[i - 1] + off[(i - 1) / 1024];
+}
+
+// Writes the fired columns of row r at begin[r]... (one warp per row; lanes
+// take 32 consecutive words, a warp prefix sum of their popcounts places each
+// lane's bits). Entries at or beyond `capacity` are not written.
+__global__ void __launch_bounds__(256) hits_write_kernel(const uint64_t *__restrict__ rows, uint64_t nrows,
+                                                         uint64_t stride, const uint64_t *__restrict__ begin,
+                                                         uint32_t *__restrict__ out, uint64_t capacity) {
+    const uint32_t lane = threadIdx.x & 31;
+    const uint64_t warps = (uint64_t)gridDim.x * (blockDim.x >> 5);
+    for (uint64_t r = (uint64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5); r < nrows; r += warps) {
+        const uint64_t *row = rows + r * stride;
+        uint64_t base = begin[r];
+        for (uint64_t w0 = 0; w0 < stride; w0 += 32) {
+            const uint64_t w = w0 + lane;
+            uint64_t bits = w < stride ? __ldg(row + w) : 0;
+            const uint32_t c = __popcll(bits);
+            uint32_t incl = c;
+            for (int d = 1; d < 32; d <<= 1) {
+                const uint32_t u = __shfl_up_sync(0xffffffffu, incl, d);
+                if (lane >= (uint32_t)d) incl += u;
+            }
+            uint64_t pos = base + incl - c;
+            while (bits) {
+                const uint32_t b = (uint32_t)__ffsll((long long)bits) - 1u;
+                bits &= bits - 1;
+                if (pos < capacity) out[pos] = (uint32_t)(w * 64 + b);
+                pos++;
+            }
+            base += __shfl_sync(0xffffffffu, incl, 31);
+        }
+    }
+}
+
 static uint32_t grid_for(uint64_t items, uint32_t threads) {
     uint64_t g = (items + threads - 1) / threads;
     if (g < 1) g = 1;
@@ -114,6 +208,30 @@ cudaError_t launch_transpose(const uint64_t *in, uint64_t rows, uint64_t in_stri
     uint64_t grid = groups < 1 ? 1 : groups;
     if (grid > 1u << 20) grid = 1u << 20;
     transpose_kernel<<<(uint32_t)grid, threads, 0, stream>>>(in, rows, in_stride, cols, out, out_stride);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_hits(const uint64_t *rows, uint64_t nrows, uint64_t stride, uint32_t *counts, uint64_t *part,
+                        uint64_t *tot, uint64_t *begin, cudaStream_t stream) {
+    if (nrows == 0) {
+        return cudaMemsetAsync(begin, 0, sizeof(uint64_t), stream);
+    }
+    const uint32_t warps_per_block = 8;
+    const uint32_t grid = grid_for(nrows, warps_per_block);
+    hits_count_kernel<<<grid, 32 * warps_per_block, 0, stream>>>(rows, nrows, stride, counts);
+    const uint64_t nblocks = (nrows + 1023) / 1024;
+    hits_scan_kernel<<<(uint32_t)nblocks, 1024, 0, stream>>>(counts, nrows, part, tot);
+    hits_block_offsets_kernel<<<1, 1, 0, stream>>>(tot, nblocks);
+    hits_begin_kernel<<<grid_for(nrows + 1, 256), 256, 0, stream>>>(part, tot, nrows, begin);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_hits_write(const uint64_t *rows, uint64_t nrows, uint64_t stride, const uint64_t *begin,
+                              uint32_t *out, uint64_t capacity, cudaStream_t stream) {
+    if (nrows == 0) return cudaSuccess;
+    const uint32_t warps_per_block = 8;
+    hits_write_kernel<<<grid_for(nrows, warps_per_block), 32 * warps_per_block, 0, stream>>>(rows, nrows, stride,
+                                                                                           begin, out, capacity);
     return cudaGetLastError();
 }
 

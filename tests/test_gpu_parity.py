@@ -334,3 +334,60 @@ def test_surface_d100_bench_configuration_sampled_parity():
     _, od = o.sample(pick, 2021, shot_offset=off, threads=16, ref=oref)
     np.testing.assert_array_equal(gd, od)
     c.close()
+
+
+def _lists_from_bits(bits):
+    """(shots, D) uint8 -> (begin, detectors) per-shot ascending lists."""
+    begin = [0]
+    dets = []
+    for row in bits:
+        idx = np.flatnonzero(row)
+        dets.extend(idx.tolist())
+        begin.append(len(dets))
+    return np.array(begin, np.uint64), np.array(dets, np.uint32)
+
+
+def test_detection_lists_match_oracle():
+    """stim_frame_sample_detections (per-shot fired-detector lists, host) equals
+    the oracle's detection events of the same shots."""
+    text = W.surface_code_memory(5, 6, 0.02)
+    S, off = 3001, 128
+    c = sg.Circuit(text)
+    begin, dets = c.sample_detections(S, 42, shot_offset=off)
+    _, od = oracle.Circuit(text).sample(np.arange(S), 42, shot_offset=off, threads=8)
+    eb, ed = _lists_from_bits(od)
+    np.testing.assert_array_equal(begin, eb)
+    np.testing.assert_array_equal(dets, ed)
+    # device outputs give the same lists
+    dbeg = torch.zeros(S + 1, dtype=torch.int64, device="cuda")
+    ddet = torch.zeros(len(ed) + 5, dtype=torch.int32, device="cuda")
+    n = sg.stim_frame_sample_detections(c.handle, S, 42, off, dbeg.data_ptr(), ddet.data_ptr(), len(ed) + 5,
+                                        sg.STIM_DEVICE, torch.cuda.current_stream().cuda_stream)
+    assert n == len(ed)
+    np.testing.assert_array_equal(dbeg.cpu().numpy().view(np.uint64), eb)
+    np.testing.assert_array_equal(ddet.cpu().numpy()[:n].view(np.uint32), ed)
+    c.close()
+
+
+def test_detection_lists_capacity_and_edges():
+    text = W.surface_code_memory(3, 3, 0.05)
+    c = sg.Circuit(text)
+    total = sg.stim_frame_sample_detections(c.handle, 500, 7, 0, 0, 0, 0, sg.STIM_HOST, 0)
+    assert total > 10
+    begin = np.zeros(501, np.uint64)
+    small = np.zeros(5, np.uint32)
+    with pytest.raises(sg.StimError) as ei:
+        sg.stim_frame_sample_detections(c.handle, 500, 7, 0, begin.ctypes.data, small.ctypes.data, 5,
+                                        sg.STIM_HOST, 0)
+    assert ei.value.code == sg.STIM_E_CAPACITY
+    fb, fd = c.sample_detections(500, 7)
+    assert int(fb[-1]) == total and len(fd) == total
+    np.testing.assert_array_equal(begin, fb)          # offsets are written in full
+    np.testing.assert_array_equal(small, fd[:5])      # and the first `capacity` entries
+    b0, d0 = c.sample_detections(0, 7)
+    assert b0.tolist() == [0] and len(d0) == 0
+    c.close()
+    nodet = sg.Circuit("H 0\nM 0\n")
+    b1, d1 = nodet.sample_detections(100, 1)
+    assert np.all(b1 == 0) and len(d1) == 0
+    nodet.close()
