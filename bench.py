@@ -556,7 +556,9 @@ def main():
 
     # ---- end to end: same steps through the public API with host output ----
     # Asynchronous host copies (STIM_ASYNC) on two alternating streams: step
-    # i's detection events travel to pinned host memory while step i+1 runs.
+    # i's detection events travel to pinned host memory while step i+1's
+    # kernels run. Two host buffers follow the library's two staging sets, so
+    # a buffer is rewritten only after its previous copy (that set's event).
     host_det = [torch.empty((D, nwords), dtype=torch.int64, pin_memory=True) for _ in range(2)]
     e2e_streams = [stream, torch.cuda.Stream()]
     e2e_steps = max(1, min(args.steps, 16))

@@ -157,9 +157,11 @@ int stim_frame_sample(stim_circuit *c, uint64_t num_shots, uint64_t seed,
  * copied out on `stream`. Without STIM_ASYNC the call returns after the copy.
  * With STIM_ASYNC it returns once the kernels and copies are enqueued: the
  * host buffers must stay valid and unread until `stream` is synchronized.
- * Asynchronous calls alternate between two staging sets, so the copies of one
- * call overlap the kernels of the next when the two run on different streams;
- * a call that reuses a set waits on the GPU for that set's previous copies.
+ * Asynchronous calls alternate between two staging sets and run their
+ * kernels in call order (each waits on the GPU for the previous asynchronous
+ * call's kernels), so on two streams the copies of one call overlap the
+ * kernels of the next; a call that reuses a set waits on the GPU for that
+ * set's previous copies.
  * Calls on one handle must still come from one host thread at a time.
  */
 int stim_frame_sample_ex(stim_circuit *c, uint64_t num_shots, uint64_t seed,

@@ -471,6 +471,7 @@ void stim_free(stim_circuit *c) {
         cudaFree(c->d_ref);
         cudaFree(c->d_detflag);
         cudaFree(c->d_status);
+        if (c->kernels_done) cudaEventDestroy(c->kernels_done);
         for (auto &sc : c->scratch) {
             cudaFree(sc.rec);
             cudaFree(sc.det);
@@ -550,6 +551,11 @@ int stim_frame_sample_ex(stim_circuit *c, uint64_t num_shots, uint64_t seed, uin
     stim_circuit::Scratch &sc = c->scratch[async ? (c->next_scratch++ & 1u) : 0u];
     if (!sc.done) STIMGB_CK(cudaEventCreateWithFlags(&sc.done, cudaEventDisableTiming), "event");
     if (sc.used) STIMGB_CK(cudaStreamWaitEvent(st, sc.done, 0), "wait for staging");
+    if (async) {
+        if (!c->kernels_done)
+            STIMGB_CK(cudaEventCreateWithFlags(&c->kernels_done, cudaEventDisableTiming), "event");
+        if (c->kernels_pending) STIMGB_CK(cudaStreamWaitEvent(st, c->kernels_done, 0), "wait for kernels");
+    }
 
     // ---- record buffers ----
     const bool meas_direct = meas_out && !shot_major && !host;
@@ -581,6 +587,10 @@ int stim_frame_sample_ex(stim_circuit *c, uint64_t num_shots, uint64_t seed, uin
         }
     }
     if ((r = launch_sampling(c, num_shots, seed, shot_offset, tc, rec, det, gframe, st)) != STIM_OK) return r;
+    if (async) {
+        STIMGB_CK(cudaEventRecord(c->kernels_done, st), "record kernels");
+        c->kernels_pending = true;
+    }
 
     // ---- output layouts ----
     auto emit = [&](uint64_t *src, uint64_t rows, uint64_t *dst) -> int {

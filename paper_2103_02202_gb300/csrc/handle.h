@@ -42,8 +42,8 @@ struct stim_circuit {
     size_t ref_words = 1;
     // Device staging of stim_frame_sample_ex (records, detection events,
     // transposes, spilled frames). Calls with STIM_ASYNC alternate between the
-    // two sets so one call's copies overlap the next call's kernels; every call
-    // waits on the GPU for the previous user of its set (done event).
+    // two sets so one call's copies overlap the next call's kernels; every
+    // call waits on the GPU for the previous user of its set (done event).
     struct Scratch {
         uint64_t *rec = nullptr;
         size_t rec_cap = 0;
@@ -61,6 +61,12 @@ struct stim_circuit {
         bool used = false;
     } scratch[2];
     unsigned next_scratch = 0;
+    // Asynchronous calls run their kernels in call order, even on different
+    // streams: each waits for the previous asynchronous call's kernels (not
+    // its copies), so kernels never share the GPU with each other while the
+    // copies of earlier calls overlap them.
+    cudaEvent_t kernels_done = nullptr;
+    bool kernels_pending = false;
     DevFrameProgram fprog[4];           // cluster sizes 1, 2, 4, 8
 };
 
