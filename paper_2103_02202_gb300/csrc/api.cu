@@ -302,7 +302,7 @@ int choose_tile(uint32_t n, uint64_t nwords, int sms, size_t smem_optin, const s
     }
     if (hint && hint->threads) {
         if ((int)hint->threads > frame_max_threads(t.W))
-            return fail(STIM_E_INVALID_ARG, "tile hint: too many threads per CTA for this many words per tile (768 for 2, 512 for 4 or 8)");
+            return fail(STIM_E_INVALID_ARG, "tile hint: too many threads per CTA for this many words per tile (448 for 1, 768 for 2, 512 for 4 or 8)");
         t.threads = hint->threads;
     } else if (t.gmem) {
         t.threads = 256;
@@ -314,7 +314,7 @@ int choose_tile(uint32_t n, uint64_t nwords, int sms, size_t smem_optin, const s
         size_t ctas = per_sm / per_cta;
         if (ctas < 1) ctas = 1;
         uint32_t th = (uint32_t)(2048 / ctas);
-        if (th > 512) th = 512;
+        if (th > (uint32_t)frame_max_threads(t.W)) th = (uint32_t)frame_max_threads(t.W);
         if (th < 256) th = 256;
         t.threads = th & ~31u;      // whole warps: the kernel's warp collectives name all 32 lanes
     }

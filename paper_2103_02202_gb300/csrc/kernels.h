@@ -41,8 +41,10 @@ constexpr uint32_t kHitQueueCap = 32;          // entries per warp
 constexpr uint32_t kTileHeaderBytes = kHitQueueOffset + 32 * kHitQueueCap * 4;
 
 // Largest CTA of a frame kernel with W words per tile: threads that apply ops
-// to two or four words at once need more registers.
-constexpr int frame_max_threads(int W) { return W >= 4 ? 512 : W == 2 ? 768 : 1024; }
+// to two or four words at once need more registers. One-word tiles are sized
+// for two CTAs of up to 448 threads per SM (72 registers, no spills).
+constexpr int frame_max_threads(int W) { return W >= 4 ? 512 : W == 2 ? 768 : 448; }
+constexpr int frame_min_ctas(int W) { return W == 1 ? 2 : 1; }
 inline size_t tile_smem_bytes(uint32_t Q, int W, bool gmem, uint32_t meta_region) {
     return kTileHeaderBytes + meta_region + (gmem ? 0 : (size_t)Q * 2 * W * 8);
 }
