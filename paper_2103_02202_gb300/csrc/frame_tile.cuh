@@ -33,11 +33,12 @@ __device__ __forceinline__ DevOp as_op(uint4 v) { return DevOp{v.x, v.y, v.z, v.
 
 // Layer barrier of the tile, split in two halves: arrive when this thread's
 // frame writes of the layer are done, wait before the next layer touches the
-// frame. The loads of the next layer's first ops are issued in between.
+// frame. A single CTA uses its CTA barrier; a cluster's release/acquire
+// barrier also orders the CTA's own shared-memory accesses.
 template <int C>
 __device__ __forceinline__ void tile_arrive() {
-    __syncthreads();
     if constexpr (C > 1) asm volatile("barrier.cluster.arrive.release.aligned;" ::: "memory");
+    else __syncthreads();
 }
 template <int C>
 __device__ __forceinline__ void tile_wait() {
@@ -532,15 +533,22 @@ __device__ __forceinline__ bool run_tile(const FrameArgs &a, unsigned char *dyn,
                     const uint4 sv = segs[s];
                     const uint32_t len = sv.x, items = sv.z * (W / V), span = (items + 31u) & ~31u;
                     const uint32_t dfrom = sv.w;
+                    bool have_next = false;      // nxt holds this item's first op
+                    uint4 nxt = make_uint4(0u, 0u, 0u, 0u);
                     for (; g < seg_start + span; g += blockDim.x) {
                         const uint32_t it = g - seg_start;
                         const bool act = it < items;
                         const uint32_t wo = act ? (it % (W / V)) * V : 0u;
                         const uint32_t op0 = sv.y + (act ? it / (W / V) : 0u) * len;
-                        uint4 nxt = __ldg(ops + op0);
+                        if (!have_next) nxt = __ldg(ops + op0);
+                        // the thread's next item of this segment, if any
+                        const uint32_t it2 = it + blockDim.x;
+                        have_next = g + blockDim.x < seg_start + span;
+                        const uint32_t op2 = sv.y + (it2 < items ? it2 / (W / V) : 0u) * len;
                         for (uint32_t j = 0; j < len; j++) {
                             const uint4 ov = nxt;
                             if (j + 1 < len) nxt = __ldg(ops + op0 + j + 1);     // one op ahead
+                            else if (have_next) nxt = __ldg(ops + op2);         // across items
                             if (j < dfrom) {
                                 if (act) frame_op<W, C, GMEM>(a, key, t, as_op(ov), wo, tile0, instr_off, meas_off);
                             } else {
