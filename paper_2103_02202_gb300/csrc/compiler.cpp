@@ -479,7 +479,8 @@ void collect_detectors(const Block &b, uint64_t *meas, HostProgram *hp) {
 namespace {
 
 struct Chain {
-    uint32_t q0, q1;            // footprint (q1 == q0 for one qubit)
+    uint32_t q0;                // first qubit of the first op (decides the owning CTA)
+    std::vector<uint32_t> qs;   // footprint
     std::vector<DevOp> ops;     // global encoding (as in HostProgram::ops)
 };
 
@@ -489,12 +490,19 @@ inline uint32_t op_q1(const DevOp &d) {
     return op_is_pair(opc) ? (d.b & kQubitMask) : op_q0(d);
 }
 
+// Longest chain: bounds the work one thread does between two barriers.
+constexpr size_t kMaxChainOps = 12;
+
 class FrameBuilder {
   public:
     FrameBuilder(const HostProgram &hp, int C, FrameProgram *fp) : hp_(hp), C_(C), fp_(fp), owner_(hp.num_qubits + 1, -1) {}
 
     // Folds the layers [first, last) (consecutive LAYER entries of hp.prog)
-    // into merged layers; returns the number of merged layers emitted.
+    // into merged layers; returns the number of merged layers emitted. A layer
+    // folds into the open merged layer when none of its ops touches qubits of
+    // two different chains: an op on qubits of one chain is appended to it
+    // (its other qubits, untouched so far in the merged layer, join the
+    // chain's footprint); an op on untouched qubits starts a new chain.
     uint32_t run(size_t first, size_t last) {
         uint32_t emitted = 0;
         for (size_t k = first; k < last; k++) {
@@ -502,21 +510,26 @@ class FrameBuilder {
             const uint32_t tot = e.n_gate + e.n_noise + e.n_collapse;
             const DevOp *ops = hp_.ops.data() + e.op_begin;
             bool fold = !chains_.empty();
-            if (fold) {
-                for (uint32_t i = 0; i < tot && fold; i++) {
-                    const int c0 = owner_[op_q0(ops[i])], c1 = owner_[op_q1(ops[i])];
-                    fold = c0 >= 0 && c0 == c1;
-                }
+            for (uint32_t i = 0; i < tot && fold; i++) {
+                const int own = chain_of(ops[i]);
+                if (own == -2 || (own >= 0 && chains_[own].ops.size() >= kMaxChainOps)) fold = false;
             }
-            if (!fold) {
-                if (!chains_.empty()) emitted += emit();
-                for (uint32_t i = 0; i < tot; i++) {
-                    Chain ch{op_q0(ops[i]), op_q1(ops[i]), {ops[i]}};
-                    owner_[ch.q0] = owner_[ch.q1] = (int)chains_.size();
-                    chains_.push_back(std::move(ch));
+            if (!fold && !chains_.empty()) emitted += emit();
+            for (uint32_t i = 0; i < tot; i++) {
+                const int own = chain_of(ops[i]);       // -1 after an emit
+                const uint32_t q[2] = {op_q0(ops[i]), op_q1(ops[i])};
+                int c = own;
+                if (c < 0) {
+                    c = (int)chains_.size();
+                    chains_.push_back(Chain{q[0], {}, {}});
                 }
-            } else {
-                for (uint32_t i = 0; i < tot; i++) chains_[owner_[op_q0(ops[i])]].ops.push_back(ops[i]);
+                chains_[c].ops.push_back(ops[i]);
+                for (uint32_t qq : q) {
+                    if (owner_[qq] < 0) {
+                        owner_[qq] = c;
+                        chains_[c].qs.push_back(qq);
+                    }
+                }
             }
         }
         if (!chains_.empty()) emitted += emit();
@@ -524,6 +537,13 @@ class FrameBuilder {
     }
 
   private:
+    // Chain owning the op's qubits: -1 none, -2 two different chains.
+    int chain_of(const DevOp &d) const {
+        const int a = owner_[op_q0(d)], b = owner_[op_q1(d)];
+        if (a >= 0 && b >= 0 && a != b) return -2;
+        return a >= 0 ? a : b;
+    }
+
     const HostProgram &hp_;
     int C_;
     FrameProgram *fp_;
@@ -600,7 +620,8 @@ class FrameBuilder {
         e.n_noise = nn;
         e.n_collapse = nc;
         fp_->prog.push_back(e);
-        for (const Chain &ch : chains_) owner_[ch.q0] = owner_[ch.q1] = -1;
+        for (const Chain &ch : chains_)
+            for (uint32_t q : ch.qs) owner_[q] = -1;
         chains_.clear();
         return 1;
     }
