@@ -17,23 +17,53 @@
 
 namespace stimgb {
 
-__global__ void detector_kernel(const uint64_t *__restrict__ rec, uint64_t rec_stride,
-                                const uint64_t *__restrict__ det_ptr, const uint32_t *__restrict__ det_meas,
-                                const uint64_t *__restrict__ ref, uint64_t ndet, uint64_t nwords,
-                                uint64_t last_mask, uint64_t *__restrict__ det, uint64_t det_stride) {
-    const uint64_t total = ndet * nwords;
-    for (uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; i < total;
-         i += (uint64_t)gridDim.x * blockDim.x) {
-        const uint64_t k = i / nwords, w = i % nwords;
+// One warp per detector row (warps stride over detectors): the detector's
+// measurement list and reference bits are warp-uniform loads, and the lanes
+// sweep the row's 64-shot words two at a time with 16-byte loads when the
+// record rows are 16-byte aligned.
+__global__ void __launch_bounds__(256) detector_kernel(const uint64_t *__restrict__ rec, uint64_t rec_stride,
+                                                       const uint64_t *__restrict__ det_ptr,
+                                                       const uint32_t *__restrict__ det_meas,
+                                                       const uint64_t *__restrict__ ref, uint64_t ndet,
+                                                       uint64_t nwords, uint64_t last_mask,
+                                                       uint64_t *__restrict__ det, uint64_t det_stride) {
+    const uint32_t lane = threadIdx.x & 31;
+    const uint64_t warps = (uint64_t)gridDim.x * (blockDim.x >> 5);
+    const bool pairs = (rec_stride % 2 == 0) && (det_stride % 2 == 0) &&
+                       ((reinterpret_cast<uintptr_t>(rec) | reinterpret_cast<uintptr_t>(det)) % 16 == 0);
+    for (uint64_t k = (uint64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5); k < ndet; k += warps) {
         const uint64_t b = __ldg(det_ptr + k), e = __ldg(det_ptr + k + 1);
-        uint64_t v = 0;
-        for (uint64_t t = b; t < e; t++) {
-            const uint32_t m = __ldg(det_meas + t);
-            const uint64_t refm = 0ull - ((__ldg(ref + (m >> 6)) >> (m & 63)) & 1ull);
-            v ^= rec[(uint64_t)m * rec_stride + w] ^ refm;
+        uint64_t *out = det + k * det_stride;
+        if (pairs) {
+            for (uint64_t w = 2 * lane; w < nwords; w += 64) {
+                uint64_t v0 = 0, v1 = 0;
+                for (uint64_t t = b; t < e; t++) {
+                    const uint32_t m = __ldg(det_meas + t);
+                    const uint64_t refm = 0ull - ((__ldg(ref + (m >> 6)) >> (m & 63)) & 1ull);
+                    const ulonglong2 r = __ldg(reinterpret_cast<const ulonglong2 *>(rec + (uint64_t)m * rec_stride + w));
+                    v0 ^= r.x ^ refm;
+                    v1 ^= r.y ^ refm;
+                }
+                if (w == nwords - 1) v0 &= last_mask;
+                if (w + 1 == nwords - 1) v1 &= last_mask;
+                if (w + 1 < nwords) {
+                    *reinterpret_cast<ulonglong2 *>(out + w) = make_ulonglong2(v0, v1);
+                } else {
+                    out[w] = v0;
+                }
+            }
+        } else {
+            for (uint64_t w = lane; w < nwords; w += 32) {
+                uint64_t v = 0;
+                for (uint64_t t = b; t < e; t++) {
+                    const uint32_t m = __ldg(det_meas + t);
+                    const uint64_t refm = 0ull - ((__ldg(ref + (m >> 6)) >> (m & 63)) & 1ull);
+                    v ^= __ldg(rec + (uint64_t)m * rec_stride + w) ^ refm;
+                }
+                if (w == nwords - 1) v &= last_mask;
+                out[w] = v;
+            }
         }
-        if (w == nwords - 1) v &= last_mask;
-        det[k * det_stride + w] = v;
     }
 }
 
@@ -194,8 +224,8 @@ cudaError_t launch_detectors(const uint64_t *rec, uint64_t rec_stride, const uin
                              uint64_t last_mask, uint64_t *det, uint64_t det_stride, cudaStream_t stream) {
     if (ndet == 0 || nwords == 0) return cudaSuccess;
     const uint32_t threads = 256;
-    detector_kernel<<<grid_for(ndet * nwords, threads), threads, 0, stream>>>(
-        rec, rec_stride, det_ptr, det_meas, ref, ndet, nwords, last_mask, det, det_stride);
+    detector_kernel<<<grid_for(ndet, threads / 32), threads, 0, stream>>>(rec, rec_stride, det_ptr, det_meas, ref,
+                                                                         ndet, nwords, last_mask, det, det_stride);
     return cudaGetLastError();
 }
 
