@@ -46,7 +46,7 @@ struct DetDesc {
     const uint64_t *ref;
     uint64_t ndet, nwords, last_mask;
     uint64_t *det;
-    uint64_t item_begin;   // prefix sum of ndet * nwords over earlier circuits
+    uint64_t row_begin;    // detector rows of earlier circuits
 };
 
 constexpr uint32_t kDescBytes = 256;   // FrameArgs copy at the start of dynamic smem
@@ -86,27 +86,34 @@ __global__ void __launch_bounds__(frame_max_threads(W), frame_min_ctas(W)) batch
     }
 }
 
-__global__ void batch_detector_kernel(const DetDesc *__restrict__ d, uint32_t k, uint64_t total) {
-    for (uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; i < total;
-         i += (uint64_t)gridDim.x * blockDim.x) {
-        uint32_t lo = 0, hi = k - 1;        // last circuit with item_begin <= i
+// One warp per detector row of the batch (rows numbered across circuits):
+// the owning circuit is found once per row, then the lanes sweep the row's
+// words as in the single-circuit detector kernel.
+__global__ void __launch_bounds__(256) batch_detector_kernel(const DetDesc *__restrict__ d, uint32_t k,
+                                                             uint64_t rows) {
+    const uint32_t lane = threadIdx.x & 31;
+    const uint64_t warps = (uint64_t)gridDim.x * (blockDim.x >> 5);
+    for (uint64_t i = (uint64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5); i < rows; i += warps) {
+        uint32_t lo = 0, hi = k - 1;        // last circuit with row_begin <= i
         while (lo < hi) {
             const uint32_t mid = (lo + hi + 1) >> 1;
-            if (d[mid].item_begin <= i) lo = mid;
+            if (d[mid].row_begin <= i) lo = mid;
             else hi = mid - 1;
         }
         const DetDesc &c = d[lo];
-        const uint64_t j = i - c.item_begin;
-        const uint64_t det = j / c.nwords, w = j % c.nwords;
+        const uint64_t det = i - c.row_begin;
         const uint64_t b = __ldg(c.det_ptr + det), e = __ldg(c.det_ptr + det + 1);
-        uint64_t v = 0;
-        for (uint64_t t = b; t < e; t++) {
-            const uint32_t m = __ldg(c.det_meas + t);
-            const uint64_t refm = 0ull - ((__ldg(c.ref + (m >> 6)) >> (m & 63)) & 1ull);
-            v ^= c.rec[(uint64_t)m * c.rec_stride + w] ^ refm;
+        uint64_t *out = c.det + det * c.nwords;
+        for (uint64_t w = lane; w < c.nwords; w += 32) {
+            uint64_t v = 0;
+            for (uint64_t t = b; t < e; t++) {
+                const uint32_t m = __ldg(c.det_meas + t);
+                const uint64_t refm = 0ull - ((__ldg(c.ref + (m >> 6)) >> (m & 63)) & 1ull);
+                v ^= __ldg(c.rec + (uint64_t)m * c.rec_stride + w) ^ refm;
+            }
+            if (w == c.nwords - 1) v &= c.last_mask;
+            out[w] = v;
         }
-        if (w == c.nwords - 1) v &= c.last_mask;
-        c.det[det * c.nwords + w] = v;
     }
 }
 
@@ -353,8 +360,8 @@ int fill_descs(stim_batch *b, const uint64_t *seeds, const uint64_t *offsets, ui
         d.nwords = nwords;
         d.last_mask = last_mask;
         d.det = det;
-        d.item_begin = b->det_total;
-        b->det_total += d.ndet * nwords;
+        d.row_begin = b->det_total;
+        b->det_total += d.ndet;
         b->h_det[i] = d;
     }
     return STIM_OK;
@@ -371,7 +378,7 @@ int enqueue(stim_batch *b, cudaStream_t st, uint32_t nitems_limit) {
                             b->smem, st),
                "batch frame kernel");
     if (b->det_total) {
-        uint64_t grid = (b->det_total + 255) / 256;
+        uint64_t grid = (b->det_total + 7) / 8;      // 8 warps (rows) per block
         if (grid > 65535ull * 32) grid = 65535ull * 32;
         batch_detector_kernel<<<(unsigned)grid, 256, 0, st>>>(b->d_det, (uint32_t)b->k, b->det_total);
         STIMGB_BCK(cudaGetLastError(), "batch detector kernel");
