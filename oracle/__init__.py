@@ -32,7 +32,9 @@ _lib = None
 
 GATES = {"H": 0, "S": 1, "CX": 2, "CZ": 3, "M": 4, "MR": 5, "R": 6,
          "X_ERROR": 7, "Z_ERROR": 8, "DEPOLARIZE1": 9, "DEPOLARIZE2": 10,
-         "DETECTOR": 11, "X": 12}
+         "DETECTOR": 11, "X": 12, "Y": 13, "Z": 14, "S_DAG": 15, "SQRT_X": 16,
+         "SQRT_X_DAG": 17, "SQRT_Y": 18, "SQRT_Y_DAG": 19, "Y_ERROR": 20,
+         "MX": 21, "MY": 22, "MRX": 23, "MRY": 24, "RX": 25, "RY": 26}
 TAG_NOISE, TAG_COLLAPSE, TAG_INIT = 0, 1, 2
 
 

@@ -46,7 +46,10 @@
 /* ------------------------------------------------------------------------ */
 enum {
     OG_H, OG_S, OG_CX, OG_CZ, OG_M, OG_MR, OG_R,
-    OG_XERR, OG_ZERR, OG_DEP1, OG_DEP2, OG_DET, OG_X /* internal only */
+    OG_XERR, OG_ZERR, OG_DEP1, OG_DEP2, OG_DET, OG_X,
+    /* wider gate set */
+    OG_Y, OG_Z, OG_SDAG, OG_SQX, OG_SQXD, OG_SQY, OG_SQYD, OG_YERR,
+    OG_MX, OG_MY, OG_MRX, OG_MRY, OG_RX, OG_RY
 };
 
 typedef struct {
@@ -169,6 +172,9 @@ static noise_word noise_for_word(uint64_t seed, int gate, const uint64_t G[64],
             r.x0 |= bit;
         } else if (gate == OG_ZERR) {
             r.z0 |= bit;
+        } else if (gate == OG_YERR) {
+            r.x0 |= bit;
+            r.z0 |= bit;
         } else if (gate == OG_DEP1) {
             uint32_t v = drawer_next(&d);
             uint32_t pa = 1 + (uint32_t)(((uint64_t)3 * v) >> 32);  /* 1 X, 2 Y, 3 Z */
@@ -269,11 +275,41 @@ static int gate_from_name(const char *w, size_t n) {
     if (IS("DEPOLARIZE1")) return OG_DEP1;
     if (IS("DEPOLARIZE2")) return OG_DEP2;
     if (IS("DETECTOR")) return OG_DET;
+    if (IS("X")) return OG_X;
+    if (IS("Y")) return OG_Y;
+    if (IS("Z")) return OG_Z;
+    if (IS("S_DAG")) return OG_SDAG;
+    if (IS("SQRT_X")) return OG_SQX;
+    if (IS("SQRT_X_DAG")) return OG_SQXD;
+    if (IS("SQRT_Y")) return OG_SQY;
+    if (IS("SQRT_Y_DAG")) return OG_SQYD;
+    if (IS("Y_ERROR")) return OG_YERR;
+    if (IS("MX")) return OG_MX;
+    if (IS("MY")) return OG_MY;
+    if (IS("MRX")) return OG_MRX;
+    if (IS("MRY")) return OG_MRY;
+    if (IS("RX")) return OG_RX;
+    if (IS("RY")) return OG_RY;
 #undef IS
     return -1;
 }
 
-static int is_noise(int g) { return g == OG_XERR || g == OG_ZERR || g == OG_DEP1 || g == OG_DEP2; }
+static int is_noise(int g) { return g == OG_XERR || g == OG_ZERR || g == OG_DEP1 || g == OG_DEP2 || g == OG_YERR; }
+static int is_1q_gate(int g) {
+    return g == OG_H || g == OG_S || g == OG_X || g == OG_Y || g == OG_Z || g == OG_SDAG || g == OG_SQX ||
+           g == OG_SQXD || g == OG_SQY || g == OG_SQYD;
+}
+/* Collapsing ops: basis (0 Z, 1 X, 2 Y) and kind (0 M, 1 MR, 2 R). */
+static int collapse_basis(int g) {
+    return (g == OG_MX || g == OG_MRX || g == OG_RX) ? 1 : (g == OG_MY || g == OG_MRY || g == OG_RY) ? 2 : 0;
+}
+static int collapse_kind(int g) {
+    return (g == OG_M || g == OG_MX || g == OG_MY) ? 0 : (g == OG_MR || g == OG_MRX || g == OG_MRY) ? 1 : 2;
+}
+static int is_collapse(int g) {
+    return g == OG_M || g == OG_MR || g == OG_R || g == OG_MX || g == OG_MY || g == OG_MRX || g == OG_MRY ||
+           g == OG_RX || g == OG_RY;
+}
 static int is_pair(int g) { return g == OG_CX || g == OG_CZ || g == OG_DEP2; }
 
 /* Parse one line [b, e) into node k. */
@@ -424,7 +460,7 @@ static int flatten(pstate *ps, const node *blk, orc_circuit *c) {
             } else {
                 c->ngate_targets += slots;
             }
-            if (k->gate == OG_M || k->gate == OG_MR) c->nmeas += k->nt;
+            if (is_collapse(k->gate) && collapse_kind(k->gate) != 2) c->nmeas += k->nt;
         }
     }
     return 0;
@@ -491,6 +527,34 @@ static int gate_images(int g, spauli img[4]) {
     case OG_X:  /* X -> X, Z -> -Z */
         img[0] = (spauli){1, 0, 0};
         img[1] = (spauli){0, 1, 1};
+        return 1;
+    case OG_Y:  /* X -> -X, Z -> -Z */
+        img[0] = (spauli){1, 0, 1};
+        img[1] = (spauli){0, 1, 1};
+        return 1;
+    case OG_Z:  /* X -> -X, Z -> Z */
+        img[0] = (spauli){1, 0, 1};
+        img[1] = (spauli){0, 1, 0};
+        return 1;
+    case OG_SDAG:  /* X -> Y, Z -> Z */
+        img[0] = (spauli){1, 1, 0};
+        img[1] = (spauli){0, 1, 0};
+        return 1;
+    case OG_SQX:   /* X -> X, Z -> Y */
+        img[0] = (spauli){1, 0, 0};
+        img[1] = (spauli){1, 1, 0};
+        return 1;
+    case OG_SQXD:  /* X -> X, Z -> -Y */
+        img[0] = (spauli){1, 0, 0};
+        img[1] = (spauli){1, 1, 1};
+        return 1;
+    case OG_SQY:   /* X -> Z, Z -> -X */
+        img[0] = (spauli){0, 1, 0};
+        img[1] = (spauli){1, 0, 1};
+        return 1;
+    case OG_SQYD:  /* X -> -Z, Z -> X */
+        img[0] = (spauli){0, 1, 1};
+        img[1] = (spauli){1, 0, 0};
         return 1;
     case OG_CX: /* X_a -> X_a X_b, Z_a -> Z_a, X_b -> X_b, Z_b -> Z_a Z_b */
         img[0] = (spauli){1 | 2, 0, 0};
@@ -840,24 +904,34 @@ int orc_reference(const orc_circuit *c, uint8_t *ref, uint8_t *detflag) {
     uint64_t m = 0;
     for (size_t i = 0; i < c->nops; i++) {
         const orc_op *o = &c->ops[i];
-        switch (o->gate) {
-        case OG_H: case OG_S:
+        if (is_1q_gate(o->gate)) {
             for (uint32_t j = 0; j < o->nt; j++) tableau_prepend(&T, o->gate, &o->t[j], tmpx, tmpz, tmps);
-            break;
-        case OG_CX: case OG_CZ:
-            for (uint32_t j = 0; j < o->nt; j += 2) tableau_prepend(&T, o->gate, &o->t[j], tmpx, tmpz, tmps);
-            break;
-        case OG_M: case OG_MR: case OG_R:
+            continue;
+        }
+        if (is_collapse(o->gate)) {
+            /* X and Y bases: the basis change (H; or S_DAG then H) that maps the
+             * measured observable to Z, the Z-basis op, then its inverse */
+            const int basis = collapse_basis(o->gate), kind = collapse_kind(o->gate);
             for (uint32_t j = 0; j < o->nt; j++) {
+                const uint32_t *q = &o->t[j];
+                if (basis == 2) tableau_prepend(&T, OG_SDAG, q, tmpx, tmpz, tmps);
+                if (basis != 0) tableau_prepend(&T, OG_H, q, tmpx, tmpz, tmps);
                 int det;
-                int r = tableau_measure(&T, o->t[j], &det);
-                if (o->gate != OG_R) {
+                int r = tableau_measure(&T, *q, &det);
+                if (kind != 2) {
                     ref[m] = (uint8_t)r;
                     if (detflag) detflag[m] = (uint8_t)det;
                     m++;
                 }
-                if (o->gate != OG_M) set_sign(&T, 2 * o->t[j] + 1, 0);   /* force |0> */
+                if (kind != 0) set_sign(&T, 2 * *q + 1, 0);   /* force the +1 eigenstate */
+                if (basis != 0) tableau_prepend(&T, OG_H, q, tmpx, tmpz, tmps);
+                if (basis == 2) tableau_prepend(&T, OG_S, q, tmpx, tmpz, tmps);
             }
+            continue;
+        }
+        switch (o->gate) {
+        case OG_CX: case OG_CZ:
+            for (uint32_t j = 0; j < o->nt; j += 2) tableau_prepend(&T, o->gate, &o->t[j], tmpx, tmpz, tmps);
             break;
         default:
             break;   /* noise and detectors do not touch the noiseless sample */
@@ -888,9 +962,9 @@ static void *frame_worker(void *arg) {
     uint8_t *x = (uint8_t *)calloc(c->n + 1, 1);
     uint8_t *z = (uint8_t *)calloc(c->n + 1, 1);
     uint8_t *flip = (uint8_t *)calloc(c->nmeas + 1, 1);
-    spauli imgH[4], imgS[4], imgCX[4], imgCZ[4];
-    gate_images(OG_H, imgH);
-    gate_images(OG_S, imgS);
+    spauli img1[OG_RY + 1][4], imgCX[4], imgCZ[4];
+    for (int g = 0; g <= OG_RY; g++)
+        if (is_1q_gate(g)) gate_images(g, img1[g]);
     gate_images(OG_CX, imgCX);
     gate_images(OG_CZ, imgCZ);
     for (size_t si = jb->begin; si < jb->end; si++) {
@@ -908,19 +982,18 @@ static void *frame_worker(void *arg) {
         for (size_t i = 0; i < c->nops; i++) {
             const orc_op *o = &c->ops[i];
             uint32_t instr = (uint32_t)i;
-            switch (o->gate) {
-            case OG_H: case OG_S: {
-                const spauli *img = o->gate == OG_H ? imgH : imgS;
+            if (is_1q_gate(o->gate)) {
                 for (uint32_t j = 0; j < o->nt; j++) {
                     uint32_t q = o->t[j];
                     uint8_t rx, rz;
                     int ph;
-                    conj_local(img, 1, x[q], z[q], &rx, &rz, &ph);
+                    conj_local(img1[o->gate], 1, x[q], z[q], &rx, &rz, &ph);
                     x[q] = rx;
                     z[q] = rz;
                 }
-                break;
+                continue;
             }
+            switch (o->gate) {
             case OG_CX: case OG_CZ: {
                 const spauli *img = o->gate == OG_CX ? imgCX : imgCZ;
                 for (uint32_t j = 0; j < o->nt; j += 2) {
@@ -934,23 +1007,32 @@ static void *frame_worker(void *arg) {
                 break;
             }
             case OG_M: case OG_MR: case OG_R:
+            case OG_MX: case OG_MY: case OG_MRX: case OG_MRY: case OG_RX: case OG_RY: {
+                const int basis = collapse_basis(o->gate), kind = collapse_kind(o->gate);
                 for (uint32_t j = 0; j < o->nt; j++) {
                     uint32_t q = o->t[j];
                     uint8_t coin = (uint8_t)((half_mask(jb->seed, TAG_COLLAPSE, instr, j, word) >> b) & 1);
-                    if (o->gate != OG_R) {
+                    uint8_t rx, rz;
+                    int ph;
+                    if (basis == 2) { conj_local(img1[OG_SDAG], 1, x[q], z[q], &rx, &rz, &ph); x[q] = rx; z[q] = rz; }
+                    if (basis != 0) { conj_local(img1[OG_H], 1, x[q], z[q], &rx, &rz, &ph); x[q] = rx; z[q] = rz; }
+                    if (kind != 2) {
                         flip[m] = x[q];
                         if (mrow) mrow[m] = (uint8_t)(jb->ref[m] ^ x[q]);
                         m++;
                     }
-                    if (o->gate == OG_M) {
+                    if (kind == 0) {
                         z[q] ^= coin;
                     } else {
                         x[q] = 0;
                         z[q] = coin;
                     }
+                    if (basis != 0) { conj_local(img1[OG_H], 1, x[q], z[q], &rx, &rz, &ph); x[q] = rx; z[q] = rz; }
+                    if (basis == 2) { conj_local(img1[OG_S], 1, x[q], z[q], &rx, &rz, &ph); x[q] = rx; z[q] = rz; }
                 }
                 break;
-            case OG_XERR: case OG_ZERR: case OG_DEP1: case OG_DEP2: {
+            }
+            case OG_XERR: case OG_ZERR: case OG_YERR: case OG_DEP1: case OG_DEP2: {
                 if (o->p <= 0) break;
                 int pair = o->gate == OG_DEP2;
                 for (uint32_t j = 0; j < o->nt; j += pair ? 2 : 1) {

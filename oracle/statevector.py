@@ -2,8 +2,9 @@
 
 Used to pin the tableau and frame oracles on small circuits (Section 5.5 of
 the paper checks gate tableaus against unitaries the same way). Holds its own
-tiny parser and the gate unitaries as plain matrices; noise channels are
-ignored (noiseless semantics only).
+tiny parser and the gate unitaries as plain matrices; measurements and resets
+in the X, Y and Z bases are projections onto the measured Pauli's eigenspaces;
+noise channels are ignored (noiseless semantics only).
 
 * ``reference(text)``: the outcome-0 noiseless sample: each measurement whose
   outcome is random (P(0) = 1/2) is projected onto 0, otherwise onto its
@@ -21,7 +22,15 @@ _S2 = 1 / np.sqrt(2)
 UNITARY = {
     "H": np.array([[1, 1], [1, -1]], complex) * _S2,
     "S": np.diag([1, 1j]).astype(complex),
+    "S_DAG": np.diag([1, -1j]).astype(complex),
     "X": np.array([[0, 1], [1, 0]], complex),
+    "Y": np.array([[0, -1j], [1j, 0]], complex),
+    "Z": np.diag([1, -1]).astype(complex),
+    # square roots: SQRT_X^2 = X, SQRT_Y^2 = Y (the e^{-i pi/4 P} forms up to phase)
+    "SQRT_X": np.array([[1 + 1j, 1 - 1j], [1 - 1j, 1 + 1j]], complex) / 2,
+    "SQRT_X_DAG": np.array([[1 - 1j, 1 + 1j], [1 + 1j, 1 - 1j]], complex) / 2,
+    "SQRT_Y": np.array([[1 + 1j, -1 - 1j], [1 + 1j, 1 + 1j]], complex) / 2,
+    "SQRT_Y_DAG": np.array([[1 - 1j, 1 - 1j], [-1 + 1j, 1 - 1j]], complex) / 2,
     # two-qubit gates in the basis |a b> with a the first target
     "CX": np.array([[1, 0, 0, 0], [0, 1, 0, 0], [0, 0, 0, 1], [0, 0, 1, 0]], complex),
     "CZ": np.diag([1, 1, 1, -1]).astype(complex),
@@ -32,7 +41,14 @@ PAULI = {
     "Y": np.array([[0, -1j], [1j, 0]], complex),
     "Z": np.array([[1, 0], [0, -1]], complex),
 }
-NOISE = {"X_ERROR", "Z_ERROR", "DEPOLARIZE1", "DEPOLARIZE2"}
+NOISE = {"X_ERROR", "Y_ERROR", "Z_ERROR", "DEPOLARIZE1", "DEPOLARIZE2"}
+ONE_QUBIT = {"H", "S", "S_DAG", "X", "Y", "Z", "SQRT_X", "SQRT_X_DAG", "SQRT_Y", "SQRT_Y_DAG"}
+# collapsing ops: measured Pauli and whether they record / reset
+COLLAPSE = {"M": ("Z", 1, 0), "MR": ("Z", 1, 1), "R": ("Z", 0, 1),
+            "MX": ("X", 1, 0), "MRX": ("X", 1, 1), "RX": ("X", 0, 1),
+            "MY": ("Y", 1, 0), "MRY": ("Y", 1, 1), "RY": ("Y", 0, 1)}
+# a Pauli that anticommutes with the measured one: maps its -1 eigenstate to +1
+FLIPPER = {"Z": "X", "X": "Z", "Y": "Z"}
 
 
 def parse(text: str):
@@ -79,7 +95,7 @@ def parse(text: str):
                 flat.append((name, [count[0] - k for k in tg]))
             else:
                 flat.append((name, tg))
-                if name in ("M", "MR"):
+                if name in COLLAPSE and COLLAPSE[name][1]:
                     count[0] += len(tg)
 
     walk(stack[0])
@@ -115,15 +131,17 @@ class State:
         out = np.tensordot(U4, self.psi, axes=([2, 3], [axa, axb]))
         self.psi = np.moveaxis(out, [0, 1], [axa, axb])
 
-    def prob0(self, q):
-        sl = [slice(None)] * self.n
-        sl[self._ax(q)] = 0
-        return float(np.sum(np.abs(self.psi[tuple(sl)]) ** 2))
+    def _projector(self, pauli, outcome):
+        return (np.eye(2) + (1 - 2 * outcome) * PAULI[pauli]) / 2
 
-    def project(self, q, outcome):
-        sl = [slice(None)] * self.n
-        sl[self._ax(q)] = 1 - outcome
-        self.psi[tuple(sl)] = 0
+    def prob0(self, q, pauli="Z"):
+        """Probability of the +1 eigenvalue (outcome 0) of `pauli` on qubit q."""
+        s2 = self.copy()
+        s2.apply1(self._projector(pauli, 0), q)
+        return float(np.sum(np.abs(s2.psi) ** 2))
+
+    def project(self, q, outcome, pauli="Z"):
+        self.apply1(self._projector(pauli, outcome), q)
         self.psi /= np.linalg.norm(self.psi)
 
     def copy(self):
@@ -147,22 +165,23 @@ def reference(text: str):
     st = State(num_qubits(ops))
     ref, det = [], []
     for name, tg in ops:
-        if name in ("H", "S"):
+        if name in ONE_QUBIT:
             for q in tg:
                 st.apply1(UNITARY[name], q)
         elif name in ("CX", "CZ"):
             for a, b in zip(tg[::2], tg[1::2]):
                 st.apply2(UNITARY[name], a, b)
-        elif name in ("M", "MR", "R"):
+        elif name in COLLAPSE:
+            pauli, records, resets = COLLAPSE[name]
             for q in tg:
-                kind, val = _measure_kind(st.prob0(q))
+                kind, val = _measure_kind(st.prob0(q, pauli))
                 r = 0 if kind == "rand" else val
-                st.project(q, r)
-                if name != "R":
+                st.project(q, r, pauli)
+                if records:
                     ref.append(r)
                     det.append(1 if kind == "det" else 0)
-                if name != "M" and r == 1:
-                    st.apply1(UNITARY["X"], q)
+                if resets and r == 1:
+                    st.apply1(PAULI[FLIPPER[pauli]], q)
     return np.array(ref, np.uint8), np.array(det, np.uint8)
 
 
@@ -171,7 +190,7 @@ def branches(text: str, max_random: int = 14):
     as a dict, by branching on both outcomes of every random measurement."""
     ops = []
     for name, tg in parse(text):
-        if name in ("M", "MR", "R"):
+        if name in COLLAPSE:
             ops += [(name, [q]) for q in tg]    # broadcast runs left to right
         else:
             ops.append((name, tg))
@@ -181,29 +200,30 @@ def branches(text: str, max_random: int = 14):
     def run(i, st, rec, prob, nrand):
         while i < len(ops):
             name, tg = ops[i]
-            if name in ("H", "S"):
+            if name in ONE_QUBIT:
                 for q in tg:
                     st.apply1(UNITARY[name], q)
             elif name in ("CX", "CZ"):
                 for a, b in zip(tg[::2], tg[1::2]):
                     st.apply2(UNITARY[name], a, b)
-            elif name in ("M", "MR", "R"):
+            elif name in COLLAPSE:
+                pauli, records, resets = COLLAPSE[name]
                 q = tg[0]
-                kind, val = _measure_kind(st.prob0(q))
+                kind, val = _measure_kind(st.prob0(q, pauli))
                 if kind == "rand":
                     assert nrand < max_random, "too many random measurements"
                     for r in (0, 1):
                         s2 = st.copy()
-                        s2.project(q, r)
-                        if name != "M" and r == 1:
-                            s2.apply1(UNITARY["X"], q)
-                        run(i + 1, s2, rec + ([r] if name != "R" else []), prob / 2, nrand + 1)
+                        s2.project(q, r, pauli)
+                        if resets and r == 1:
+                            s2.apply1(PAULI[FLIPPER[pauli]], q)
+                        run(i + 1, s2, rec + ([r] if records else []), prob / 2, nrand + 1)
                     return
-                st.project(q, val)
-                if name != "R":
+                st.project(q, val, pauli)
+                if records:
                     rec = rec + [val]
-                if name != "M" and val == 1:
-                    st.apply1(UNITARY["X"], q)
+                if resets and val == 1:
+                    st.apply1(PAULI[FLIPPER[pauli]], q)
             i += 1
         key = tuple(rec)
         out[key] = out.get(key, 0.0) + prob

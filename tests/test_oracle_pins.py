@@ -39,7 +39,9 @@ def test_xz_encoding_golden():
         np.testing.assert_allclose(m, P[name])
 
 
-@pytest.mark.parametrize("gate,k", [("H", 1), ("S", 1), ("X", 1), ("CX", 2), ("CZ", 2)])
+@pytest.mark.parametrize("gate,k", [("H", 1), ("S", 1), ("X", 1), ("CX", 2), ("CZ", 2), ("Y", 1), ("Z", 1),
+                                    ("S_DAG", 1), ("SQRT_X", 1), ("SQRT_X_DAG", 1), ("SQRT_Y", 1),
+                                    ("SQRT_Y_DAG", 1)])
 def test_gate_conjugation_matches_unitary(gate, k):
     """U^dagger P U == i^ph * image for every local Pauli (the paper's
     unitary-vs-tableau cross-check, Section 5.5)."""
@@ -176,6 +178,86 @@ def test_reference_matches_statevector_random():
         np.testing.assert_array_equal(det, det2, err_msg=txt)
 
 
+WIDE_1Q = ["H", "S", "S_DAG", "X", "Y", "Z", "SQRT_X", "SQRT_X_DAG", "SQRT_Y", "SQRT_Y_DAG"]
+WIDE_COLLAPSE = ["M", "MR", "R", "MX", "MY", "MRX", "MRY", "RX", "RY"]
+
+
+def _rand_wide_circuit(rng, n, L):
+    """Random circuits over the wider gate set: all one-qubit Cliffords,
+    CX/CZ, and measurements/resets in the X, Y and Z bases."""
+    lines = []
+    for _ in range(L):
+        kind = rng.random()
+        if kind < 0.45:
+            g = str(rng.choice(WIDE_1Q))
+            k = int(rng.integers(1, n + 1))
+            lines.append(f"{g} " + " ".join(map(str, rng.choice(n, k, replace=False))))
+        elif kind < 0.7 and n >= 2:
+            a, b = rng.choice(n, 2, replace=False)
+            lines.append(f"{str(rng.choice(['CX', 'CZ']))} {a} {b}")
+        else:
+            g = str(rng.choice(WIDE_COLLAPSE))
+            k = int(rng.integers(1, n + 1))
+            lines.append(f"{g} " + " ".join(map(str, rng.choice(n, k, replace=False))))
+    lines.append(str(rng.choice(["M", "MX", "MY"])) + " " + " ".join(map(str, range(n))))
+    return "\n".join(lines) + "\n"
+
+
+def test_reference_wide_gate_set_matches_statevector():
+    """Reference samples over the wider gate set (one-qubit Cliffords and X/Y
+    basis measurements and resets) equal the state-vector outcome-0 samples,
+    with measurements as projections onto Pauli eigenspaces."""
+    rng = np.random.default_rng(2103)
+    for _ in range(300):
+        n = int(rng.integers(1, 7))
+        txt = _rand_wide_circuit(rng, n, int(rng.integers(1, 40)))
+        ref, det = oracle.Circuit(txt).reference()
+        ref2, det2 = sv.reference(txt)
+        np.testing.assert_array_equal(ref, ref2, err_msg=txt)
+        np.testing.assert_array_equal(det, det2, err_msg=txt)
+
+
+def test_frame_wide_gate_set_support():
+    """Noiseless shots over the wider gate set stay inside the state-vector
+    branch support, with branch frequencies near their probabilities."""
+    rng = np.random.default_rng(2104)
+    checked = 0
+    while checked < 12:
+        n = int(rng.integers(2, 5))
+        txt = _rand_wide_circuit(rng, n, int(rng.integers(4, 20)))
+        try:
+            br = sv.branches(txt)
+        except AssertionError:
+            continue
+        if len(br) > 64:
+            continue
+        meas, _ = oracle.Circuit(txt).sample(np.arange(2048), seed=int(rng.integers(0, 2**62)))
+        counts = {}
+        for row in meas:
+            k = tuple(int(b) for b in row)
+            assert k in br, (txt, k)
+            counts[k] = counts.get(k, 0) + 1
+        if len(br) > 1:
+            chi2 = sum((counts.get(k, 0) - 2048 * p) ** 2 / (2048 * p) for k, p in br.items())
+            dof = len(br) - 1
+            assert chi2 < dof + 6 * math.sqrt(2 * dof) + 10, (txt, chi2, dof)
+        checked += 1
+
+
+def test_basis_measurement_special_cases():
+    # |+> measured in X is deterministic 0, |-> gives 1; |+i> in Y gives 0
+    ref, det = oracle.Circuit("H 0\nMX 0\nX 0\nZ 0\nMX 0\n").reference()
+    assert list(ref) == [0, 1] and list(det) == [1, 1]
+    ref, det = oracle.Circuit("H 0\nS 0\nMY 0\nS_DAG 0\nS_DAG 0\nMY 0\n").reference()
+    assert list(ref) == [0, 1] and list(det) == [1, 1]
+    # RX prepares |+>: a following MX is deterministic 0; M after RX is random
+    ref, det = oracle.Circuit("X 0\nRX 0\nMX 0\nM 0\n").reference()
+    assert list(ref) == [0, 0] and list(det) == [1, 0]
+    # SQRT_X twice is X (up to phase): |0> -> |1>
+    ref, det = oracle.Circuit("SQRT_X 0\nSQRT_X 0\nM 0\nSQRT_Y 0\nSQRT_Y_DAG 0\nM 0\n").reference()
+    assert list(ref) == [1, 1] and list(det) == [1, 1]
+
+
 def test_reference_matches_statevector_surface_d3():
     txt = W.surface_code_memory(3, 2, 0.0)
     ref, det = oracle.Circuit(txt).reference()
@@ -291,6 +373,20 @@ def test_z_error_rate_in_x_basis():
     c = oracle.Circuit(f"Z_ERROR({p}) {_qs(n)}\nM {_qs(n)}\n")
     meas, _ = c.sample(np.arange(256), seed=6)
     assert meas.sum() == 0
+
+
+@pytest.mark.parametrize("basis,rate", [("M", 1.0), ("MX", 1.0), ("MY", 0.0)])
+def test_y_error_rates(basis, rate):
+    """Y_ERROR(p) flips Z- and X-basis measurements with probability p and
+    leaves Y-basis measurements alone."""
+    p, n = 0.04, 1000
+    prep = {"M": "", "MX": f"H {_qs(n)}\n", "MY": f"H {_qs(n)}\nS {_qs(n)}\n"}[basis]
+    c = oracle.Circuit(f"{prep}Y_ERROR({p}) {_qs(n)}\n{basis} {_qs(n)}\n")
+    meas, _ = c.sample(np.arange(1024), seed=8, threads=4)
+    if rate == 0.0:
+        assert meas.sum() == 0
+    else:
+        assert _zscore(int(meas.sum()), meas.size, p * rate) < 5
 
 
 def test_depolarize1_rates():
