@@ -45,7 +45,9 @@ void geometric_table(double p, uint64_t G[64]) {
 namespace {
 
 enum ParsedGate {
-    PG_H, PG_S, PG_CX, PG_CZ, PG_M, PG_MR, PG_R, PG_XERR, PG_ZERR, PG_DEP1, PG_DEP2, PG_DET
+    PG_H, PG_S, PG_CX, PG_CZ, PG_M, PG_MR, PG_R, PG_XERR, PG_ZERR, PG_DEP1, PG_DEP2, PG_DET,
+    PG_X, PG_Y, PG_Z, PG_SDAG, PG_SQX, PG_SQXD, PG_SQY, PG_SQYD, PG_YERR,
+    PG_MX, PG_MY, PG_MRX, PG_MRY, PG_RX, PG_RY
 };
 
 struct Instr {
@@ -154,7 +156,10 @@ class Parser {
             {"H", PG_H}, {"S", PG_S}, {"CX", PG_CX}, {"CNOT", PG_CX}, {"CZ", PG_CZ},
             {"M", PG_M}, {"MR", PG_MR}, {"R", PG_R}, {"X_ERROR", PG_XERR},
             {"Z_ERROR", PG_ZERR}, {"DEPOLARIZE1", PG_DEP1}, {"DEPOLARIZE2", PG_DEP2},
-            {"DETECTOR", PG_DET}};
+            {"DETECTOR", PG_DET}, {"X", PG_X}, {"Y", PG_Y}, {"Z", PG_Z}, {"S_DAG", PG_SDAG},
+            {"SQRT_X", PG_SQX}, {"SQRT_X_DAG", PG_SQXD}, {"SQRT_Y", PG_SQY}, {"SQRT_Y_DAG", PG_SQYD},
+            {"Y_ERROR", PG_YERR}, {"MX", PG_MX}, {"MY", PG_MY}, {"MRX", PG_MRX}, {"MRY", PG_MRY},
+            {"RX", PG_RX}, {"RY", PG_RY}};
         auto it = kNames.find(name);
         if (name.empty() || it == kNames.end()) {
             size_t j = i;
@@ -183,7 +188,7 @@ class Parser {
             }
             i = close + 1;
         }
-        bool noise = ins->gate >= PG_XERR && ins->gate <= PG_DEP2;
+        bool noise = (ins->gate >= PG_XERR && ins->gate <= PG_DEP2) || ins->gate == PG_YERR;
         if (noise) {
             if (args.size() != 1) fail(lo, "noise channel takes exactly one probability");
             ins->p = args[0];
@@ -229,21 +234,41 @@ class Parser {
     }
 };
 
+// Opcode of an instruction; measurements and resets in the X and Y bases map
+// to their Z-basis op, emitted between basis changes (basis_of).
 uint32_t opcode_of(int pg) {
     switch (pg) {
         case PG_H: return OP_H;
         case PG_S: return OP_S;
         case PG_CX: return OP_CX;
         case PG_CZ: return OP_CZ;
-        case PG_M: return OP_M;
-        case PG_MR: return OP_MR;
-        case PG_R: return OP_R;
+        case PG_M: case PG_MX: case PG_MY: return OP_M;
+        case PG_MR: case PG_MRX: case PG_MRY: return OP_MR;
+        case PG_R: case PG_RX: case PG_RY: return OP_R;
         case PG_XERR: return OP_XERR;
         case PG_ZERR: return OP_ZERR;
+        case PG_YERR: return OP_YERR;
         case PG_DEP1: return OP_DEP1;
+        case PG_X: return OP_X;
+        case PG_Y: return OP_Y;
+        case PG_Z: return OP_Z;
+        case PG_SDAG: return OP_SDAG;
+        case PG_SQX: return OP_SX;
+        case PG_SQXD: return OP_SXD;
+        case PG_SQY: return OP_SY;
+        case PG_SQYD: return OP_SYD;
         default: return OP_DEP2;
     }
 }
+
+// Measurement basis of a collapsing instruction: 0 Z, 1 X, 2 Y.
+int basis_of(int pg) {
+    if (pg == PG_MX || pg == PG_MRX || pg == PG_RX) return 1;
+    if (pg == PG_MY || pg == PG_MRY || pg == PG_RY) return 2;
+    return 0;
+}
+
+bool records(int pg) { return pg == PG_M || pg == PG_MR || pg == PG_MX || pg == PG_MY || pg == PG_MRX || pg == PG_MRY; }
 
 struct Counts {
     uint64_t instr = 0, meas = 0, det = 0, det_entries = 0;
@@ -288,7 +313,7 @@ void count_block(const Block &b, Counts *c, uint32_t *max_qubit, bool *any_qubit
         c->targets[op] += slots;
         if (op_is_noise(op)) c->noise_t += slots;
         else c->gate_t += slots;
-        if (in.gate == PG_M || in.gate == PG_MR) c->meas += in.targets.size();
+        if (records(in.gate)) c->meas += in.targets.size();
     }
 }
 
@@ -346,6 +371,7 @@ class Emitter {
                 }
                 bool pair = op_is_pair(op);
                 size_t step = pair ? 2 : 1;
+                const int basis = basis_of(in.gate);
                 for (size_t k = 0; k < in.targets.size(); k += step) {
                     DevOp d{};
                     uint32_t qa = in.targets[k];
@@ -360,7 +386,13 @@ class Emitter {
                     } else {
                         d.b = table << 24;
                     }
+                    // X basis: H, op, H. Y basis: S_DAG, H, op, H, S (the basis
+                    // change maps the measured Pauli to Z and back).
+                    if (basis == 2) place(basis_gate(OP_SDAG, qa, d.instr), qa, qa, false);
+                    if (basis != 0) place(basis_gate(OP_H, qa, d.instr), qa, qa, false);
                     place(d, qa, qb, op_is_collapse(op));
+                    if (basis != 0) place(basis_gate(OP_H, qa, d.instr), qa, qa, false);
+                    if (basis == 2) place(basis_gate(OP_S, qa, d.instr), qa, qa, false);
                 }
             }
             instr++;
@@ -388,6 +420,13 @@ class Emitter {
     }
 
     uint32_t lastq(uint32_t q) const { return stamp_[q] == seg_ ? last_[q] : 0; }
+
+    static DevOp basis_gate(uint32_t op, uint32_t q, uint32_t instr) {
+        DevOp g{};
+        g.a = (op << 24) | q;
+        g.instr = instr;
+        return g;
+    }
 
     void place(const DevOp &d, uint32_t qa, uint32_t qb, bool collapse) {
         uint32_t L = lastq(qa);
@@ -458,7 +497,7 @@ void collect_detectors(const Block &b, uint64_t *meas, HostProgram *hp) {
             continue;
         }
         const Instr &in = nd.ins;
-        if (in.gate == PG_M || in.gate == PG_MR) {
+        if (records(in.gate)) {
             *meas += in.targets.size();
         } else if (in.gate == PG_DET) {
             for (uint32_t k : in.targets) {
@@ -511,11 +550,13 @@ class FrameBuilder {
             const DevOp *ops = hp_.ops.data() + e.op_begin;
             bool fold = !chains_.empty();
             for (uint32_t i = 0; i < tot && fold; i++) {
+                if (frame_opcode(ops[i].a >> 24) == OP_COUNT) continue;     // no frame action
                 const int own = chain_of(ops[i]);
                 if (own == -2 || (own >= 0 && chains_[own].ops.size() >= kMaxChainOps)) fold = false;
             }
             if (!fold && !chains_.empty()) emitted += emit();
             for (uint32_t i = 0; i < tot; i++) {
+                if (frame_opcode(ops[i].a >> 24) == OP_COUNT) continue;
                 const int own = chain_of(ops[i]);       // -1 after an emit
                 const uint32_t q[2] = {op_q0(ops[i]), op_q1(ops[i])};
                 int c = own;
@@ -555,7 +596,7 @@ class FrameBuilder {
     DevOp encode(const DevOp &d) const {
         const uint32_t opc = d.a >> 24;
         DevOp f = d;
-        f.a = (opc << 28) | ref(op_q0(d));
+        f.a = (frame_opcode(opc) << 28) | ref(op_q0(d));
         if (op_is_pair(opc)) {
             f.b = ref(d.b & kQubitMask);
             if (opc == OP_DEP2) f.slot = d.slot | ((d.b >> 24) << 24);
@@ -579,8 +620,10 @@ class FrameBuilder {
             auto sig_less = [&](uint32_t x, uint32_t y) {
                 const auto &a = chains_[x].ops, &b = chains_[y].ops;
                 if (a.size() != b.size()) return a.size() < b.size();
-                for (size_t j = 0; j < a.size(); j++)
-                    if ((a[j].a >> 24) != (b[j].a >> 24)) return (a[j].a >> 24) < (b[j].a >> 24);
+                for (size_t j = 0; j < a.size(); j++) {
+                    const uint32_t fa = frame_opcode(a[j].a >> 24), fb = frame_opcode(b[j].a >> 24);
+                    if (fa != fb) return fa < fb;
+                }
                 return false;
             };
             std::stable_sort(by_rank[r].begin(), by_rank[r].end(), sig_less);

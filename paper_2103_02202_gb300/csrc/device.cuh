@@ -120,6 +120,9 @@ __device__ __forceinline__ void noise_masks_slow(uint32_t opc, const uint64_t *_
             xa |= bit;
         } else if (opc == OP_ZERR) {
             za |= bit;
+        } else if (opc == OP_YERR) {
+            xa |= bit;
+            za |= bit;
         } else if (opc == OP_DEP1) {
             const uint32_t pa = 1u + (uint32_t)((3ull * next()) >> 32);
             if (pa <= 2u) xa |= bit;

@@ -299,6 +299,13 @@ __device__ __forceinline__ void frame_op(const FrameArgs &a, const SmemKeys key,
             qa.store_z(t, pa.z);
             break;
         }
+        case OP_SX: {       // SQRT_X, SQRT_X_DAG: Z -> +-Y
+            qa.load(t, pa);
+#pragma unroll
+            for (int i = 0; i < V; i++) pa.x[i] ^= pa.z[i];
+            qa.store_x(t, pa.x);
+            break;
+        }
         case OP_CX: {
             const Qubit<W, C, GMEM> qb(t, op.b, wo);
             Planes<V> pb;

@@ -8,9 +8,12 @@
 // (which swaps the X_q and Z_q columns) is a swap of two permutation entries.
 //
 // Folding a gate prepends its inverse: new column(g) = T(G^dagger g G),
-//   S:  X_a <- -i X_a Z_a
+//   S:  X_a <- -i X_a Z_a          S_DAG: X_a <- +i X_a Z_a
+//   SQRT_X: Z_a <- -i Z_a X_a      SQRT_X_DAG: Z_a <- +i Z_a X_a
 //   CX: X_c <- X_c X_t,  Z_t <- Z_t Z_c
 //   CZ: X_a <- X_a Z_b,  X_b <- X_b Z_a
+//   X, Y, Z negate the anticommuting columns; SQRT_Y(_DAG) swap the two
+//   columns (like H) and negate one of them.
 // each a column product whose phase is accumulated with the two-bit-counter
 // method of the paper's Pauli-multiplication figure (one warp per product,
 // warp-reduced popcounts).
@@ -384,6 +387,39 @@ __global__ void __launch_bounds__(512) tableau_kernel(TabArgs a) {
                     case OP_CZ:
                         if (k == 0) column_product<L1>(a, 2 * qa, 2 * qb + 1, 0u, lane);
                         else column_product<L1>(a, 2 * qb, 2 * qa + 1, 0u, lane);
+                        break;
+                    case OP_SDAG:   // X_a <- +i X_a Z_a
+                        if (k == 0) column_product<L1>(a, 2 * qa, 2 * qa + 1, 1u, lane);
+                        break;
+                    case OP_SX:     // Z_a <- Y_a = -i Z_a X_a
+                        if (k == 0) column_product<L1>(a, 2 * qa + 1, 2 * qa, 3u, lane);
+                        break;
+                    case OP_SXD:    // Z_a <- -Y_a = +i Z_a X_a
+                        if (k == 0) column_product<L1>(a, 2 * qa + 1, 2 * qa, 1u, lane);
+                        break;
+                    case OP_X:      // Z_a <- -Z_a
+                    case OP_Y:      // X_a <- -X_a, Z_a <- -Z_a
+                    case OP_Z:      // X_a <- -X_a
+                        if (k == 0 && lane == 0) {
+                            if (opc != OP_X) {
+                                const uint32_t c = ld_u32<L1>(a.perm + 2 * qa);
+                                st_tab<L1>(a.sign + c, ld_u32<L1>(a.sign + c) ^ 1u);
+                            }
+                            if (opc != OP_Z) {
+                                const uint32_t c = ld_u32<L1>(a.perm + 2 * qa + 1);
+                                st_tab<L1>(a.sign + c, ld_u32<L1>(a.sign + c) ^ 1u);
+                            }
+                        }
+                        break;
+                    case OP_SY:     // X_a <- Z_a, Z_a <- -X_a: swap, then negate the new Z column
+                    case OP_SYD:    // X_a <- -Z_a, Z_a <- X_a: swap, then negate the new X column
+                        if (k == 0 && lane == 0) {
+                            const uint32_t u = ld_u32<L1>(a.perm + 2 * qa), v = ld_u32<L1>(a.perm + 2 * qa + 1);
+                            st_tab<L1>(a.perm + 2 * qa, v);
+                            st_tab<L1>(a.perm + 2 * qa + 1, u);
+                            const uint32_t c = opc == OP_SY ? u : v;
+                            st_tab<L1>(a.sign + c, ld_u32<L1>(a.sign + c) ^ 1u);
+                        }
                         break;
                     default:
                         break;

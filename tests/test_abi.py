@@ -68,6 +68,9 @@ CIRCUITS = {
     "nested": "REPEAT 3 {\n H 0\n REPEAT 2 {\n CX 0 1\n M 1\n }\n DETECTOR rec[-1] rec[-2]\n}\nM 0\n",
     "empty": "",
     "comments": "# only a comment\n\n   \n",
+    "wide_gate_set": ("H 0\nSQRT_X 1 2\nSQRT_Y_DAG 3\nMX 0 1\nY_ERROR(0.1) 0 3\nMRY 1\nRX 2\nS_DAG 2\n"
+                      "X 2\nY 0\nZ 3\nSQRT_X_DAG 0\nSQRT_Y 1\nRY 3\nMRX 0\nMY 3\nM 2\n"
+                      "DETECTOR rec[-1] rec[-2]\n"),
 }
 
 

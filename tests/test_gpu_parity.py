@@ -391,3 +391,66 @@ def test_detection_lists_capacity_and_edges():
     b1, d1 = nodet.sample_detections(100, 1)
     assert np.all(b1 == 0) and len(d1) == 0
     nodet.close()
+
+
+WIDE_1Q = ["H", "S", "S_DAG", "X", "Y", "Z", "SQRT_X", "SQRT_X_DAG", "SQRT_Y", "SQRT_Y_DAG"]
+WIDE_COLLAPSE = ["M", "MR", "R", "MX", "MY", "MRX", "MRY", "RX", "RY"]
+WIDE_NOISE = ["X_ERROR", "Y_ERROR", "Z_ERROR", "DEPOLARIZE1", "DEPOLARIZE2"]
+
+
+def _wide_circuit(rng, n, L):
+    lines = []
+    for _ in range(L):
+        kind = rng.random()
+        if kind < 0.4:
+            g = str(rng.choice(WIDE_1Q))
+            k = int(rng.integers(1, n + 1))
+            lines.append(f"{g} " + " ".join(map(str, rng.choice(n, k, replace=False))))
+        elif kind < 0.6:
+            a, b = rng.choice(n, 2, replace=False)
+            lines.append(f"{str(rng.choice(['CX', 'CZ']))} {a} {b}")
+        elif kind < 0.8:
+            ch = str(rng.choice(WIDE_NOISE))
+            p = float(rng.choice([0.02, 0.3, 1.0]))
+            if ch == "DEPOLARIZE2":
+                a, b = rng.choice(n, 2, replace=False)
+                lines.append(f"{ch}({p}) {a} {b}")
+            else:
+                lines.append(f"{ch}({p}) " + " ".join(map(str, rng.choice(n, int(rng.integers(1, n + 1)), replace=False))))
+        else:
+            g = str(rng.choice(WIDE_COLLAPSE))
+            k = int(rng.integers(1, n + 1))
+            lines.append(f"{g} " + " ".join(map(str, rng.choice(n, k, replace=False))))
+            if g[0] == "M":
+                lines.append("DETECTOR rec[-1]")
+    lines.append(str(rng.choice(["M", "MX", "MY"])) + " " + " ".join(map(str, range(n))))
+    lines.append("DETECTOR rec[-1] rec[-2]")
+    return "\n".join(lines) + "\n"
+
+
+def test_wide_gate_set_reference_and_samples_match_oracle():
+    """The wider gate set (one-qubit Cliffords, Paulis, Y_ERROR, X/Y-basis
+    measurements and resets): GPU reference and records equal the oracle's."""
+    rng = np.random.default_rng(77)
+    for it in range(30):
+        n = int(rng.integers(2, 40))
+        text = _wide_circuit(rng, n, int(rng.integers(5, 60)))
+        gr, gd = gpu_reference(text)
+        orf, odf = oracle.Circuit(text).reference()
+        np.testing.assert_array_equal(gr, orf, err_msg=text)
+        np.testing.assert_array_equal(gd, odf, err_msg=text)
+        shots = int(rng.integers(1, 700))
+        mb, db = gpu_sample(text, shots, 1000 + it)
+        om, od = oracle.Circuit(text).sample(np.arange(shots), 1000 + it, threads=8)
+        np.testing.assert_array_equal(mb, om, err_msg=text)
+        np.testing.assert_array_equal(db, od, err_msg=text)
+
+
+@pytest.mark.parametrize("hint", [(1, 64, 0, 2), (4, 128, 0, 1), (8, 256, 0, 1), (2, 128, 1, 1)])
+def test_wide_gate_set_tile_shapes(hint):
+    rng = np.random.default_rng(78)
+    text = _wide_circuit(rng, 30, 80)
+    mb, db = gpu_sample(text, 1000, 5, hint=hint)
+    om, od = oracle.Circuit(text).sample(np.arange(1000), 5, threads=8)
+    np.testing.assert_array_equal(mb, om)
+    np.testing.assert_array_equal(db, od)
