@@ -63,10 +63,10 @@ typedef struct stim_circuit stim_circuit;
 
 typedef struct {
     uint32_t num_qubits;         /* max qubit target + 1 */
-    uint64_t num_measurements;   /* M: targets of M and MR, in order */
+    uint64_t num_measurements;   /* M: targets of M, MR, MX, MY, MRX, MRY, in order */
     uint64_t num_detectors;      /* D: DETECTOR instructions, in order */
-    uint64_t num_gate_targets;   /* H/S/M/MR/R targets plus CX/CZ pairs */
-    uint64_t num_noise_targets;  /* X_ERROR/Z_ERROR/DEPOLARIZE1 targets plus DEPOLARIZE2 pairs */
+    uint64_t num_gate_targets;   /* one-qubit gate, measurement and reset targets plus CX/CZ pairs */
+    uint64_t num_noise_targets;  /* X/Y/Z_ERROR, DEPOLARIZE1 targets plus DEPOLARIZE2 pairs */
     uint64_t num_instructions;   /* instruction lines after REPEAT flattening */
     uint64_t num_layers;         /* fused layers executed per shot (loops unrolled) */
     uint64_t num_program_layers; /* fused layers stored (loop bodies once) */
@@ -83,10 +83,13 @@ typedef struct {
 /*
  * stim_compile -- parse and compile circuit text (Section 5.8 line format).
  *
- * Gate set: H, S, CX (alias CNOT), CZ, M, MR, R, X_ERROR(p), Z_ERROR(p),
- * DEPOLARIZE1(p), DEPOLARIZE2(p), DETECTOR rec[-k]... (optional parenthesised
- * coordinates on DETECTOR are ignored), REPEAT N { ... }, '#' comments.
- * Broadcast targets run left to right (pairs for two-qubit gates).
+ * Gate set: H, S, S_DAG, X, Y, Z, SQRT_X, SQRT_X_DAG, SQRT_Y, SQRT_Y_DAG,
+ * CX (alias CNOT), CZ; M, MR, R and their X- and Y-basis forms MX, MY, MRX,
+ * MRY, RX, RY (random outcomes of the reference sample are the +1
+ * eigenvalue); X_ERROR(p), Y_ERROR(p), Z_ERROR(p), DEPOLARIZE1(p),
+ * DEPOLARIZE2(p); DETECTOR rec[-k]... (optional parenthesised coordinates on
+ * DETECTOR are ignored), REPEAT N { ... }, '#' comments. Broadcast targets
+ * run left to right (pairs for two-qubit gates).
  *
  * text/len: the circuit (need not be NUL-terminated). *out receives a new
  * handle on success; the caller frees it with stim_free(). Compilation is
