@@ -95,9 +95,10 @@ __device__ __forceinline__ int geo_gap(const uint64_t *__restrict__ G, uint32_t 
 // draw u gives the gap min{k : u < G[k]} to the next error; the error process
 // stops at the first draw with u >= G[remaining - 1] (next error beyond bit
 // 63). The caller has drawn block 0 and found an error: its first word, draw
-// 0, satisfies blk0.x < G[63]. DEPOLARIZE1 spends one more draw v per error
-// on the Pauli 1 + floor(3v / 2^32) (1 X, 2 Y, 3 Z); DEPOLARIZE2 on
-// c = 1 + floor(15v / 2^32), first-qubit Pauli c >> 2, second c & 3.
+// 0, satisfies blk0.x < G[63]. X_ERROR, Y_ERROR and Z_ERROR put X, Y or Z at
+// each error; DEPOLARIZE1 spends one more draw v per error on the Pauli
+// 1 + floor(3v / 2^32) (1 X, 2 Y, 3 Z); DEPOLARIZE2 on c = 1 + floor(15v / 2^32),
+// first-qubit Pauli c >> 2, second c & 3.
 template <class K>
 __device__ __forceinline__ void noise_masks_slow(uint32_t opc, const uint64_t *__restrict__ G, K key, uint32_t instr,
                                                  uint32_t slot, uint32_t word, uint4 blk0, uint64_t &xa,
@@ -120,20 +121,20 @@ __device__ __forceinline__ void noise_masks_slow(uint32_t opc, const uint64_t *_
             xa |= bit;
         } else if (opc == OP_ZERR) {
             za |= bit;
-        } else if (opc == OP_YERR) {
-            xa |= bit;
-            za |= bit;
         } else if (opc == OP_DEP1) {
             const uint32_t pa = 1u + (uint32_t)((3ull * next()) >> 32);
             if (pa <= 2u) xa |= bit;
             if (pa >= 2u) za |= bit;
-        } else {
+        } else if (opc == OP_DEP2) {
             const uint32_t c = 1u + (uint32_t)((15ull * next()) >> 32);
             const uint32_t pa = c >> 2, pb = c & 3u;
             if (pa == 1u || pa == 2u) xa |= bit;
             if (pa >= 2u) za |= bit;
             if (pb == 1u || pb == 2u) xb |= bit;
             if (pb >= 2u) zb |= bit;
+        } else {                // Y_ERROR
+            xa |= bit;
+            za |= bit;
         }
         if (pos >= 63) break;
         u = next();

@@ -274,7 +274,7 @@ __device__ __forceinline__ void frame_op(const FrameArgs &a, const SmemKeys key,
     const uint32_t opc = op.a >> 28;
     const uint32_t lw0 = tile0 + wo;                   // first word within the call
     const uint32_t gw0 = (uint32_t)a.word0 + lw0;      // first global 64-shot word (RNG counter)
-    if (opc >= OP_XERR) {
+    if (opc - OP_XERR <= OP_YERR - OP_XERR) {      // noise channels (unsigned range test)
         noise_op<W, C, GMEM>(a, key, t, op, wo, gw0, instr_off);
         return;
     }

@@ -17,19 +17,20 @@
 namespace stimgb {
 
 // Opcodes 0..12 also appear in frame programs (4 bits there); the ones after
-// OP_YERR are gates that only the reference tableau distinguishes: in the
+// OP_SX are gates that only the reference tableau distinguishes: in the
 // frame they act as OP_S (S_DAG), OP_SX (SQRT_X_DAG), OP_H (SQRT_Y,
 // SQRT_Y_DAG) or not at all (the Paulis X, Y, Z, which commute with every
 // frame up to sign).
 enum Opcode : uint32_t {
-    OP_H = 0, OP_S, OP_CX, OP_CZ, OP_SX,           // Clifford gates (OP_SX = SQRT_X)
+    OP_H = 0, OP_S, OP_CX, OP_CZ,                  // Clifford gates
     OP_M, OP_MR, OP_R,                             // collapsing operations (Z basis)
     OP_XERR, OP_ZERR, OP_DEP1, OP_DEP2, OP_YERR,   // Pauli noise channels
+    OP_SX,                                         // SQRT_X (frame: x ^= z)
     OP_X, OP_Y, OP_Z, OP_SDAG, OP_SXD, OP_SY, OP_SYD,   // tableau-only gate variants
     OP_COUNT
 };
 
-inline bool op_is_gate(uint32_t o) { return o <= OP_SX || (o >= OP_X && o < OP_COUNT); }
+inline bool op_is_gate(uint32_t o) { return o <= OP_CZ || (o >= OP_SX && o < OP_COUNT); }
 inline bool op_is_collapse(uint32_t o) { return o >= OP_M && o <= OP_R; }
 inline bool op_is_noise(uint32_t o) { return o >= OP_XERR && o <= OP_YERR; }
 inline bool op_is_pair(uint32_t o) { return o == OP_CX || o == OP_CZ || o == OP_DEP2; }
