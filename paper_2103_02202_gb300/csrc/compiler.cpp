@@ -564,7 +564,17 @@ class FrameBuilder {
                     c = (int)chains_.size();
                     chains_.push_back(Chain{q[0], {}, {}});
                 }
-                chains_[c].ops.push_back(ops[i]);
+                if (frame_opcode(ops[i].a >> 24) == OP_SX) {
+                    // SQRT_X(_DAG) acts on frames as x ^= z, i.e. H S H
+                    DevOp h = ops[i], sg = ops[i];
+                    h.a = (OP_H << 24) | q[0];
+                    sg.a = (OP_S << 24) | q[0];
+                    chains_[c].ops.push_back(h);
+                    chains_[c].ops.push_back(sg);
+                    chains_[c].ops.push_back(h);
+                } else {
+                    chains_[c].ops.push_back(ops[i]);
+                }
                 for (uint32_t qq : q) {
                     if (owner_[qq] < 0) {
                         owner_[qq] = c;

@@ -274,7 +274,7 @@ __device__ __forceinline__ void frame_op(const FrameArgs &a, const SmemKeys key,
     const uint32_t opc = op.a >> 28;
     const uint32_t lw0 = tile0 + wo;                   // first word within the call
     const uint32_t gw0 = (uint32_t)a.word0 + lw0;      // first global 64-shot word (RNG counter)
-    if (opc - OP_XERR <= OP_YERR - OP_XERR) {      // noise channels (unsigned range test)
+    if (opc >= OP_XERR) {      // noise channels: frame programs hold no opcode above OP_YERR
         noise_op<W, C, GMEM>(a, key, t, op, wo, gw0, instr_off);
         return;
     }
@@ -297,13 +297,6 @@ __device__ __forceinline__ void frame_op(const FrameArgs &a, const SmemKeys key,
 #pragma unroll
             for (int i = 0; i < V; i++) pa.z[i] ^= pa.x[i];
             qa.store_z(t, pa.z);
-            break;
-        }
-        case OP_SX: {       // SQRT_X, SQRT_X_DAG: Z -> +-Y
-            qa.load(t, pa);
-#pragma unroll
-            for (int i = 0; i < V; i++) pa.x[i] ^= pa.z[i];
-            qa.store_x(t, pa.x);
             break;
         }
         case OP_CX: {

@@ -16,10 +16,10 @@
 
 namespace stimgb {
 
-// Opcodes 0..12 also appear in frame programs (4 bits there); the ones after
-// OP_SX are gates that only the reference tableau distinguishes: in the
-// frame they act as OP_S (S_DAG), OP_SX (SQRT_X_DAG), OP_H (SQRT_Y,
-// SQRT_Y_DAG) or not at all (the Paulis X, Y, Z, which commute with every
+// Opcodes 0..11 also appear in frame programs (4 bits there). OP_SX and the
+// ones after it are gates that only the reference tableau tells apart: frame
+// programs replace SQRT_X and SQRT_X_DAG (x ^= z) by H S H, S_DAG by S, SQRT_Y
+// and SQRT_Y_DAG by H, and drop the Paulis X, Y, Z (they commute with every
 // frame up to sign).
 enum Opcode : uint32_t {
     OP_H = 0, OP_S, OP_CX, OP_CZ,                  // Clifford gates
@@ -40,7 +40,7 @@ inline uint32_t frame_opcode(uint32_t o) {
     switch (o) {
         case OP_X: case OP_Y: case OP_Z: return OP_COUNT;
         case OP_SDAG: return OP_S;
-        case OP_SXD: return OP_SX;
+        case OP_SXD: return OP_SX;      // expanded to H S H by the frame builder
         case OP_SY: case OP_SYD: return OP_H;
         default: return o;
     }
