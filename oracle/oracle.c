@@ -18,7 +18,13 @@
  *     CNOTs from a pivot, a single-qubit collapse gate and an X;
  *   - the Pauli frame simulator (Section 3, enumerated steps), one shot at a
  *     time with one byte per qubit per plane;
- *   - detectors as the XOR of measurement flips (Section 5.6).
+ *   - detectors as the XOR of measurement flips (Section 5.6);
+ *   - classically controlled Paulis (Section 3, "Tracking Corrections"):
+ *     "CX rec[-k] q" applies X to q and "CZ rec[-k] q" Z when measurement
+ *     record -k is 1. The tableau applies the Pauli when the reference
+ *     outcome is 1; the frame applies it where the shot's record differs
+ *     from the reference (the flip bit), which is the correction moved into
+ *     the frame.
  *
  * Readings where the paper is silent (the same on the GPU side, defined
  * independently there):
@@ -294,6 +300,11 @@ static int gate_from_name(const char *w, size_t n) {
     return -1;
 }
 
+/* A CX/CZ target with this bit set is a measurement record (the control of a
+ * classically controlled Pauli): lookback k while parsing, absolute index
+ * after flattening. */
+#define REC_FLAG 0x80000000u
+
 static int is_noise(int g) { return g == OG_XERR || g == OG_ZERR || g == OG_DEP1 || g == OG_DEP2 || g == OG_YERR; }
 static int is_1q_gate(int g) {
     return g == OG_H || g == OG_S || g == OG_X || g == OG_Y || g == OG_Z || g == OG_SDAG || g == OG_SQX ||
@@ -355,7 +366,16 @@ static int parse_line(pstate *ps, const char *b, const char *e, node *k) {
         while (p < e && (*p == ' ' || *p == '\t')) p++;
         if (p >= e) break;
         uint64_t v = 0;
-        if (g == OG_DET) {
+        if ((g == OG_CX || g == OG_CZ) && e - p >= 6 && strncmp(p, "rec[-", 5) == 0) {
+            /* classically controlled Pauli: the control is a measurement record */
+            p += 5;
+            if (p >= e || *p < '0' || *p > '9') return perr(ps, "expected rec[-k]");
+            while (p < e && *p >= '0' && *p <= '9') { v = v * 10 + (uint64_t)(*p - '0'); if (v >= REC_FLAG) return perr(ps, "lookback too large"); p++; }
+            if (p >= e || *p != ']') return perr(ps, "expected ]");
+            p++;
+            if (v == 0) return perr(ps, "rec[-0] is not a measurement");
+            v |= REC_FLAG;
+        } else if (g == OG_DET) {
             if (e - p < 6 || strncmp(p, "rec[-", 5) != 0) return perr(ps, "expected rec[-k]");
             p += 5;
             if (p >= e || *p < '0' || *p > '9') return perr(ps, "expected rec[-k]");
@@ -373,8 +393,11 @@ static int parse_line(pstate *ps, const char *b, const char *e, node *k) {
     }
     if (is_pair(g)) {
         if (k->nt % 2) return perr(ps, "two-qubit gate needs an even number of targets");
-        for (uint32_t i = 0; i < k->nt; i += 2)
+        for (uint32_t i = 0; i < k->nt; i += 2) {
             if (k->t[i] == k->t[i + 1]) return perr(ps, "two-qubit gate on one qubit");
+            if ((k->t[i] & REC_FLAG) && (k->t[i + 1] & REC_FLAG)) return perr(ps, "two measurement records in a pair");
+            if (g == OG_CX && (k->t[i + 1] & REC_FLAG)) return perr(ps, "CX takes a measurement record only as control");
+        }
     }
     return 0;
 }
@@ -451,8 +474,15 @@ static int flatten(pstate *ps, const node *blk, orc_circuit *c) {
             c->ndet++;
         } else {
             memcpy(o->t, k->t, k->nt * sizeof(uint32_t));
-            for (uint32_t j = 0; j < k->nt; j++)
+            for (uint32_t j = 0; j < k->nt; j++) {
+                if (k->t[j] & REC_FLAG) {      /* rec[-k] -> absolute measurement index */
+                    uint32_t back = k->t[j] & ~REC_FLAG;
+                    if ((uint64_t)back > c->nmeas) return perr(ps, "rec[-%u] reaches before the first measurement", back);
+                    o->t[j] = REC_FLAG | (uint32_t)(c->nmeas - back);
+                    continue;
+                }
                 if (k->t[j] + 1 > c->n) c->n = k->t[j] + 1;
+            }
             uint64_t slots = is_pair(k->gate) ? k->nt / 2 : k->nt;
             if (is_noise(k->gate)) {
                 c->nnoise_targets += slots;
@@ -931,7 +961,17 @@ int orc_reference(const orc_circuit *c, uint8_t *ref, uint8_t *detflag) {
         }
         switch (o->gate) {
         case OG_CX: case OG_CZ:
-            for (uint32_t j = 0; j < o->nt; j += 2) tableau_prepend(&T, o->gate, &o->t[j], tmpx, tmpz, tmps);
+            for (uint32_t j = 0; j < o->nt; j += 2) {
+                const uint32_t a = o->t[j], b = o->t[j + 1];
+                if ((a | b) & REC_FLAG) {
+                    /* classically controlled X (CX) or Z (CZ) on the qubit,
+                     * applied when the reference recorded a 1 */
+                    const uint32_t rec = (a & REC_FLAG) ? a : b, q = (a & REC_FLAG) ? b : a;
+                    if (ref[rec & ~REC_FLAG]) tableau_prepend(&T, o->gate == OG_CX ? OG_X : OG_Z, &q, tmpx, tmpz, tmps);
+                    continue;
+                }
+                tableau_prepend(&T, o->gate, &o->t[j], tmpx, tmpz, tmps);
+            }
             break;
         default:
             break;   /* noise and detectors do not touch the noiseless sample */
@@ -998,6 +1038,15 @@ static void *frame_worker(void *arg) {
                 const spauli *img = o->gate == OG_CX ? imgCX : imgCZ;
                 for (uint32_t j = 0; j < o->nt; j += 2) {
                     uint32_t a = o->t[j], bq = o->t[j + 1];
+                    if ((a | bq) & REC_FLAG) {
+                        /* the frame gains the Pauli exactly when the record
+                         * differs from the reference (its flip) */
+                        const uint32_t rec = (a & REC_FLAG) ? a : bq, q = (a & REC_FLAG) ? bq : a;
+                        const uint8_t f = flip[rec & ~REC_FLAG];
+                        if (o->gate == OG_CX) x[q] ^= f;
+                        else z[q] ^= f;
+                        continue;
+                    }
                     uint8_t rx, rz;
                     int ph;
                     conj_local(img, 2, (uint8_t)(x[a] | (x[bq] << 1)), (uint8_t)(z[a] | (z[bq] << 1)), &rx, &rz, &ph);

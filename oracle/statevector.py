@@ -77,7 +77,9 @@ def parse(text: str):
         if name == "DETECTOR":
             tg = [int(re.fullmatch(r"rec\[-(\d+)\]", t).group(1)) for t in toks]
         else:
-            tg = [int(t) for t in toks]
+            # CX/CZ may take a measurement record rec[-k] as control (a
+            # classically controlled X or Z): kept as ("rec", k) until flattening
+            tg = [("rec", int(t[5:-1])) if t.startswith("rec[-") else int(t) for t in toks]
         stack[-1].append((name, tg))
     assert len(stack) == 1
 
@@ -94,7 +96,7 @@ def parse(text: str):
             if name == "DETECTOR":
                 flat.append((name, [count[0] - k for k in tg]))
             else:
-                flat.append((name, tg))
+                flat.append((name, [("rec", count[0] - t[1]) if isinstance(t, tuple) else t for t in tg]))
                 if name in COLLAPSE and COLLAPSE[name][1]:
                     count[0] += len(tg)
 
@@ -105,9 +107,21 @@ def parse(text: str):
 def num_qubits(ops) -> int:
     n = 0
     for name, tg in ops:
-        if name != "DETECTOR" and tg:
-            n = max(n, max(tg) + 1)
+        qs = [t for t in tg if not isinstance(t, tuple)]
+        if name != "DETECTOR" and qs:
+            n = max(n, max(qs) + 1)
     return n
+
+
+def _two_qubit(st, name, a, b, rec):
+    """CX/CZ on qubits, or the classically controlled X/Z when one side is a
+    measurement record (applied when that record is 1)."""
+    if isinstance(a, tuple) or isinstance(b, tuple):
+        m, q = (a[1], b) if isinstance(a, tuple) else (b[1], a)
+        if rec[m]:
+            st.apply1(PAULI["X" if name == "CX" else "Z"], q)
+    else:
+        st.apply2(UNITARY[name], a, b)
 
 
 class State:
@@ -170,7 +184,7 @@ def reference(text: str):
                 st.apply1(UNITARY[name], q)
         elif name in ("CX", "CZ"):
             for a, b in zip(tg[::2], tg[1::2]):
-                st.apply2(UNITARY[name], a, b)
+                _two_qubit(st, name, a, b, ref)
         elif name in COLLAPSE:
             pauli, records, resets = COLLAPSE[name]
             for q in tg:
@@ -205,7 +219,7 @@ def branches(text: str, max_random: int = 14):
                     st.apply1(UNITARY[name], q)
             elif name in ("CX", "CZ"):
                 for a, b in zip(tg[::2], tg[1::2]):
-                    st.apply2(UNITARY[name], a, b)
+                    _two_qubit(st, name, a, b, rec)
             elif name in COLLAPSE:
                 pauli, records, resets = COLLAPSE[name]
                 q = tg[0]

@@ -182,12 +182,19 @@ WIDE_1Q = ["H", "S", "S_DAG", "X", "Y", "Z", "SQRT_X", "SQRT_X_DAG", "SQRT_Y", "
 WIDE_COLLAPSE = ["M", "MR", "R", "MX", "MY", "MRX", "MRY", "RX", "RY"]
 
 
-def _rand_wide_circuit(rng, n, L):
+def _rand_wide_circuit(rng, n, L, feedforward=False):
     """Random circuits over the wider gate set: all one-qubit Cliffords,
-    CX/CZ, and measurements/resets in the X, Y and Z bases."""
+    CX/CZ, measurements/resets in the X, Y and Z bases and (optionally)
+    classically controlled X/Z on earlier measurement records."""
     lines = []
+    nmeas = 0
     for _ in range(L):
         kind = rng.random()
+        if feedforward and nmeas and kind < 0.15:
+            k = int(rng.integers(1, nmeas + 1))
+            q = int(rng.integers(n))
+            lines.append(f"CX rec[-{k}] {q}" if rng.random() < 0.5 else f"CZ {q} rec[-{k}]")
+            continue
         if kind < 0.45:
             g = str(rng.choice(WIDE_1Q))
             k = int(rng.integers(1, n + 1))
@@ -199,6 +206,8 @@ def _rand_wide_circuit(rng, n, L):
             g = str(rng.choice(WIDE_COLLAPSE))
             k = int(rng.integers(1, n + 1))
             lines.append(f"{g} " + " ".join(map(str, rng.choice(n, k, replace=False))))
+            if g[0] == "M":
+                nmeas += k
     lines.append(str(rng.choice(["M", "MX", "MY"])) + " " + " ".join(map(str, range(n))))
     return "\n".join(lines) + "\n"
 
@@ -242,6 +251,56 @@ def test_frame_wide_gate_set_support():
             dof = len(br) - 1
             assert chi2 < dof + 6 * math.sqrt(2 * dof) + 10, (txt, chi2, dof)
         checked += 1
+
+
+def test_feedforward_matches_statevector():
+    """Classically controlled X/Z (CX rec[-k] q, CZ q rec[-k]): tableau
+    references equal the state-vector outcome-0 samples, and frame shots lie
+    in the state-vector branch support (the Pauli applied when the record is 1)."""
+    rng = np.random.default_rng(2105)
+    for _ in range(200):
+        n = int(rng.integers(1, 6))
+        txt = _rand_wide_circuit(rng, n, int(rng.integers(1, 40)), feedforward=True)
+        ref, det = oracle.Circuit(txt).reference()
+        ref2, det2 = sv.reference(txt)
+        np.testing.assert_array_equal(ref, ref2, err_msg=txt)
+        np.testing.assert_array_equal(det, det2, err_msg=txt)
+    checked = 0
+    while checked < 10:
+        n = int(rng.integers(2, 5))
+        txt = _rand_wide_circuit(rng, n, int(rng.integers(4, 20)), feedforward=True)
+        if "rec[" not in txt:
+            continue
+        try:
+            br = sv.branches(txt)
+        except AssertionError:
+            continue
+        if len(br) > 64:
+            continue
+        meas, _ = oracle.Circuit(txt).sample(np.arange(1024), seed=int(rng.integers(0, 2**62)))
+        for row in meas:
+            assert tuple(int(b) for b in row) in br, txt
+        checked += 1
+
+
+@pytest.mark.parametrize("prep,basis,out", [("X 0", "M", 1), ("H 0", "MX", 0), ("H 0\nS 0", "MY", 0),
+                                            ("H 0\nZ 0", "MX", 1)])
+def test_teleportation_with_feedforward(prep, basis, out):
+    """Teleporting a prepared one-qubit state with corrections from the two
+    Bell-measurement records gives a deterministic result on every shot."""
+    txt = (f"{prep}\nH 1\nCX 1 2\nCX 0 1\nH 0\nM 0 1\nCX rec[-1] 2\nCZ rec[-2] 2\n{basis} 2\n")
+    ref, det = oracle.Circuit(txt).reference()
+    assert int(ref[2]) == out and int(det[2]) == 1
+    meas, _ = oracle.Circuit(txt).sample(np.arange(512), seed=5)
+    assert np.all(meas[:, 2] == out)
+    assert 0.35 < meas[:, 0].mean() < 0.65 and 0.35 < meas[:, 1].mean() < 0.65
+
+
+def test_feedforward_parse_errors():
+    for bad in ("M 0\nCX 1 rec[-1]\n", "M 0\nCX rec[-0] 1\n", "M 0 1\nCZ rec[-1] rec[-2]\n",
+                "CX rec[-1] 0\n"):
+        with pytest.raises(ValueError):
+            oracle.Circuit(bad)
 
 
 def test_basis_measurement_special_cases():
