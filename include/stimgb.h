@@ -89,15 +89,21 @@ typedef struct {
  * eigenvalue); X_ERROR(p), Y_ERROR(p), Z_ERROR(p), DEPOLARIZE1(p),
  * DEPOLARIZE2(p); DETECTOR rec[-k]... (optional parenthesised coordinates on
  * DETECTOR are ignored), REPEAT N { ... }, '#' comments. Broadcast targets
- * run left to right (pairs for two-qubit gates).
+ * run left to right (pairs for two-qubit gates). A pair of CX may name a
+ * measurement record rec[-k] as its control, a pair of CZ on either side:
+ * the other target gets X (CX) or Z (CZ) in the shots whose record is 1,
+ * the classically controlled Paulis a Pauli frame tracks in place of the
+ * qubits (Section 3, "Tracking Corrections"). Sampling a circuit that has
+ * them keeps its measurement records in device memory even when only
+ * detection events are asked for.
  *
  * text/len: the circuit (need not be NUL-terminated). *out receives a new
  * handle on success; the caller frees it with stim_free(). Compilation is
  * host-only; device memory is allocated on the current device at the first
  * sampling call. Errors: STIM_E_PARSE (unknown gate, bad target, odd target
  * count or repeated qubit pair on a two-qubit gate, p outside [0, 1], wrong
- * argument count, rec[-k] before the first measurement or k = 0, unbalanced
- * or zero REPEAT), STIM_E_UNSUPPORTED (more than 2^24 qubits, 2^28
+ * argument count, rec[-k] before the first measurement or k = 0, a record
+ * as CX target or on both sides of a pair, unbalanced or zero REPEAT), STIM_E_UNSUPPORTED (more than 2^24 qubits, 2^28
  * flattened instructions or 2^32 measurements), STIM_E_INVALID_ARG,
  * STIM_E_OOM.
  */

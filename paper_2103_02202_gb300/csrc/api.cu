@@ -559,7 +559,8 @@ int stim_frame_sample_ex(stim_circuit *c, uint64_t num_shots, uint64_t seed, uin
 
     // ---- record buffers ----
     const bool meas_direct = meas_out && !shot_major && !host;
-    const bool need_rec = (meas_out || det_out) && M > 0;
+    // classically controlled ops read the records back inside the frame kernel
+    const bool need_rec = (meas_out || det_out || hp.num_feedforward > 0) && M > 0;
     uint64_t *rec = nullptr;
     if (need_rec) {
         if (meas_direct) {

@@ -316,7 +316,7 @@ int fill_descs(stim_batch *b, const uint64_t *seeds, const uint64_t *offsets, ui
         uint64_t *meas = meas_out ? meas_out[i] : nullptr;
         uint64_t *det = det_out ? det_out[i] : nullptr;
         uint64_t *rec = meas;
-        if (!rec && det && hp.num_det > 0 && hp.num_meas > 0) {
+        if (!rec && hp.num_meas > 0 && ((det && hp.num_det > 0) || hp.num_feedforward > 0)) {
             const size_t need = hp.num_meas * nwords;
             if (b->rec_cap[i] < need) {
                 cudaFree(b->rec_scratch[i]);

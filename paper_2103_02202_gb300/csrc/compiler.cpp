@@ -13,6 +13,9 @@
 //   * REPEAT bodies are compiled once and wrapped in LOOP entries;
 //   * DETECTOR lookbacks rec[-k] are resolved to absolute measurement indices
 //     in a flattened CSR list;
+//   * a rec[-k] target in a CX (as control) or CZ pair makes a classically
+//     controlled X or Z on the other target (OP_FFX, OP_FFZ), placed after
+//     every collapsing op emitted before it;
 //   * each distinct noise probability gets a 64-entry geometric threshold
 //     table (Section 5.4's gap sampling, in exact integer form).
 #include <algorithm>
@@ -50,10 +53,13 @@ enum ParsedGate {
     PG_MX, PG_MY, PG_MRX, PG_MRY, PG_RX, PG_RY
 };
 
+// A measurement-record target rec[-k] in a CX/CZ pair: kRecTarget | k.
+constexpr uint32_t kRecTarget = 1u << 31;
+
 struct Instr {
     int gate = 0;
     double p = 0;
-    std::vector<uint32_t> targets;   // qubits, or lookbacks k for DETECTOR
+    std::vector<uint32_t> targets;   // qubits (kRecTarget | k for rec[-k] in CX/CZ), or lookbacks k for DETECTOR
     int line = 0;
 };
 
@@ -202,7 +208,9 @@ class Parser {
             if (i >= hi) break;
             size_t t0 = i;
             uint64_t v = 0;
-            if (ins->gate == PG_DET) {
+            const bool rec_target = (ins->gate == PG_CX || ins->gate == PG_CZ) && hi - i >= 6 &&
+                                    memcmp(ln + i, "rec[-", 5) == 0;
+            if (ins->gate == PG_DET || rec_target) {
                 if (hi - i < 6 || memcmp(ln + i, "rec[-", 5) != 0) fail(i, "expected a rec[-k] target");
                 i += 5;
                 if (i >= hi || !isdigit((unsigned char)ln[i])) fail(i, "expected a rec[-k] target");
@@ -214,6 +222,10 @@ class Parser {
                 if (i >= hi || ln[i] != ']') fail(i, "expected ']'");
                 i++;
                 if (v == 0) fail(t0, "rec[-0] does not name a measurement");
+                if (rec_target) {
+                    if (v >= kRecTarget) fail(t0, "lookback too large");
+                    v |= kRecTarget;
+                }
             } else {
                 if (!isdigit((unsigned char)ln[i])) fail(i, "qubit targets are non-negative integers");
                 while (i < hi && isdigit((unsigned char)ln[i])) {
@@ -228,8 +240,12 @@ class Parser {
         bool pair = ins->gate == PG_CX || ins->gate == PG_CZ || ins->gate == PG_DEP2;
         if (pair) {
             if (ins->targets.size() % 2) fail(lo, "two-qubit gate needs an even number of targets");
-            for (size_t k = 0; k < ins->targets.size(); k += 2)
-                if (ins->targets[k] == ins->targets[k + 1]) fail(lo, "two-qubit gate applied to one qubit");
+            for (size_t k = 0; k < ins->targets.size(); k += 2) {
+                const uint32_t ta = ins->targets[k], tb = ins->targets[k + 1];
+                if (ta == tb) fail(lo, "two-qubit gate applied to one qubit");
+                if ((ta & tb) & kRecTarget) fail(lo, "a pair of two measurement records");
+                if (ins->gate == PG_CX && (tb & kRecTarget)) fail(lo, "CX takes a measurement record only as control");
+            }
         }
     }
 };
@@ -268,11 +284,18 @@ int basis_of(int pg) {
     return 0;
 }
 
+// Opcode of one CX/CZ pair: classically controlled X/Z when a target is a
+// measurement record.
+uint32_t pair_opcode(int pg, uint32_t ta, uint32_t tb) {
+    if ((ta | tb) & kRecTarget) return pg == PG_CX ? OP_FFX : OP_FFZ;
+    return opcode_of(pg);
+}
+
 bool records(int pg) { return pg == PG_M || pg == PG_MR || pg == PG_MX || pg == PG_MY || pg == PG_MRX || pg == PG_MRY; }
 
 struct Counts {
     uint64_t instr = 0, meas = 0, det = 0, det_entries = 0;
-    uint64_t gate_t = 0, noise_t = 0;
+    uint64_t gate_t = 0, noise_t = 0, ff_t = 0;
     uint64_t targets[OP_COUNT] = {0};
 };
 
@@ -293,6 +316,7 @@ void count_block(const Block &b, Counts *c, uint32_t *max_qubit, bool *any_qubit
             c->det_entries += mul(inner.det_entries);
             c->gate_t += mul(inner.gate_t);
             c->noise_t += mul(inner.noise_t);
+            c->ff_t += mul(inner.ff_t);
             for (int k = 0; k < (int)OP_COUNT; k++) c->targets[k] += mul(inner.targets[k]);
             if (c->instr > kMaxInstr) throw ParseError{STIM_E_UNSUPPORTED, "more than 2^28 instructions after flattening"};
             continue;
@@ -305,12 +329,21 @@ void count_block(const Block &b, Counts *c, uint32_t *max_qubit, bool *any_qubit
             continue;
         }
         for (uint32_t q : in.targets) {
+            if (q & kRecTarget) continue;
             if (!*any_qubit || q > *max_qubit) *max_qubit = q;
             *any_qubit = true;
         }
         uint32_t op = opcode_of(in.gate);
         uint64_t slots = op_is_pair(op) ? in.targets.size() / 2 : in.targets.size();
-        c->targets[op] += slots;
+        if (op == OP_CX || op == OP_CZ) {
+            for (size_t k = 0; k < in.targets.size(); k += 2) {
+                const uint32_t po = pair_opcode(in.gate, in.targets[k], in.targets[k + 1]);
+                c->targets[po]++;
+                if (op_is_feedforward(po)) c->ff_t++;
+            }
+        } else {
+            c->targets[op] += slots;
+        }
         if (op_is_noise(op)) c->noise_t += slots;
         else c->gate_t += slots;
         if (records(in.gate)) c->meas += in.targets.size();
@@ -376,9 +409,25 @@ class Emitter {
                     DevOp d{};
                     uint32_t qa = in.targets[k];
                     uint32_t qb = pair ? in.targets[k + 1] : qa;
-                    d.a = (op << 24) | qa;
                     d.instr = (uint32_t)instr;
                     d.slot = (uint32_t)(k / step);
+                    if (pair && ((qa | qb) & kRecTarget)) {
+                        // X or Z on the qubit target, controlled by the record
+                        const uint32_t ff = pair_opcode(in.gate, qa, qb);
+                        const uint32_t lookback = ((qa & kRecTarget) ? qa : qb) & ~kRecTarget;
+                        const uint32_t q = (qa & kRecTarget) ? qb : qa;
+                        if (lookback > meas) {
+                            char buf[128];
+                            snprintf(buf, sizeof buf, "line %d: rec[-%u] reaches before the first measurement",
+                                     in.line, lookback);
+                            throw ParseError{STIM_E_PARSE, buf};
+                        }
+                        d.a = (ff << 24) | q;
+                        d.b = (uint32_t)(meas - lookback);
+                        place(d, q, q, false, true);
+                        continue;
+                    }
+                    d.a = (op << 24) | qa;
                     if (op == OP_M || op == OP_MR) {
                         d.b = (uint32_t)meas++;
                     } else if (pair) {
@@ -428,12 +477,15 @@ class Emitter {
         return g;
     }
 
-    void place(const DevOp &d, uint32_t qa, uint32_t qb, bool collapse) {
+    // after_collapses: a classically controlled op goes after every layer
+    // holding a collapsing op (its record is written there).
+    void place(const DevOp &d, uint32_t qa, uint32_t qb, bool collapse, bool after_collapses = false) {
         uint32_t L = lastq(qa);
         uint32_t Lb = lastq(qb);
         if (Lb > L) L = Lb;
         // L is the first layer index after every layer touching the qubits
         if (collapse && last_collapse_ > 0 && last_collapse_ - 1 > L) L = last_collapse_ - 1;
+        if (after_collapses && last_collapse_ > L) L = last_collapse_;
         if (L >= layers_.size()) layers_.resize(L + 1);
         uint32_t op = d.a >> 24;
         if (op_is_gate(op)) layers_[L].gate.push_back(d);
@@ -550,6 +602,7 @@ class FrameBuilder {
             const DevOp *ops = hp_.ops.data() + e.op_begin;
             bool fold = !chains_.empty();
             for (uint32_t i = 0; i < tot && fold; i++) {
+                if (op_is_feedforward(ops[i].a >> 24)) fold = false;       // reads a record of another thread
                 if (frame_opcode(ops[i].a >> 24) == OP_COUNT) continue;     // no frame action
                 const int own = chain_of(ops[i]);
                 if (own == -2 || (own >= 0 && chains_[own].ops.size() >= kMaxChainOps)) fold = false;
@@ -745,6 +798,7 @@ int compile_circuit(const char *text, size_t len, HostProgram *out, std::string 
         hp.num_gate_targets = c.gate_t;
         hp.num_noise_targets = c.noise_t;
         hp.num_instr = c.instr;
+        hp.num_feedforward = c.ff_t;
         for (int k = 0; k < (int)OP_COUNT; k++) hp.exec_targets[k] = c.targets[k];
         hp.det_ptr.reserve(c.det + 1);
         hp.det_ptr.push_back(0);

@@ -274,7 +274,7 @@ __device__ __forceinline__ void frame_op(const FrameArgs &a, const SmemKeys key,
     const uint32_t opc = op.a >> 28;
     const uint32_t lw0 = tile0 + wo;                   // first word within the call
     const uint32_t gw0 = (uint32_t)a.word0 + lw0;      // first global 64-shot word (RNG counter)
-    if (opc >= OP_XERR) {      // noise channels: frame programs hold no opcode above OP_YERR
+    if (opc - OP_XERR <= OP_YERR - OP_XERR) {      // noise channels
         noise_op<W, C, GMEM>(a, key, t, op, wo, gw0, instr_off);
         return;
     }
@@ -360,6 +360,30 @@ __device__ __forceinline__ void frame_op(const FrameArgs &a, const SmemKeys key,
             }
             break;
         }
+        case OP_FFX:
+        case OP_FFZ: {
+            // classically controlled X / Z: applied where the shot's record
+            // differs from the reference (the record row was written in an
+            // earlier merged layer, before the layer barrier)
+            if (a.rec == nullptr) break;
+            const uint32_t m = op.b + meas_off;
+            const uint64_t refm = 0ull - ((__ldg(a.ref + (m >> 6)) >> (m & 63)) & 1ull);
+            const uint64_t *row = a.rec + (uint64_t)m * a.rec_stride;
+            uint64_t f[V];
+#pragma unroll
+            for (int i = 0; i < V; i++) f[i] = lw0 + i < a.nwords ? row[lw0 + i] ^ refm : 0ull;
+            qa.load(t, pa);
+            if (opc == OP_FFX) {
+#pragma unroll
+                for (int i = 0; i < V; i++) pa.x[i] ^= f[i];
+                qa.store_x(t, pa.x);
+            } else {
+#pragma unroll
+                for (int i = 0; i < V; i++) pa.z[i] ^= f[i];
+                qa.store_z(t, pa.z);
+            }
+            break;
+        }
         default:
             break;
     }
@@ -431,7 +455,7 @@ __device__ __forceinline__ void deferred_hit(const FrameArgs &a, const SmemKeys 
     const uint32_t oi = e >> 3, w = e & 7u;
     const uint4 ov = __ldg(reinterpret_cast<const uint4 *>(a.ops) + first + oi);
     const uint32_t opc = ov.x >> 28;
-    if (opc < OP_XERR) return;      // only noise ops are queued
+    if (opc - OP_XERR > OP_YERR - OP_XERR) return;      // only noise ops are queued
     const bool pair = opc == OP_DEP2;
     const uint32_t tbl = pair ? (ov.w >> 24) : ov.y;
     const uint32_t slot = pair ? (ov.w & 0xFFFFFFu) : ov.w;

@@ -16,21 +16,26 @@
 
 namespace stimgb {
 
-// Opcodes 0..11 also appear in frame programs (4 bits there). OP_SX and the
+// Opcodes 0..13 also appear in frame programs (4 bits there). OP_SX and the
 // ones after it are gates that only the reference tableau tells apart: frame
 // programs replace SQRT_X and SQRT_X_DAG (x ^= z) by H S H, S_DAG by S, SQRT_Y
 // and SQRT_Y_DAG by H, and drop the Paulis X, Y, Z (they commute with every
-// frame up to sign).
+// frame up to sign). OP_FFX and OP_FFZ are X and Z controlled by a
+// measurement record ("CX rec[-k] q", "CZ rec[-k] q"): the tableau applies
+// them when the reference outcome is 1, the frame where a shot's record
+// differs from the reference.
 enum Opcode : uint32_t {
     OP_H = 0, OP_S, OP_CX, OP_CZ,                  // Clifford gates
     OP_M, OP_MR, OP_R,                             // collapsing operations (Z basis)
     OP_XERR, OP_ZERR, OP_DEP1, OP_DEP2, OP_YERR,   // Pauli noise channels
+    OP_FFX, OP_FFZ,                                // classically controlled X, Z
     OP_SX,                                         // SQRT_X (frame: x ^= z)
     OP_X, OP_Y, OP_Z, OP_SDAG, OP_SXD, OP_SY, OP_SYD,   // tableau-only gate variants
     OP_COUNT
 };
 
-inline bool op_is_gate(uint32_t o) { return o <= OP_CZ || (o >= OP_SX && o < OP_COUNT); }
+inline bool op_is_gate(uint32_t o) { return o <= OP_CZ || (o >= OP_FFX && o < OP_COUNT); }
+inline bool op_is_feedforward(uint32_t o) { return o == OP_FFX || o == OP_FFZ; }
 inline bool op_is_collapse(uint32_t o) { return o >= OP_M && o <= OP_R; }
 inline bool op_is_noise(uint32_t o) { return o >= OP_XERR && o <= OP_YERR; }
 inline bool op_is_pair(uint32_t o) { return o == OP_CX || o == OP_CZ || o == OP_DEP2; }
@@ -55,7 +60,8 @@ constexpr int kMaxLoopDepth = 16;
 //   a:     opcode << 24 | qubit a  (8-bit host opcode)
 //   b:     qubit b | table << 24 (two-qubit ops, noise table in the top byte)
 //          table << 24 (one-qubit noise)
-//          measurement index of the first loop iteration (M, MR)
+//          measurement index of the first loop iteration (M, MR; the
+//          controlling record of OP_FFX, OP_FFZ)
 //   instr: flattened instruction ordinal of the first loop iteration
 //   slot:  target index (one-qubit ops) or pair index (two-qubit ops)
 struct DevOp {
@@ -87,6 +93,7 @@ struct HostProgram {
     uint64_t num_meas = 0, num_det = 0;
     uint64_t num_gate_targets = 0, num_noise_targets = 0, num_instr = 0;
     uint64_t num_layers_exec = 0;           // layer executions with loops unrolled
+    uint64_t num_feedforward = 0;           // classically controlled X/Z targets (loops unrolled)
     uint64_t num_layers_stored = 0;
     uint32_t max_layer_ops = 0;
     uint32_t max_loop_depth = 0;
@@ -111,7 +118,10 @@ struct HostProgram {
 // its slice; its chains of a merged layer are grouped into segments of equal
 // opcode signature (so warps run uniform code). Noise ops at the end of a
 // chain (defer_from onwards) touch nothing the chain reads later, and their
-// error masks commute, so the kernel may apply them after the chain.
+// error masks commute, so the kernel may apply them after the chain. A layer
+// holding a classically controlled op never folds into the open merged layer:
+// the record it reads was written by another thread, and the barrier that
+// ends the previous merged layer makes that write visible.
 //
 // Entries mirror HostProgram::prog except that folded LAYER entries are
 // removed; a LAYER's op_begin indexes rank_tab, whose C + 1 values bound
@@ -120,7 +130,7 @@ struct HostProgram {
 // Op encoding:
 //   a:     opcode << 28 | reference of qubit a
 //   b:     two-qubit ops: reference of qubit b
-//          M, MR: measurement index of the first loop iteration
+//          M, MR, FFX, FFZ: measurement index of the first loop iteration
 //          one-qubit noise: table index
 //   instr: flattened instruction ordinal of the first loop iteration
 //   slot:  target slot; DEPOLARIZE2 keeps its table index in bits 24..31

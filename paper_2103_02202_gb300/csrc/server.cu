@@ -176,7 +176,7 @@ void plan(stim_server *s, Request *r) {
     const bool want_meas = (r->outputs & STIM_OUT_MEAS) != 0, want_det = (r->outputs & STIM_OUT_DET) != 0;
     r->meas_words = want_meas ? hp.num_meas * w : 0;
     r->det_words = want_det ? hp.num_det * w : 0;
-    r->rec_words = (want_det && !want_meas && hp.num_det) ? hp.num_meas * w : 0;
+    r->rec_words = (!want_meas && ((want_det && hp.num_det) || hp.num_feedforward)) ? hp.num_meas * w : 0;
     const size_t total = 8 * (r->meas_words + r->det_words + r->rec_words + r->gframe_words) + 4 * 256;
     if (total > s->arena.size()) {
         r->error = STIM_E_UNSUPPORTED;

@@ -411,6 +411,16 @@ __global__ void __launch_bounds__(512) tableau_kernel(TabArgs a) {
                             }
                         }
                         break;
+                    case OP_FFX:    // X_a (Z_a <- -Z_a) when the reference outcome of the record is 1
+                    case OP_FFZ:    // Z_a (X_a <- -X_a) likewise
+                        if (k == 0 && lane == 0) {
+                            const uint32_t m = op.b + meas_off;
+                            if ((ld_u64<L1>(a.ref + (m >> 6)) >> (m & 63)) & 1ull) {
+                                const uint32_t c = ld_u32<L1>(a.perm + 2 * qa + (opc == OP_FFX ? 1u : 0u));
+                                st_tab<L1>(a.sign + c, ld_u32<L1>(a.sign + c) ^ 1u);
+                            }
+                        }
+                        break;
                     case OP_SY:     // X_a <- Z_a, Z_a <- -X_a: swap, then negate the new Z column
                     case OP_SYD:    // X_a <- -Z_a, Z_a <- X_a: swap, then negate the new X column
                         if (k == 0 && lane == 0) {

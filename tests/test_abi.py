@@ -71,6 +71,8 @@ CIRCUITS = {
     "wide_gate_set": ("H 0\nSQRT_X 1 2\nSQRT_Y_DAG 3\nMX 0 1\nY_ERROR(0.1) 0 3\nMRY 1\nRX 2\nS_DAG 2\n"
                       "X 2\nY 0\nZ 3\nSQRT_X_DAG 0\nSQRT_Y 1\nRY 3\nMRX 0\nMY 3\nM 2\n"
                       "DETECTOR rec[-1] rec[-2]\n"),
+    "feedforward": ("H 0 1\nM 0 1\nCX rec[-1] 2 rec[-2] 3\nCZ 2 rec[-1]\nREPEAT 3 {\n"
+                    "CZ rec[-2] 0\nMR 1 2\nDETECTOR rec[-1]\n}\nM 3\n"),
 }
 
 
@@ -122,6 +124,14 @@ BAD = [
     ("REPEAT 0 {\nH 0\n}\n", sg.STIM_E_PARSE),
     ("REPEAT x {\nH 0\n}\n", sg.STIM_E_PARSE),
     ("H 16777216\n", sg.STIM_E_UNSUPPORTED),
+    ("M 0\nCX 1 rec[-1]\n", sg.STIM_E_PARSE),
+    ("M 0\nCX rec[-0] 1\n", sg.STIM_E_PARSE),
+    ("M 0 1\nCZ rec[-1] rec[-2]\n", sg.STIM_E_PARSE),
+    ("CX rec[-1] 0\n", sg.STIM_E_PARSE),
+    ("M 0\nCX rec[-2] 1\n", sg.STIM_E_PARSE),
+    ("REPEAT 2 {\nCX rec[-1] 0\nM 0\n}\n", sg.STIM_E_PARSE),
+    ("M 0\nDEPOLARIZE2(0.1) rec[-1] 0\n", sg.STIM_E_PARSE),
+    ("M 0\nH rec[-1]\n", sg.STIM_E_PARSE),
 ]
 
 

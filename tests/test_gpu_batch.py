@@ -91,3 +91,28 @@ def test_batch_matches_oracle_on_sampled_shots():
         np.testing.assert_array_equal(gm, om)
         np.testing.assert_array_equal(gd, od)
     b.close()
+
+
+def test_batch_feedforward_detectors_only():
+    """Circuits with classically controlled X/Z in a batch, detection events
+    only: the batch keeps their records in scratch and matches the plain
+    entry point and the oracle."""
+    texts = ["H 0 1\nM 0 1\nCX rec[-1] 2\nCZ rec[-2] 2\nREPEAT 20 {\nH 3\nCX rec[-1] 3\n"
+             "X_ERROR(0.1) 2\nMR 2 3\nDETECTOR rec[-1] rec[-2]\nCZ 2 rec[-2]\nH 2\n}\nM 2\nDETECTOR rec[-1]\n",
+             W.surface_code_memory(3, 3, 1e-3)]
+    shots = [900, 300]
+    cs = [sg.Circuit(t) for t in texts]
+    b = sg.Batch(cs, shots)
+    out = b.sample([7, 8], meas=False)
+    torch.cuda.synchronize()
+    for c, t, S, sd, (m, d) in zip(cs, texts, shots, [7, 8], out):
+        assert m is None
+        _, pd = c.sample(S, sd, meas=False)
+        torch.cuda.synchronize()
+        assert torch.equal(d, pd)
+    o = oracle.Circuit(texts[0])
+    _, od = o.sample(np.arange(shots[0]), 7, threads=4)
+    dd = out[0][1].cpu().numpy().view(np.uint64)
+    got = np.unpackbits(dd.view(np.uint8).reshape(dd.shape[0], -1), axis=1, bitorder="little")[:, :shots[0]].T
+    np.testing.assert_array_equal(got, od)
+    b.close()

@@ -398,10 +398,16 @@ WIDE_COLLAPSE = ["M", "MR", "R", "MX", "MY", "MRX", "MRY", "RX", "RY"]
 WIDE_NOISE = ["X_ERROR", "Y_ERROR", "Z_ERROR", "DEPOLARIZE1", "DEPOLARIZE2"]
 
 
-def _wide_circuit(rng, n, L):
+def _wide_circuit(rng, n, L, feedforward=False):
     lines = []
+    nmeas = 0
     for _ in range(L):
         kind = rng.random()
+        if feedforward and nmeas and kind < 0.15:
+            k = int(rng.integers(1, min(nmeas, 12) + 1))
+            q = int(rng.integers(n))
+            lines.append(f"CX rec[-{k}] {q}" if rng.random() < 0.5 else f"CZ {q} rec[-{k}]")
+            continue
         if kind < 0.4:
             g = str(rng.choice(WIDE_1Q))
             k = int(rng.integers(1, n + 1))
@@ -423,6 +429,7 @@ def _wide_circuit(rng, n, L):
             lines.append(f"{g} " + " ".join(map(str, rng.choice(n, k, replace=False))))
             if g[0] == "M":
                 lines.append("DETECTOR rec[-1]")
+                nmeas += k
     lines.append(str(rng.choice(["M", "MX", "MY"])) + " " + " ".join(map(str, range(n))))
     lines.append("DETECTOR rec[-1] rec[-2]")
     return "\n".join(lines) + "\n"
@@ -454,3 +461,87 @@ def test_wide_gate_set_tile_shapes(hint):
     om, od = oracle.Circuit(text).sample(np.arange(1000), 5, threads=8)
     np.testing.assert_array_equal(mb, om)
     np.testing.assert_array_equal(db, od)
+
+
+def _feedforward_loop_circuit(rng, n, reps):
+    """A REPEAT body whose classically controlled ops read records of the
+    previous iteration and of the measurements before the loop."""
+    body = []
+    for _ in range(int(rng.integers(4, 12))):
+        kind = rng.random()
+        if kind < 0.3:
+            k = int(rng.integers(1, n + 1))
+            q = int(rng.integers(n))
+            body.append(f"CX rec[-{k}] {q}" if rng.random() < 0.5 else f"CZ rec[-{k}] {q}")
+        elif kind < 0.55:
+            a, b = rng.choice(n, 2, replace=False)
+            body.append(f"{str(rng.choice(['CX', 'CZ']))} {a} {b}")
+        elif kind < 0.75:
+            body.append(f"{str(rng.choice(WIDE_1Q))} {int(rng.integers(n))}")
+        else:
+            ch = str(rng.choice(["X_ERROR", "Z_ERROR", "DEPOLARIZE1"]))
+            body.append(f"{ch}(0.05) {int(rng.integers(n))}")
+    body.append("MR " + " ".join(map(str, range(n))))
+    body.append("DETECTOR rec[-1] rec[-2]")
+    return ("H " + " ".join(map(str, range(n))) + "\nM " + " ".join(map(str, range(n))) +
+            f"\nREPEAT {reps} {{\n" + "\n".join(body) + "\n}\nM 0\nDETECTOR rec[-1]\n")
+
+
+def test_feedforward_reference_and_samples_match_oracle():
+    """Classically controlled X/Z (CX rec[-k] q, CZ q rec[-k]): GPU reference
+    and records equal the oracle's, including loops that read records of the
+    previous iteration."""
+    rng = np.random.default_rng(2105)
+    for it in range(30):
+        n = int(rng.integers(2, 40))
+        if it % 3 == 2:
+            text = _feedforward_loop_circuit(rng, min(n, 8), int(rng.integers(2, 30)))
+        else:
+            text = _wide_circuit(rng, n, int(rng.integers(5, 60)), feedforward=True)
+        gr, gd = gpu_reference(text)
+        orf, odf = oracle.Circuit(text).reference()
+        np.testing.assert_array_equal(gr, orf, err_msg=text)
+        np.testing.assert_array_equal(gd, odf, err_msg=text)
+        shots = int(rng.integers(1, 700))
+        mb, db = gpu_sample(text, shots, 3000 + it)
+        om, od = oracle.Circuit(text).sample(np.arange(shots), 3000 + it, threads=8)
+        np.testing.assert_array_equal(mb, om, err_msg=text)
+        np.testing.assert_array_equal(db, od, err_msg=text)
+
+
+@pytest.mark.parametrize("hint", [(1, 64, 0, 2), (4, 128, 0, 1), (8, 256, 0, 1), (2, 128, 1, 1), (1, 96, 0, 4)])
+def test_feedforward_tile_shapes(hint):
+    rng = np.random.default_rng(2106)
+    text = _wide_circuit(rng, 30, 120, feedforward=True) + _feedforward_loop_circuit(rng, 6, 9)
+    mb, db = gpu_sample(text, 1000, 5, hint=hint)
+    om, od = oracle.Circuit(text).sample(np.arange(1000), 5, threads=8)
+    np.testing.assert_array_equal(mb, om)
+    np.testing.assert_array_equal(db, od)
+
+
+def test_feedforward_detectors_only_and_detection_lists():
+    """Detection events alone (no measurement output buffer) still see the
+    classically controlled ops: the records are kept in scratch."""
+    rng = np.random.default_rng(2107)
+    text = _feedforward_loop_circuit(rng, 7, 25)
+    shots = 777
+    c = sg.Circuit(text)
+    _, d = c.sample(shots, 11, meas=False)
+    torch.cuda.synchronize()
+    db = words_to_bits(to_np(d), shots).T
+    _, dh = c.sample_host(shots, 11, meas=False, shot_major=True)
+    begin, dets = c.sample_detections(shots, 11)
+    c.close()
+    _, od = oracle.Circuit(text).sample(np.arange(shots), 11, threads=8)
+    np.testing.assert_array_equal(db, od)
+    np.testing.assert_array_equal(words_to_bits(dh, od.shape[1]), od)
+    lists = [list(np.flatnonzero(row)) for row in od]
+    got = [list(dets[begin[s]:begin[s + 1]]) for s in range(shots)]
+    assert got == lists
+
+
+def test_teleportation_is_deterministic_on_the_gpu():
+    txt = "H 0\nS 0\nH 1\nCX 1 2\nCX 0 1\nH 0\nM 0 1\nCX rec[-1] 2\nCZ rec[-2] 2\nMY 2\n"
+    mb, _ = gpu_sample(txt, 5000, 9)
+    assert np.all(mb[:, 2] == 0)
+    assert 0.45 < mb[:, 0].mean() < 0.55 and 0.45 < mb[:, 1].mean() < 0.55

@@ -118,3 +118,24 @@ def test_cancel_and_wait_timeout():
         srv.wait(r)
         srv.release(r)
     srv.close()
+
+
+def test_feedforward_detectors_only_request():
+    """A detectors-only request for a circuit with classically controlled ops
+    reserves record scratch and matches the plain entry point."""
+    text = ("H 0 1\nM 0 1\nREPEAT 30 {\nCX rec[-1] 2\nCZ 2 rec[-2]\nDEPOLARIZE1(0.05) 2\nMR 2\n"
+            "DETECTOR rec[-1]\nH 0\nM 0\n}\n")
+    c = sg.Circuit(text)
+    srv = sg.Server(64 << 20, streams=2)
+    rid = srv.submit(c, 1500, 42, 64, outputs=sg.STIM_OUT_DET)
+    srv.wait(rid)
+    d = torch.empty((c.num_detectors, (1500 + 63) // 64), dtype=torch.int64, device="cuda")
+    s = torch.cuda.current_stream()
+    sg._check(sg.library().stim_server_copy_result(srv.handle, rid, None, d.data_ptr(), sg.STIM_DEVICE,
+                                                   s.cuda_stream))
+    _, pd = c.sample(1500, 42, shot_offset=64, meas=False)
+    torch.cuda.synchronize()
+    assert torch.equal(d, pd)
+    srv.release(rid)
+    srv.close()
+    c.close()

@@ -77,3 +77,22 @@ def test_noalloc_rejects_oversize_and_missing_setup():
     assert rc == sg.STIM_E_UNSUPPORTED
     assert "32 MiB" in sg.stim_last_error()
     c.close()
+
+
+def test_noalloc_with_classically_controlled_ops():
+    text = ("H 0 1\nM 0 1\nREPEAT 12 {\nCX rec[-1] 2\nCZ 2 rec[-2]\nX_ERROR(0.05) 2\nMR 2\n"
+            "DETECTOR rec[-1]\nH 0\nM 0\n}\n")
+    c = sg.Circuit(text)
+    lib = sg.library()
+    stream = torch.cuda.current_stream().cuda_stream
+    ref = torch.zeros(max((c.num_measurements + 63) // 64, 1), dtype=torch.int64, device="cuda")
+    assert lib.stim_reference_sample(c.handle, ref.data_ptr(), None, 0, stream) == sg.STIM_OK
+    shots = 2000
+    nw = (shots + 63) // 64
+    got = torch.full((c.num_detectors, nw), -1, dtype=torch.int64, device="cuda")
+    rc = lib.stim_frame_sample_noalloc(c.handle, shots, 3, 0, got.data_ptr(), stream)
+    assert rc == sg.STIM_OK, sg.stim_last_error()
+    _, want = c.sample(shots, 3, meas=False)
+    torch.cuda.synchronize()
+    assert torch.equal(want, got)
+    c.close()
