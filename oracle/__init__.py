@@ -108,10 +108,11 @@ class Circuit:
         if L.orc_parse(text.encode(), ctypes.byref(h), err, 512) != 0:
             raise OracleError(err.value.decode())
         self._h = h
-        info = (ctypes.c_uint64 * 6)()
+        info = (ctypes.c_uint64 * 7)()
         L.orc_info(h, info)
         (self.num_qubits, self.num_measurements, self.num_detectors,
-         self.num_gate_targets, self.num_noise_targets, self.num_instructions) = map(int, info)
+         self.num_gate_targets, self.num_noise_targets, self.num_instructions,
+         self.num_observables) = map(int, info)
         self._ref = None
 
     def __del__(self):
@@ -134,13 +135,14 @@ class Circuit:
     def sample(self, shots, seed: int, shot_offset: int = 0, *, threads: int = 1,
                ref: np.ndarray | None = None):
         """Per-shot frame simulation of the given shot indices (global index =
-        shot_offset + shots[i]). Returns (meas [k, M] uint8, dets [k, D] uint8)."""
+        shot_offset + shots[i]). Returns (meas [k, M] uint8, dets [k, D + K] uint8):
+        the D detectors, then the K observables (OBSERVABLE_INCLUDE)."""
         shots = np.ascontiguousarray(np.asarray(shots, dtype=np.uint64))
         if ref is None:
             ref = self.reference()[0]
         ref = np.ascontiguousarray(ref, dtype=np.uint8)
         k = len(shots)
-        M, D = self.num_measurements, self.num_detectors
+        M, D = self.num_measurements, self.num_detectors + self.num_observables
         meas = np.zeros((k, max(M, 1)), np.uint8)
         dets = np.zeros((k, max(D, 1)), np.uint8)
         lib().orc_frame_shots(self._h, _ptr(ref if M else np.zeros(1, np.uint8)),

@@ -18,7 +18,10 @@
  *     CNOTs from a pivot, a single-qubit collapse gate and an X;
  *   - the Pauli frame simulator (Section 3, enumerated steps), one shot at a
  *     time with one byte per qubit per plane;
- *   - detectors as the XOR of measurement flips (Section 5.6);
+ *   - detectors as the XOR of measurement flips (Section 5.6); logical
+ *     observables (OBSERVABLE_INCLUDE(k) rec[-a] ..., the logical errors of
+ *     Section 1 made an output) the same way, accumulated per index over
+ *     every instruction naming it and output after the detectors;
  *   - classically controlled Paulis (Section 3, "Tracking Corrections"):
  *     "CX rec[-k] q" applies X to q and "CZ rec[-k] q" Z when measurement
  *     record -k is 1. The tableau applies the Pauli when the reference
@@ -55,20 +58,22 @@ enum {
     OG_XERR, OG_ZERR, OG_DEP1, OG_DEP2, OG_DET, OG_X,
     /* wider gate set */
     OG_Y, OG_Z, OG_SDAG, OG_SQX, OG_SQXD, OG_SQY, OG_SQYD, OG_YERR,
-    OG_MX, OG_MY, OG_MRX, OG_MRY, OG_RX, OG_RY
+    OG_MX, OG_MY, OG_MRX, OG_MRY, OG_RX, OG_RY,
+    OG_OBS              /* OBSERVABLE_INCLUDE(k) rec[-a] ... */
 };
 
 typedef struct {
     int gate;
     double p;
     uint32_t nt;
-    uint32_t *t;        /* qubits, or absolute measurement indices (DETECTOR) */
+    uint32_t *t;        /* qubits, or absolute measurement indices (DETECTOR, OBSERVABLE_INCLUDE) */
     uint64_t G[64];     /* geometric table (noise ops only) */
 } orc_op;
 
 typedef struct {
     uint32_t n;         /* qubits */
     uint64_t nmeas, ndet, ngate_targets, nnoise_targets;
+    uint64_t nobs;      /* observables: largest OBSERVABLE_INCLUDE index + 1 */
     size_t nops, cap;
     orc_op *ops;        /* flattened: ops[i] has instruction ordinal i */
 } orc_circuit;
@@ -281,6 +286,7 @@ static int gate_from_name(const char *w, size_t n) {
     if (IS("DEPOLARIZE1")) return OG_DEP1;
     if (IS("DEPOLARIZE2")) return OG_DEP2;
     if (IS("DETECTOR")) return OG_DET;
+    if (IS("OBSERVABLE_INCLUDE")) return OG_OBS;
     if (IS("X")) return OG_X;
     if (IS("Y")) return OG_Y;
     if (IS("Z")) return OG_Z;
@@ -356,6 +362,9 @@ static int parse_line(pstate *ps, const char *b, const char *e, node *k) {
     if (is_noise(g)) {
         if (nargs != 1) return perr(ps, "noise channel takes one probability");
         if (!(k->p >= 0.0 && k->p <= 1.0)) return perr(ps, "probability outside [0, 1]");
+    } else if (g == OG_OBS) {
+        if (nargs != 1) return perr(ps, "OBSERVABLE_INCLUDE takes one index");
+        if (!(k->p >= 0.0 && k->p < 65536.0) || k->p != floor(k->p)) return perr(ps, "bad observable index");
     } else if (g != OG_DET && nargs != 0) {
         return perr(ps, "gate takes no arguments");
     }
@@ -375,7 +384,7 @@ static int parse_line(pstate *ps, const char *b, const char *e, node *k) {
             p++;
             if (v == 0) return perr(ps, "rec[-0] is not a measurement");
             v |= REC_FLAG;
-        } else if (g == OG_DET) {
+        } else if (g == OG_DET || g == OG_OBS) {
             if (e - p < 6 || strncmp(p, "rec[-", 5) != 0) return perr(ps, "expected rec[-k]");
             p += 5;
             if (p >= e || *p < '0' || *p > '9') return perr(ps, "expected rec[-k]");
@@ -466,12 +475,13 @@ static int flatten(pstate *ps, const node *blk, orc_circuit *c) {
         o->p = k->p;
         o->nt = k->nt;
         o->t = (uint32_t *)malloc((k->nt ? k->nt : 1) * sizeof(uint32_t));
-        if (k->gate == OG_DET) {
+        if (k->gate == OG_DET || k->gate == OG_OBS) {
             for (uint32_t j = 0; j < k->nt; j++) {
                 if ((uint64_t)k->t[j] > c->nmeas) return perr(ps, "rec[-%u] reaches before the first measurement", k->t[j]);
                 o->t[j] = (uint32_t)(c->nmeas - k->t[j]);
             }
-            c->ndet++;
+            if (k->gate == OG_DET) c->ndet++;
+            else if ((uint64_t)k->p + 1 > c->nobs) c->nobs = (uint64_t)k->p + 1;
         } else {
             memcpy(o->t, k->t, k->nt * sizeof(uint32_t));
             for (uint32_t j = 0; j < k->nt; j++) {
@@ -526,14 +536,15 @@ int orc_parse(const char *text, orc_circuit **out, char *err, size_t errlen) {
     return 0;
 }
 
-/* n, M, D, gate targets, noise targets, instructions */
-void orc_info(const orc_circuit *c, uint64_t out[6]) {
+/* n, M, D, gate targets, noise targets, instructions, observables */
+void orc_info(const orc_circuit *c, uint64_t out[7]) {
     out[0] = c->n;
     out[1] = c->nmeas;
     out[2] = c->ndet;
     out[3] = c->ngate_targets;
     out[4] = c->nnoise_targets;
     out[5] = c->nops;
+    out[6] = c->nobs;
 }
 
 /* ------------------------------------------------------------------------ */
@@ -1012,7 +1023,9 @@ static void *frame_worker(void *arg) {
         uint64_t word = shot / 64;
         int b = (int)(shot % 64);
         uint8_t *mrow = jb->meas ? jb->meas + si * c->nmeas : NULL;
-        uint8_t *drow = jb->dets ? jb->dets + si * c->ndet : NULL;
+        /* detection-event row: D detectors, then the observables */
+        uint8_t *drow = jb->dets ? jb->dets + si * (c->ndet + c->nobs) : NULL;
+        if (drow) memset(drow + c->ndet, 0, c->nobs);
         /* Step 2: every qubit starts as I or Z with probability 1/2. */
         for (uint32_t q = 0; q < c->n; q++) {
             x[q] = 0;
@@ -1103,6 +1116,12 @@ static void *frame_worker(void *arg) {
                 for (uint32_t j = 0; j < o->nt; j++) v ^= flip[o->t[j]];
                 if (drow) drow[dk] = v;
                 dk++;
+                break;
+            }
+            case OG_OBS: {      /* an observable is the XOR of the flips of every record it includes */
+                uint8_t v = 0;
+                for (uint32_t j = 0; j < o->nt; j++) v ^= flip[o->t[j]];
+                if (drow) drow[c->ndet + (uint64_t)o->p] ^= v;
                 break;
             }
             }

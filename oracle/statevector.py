@@ -74,7 +74,7 @@ def parse(text: str):
         if name == "CNOT":
             name = "CX"
         toks = m.group(3).split()
-        if name == "DETECTOR":
+        if name in ("DETECTOR", "OBSERVABLE_INCLUDE"):
             tg = [int(re.fullmatch(r"rec\[-(\d+)\]", t).group(1)) for t in toks]
         else:
             # CX/CZ may take a measurement record rec[-k] as control (a
@@ -93,7 +93,7 @@ def parse(text: str):
                     walk(it[2])
                 continue
             name, tg = it
-            if name == "DETECTOR":
+            if name in ("DETECTOR", "OBSERVABLE_INCLUDE"):
                 flat.append((name, [count[0] - k for k in tg]))
             else:
                 flat.append((name, [("rec", count[0] - t[1]) if isinstance(t, tuple) else t for t in tg]))
@@ -108,7 +108,7 @@ def num_qubits(ops) -> int:
     n = 0
     for name, tg in ops:
         qs = [t for t in tg if not isinstance(t, tuple)]
-        if name != "DETECTOR" and qs:
+        if name not in ("DETECTOR", "OBSERVABLE_INCLUDE") and qs:
             n = max(n, max(qs) + 1)
     return n
 

@@ -623,3 +623,97 @@ def test_noise_mask_structure():
     hm = oracle.half_mask(seed, oracle.TAG_COLLAPSE, instr, slot, word)
     blk = oracle.philox([0, slot, (1 << 28) | instr, word], [seed & 0xFFFFFFFF, seed >> 32])
     assert hm == int(blk[0]) | (int(blk[1]) << 32)
+
+
+# ---------------------------------------------------------------------------
+# Logical observables (OBSERVABLE_INCLUDE): D detectors, then K observables,
+# each the XOR of the flips of every record it includes.
+# ---------------------------------------------------------------------------
+def _rep_memory(d, rounds, p, final_noise=0.0):
+    """Repetition-code memory ending with a data-qubit readout; the logical
+    observable is the last data qubit's final measurement."""
+    txt = W.repetition_code(d, rounds, p)
+    data = " ".join(str(q) for q in range(0, 2 * d + 1, 2))
+    if final_noise:
+        txt += f"X_ERROR({final_noise}) {2 * d}\n"
+    txt += f"M {data}\nOBSERVABLE_INCLUDE(0) rec[-1]\n"
+    return txt
+
+
+def test_observable_of_noiseless_memory_never_flips():
+    c = oracle.Circuit(_rep_memory(4, 6, 0.0))
+    assert c.num_observables == 1 and c.num_detectors == 0
+    _, dets = c.sample(np.arange(400), seed=3)
+    assert dets.shape == (400, 1) and not dets.any()
+
+
+def test_observable_flips_with_certain_error():
+    # X_ERROR(1) on the observable's qubit right before its readout: every shot flips
+    c = oracle.Circuit(_rep_memory(3, 2, 0.0, final_noise=1.0))
+    _, dets = c.sample(np.arange(300), seed=4)
+    assert dets[:, 0].all()
+
+
+def test_observable_flip_rate_matches_p():
+    p, n = 0.2, 20000
+    c = oracle.Circuit("R 0\nX_ERROR(0.2) 0\nM 0\nOBSERVABLE_INCLUDE(0) rec[-1]\n")
+    _, dets = c.sample(np.arange(n), seed=5, threads=8)
+    sd = math.sqrt(p * (1 - p) / n)
+    assert abs(dets[:, 0].mean() - p) < 5 * sd
+
+
+def test_observables_accumulate_index_gaps_and_loops():
+    txt = ("H 0 1\nM 0 1\nOBSERVABLE_INCLUDE(2) rec[-1]\nOBSERVABLE_INCLUDE(2) rec[-1]\n"
+           "REPEAT 3 {\nH 2\nM 2\nOBSERVABLE_INCLUDE(1) rec[-1]\n}\nDETECTOR rec[-4]\n")
+    c = oracle.Circuit(txt)
+    assert c.num_observables == 3 and c.num_detectors == 1
+    meas, dets = c.sample(np.arange(500), seed=6)
+    assert dets.shape == (500, 4)
+    ref = c.reference()[0]
+    flips = meas ^ ref
+    np.testing.assert_array_equal(dets[:, 0], flips[:, 1])                      # DETECTOR rec[-4]
+    assert not dets[:, 1].any() and not dets[:, 3].any()                          # index 0 unused; 2 cancels
+    np.testing.assert_array_equal(dets[:, 2], flips[:, 2] ^ flips[:, 3] ^ flips[:, 4])
+    assert 0.4 < dets[:, 2].mean() < 0.6
+
+
+def test_deterministic_parities_as_observables_never_flip():
+    """Any parity of records that the state vector finds deterministic (the
+    same in every branch) is an observable that never flips in noiseless
+    frame sampling: the collapse coins cancel in it."""
+    rng = np.random.default_rng(2200)
+    checked = 0
+    while checked < 12:
+        n = int(rng.integers(2, 5))
+        txt = _rand_wide_circuit(rng, n, int(rng.integers(4, 18)))
+        txt = "\n".join(l for l in txt.splitlines() if "ERROR" not in l and "DEPOLARIZE" not in l) + "\n"
+        try:
+            br = sv.branches(txt)
+        except AssertionError:
+            continue
+        if len(br) > 64 or len(br) < 2:
+            continue
+        outs = np.array(sorted(br), np.uint8)
+        M = outs.shape[1]
+        found = None
+        for mask in range(1, min(1 << M, 1 << 12)):
+            sel = [i for i in range(M) if (mask >> i) & 1]
+            par = np.bitwise_xor.reduce(outs[:, sel], axis=1)
+            if np.all(par == par[0]) and len(sel) >= 2:
+                found = sel
+                break
+        if found is None:
+            continue
+        obs = "OBSERVABLE_INCLUDE(0) " + " ".join(f"rec[-{M - i}]" for i in found) + "\n"
+        c = oracle.Circuit(txt + obs)
+        _, dets = c.sample(np.arange(256), seed=int(rng.integers(2**62)))
+        assert not dets[:, -1].any(), txt + obs
+        checked += 1
+
+
+def test_observable_parse_errors():
+    for bad in ("M 0\nOBSERVABLE_INCLUDE rec[-1]\n", "M 0\nOBSERVABLE_INCLUDE(0.5) rec[-1]\n",
+                "M 0\nOBSERVABLE_INCLUDE(-1) rec[-1]\n", "M 0\nOBSERVABLE_INCLUDE(0) 0\n",
+                "M 0\nOBSERVABLE_INCLUDE(0) rec[-2]\n", "M 0\nOBSERVABLE_INCLUDE(1, 2) rec[-1]\n"):
+        with pytest.raises(ValueError):
+            oracle.Circuit(bad)
