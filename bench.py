@@ -291,8 +291,8 @@ def run_batch_workload(args):
     outs = []
     for c, S in zip(cs, shots):
         w = (S + 63) // 64
-        if c.num_detectors:
-            outs.append((None, torch.empty((c.num_detectors, w), dtype=torch.int64, device="cuda")))
+        if c.num_detector_rows:
+            outs.append((None, torch.empty((c.num_detector_rows, w), dtype=torch.int64, device="cuda")))
         else:
             outs.append((torch.empty((c.num_measurements, w), dtype=torch.int64, device="cuda"), None))
     gate_shots = sum(c.info["num_gate_targets"] * S for c, S in zip(cs, shots))
@@ -359,7 +359,7 @@ def run_serve_workload(args):
     srv = sg.Server(150 << 30, streams=16)
 
     def outputs(c):
-        return sg.STIM_OUT_DET if c.num_detectors else sg.STIM_OUT_MEAS
+        return sg.STIM_OUT_DET if c.num_detector_rows else sg.STIM_OUT_MEAS
 
     # capacity: a burst of requests drawn like the stream, all submitted at once
     _, probe = W.serve_requests(seed=99, count=min(600, args.requests))
@@ -461,7 +461,7 @@ def main():
     circ = sg.Circuit(text)
     compile_s = time.perf_counter() - t0
     info = circ.info
-    n, M, D = info["num_qubits"], info["num_measurements"], info["num_detectors"]
+    n, M, D = info["num_qubits"], info["num_measurements"], info["num_detectors"] + info["num_observables"]
     counts = target_counts(text)
     gate_targets = sum(counts.get(g, 0) for g in BITS_PER_TARGET)
     assert gate_targets == info["num_gate_targets"], (gate_targets, info)

@@ -64,12 +64,15 @@ typedef struct stim_circuit stim_circuit;
 typedef struct {
     uint32_t num_qubits;         /* max qubit target + 1 */
     uint64_t num_measurements;   /* M: targets of M, MR, MX, MY, MRX, MRY, in order */
-    uint64_t num_detectors;      /* D: DETECTOR instructions, in order */
+    uint64_t num_detectors;      /* D: DETECTOR instructions, in order; detection-event
+                                    outputs hold D + K rows: the detectors, then the
+                                    K logical observables */
     uint64_t num_gate_targets;   /* one-qubit gate, measurement and reset targets plus CX/CZ pairs */
     uint64_t num_noise_targets;  /* X/Y/Z_ERROR, DEPOLARIZE1 targets plus DEPOLARIZE2 pairs */
     uint64_t num_instructions;   /* instruction lines after REPEAT flattening */
     uint64_t num_layers;         /* fused layers executed per shot (loops unrolled) */
     uint64_t num_program_layers; /* fused layers stored (loop bodies once) */
+    uint64_t num_observables;    /* K: largest OBSERVABLE_INCLUDE index + 1 (0 without any) */
 } stim_info;
 
 /* Tile choice for the frame kernel; zero fields mean "let the library pick". */
@@ -95,7 +98,12 @@ typedef struct {
  * the classically controlled Paulis a Pauli frame tracks in place of the
  * qubits (Section 3, "Tracking Corrections"). Sampling a circuit that has
  * them keeps its measurement records in device memory even when only
- * detection events are asked for.
+ * detection events are asked for. OBSERVABLE_INCLUDE(k) rec[-a]... adds the
+ * records to logical observable k (0 <= k < 65536; several instructions with
+ * one index accumulate): its output bit is the XOR of the flips of all the
+ * records it includes, i.e. whether the shot's noise flipped the logical
+ * observable, and observables follow the D detectors as rows D..D+K-1 of every
+ * detection-event output (K = largest index + 1).
  *
  * text/len: the circuit (need not be NUL-terminated). *out receives a new
  * handle on success; the caller frees it with stim_free(). Compilation is
@@ -148,8 +156,9 @@ int stim_reference_sample(stim_circuit *c, uint64_t *ref_bits, uint64_t *det_bit
  * meas_out: may be NULL. MEAS_MAJOR: M rows of ceil(num_shots/64) words.
  *   SHOT_MAJOR: num_shots rows of ceil(M/64) words.
  * det_out: may be NULL. Detection events (XOR of the flips of a detector's
- *   measurements, Section 5.6). MEAS_MAJOR: D rows of ceil(num_shots/64)
- *   words. SHOT_MAJOR: num_shots rows of ceil(D/64) words.
+ *   measurements, Section 5.6), then the K observable flips: with R = D + K,
+ *   MEAS_MAJOR: R rows of ceil(num_shots/64) words. SHOT_MAJOR: num_shots
+ *   rows of ceil(R/64) words.
  * The reference sample is computed first if the handle has none.
  * Errors: STIM_E_INVALID_ARG, STIM_E_OOM, STIM_E_CUDA, STIM_E_TIMEOUT.
  */
@@ -182,7 +191,8 @@ int stim_frame_sample_ex(stim_circuit *c, uint64_t num_shots, uint64_t seed,
  * shot_offset+num_shots-1 (as stim_frame_sample_ex) as per-shot lists of the
  * fired detectors, the "hits" form of the paper's output formats (Section
  * 5.6): detectors[shot_begin[s] .. shot_begin[s+1]) are the indices of the
- * detectors that fired in shot s (0-based within the call), ascending.
+ * detectors that fired in shot s (0-based within the call), ascending; a
+ * flipped logical observable k appears as index D + k.
  *
  * shot_begin: num_shots + 1 offsets (uint64), may be NULL.
  * detectors: uint32 detector indices, room for `capacity` entries; may be NULL
@@ -217,7 +227,7 @@ int stim_frame_sample_detections(stim_circuit *c, uint64_t num_shots, uint64_t s
  * stim_batch_sample runs the plan on `stream`: circuit i samples its
  * num_shots[i] shots with global shot indices shot_offsets[i] + 0.. (offsets
  * may be NULL = all 0; multiples of 64) under seeds[i]. meas_out[i] and
- * det_out[i] are device memory in MEAS_MAJOR layout (M or D rows of
+ * det_out[i] are device memory in MEAS_MAJOR layout (M or D + K rows of
  * ceil(num_shots[i]/64) words); either array or entry may be NULL. Results
  * equal stim_frame_sample_ex bit for bit. The work is captured in a CUDA
  * graph on the first call for a given set of non-NULL outputs and replayed
@@ -274,7 +284,7 @@ typedef struct {
     uint64_t num_shots;
     uint64_t words_per_row;   /* ceil(num_shots / 64) */
     uint64_t *meas;           /* M rows, device memory (NULL if not requested) */
-    uint64_t *det;            /* D rows, device memory (NULL if not requested) */
+    uint64_t *det;            /* D + K rows, device memory (NULL if not requested) */
     double queue_s;           /* submission to admission */
     double latency_s;         /* submission to completion */
 } stim_result;
@@ -319,7 +329,7 @@ void stim_server_destroy(stim_server *s);
  *
  * Same shots, same bits as stim_frame_sample_ex(c, num_shots, seed,
  * shot_offset, NULL, det_out, STIM_MEAS_MAJOR | STIM_DEVICE, NULL, stream).
- * det_out: device memory, D rows of ceil(num_shots/64) words (MEAS_MAJOR).
+ * det_out: device memory, D + K rows of ceil(num_shots/64) words (MEAS_MAJOR).
  * Asynchronous on `stream`.
  *
  * Preconditions and limits:

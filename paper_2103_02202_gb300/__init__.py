@@ -68,7 +68,8 @@ class StimInfo(ctypes.Structure):
     _fields_ = [("num_qubits", ctypes.c_uint32), ("num_measurements", ctypes.c_uint64),
                 ("num_detectors", ctypes.c_uint64), ("num_gate_targets", ctypes.c_uint64),
                 ("num_noise_targets", ctypes.c_uint64), ("num_instructions", ctypes.c_uint64),
-                ("num_layers", ctypes.c_uint64), ("num_program_layers", ctypes.c_uint64)]
+                ("num_layers", ctypes.c_uint64), ("num_program_layers", ctypes.c_uint64),
+                ("num_observables", ctypes.c_uint64)]
 
 
 class StimTileHint(ctypes.Structure):
@@ -309,6 +310,9 @@ class Circuit:
         self.num_qubits = self.info["num_qubits"]
         self.num_measurements = self.info["num_measurements"]
         self.num_detectors = self.info["num_detectors"]
+        self.num_observables = self.info["num_observables"]
+        # rows of a detection-event output: the detectors, then the observables
+        self.num_detector_rows = self.num_detectors + self.num_observables
 
     def close(self):
         if getattr(self, "handle", None):
@@ -336,7 +340,7 @@ class Circuit:
                meas: bool = True, dets: bool = True, hint=None, stream=None):
         """Sample on the device; returns (meas, dets) int64 tensors (None when not asked)."""
         import torch
-        M, D = self.num_measurements, self.num_detectors
+        M, D = self.num_measurements, self.num_detector_rows
         if shot_major:
             ms = (num_shots, _words(M))
             ds = (num_shots, _words(D))
@@ -356,7 +360,7 @@ class Circuit:
     def sample_host(self, num_shots: int, seed: int, *, shot_offset: int = 0, shot_major: bool = False,
                     meas: bool = True, dets: bool = True, hint=None):
         """Sample into host numpy uint64 arrays through the STIM_HOST path."""
-        M, D = self.num_measurements, self.num_detectors
+        M, D = self.num_measurements, self.num_detector_rows
         if shot_major:
             ms, ds = (num_shots, _words(M)), (num_shots, _words(D))
         else:
@@ -406,8 +410,8 @@ class Batch:
                 w = _words(S)
                 m = torch.empty((c.num_measurements, w), dtype=torch.int64, device="cuda") \
                     if meas and c.num_measurements else None
-                d = torch.empty((c.num_detectors, w), dtype=torch.int64, device="cuda") \
-                    if dets and c.num_detectors else None
+                d = torch.empty((c.num_detector_rows, w), dtype=torch.int64, device="cuda") \
+                    if dets and c.num_detector_rows else None
                 out.append((m, d))
         stim_batch_sample(self.plan, seeds, shot_offsets,
                           [m.data_ptr() if m is not None else 0 for m, _ in out],
@@ -458,7 +462,7 @@ class Server:
         import torch
         w = _words(num_shots)
         m = torch.empty((circuit.num_measurements, w), dtype=torch.int64, device="cuda")
-        d = torch.empty((circuit.num_detectors, w), dtype=torch.int64, device="cuda")
+        d = torch.empty((circuit.num_detector_rows, w), dtype=torch.int64, device="cuda")
         s = torch.cuda.current_stream()
         _check(library().stim_server_copy_result(self.handle, rid, m.data_ptr() if m.numel() else None,
                                                  d.data_ptr() if d.numel() else None, STIM_DEVICE, s.cuda_stream))

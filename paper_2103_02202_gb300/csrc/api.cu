@@ -447,7 +447,8 @@ int stim_info_get(const stim_circuit *c, stim_info *out) {
     const HostProgram &hp = c->hp;
     out->num_qubits = hp.num_qubits;
     out->num_measurements = hp.num_meas;
-    out->num_detectors = hp.num_det;
+    out->num_detectors = hp.num_det - hp.num_obs;
+    out->num_observables = hp.num_obs;
     out->num_gate_targets = hp.num_gate_targets;
     out->num_noise_targets = hp.num_noise_targets;
     out->num_instructions = hp.num_instr;

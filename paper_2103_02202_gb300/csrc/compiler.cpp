@@ -12,7 +12,8 @@
 //     order (the outcome-0 reference sample depends on that order);
 //   * REPEAT bodies are compiled once and wrapped in LOOP entries;
 //   * DETECTOR lookbacks rec[-k] are resolved to absolute measurement indices
-//     in a flattened CSR list;
+//     in a flattened CSR list, followed by one row per logical observable
+//     (all OBSERVABLE_INCLUDE(k) lookbacks of index k);
 //   * a rec[-k] target in a CX (as control) or CZ pair makes a classically
 //     controlled X or Z on the other target (OP_FFX, OP_FFZ), placed after
 //     every collapsing op emitted before it;
@@ -50,7 +51,7 @@ namespace {
 enum ParsedGate {
     PG_H, PG_S, PG_CX, PG_CZ, PG_M, PG_MR, PG_R, PG_XERR, PG_ZERR, PG_DEP1, PG_DEP2, PG_DET,
     PG_X, PG_Y, PG_Z, PG_SDAG, PG_SQX, PG_SQXD, PG_SQY, PG_SQYD, PG_YERR,
-    PG_MX, PG_MY, PG_MRX, PG_MRY, PG_RX, PG_RY
+    PG_MX, PG_MY, PG_MRX, PG_MRY, PG_RX, PG_RY, PG_OBS
 };
 
 // A measurement-record target rec[-k] in a CX/CZ pair: kRecTarget | k.
@@ -165,7 +166,7 @@ class Parser {
             {"DETECTOR", PG_DET}, {"X", PG_X}, {"Y", PG_Y}, {"Z", PG_Z}, {"S_DAG", PG_SDAG},
             {"SQRT_X", PG_SQX}, {"SQRT_X_DAG", PG_SQXD}, {"SQRT_Y", PG_SQY}, {"SQRT_Y_DAG", PG_SQYD},
             {"Y_ERROR", PG_YERR}, {"MX", PG_MX}, {"MY", PG_MY}, {"MRX", PG_MRX}, {"MRY", PG_MRY},
-            {"RX", PG_RX}, {"RY", PG_RY}};
+            {"RX", PG_RX}, {"RY", PG_RY}, {"OBSERVABLE_INCLUDE", PG_OBS}};
         auto it = kNames.find(name);
         if (name.empty() || it == kNames.end()) {
             size_t j = i;
@@ -199,6 +200,11 @@ class Parser {
             if (args.size() != 1) fail(lo, "noise channel takes exactly one probability");
             ins->p = args[0];
             if (!(ins->p >= 0.0 && ins->p <= 1.0)) fail(lo, "probability outside [0, 1]");
+        } else if (ins->gate == PG_OBS) {
+            if (args.size() != 1) fail(lo, "OBSERVABLE_INCLUDE takes one index");
+            ins->p = args[0];
+            if (!(ins->p >= 0.0 && ins->p < 65536.0) || ins->p != std::floor(ins->p))
+                fail(lo, "observable index is not an integer in [0, 65535]");
         } else if (ins->gate != PG_DET && !args.empty()) {
             fail(lo, "gate takes no arguments");
         }
@@ -210,7 +216,7 @@ class Parser {
             uint64_t v = 0;
             const bool rec_target = (ins->gate == PG_CX || ins->gate == PG_CZ) && hi - i >= 6 &&
                                     memcmp(ln + i, "rec[-", 5) == 0;
-            if (ins->gate == PG_DET || rec_target) {
+            if (ins->gate == PG_DET || ins->gate == PG_OBS || rec_target) {
                 if (hi - i < 6 || memcmp(ln + i, "rec[-", 5) != 0) fail(i, "expected a rec[-k] target");
                 i += 5;
                 if (i >= hi || !isdigit((unsigned char)ln[i])) fail(i, "expected a rec[-k] target");
@@ -295,6 +301,7 @@ bool records(int pg) { return pg == PG_M || pg == PG_MR || pg == PG_MX || pg == 
 
 struct Counts {
     uint64_t instr = 0, meas = 0, det = 0, det_entries = 0;
+    uint64_t obs = 0;                   // largest observable index + 1
     uint64_t gate_t = 0, noise_t = 0, ff_t = 0;
     uint64_t targets[OP_COUNT] = {0};
 };
@@ -314,6 +321,7 @@ void count_block(const Block &b, Counts *c, uint32_t *max_qubit, bool *any_qubit
             c->meas += mul(inner.meas);
             c->det += mul(inner.det);
             c->det_entries += mul(inner.det_entries);
+            c->obs = std::max(c->obs, inner.obs);
             c->gate_t += mul(inner.gate_t);
             c->noise_t += mul(inner.noise_t);
             c->ff_t += mul(inner.ff_t);
@@ -326,6 +334,11 @@ void count_block(const Block &b, Counts *c, uint32_t *max_qubit, bool *any_qubit
         if (in.gate == PG_DET) {
             c->det++;
             c->det_entries += in.targets.size();
+            continue;
+        }
+        if (in.gate == PG_OBS) {
+            c->det_entries += in.targets.size();
+            c->obs = std::max<uint64_t>(c->obs, (uint64_t)in.p + 1);
             continue;
         }
         for (uint32_t q : in.targets) {
@@ -392,7 +405,7 @@ class Emitter {
                 continue;
             }
             const Instr &in = nd.ins;
-            if (in.gate != PG_DET) {
+            if (in.gate != PG_DET && in.gate != PG_OBS) {
                 uint32_t op = opcode_of(in.gate);
                 uint32_t table = 0;
                 if (op_is_noise(op)) {
@@ -542,25 +555,27 @@ class Emitter {
 };
 
 // Flattened detector list: absolute measurement index of every rec[-k].
-void collect_detectors(const Block &b, uint64_t *meas, HostProgram *hp) {
+// Observable lookbacks go to obs[k] (appended after the detectors by the caller).
+void collect_detectors(const Block &b, uint64_t *meas, HostProgram *hp, std::vector<std::vector<uint32_t>> *obs) {
     for (const Node &nd : b.items) {
         if (nd.block) {
-            for (uint64_t r = 0; r < nd.block->reps; r++) collect_detectors(*nd.block, meas, hp);
+            for (uint64_t r = 0; r < nd.block->reps; r++) collect_detectors(*nd.block, meas, hp, obs);
             continue;
         }
         const Instr &in = nd.ins;
         if (records(in.gate)) {
             *meas += in.targets.size();
-        } else if (in.gate == PG_DET) {
+        } else if (in.gate == PG_DET || in.gate == PG_OBS) {
+            std::vector<uint32_t> &dst = in.gate == PG_DET ? hp->det_meas : (*obs)[(size_t)in.p];
             for (uint32_t k : in.targets) {
                 if (k > *meas) {
                     char buf[128];
                     snprintf(buf, sizeof buf, "line %d: rec[-%u] reaches before the first measurement", in.line, k);
                     throw ParseError{STIM_E_PARSE, buf};
                 }
-                hp->det_meas.push_back((uint32_t)(*meas - k));
+                dst.push_back((uint32_t)(*meas - k));
             }
-            hp->det_ptr.push_back(hp->det_meas.size());
+            if (in.gate == PG_DET) hp->det_ptr.push_back(hp->det_meas.size());
         }
     }
 }
@@ -794,7 +809,8 @@ int compile_circuit(const char *text, size_t len, HostProgram *out, std::string 
         HostProgram hp;
         hp.num_qubits = any ? maxq + 1 : 0;
         hp.num_meas = c.meas;
-        hp.num_det = c.det;
+        hp.num_det = c.det + c.obs;     // detection-event rows: detectors, then observables
+        hp.num_obs = c.obs;
         hp.num_gate_targets = c.gate_t;
         hp.num_noise_targets = c.noise_t;
         hp.num_instr = c.instr;
@@ -804,7 +820,12 @@ int compile_circuit(const char *text, size_t len, HostProgram *out, std::string 
         hp.det_ptr.push_back(0);
         hp.det_meas.reserve(c.det_entries);
         uint64_t m = 0;
-        collect_detectors(root, &m, &hp);
+        std::vector<std::vector<uint32_t>> obs((size_t)c.obs);
+        collect_detectors(root, &m, &hp, &obs);
+        for (const std::vector<uint32_t> &o : obs) {
+            hp.det_meas.insert(hp.det_meas.end(), o.begin(), o.end());
+            hp.det_ptr.push_back(hp.det_meas.size());
+        }
         Emitter em(&hp, hp.num_qubits ? hp.num_qubits : 1);
         hp.num_layers_exec = em.emit(root, 0, 0, 0);
         *out = std::move(hp);

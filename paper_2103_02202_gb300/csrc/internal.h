@@ -90,7 +90,9 @@ struct ProgEntry {
 
 struct HostProgram {
     uint32_t num_qubits = 0;
-    uint64_t num_meas = 0, num_det = 0;
+    uint64_t num_meas = 0;
+    uint64_t num_det = 0;                   // detection-event rows: DETECTORs, then num_obs observables
+    uint64_t num_obs = 0;                   // logical observables (largest OBSERVABLE_INCLUDE index + 1)
     uint64_t num_gate_targets = 0, num_noise_targets = 0, num_instr = 0;
     uint64_t num_layers_exec = 0;           // layer executions with loops unrolled
     uint64_t num_feedforward = 0;           // classically controlled X/Z targets (loops unrolled)
@@ -101,7 +103,7 @@ struct HostProgram {
     std::vector<DevOp> ops;
     std::vector<uint64_t> geo;              // [num_tables][64] geometric thresholds
     std::vector<double> table_p;
-    std::vector<uint64_t> det_ptr;          // D + 1 offsets into det_meas
+    std::vector<uint64_t> det_ptr;          // num_det + 1 offsets into det_meas
     std::vector<uint32_t> det_meas;         // absolute measurement indices
     // per-op-type target counts with loops unrolled (for bench accounting)
     uint64_t exec_targets[OP_COUNT] = {0};

@@ -146,12 +146,31 @@ def _surface_round(lay: SurfaceCodeLayout, p: float) -> list:
     return out
 
 
-def surface_code_memory(d: int, rounds: int, p: float) -> str:
+def logical_z_support(lay: SurfaceCodeLayout) -> list:
+    """Data qubits of a logical Z: a straight line of data qubits across the
+    patch whose overlap with every X plaquette is even (so it commutes with
+    all X stabilizers)."""
+    coords = {q: c for c, q in lay.index.items()}
+    xs = [set(lay.neighbors[a].values()) for a in lay.x_anc]
+    for axis in (0, 1):
+        lines = {}
+        for q in lay.data:
+            lines.setdefault(coords[q][axis], []).append(q)
+        for key in sorted(lines):
+            sup = set(lines[key])
+            if len(sup) == lay.d and all(len(sup & x) % 2 == 0 for x in xs):
+                return sorted(sup)
+    raise RuntimeError("no logical Z line found")
+
+
+def surface_code_memory(d: int, rounds: int, p: float, observable: bool = False) -> str:
     """Z-basis memory experiment on the distance-d rotated surface code.
 
     Round 1 carries detectors on Z-type measure qubits only; each later round
     compares every measure qubit with its previous result; the final data
-    measurement closes each Z plaquette against its last round.
+    measurement closes each Z plaquette against its last round. With
+    observable=True the final data measurements of a logical Z line are
+    logical observable 0 (OBSERVABLE_INCLUDE(0)).
     """
     if rounds < 1:
         raise ValueError("rounds must be >= 1")
@@ -180,6 +199,9 @@ def surface_code_memory(d: int, rounds: int, p: float) -> str:
         recs = [f"rec[-{nd - pos_data[q]}]" for q in lay.neighbors[a].values()]
         recs.append(f"rec[-{nd + na - pos_in_round[a]}]")
         lines.append("DETECTOR " + " ".join(recs))
+    if observable:
+        lines.append("OBSERVABLE_INCLUDE(0) " +
+                     " ".join(f"rec[-{nd - pos_data[q]}]" for q in logical_z_support(lay)))
     return "\n".join(lines) + "\n"
 
 

@@ -73,6 +73,8 @@ CIRCUITS = {
                       "DETECTOR rec[-1] rec[-2]\n"),
     "feedforward": ("H 0 1\nM 0 1\nCX rec[-1] 2 rec[-2] 3\nCZ 2 rec[-1]\nREPEAT 3 {\n"
                     "CZ rec[-2] 0\nMR 1 2\nDETECTOR rec[-1]\n}\nM 3\n"),
+    "observables": ("H 0\nM 0 1\nOBSERVABLE_INCLUDE(3) rec[-1]\nREPEAT 4 {\nMR 1\nDETECTOR rec[-1]\n"
+                    "OBSERVABLE_INCLUDE(1) rec[-1] rec[-2]\n}\n"),
 }
 
 
@@ -91,6 +93,7 @@ def test_counts_match_oracle(name):
     assert info["num_gate_targets"] == o.num_gate_targets
     assert info["num_noise_targets"] == o.num_noise_targets
     assert info["num_instructions"] == o.num_instructions
+    assert info["num_observables"] == o.num_observables
 
 
 def test_surface_code_layers_are_fused():
@@ -132,6 +135,13 @@ BAD = [
     ("REPEAT 2 {\nCX rec[-1] 0\nM 0\n}\n", sg.STIM_E_PARSE),
     ("M 0\nDEPOLARIZE2(0.1) rec[-1] 0\n", sg.STIM_E_PARSE),
     ("M 0\nH rec[-1]\n", sg.STIM_E_PARSE),
+    ("M 0\nOBSERVABLE_INCLUDE rec[-1]\n", sg.STIM_E_PARSE),
+    ("M 0\nOBSERVABLE_INCLUDE(0.5) rec[-1]\n", sg.STIM_E_PARSE),
+    ("M 0\nOBSERVABLE_INCLUDE(-1) rec[-1]\n", sg.STIM_E_PARSE),
+    ("M 0\nOBSERVABLE_INCLUDE(0) 0\n", sg.STIM_E_PARSE),
+    ("M 0\nOBSERVABLE_INCLUDE(0) rec[-2]\n", sg.STIM_E_PARSE),
+    ("M 0\nOBSERVABLE_INCLUDE(1, 2) rec[-1]\n", sg.STIM_E_PARSE),
+    ("M 0\nOBSERVABLE_INCLUDE(65536) rec[-1]\n", sg.STIM_E_PARSE),
 ]
 
 

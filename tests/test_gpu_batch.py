@@ -116,3 +116,19 @@ def test_batch_feedforward_detectors_only():
     got = np.unpackbits(dd.view(np.uint8).reshape(dd.shape[0], -1), axis=1, bitorder="little")[:, :shots[0]].T
     np.testing.assert_array_equal(got, od)
     b.close()
+
+
+def test_batch_with_observables_equals_plain():
+    texts = [W.surface_code_memory(3, 4, 0.01, observable=True),
+             "M 0\nOBSERVABLE_INCLUDE(1) rec[-1]\nX_ERROR(0.3) 1\nM 1\nOBSERVABLE_INCLUDE(0) rec[-1]\n"]
+    shots = [700, 1300]
+    cs = [sg.Circuit(t) for t in texts]
+    b = sg.Batch(cs, shots)
+    out = b.sample([1, 2])
+    torch.cuda.synchronize()
+    for c, S, sd, (m, d) in zip(cs, shots, [1, 2], out):
+        assert d.shape[0] == c.num_detector_rows
+        pm, pd = c.sample(S, sd)
+        torch.cuda.synchronize()
+        assert torch.equal(m, pm) and torch.equal(d, pd)
+    b.close()

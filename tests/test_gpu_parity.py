@@ -545,3 +545,34 @@ def test_teleportation_is_deterministic_on_the_gpu():
     mb, _ = gpu_sample(txt, 5000, 9)
     assert np.all(mb[:, 2] == 0)
     assert 0.45 < mb[:, 0].mean() < 0.55 and 0.45 < mb[:, 1].mean() < 0.55
+
+
+OBS_TEXTS = [
+    W.surface_code_memory(5, 5, 0.01, observable=True),
+    ("H 0 1\nM 0 1\nOBSERVABLE_INCLUDE(2) rec[-1]\nOBSERVABLE_INCLUDE(2) rec[-2]\n"
+     "REPEAT 7 {\nH 2\nX_ERROR(0.1) 2\nM 2\nOBSERVABLE_INCLUDE(1) rec[-1]\nDETECTOR rec[-1]\n}\n"
+     "CX rec[-1] 3\nM 3\nOBSERVABLE_INCLUDE(0) rec[-1]\n"),
+]
+
+
+@pytest.mark.parametrize("idx", range(len(OBS_TEXTS)))
+def test_observables_match_oracle(idx):
+    """Logical observables follow the detectors as rows D..D+K-1 of every
+    detection-event output: dense device, shot-major host and per-shot lists."""
+    text = OBS_TEXTS[idx]
+    shots = 1111
+    c = sg.Circuit(text)
+    assert c.num_observables >= 1
+    m, d = c.sample(shots, 21)
+    torch.cuda.synchronize()
+    R = c.num_detector_rows
+    db = words_to_bits(to_np(d), shots).T
+    _, dh = c.sample_host(shots, 21, meas=False, shot_major=True)
+    begin, dets = c.sample_detections(shots, 21)
+    c.close()
+    _, od = oracle.Circuit(text).sample(np.arange(shots), 21, threads=8)
+    assert od.shape[1] == R
+    np.testing.assert_array_equal(db, od)
+    np.testing.assert_array_equal(words_to_bits(dh, R), od)
+    got = [list(dets[begin[s]:begin[s + 1]]) for s in range(shots)]
+    assert got == [list(np.flatnonzero(row)) for row in od]

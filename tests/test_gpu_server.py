@@ -139,3 +139,18 @@ def test_feedforward_detectors_only_request():
     srv.release(rid)
     srv.close()
     c.close()
+
+
+def test_observable_rows_in_server_results():
+    c = sg.Circuit(W.surface_code_memory(3, 3, 0.01, observable=True))
+    srv = sg.Server(64 << 20, streams=2)
+    rid = srv.submit(c, 900, 5)
+    srv.wait(rid)
+    m, d = srv.fetch(c, rid, 900)
+    pm, pd = c.sample(900, 5)
+    torch.cuda.synchronize()
+    assert d.shape[0] == c.num_detectors + 1
+    assert torch.equal(m, pm) and torch.equal(d, pd)
+    srv.release(rid)
+    srv.close()
+    c.close()

@@ -717,3 +717,15 @@ def test_observable_parse_errors():
                 "M 0\nOBSERVABLE_INCLUDE(0) rec[-2]\n", "M 0\nOBSERVABLE_INCLUDE(1, 2) rec[-1]\n"):
         with pytest.raises(ValueError):
             oracle.Circuit(bad)
+
+
+@pytest.mark.parametrize("d", [3, 5])
+def test_surface_code_logical_observable_is_deterministic(d):
+    """The logical Z line chosen by the workload generator commutes with every
+    X stabilizer: without noise its parity never flips; with noise it does."""
+    c = oracle.Circuit(W.surface_code_memory(d, 3, 0.0, observable=True))
+    _, dets = c.sample(np.arange(512), seed=d, threads=8)
+    assert c.num_observables == 1 and not dets.any()
+    c = oracle.Circuit(W.surface_code_memory(d, 3, 0.02, observable=True))
+    _, dets = c.sample(np.arange(512), seed=d, threads=8)
+    assert dets[:, -1].any()
