@@ -40,7 +40,12 @@
  *     geometric sampling of gaps, made exact): t = round-half-even(p * 2^32),
  *     S_0 = 2^32, S_{k+1} = floor(S_k (2^32 - t) / 2^32), G[k] = 2^32 - S_{k+1};
  *   - DEPOLARIZE1 picks X, Y, Z uniformly; DEPOLARIZE2 one of the 15
- *     non-identity two-qubit Paulis uniformly.
+ *     non-identity two-qubit Paulis uniformly;
+ *   - PAULI_CHANNEL_1(px, py, pz) and PAULI_CHANNEL_2(p_IX, ..., p_ZZ) (the
+ *     15 pair Paulis in the order IX, IY, IZ, XI, ..., ZZ) hit with the total
+ *     probability p (gap sampling as above) and pick the Pauli of each hit
+ *     by a fresh draw against the cumulative thresholds
+ *     round-half-even(2^32 * partial sum / p).
  */
 #include <math.h>
 #include <pthread.h>
@@ -59,7 +64,8 @@ enum {
     /* wider gate set */
     OG_Y, OG_Z, OG_SDAG, OG_SQX, OG_SQXD, OG_SQY, OG_SQYD, OG_YERR,
     OG_MX, OG_MY, OG_MRX, OG_MRY, OG_RX, OG_RY,
-    OG_OBS              /* OBSERVABLE_INCLUDE(k) rec[-a] ... */
+    OG_OBS,             /* OBSERVABLE_INCLUDE(k) rec[-a] ... */
+    OG_PC1, OG_PC2      /* PAULI_CHANNEL_1(px, py, pz), PAULI_CHANNEL_2(p_IX, ..., p_ZZ) */
 };
 
 typedef struct {
@@ -68,6 +74,7 @@ typedef struct {
     uint32_t nt;
     uint32_t *t;        /* qubits, or absolute measurement indices (DETECTOR, OBSERVABLE_INCLUDE) */
     uint64_t G[64];     /* geometric table (noise ops only) */
+    uint64_t C[15];     /* Pauli channels: cumulative choice thresholds */
 } orc_op;
 
 typedef struct {
@@ -168,7 +175,17 @@ static int gap_of(const uint64_t G[64], uint32_t u) {
  * x0/z0 act on the first (or only) qubit, x1/z1 on the second. */
 typedef struct { uint64_t x0, z0, x1, z1; } noise_word;
 
-static noise_word noise_for_word(uint64_t seed, int gate, const uint64_t G[64],
+/* Pauli channels: 1 + the number of cumulative thresholds C[i] <= v, i.e.
+ * the index (1 X, 2 Y, 3 Z; or 4a + b for the pair Pauli (a, b)) of the
+ * probability interval that holds the draw v. */
+static uint32_t channel_pick(const uint64_t C[15], int m, uint32_t v) {
+    uint32_t c = 1;
+    for (int i = 0; i < m - 1; i++)
+        if ((uint64_t)v >= C[i]) c++;
+    return c;
+}
+
+static noise_word noise_for_word(uint64_t seed, int gate, const uint64_t G[64], const uint64_t *C,
                                  uint32_t instr, uint32_t slot, uint64_t word) {
     noise_word r = {0, 0, 0, 0};
     drawer d;
@@ -186,14 +203,15 @@ static noise_word noise_for_word(uint64_t seed, int gate, const uint64_t G[64],
         } else if (gate == OG_YERR) {
             r.x0 |= bit;
             r.z0 |= bit;
-        } else if (gate == OG_DEP1) {
+        } else if (gate == OG_DEP1 || gate == OG_PC1) {
             uint32_t v = drawer_next(&d);
-            uint32_t pa = 1 + (uint32_t)(((uint64_t)3 * v) >> 32);  /* 1 X, 2 Y, 3 Z */
+            uint32_t pa = gate == OG_DEP1 ? 1 + (uint32_t)(((uint64_t)3 * v) >> 32)   /* 1 X, 2 Y, 3 Z */
+                                          : channel_pick(C, 3, v);
             if (pa == 1 || pa == 2) r.x0 |= bit;
             if (pa == 2 || pa == 3) r.z0 |= bit;
-        } else { /* DEP2 */
+        } else { /* DEP2, PC2 */
             uint32_t v = drawer_next(&d);
-            uint32_t c = 1 + (uint32_t)(((uint64_t)15 * v) >> 32);
+            uint32_t c = gate == OG_DEP2 ? 1 + (uint32_t)(((uint64_t)15 * v) >> 32) : channel_pick(C, 15, v);
             uint32_t pa = c >> 2, pb = c & 3;                 /* 0 I, 1 X, 2 Y, 3 Z */
             if (pa == 1 || pa == 2) r.x0 |= bit;
             if (pa == 2 || pa == 3) r.z0 |= bit;
@@ -210,7 +228,7 @@ void orc_noise_word(uint64_t seed, int gate, double p, uint32_t instr, uint32_t 
     uint64_t G[64];
     orc_geo_table(p, G);
     noise_word r = {0, 0, 0, 0};
-    if (p > 0) r = noise_for_word(seed, gate, G, instr, slot, word);
+    if (p > 0) r = noise_for_word(seed, gate, G, NULL, instr, slot, word);
     out[0] = r.x0; out[1] = r.z0; out[2] = r.x1; out[3] = r.z1;
 }
 
@@ -224,6 +242,8 @@ struct node {
     /* leaf */
     int gate;
     double p;
+    double args[15];  /* every parenthesised argument (Pauli channels) */
+    int nargs;
     uint32_t nt;
     uint32_t *t;      /* qubits, or lookbacks k of rec[-k] */
     /* block */
@@ -287,6 +307,8 @@ static int gate_from_name(const char *w, size_t n) {
     if (IS("DEPOLARIZE2")) return OG_DEP2;
     if (IS("DETECTOR")) return OG_DET;
     if (IS("OBSERVABLE_INCLUDE")) return OG_OBS;
+    if (IS("PAULI_CHANNEL_1")) return OG_PC1;
+    if (IS("PAULI_CHANNEL_2")) return OG_PC2;
     if (IS("X")) return OG_X;
     if (IS("Y")) return OG_Y;
     if (IS("Z")) return OG_Z;
@@ -311,7 +333,9 @@ static int gate_from_name(const char *w, size_t n) {
  * after flattening. */
 #define REC_FLAG 0x80000000u
 
-static int is_noise(int g) { return g == OG_XERR || g == OG_ZERR || g == OG_DEP1 || g == OG_DEP2 || g == OG_YERR; }
+static int is_noise(int g) {
+    return g == OG_XERR || g == OG_ZERR || g == OG_DEP1 || g == OG_DEP2 || g == OG_YERR || g == OG_PC1 || g == OG_PC2;
+}
 static int is_1q_gate(int g) {
     return g == OG_H || g == OG_S || g == OG_X || g == OG_Y || g == OG_Z || g == OG_SDAG || g == OG_SQX ||
            g == OG_SQXD || g == OG_SQY || g == OG_SQYD;
@@ -327,7 +351,7 @@ static int is_collapse(int g) {
     return g == OG_M || g == OG_MR || g == OG_R || g == OG_MX || g == OG_MY || g == OG_MRX || g == OG_MRY ||
            g == OG_RX || g == OG_RY;
 }
-static int is_pair(int g) { return g == OG_CX || g == OG_CZ || g == OG_DEP2; }
+static int is_pair(int g) { return g == OG_CX || g == OG_CZ || g == OG_DEP2 || g == OG_PC2; }
 
 /* Parse one line [b, e) into node k. */
 static int parse_line(pstate *ps, const char *b, const char *e, node *k) {
@@ -352,6 +376,7 @@ static int parse_line(pstate *ps, const char *b, const char *e, node *k) {
             while (*endp == ' ' || *endp == '\t') endp++;
             if (endp == buf || *endp) return perr(ps, "bad argument");
             if (nargs == 0) k->p = v;
+            if (nargs < 15) k->args[nargs] = v;
             nargs++;
             p += m;
             if (p < e && *p == ',') { p++; continue; }
@@ -359,7 +384,19 @@ static int parse_line(pstate *ps, const char *b, const char *e, node *k) {
             return perr(ps, "unterminated argument list");
         }
     }
-    if (is_noise(g)) {
+    k->nargs = nargs;
+    if (g == OG_PC1 || g == OG_PC2) {
+        /* the channel's total probability is the left-to-right sum of its arguments */
+        int want = g == OG_PC1 ? 3 : 15;
+        if (nargs != want) return perr(ps, "Pauli channel takes %d probabilities", want);
+        double sum = 0;
+        for (int i = 0; i < want; i++) {
+            if (!(k->args[i] >= 0.0 && k->args[i] <= 1.0)) return perr(ps, "probability outside [0, 1]");
+            sum += k->args[i];
+        }
+        if (!(sum <= 1.0)) return perr(ps, "Pauli channel probabilities sum above 1");
+        k->p = sum;
+    } else if (is_noise(g)) {
         if (nargs != 1) return perr(ps, "noise channel takes one probability");
         if (!(k->p >= 0.0 && k->p <= 1.0)) return perr(ps, "probability outside [0, 1]");
     } else if (g == OG_OBS) {
@@ -461,6 +498,25 @@ static orc_op *push_op(orc_circuit *c) {
     return o;
 }
 
+/* Choice thresholds of a Pauli channel with probabilities q_1..q_m (m = 3 or
+ * 15) and total p: C[i] = round-half-even(2^32 (q_1 + ... + q_{i+1}) / p)
+ * for i < m - 1 (sums taken left to right in double precision), unused
+ * entries 2^32. A hit takes Pauli 1 + #{i : v >= C[i]} for a fresh draw v,
+ * so Pauli j has probability q_j / p up to 2^-32 rounding. */
+static void pauli_channel_thresholds(const node *k, uint64_t C[15]) {
+    const int m = k->gate == OG_PC1 ? 3 : 15;
+    double sum = 0;
+    for (int i = 0; i < 15; i++) C[i] = (uint64_t)1 << 32;
+    if (!(k->p > 0)) return;
+    for (int i = 0; i < m - 1; i++) {
+        sum += k->args[i];
+        long long t = llrint(ldexp(sum / k->p, 32));
+        if (t < 0) t = 0;
+        if (t > (1LL << 32)) t = 1LL << 32;
+        C[i] = (uint64_t)t;
+    }
+}
+
 static int flatten(pstate *ps, const node *blk, orc_circuit *c) {
     for (size_t i = 0; i < blk->nkids; i++) {
         const node *k = &blk->kids[i];
@@ -497,6 +553,7 @@ static int flatten(pstate *ps, const node *blk, orc_circuit *c) {
             if (is_noise(k->gate)) {
                 c->nnoise_targets += slots;
                 orc_geo_table(k->p, o->G);
+                if (k->gate == OG_PC1 || k->gate == OG_PC2) pauli_channel_thresholds(k, o->C);
             } else {
                 c->ngate_targets += slots;
             }
@@ -1094,12 +1151,12 @@ static void *frame_worker(void *arg) {
                 }
                 break;
             }
-            case OG_XERR: case OG_ZERR: case OG_YERR: case OG_DEP1: case OG_DEP2: {
+            case OG_XERR: case OG_ZERR: case OG_YERR: case OG_DEP1: case OG_DEP2: case OG_PC1: case OG_PC2: {
                 if (o->p <= 0) break;
-                int pair = o->gate == OG_DEP2;
+                int pair = is_pair(o->gate);
                 for (uint32_t j = 0; j < o->nt; j += pair ? 2 : 1) {
                     uint32_t slot = pair ? j / 2 : j;
-                    noise_word nwd = noise_for_word(jb->seed, o->gate, o->G, instr, slot, word);
+                    noise_word nwd = noise_for_word(jb->seed, o->gate, o->G, o->C, instr, slot, word);
                     uint32_t a = o->t[j];
                     x[a] ^= (uint8_t)((nwd.x0 >> b) & 1);
                     z[a] ^= (uint8_t)((nwd.z0 >> b) & 1);

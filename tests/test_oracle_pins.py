@@ -729,3 +729,72 @@ def test_surface_code_logical_observable_is_deterministic(d):
     c = oracle.Circuit(W.surface_code_memory(d, 3, 0.02, observable=True))
     _, dets = c.sample(np.arange(512), seed=d, threads=8)
     assert dets[:, -1].any()
+
+
+# ---------------------------------------------------------------------------
+# Pauli channels. Each channel qubit is half of a Bell pair with an ancilla; a
+# Bell measurement afterwards reads the Pauli that hit it: (XX flip, ZZ flip)
+# = (0, 1) X, (1, 1) Y, (1, 0) Z, so every Pauli's rate is observable.
+# ---------------------------------------------------------------------------
+_PAULI_OF = {(0, 0): 0, (0, 1): 1, (1, 1): 2, (1, 0): 3}      # I, X, Y, Z
+
+
+def _bell_probe(channel, nq):
+    qs = list(range(nq))
+    anc = [q + nq for q in qs]
+    pre = "".join(f"H {q}\nCX {q} {a}\n" for q, a in zip(qs, anc))
+    post = "".join(f"CX {q} {a}\nH {q}\nM {q} {a}\n" for q, a in zip(qs, anc))
+    return pre + channel + "\n" + post
+
+
+def _pauli_counts(text, nq, shots, seed):
+    c = oracle.Circuit(text)
+    ref = c.reference()[0]
+    assert not ref.any()            # the Bell measurements are deterministic without noise
+    meas, _ = c.sample(np.arange(shots), seed, threads=8)
+    idx = np.zeros(shots, np.int64)
+    for k in range(nq):
+        p = np.array([_PAULI_OF[(int(a), int(b))] for a, b in meas[:, 2 * k:2 * k + 2]])
+        idx = idx * 4 + p
+    return np.bincount(idx, minlength=4 ** nq)
+
+
+def test_pauli_channel_1_rates():
+    probs = [0.1, 0.2, 0.05]
+    shots = 60000
+    cnt = _pauli_counts(_bell_probe("PAULI_CHANNEL_1(0.1, 0.2, 0.05) 0", 1), 1, shots, 7)
+    want = np.array([1 - sum(probs)] + probs)
+    sd = np.sqrt(want * (1 - want) / shots)
+    assert np.all(np.abs(cnt / shots - want) < 5 * sd + 1e-12), (cnt / shots, want)
+
+
+def test_pauli_channel_2_rates():
+    probs = [0.01, 0.02, 0.03, 0.04, 0.005, 0.0, 0.015, 0.02, 0.01, 0.03, 0.0, 0.025, 0.02, 0.01, 0.05]
+    shots = 60000
+    args = ", ".join(map(str, probs))
+    cnt = _pauli_counts(_bell_probe(f"PAULI_CHANNEL_2({args}) 0 1", 2), 2, shots, 8)
+    want = np.array([1 - sum(probs)] + probs)        # index 4a + b, a on qubit 0
+    sd = np.sqrt(want * (1 - want) / shots)
+    assert np.all(np.abs(cnt / shots - want) < 5 * sd + 1e-12), (cnt / shots, want)
+    assert cnt[6] == 0 and cnt[11] == 0               # XY and YZ have probability 0
+
+
+def test_pauli_channel_special_cases():
+    # probability-one Y: every shot reads Y
+    cnt = _pauli_counts(_bell_probe("PAULI_CHANNEL_1(0, 1, 0) 0", 1), 1, 500, 9)
+    assert cnt[2] == 500
+    # a single non-zero pair Pauli: only ZX or nothing
+    cnt = _pauli_counts(_bell_probe("PAULI_CHANNEL_2(0,0,0,0,0,0,0,0,0,0,0,0,0.4,0,0) 0 1", 2), 2, 4000, 10)
+    assert cnt[0] + cnt[13] == 4000 and 0.35 < cnt[13] / 4000 < 0.45
+    # an all-zero channel never hits
+    c = oracle.Circuit("PAULI_CHANNEL_1(0, 0, 0) 0\nM 0\n")
+    assert not c.sample(np.arange(256), 4)[0].any()
+
+
+def test_pauli_channel_parse_errors():
+    for bad in ("PAULI_CHANNEL_1(0.1, 0.2) 0\n", "PAULI_CHANNEL_1(0.5, 0.4, 0.2) 0\n",
+                "PAULI_CHANNEL_1(-0.1, 0.2, 0.1) 0\n", "PAULI_CHANNEL_2(0.1) 0 1\n",
+                "PAULI_CHANNEL_2(" + ", ".join(["0.01"] * 15) + ") 0\n",
+                "PAULI_CHANNEL_2(" + ", ".join(["0.01"] * 15) + ") 1 1\n"):
+        with pytest.raises(ValueError):
+            oracle.Circuit(bad)
