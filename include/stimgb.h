@@ -90,7 +90,9 @@ typedef struct {
  * CX (alias CNOT), CZ; M, MR, R and their X- and Y-basis forms MX, MY, MRX,
  * MRY, RX, RY (random outcomes of the reference sample are the +1
  * eigenvalue); X_ERROR(p), Y_ERROR(p), Z_ERROR(p), DEPOLARIZE1(p),
- * DEPOLARIZE2(p); DETECTOR rec[-k]... (optional parenthesised coordinates on
+ * DEPOLARIZE2(p), PAULI_CHANNEL_1(px, py, pz), PAULI_CHANNEL_2(p_IX, p_IY,
+ * p_IZ, p_XI, ..., p_ZZ) (probabilities in [0, 1] summing to at most 1; the
+ * first letter acts on the first target of a pair); DETECTOR rec[-k]... (optional parenthesised coordinates on
  * DETECTOR are ignored), REPEAT N { ... }, '#' comments. Broadcast targets
  * run left to right (pairs for two-qubit gates). A pair of CX may name a
  * measurement record rec[-k] as its control, a pair of CZ on either side:

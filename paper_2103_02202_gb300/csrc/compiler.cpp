@@ -51,7 +51,7 @@ namespace {
 enum ParsedGate {
     PG_H, PG_S, PG_CX, PG_CZ, PG_M, PG_MR, PG_R, PG_XERR, PG_ZERR, PG_DEP1, PG_DEP2, PG_DET,
     PG_X, PG_Y, PG_Z, PG_SDAG, PG_SQX, PG_SQXD, PG_SQY, PG_SQYD, PG_YERR,
-    PG_MX, PG_MY, PG_MRX, PG_MRY, PG_RX, PG_RY, PG_OBS
+    PG_MX, PG_MY, PG_MRX, PG_MRY, PG_RX, PG_RY, PG_OBS, PG_PC1, PG_PC2
 };
 
 // A measurement-record target rec[-k] in a CX/CZ pair: kRecTarget | k.
@@ -59,7 +59,8 @@ constexpr uint32_t kRecTarget = 1u << 31;
 
 struct Instr {
     int gate = 0;
-    double p = 0;
+    double p = 0;                    // noise probability (Pauli channels: the sum of args)
+    std::vector<double> args;        // Pauli channels: the 3 or 15 probabilities
     std::vector<uint32_t> targets;   // qubits (kRecTarget | k for rec[-k] in CX/CZ), or lookbacks k for DETECTOR
     int line = 0;
 };
@@ -166,7 +167,8 @@ class Parser {
             {"DETECTOR", PG_DET}, {"X", PG_X}, {"Y", PG_Y}, {"Z", PG_Z}, {"S_DAG", PG_SDAG},
             {"SQRT_X", PG_SQX}, {"SQRT_X_DAG", PG_SQXD}, {"SQRT_Y", PG_SQY}, {"SQRT_Y_DAG", PG_SQYD},
             {"Y_ERROR", PG_YERR}, {"MX", PG_MX}, {"MY", PG_MY}, {"MRX", PG_MRX}, {"MRY", PG_MRY},
-            {"RX", PG_RX}, {"RY", PG_RY}, {"OBSERVABLE_INCLUDE", PG_OBS}};
+            {"RX", PG_RX}, {"RY", PG_RY}, {"OBSERVABLE_INCLUDE", PG_OBS},
+            {"PAULI_CHANNEL_1", PG_PC1}, {"PAULI_CHANNEL_2", PG_PC2}};
         auto it = kNames.find(name);
         if (name.empty() || it == kNames.end()) {
             size_t j = i;
@@ -196,7 +198,19 @@ class Parser {
             i = close + 1;
         }
         bool noise = (ins->gate >= PG_XERR && ins->gate <= PG_DEP2) || ins->gate == PG_YERR;
-        if (noise) {
+        if (ins->gate == PG_PC1 || ins->gate == PG_PC2) {
+            const size_t want = ins->gate == PG_PC1 ? 3 : 15;
+            if (args.size() != want)
+                fail(lo, ins->gate == PG_PC1 ? "PAULI_CHANNEL_1 takes 3 probabilities" : "PAULI_CHANNEL_2 takes 15 probabilities");
+            double total = 0;       // summed left to right
+            for (double v : args) {
+                if (!(v >= 0.0 && v <= 1.0)) fail(lo, "probability outside [0, 1]");
+                total += v;
+            }
+            if (!(total <= 1.0)) fail(lo, "Pauli channel probabilities sum above 1");
+            ins->p = total;
+            ins->args = args;
+        } else if (noise) {
             if (args.size() != 1) fail(lo, "noise channel takes exactly one probability");
             ins->p = args[0];
             if (!(ins->p >= 0.0 && ins->p <= 1.0)) fail(lo, "probability outside [0, 1]");
@@ -243,7 +257,7 @@ class Parser {
             if (i < hi && !space(ln[i])) fail(i, "bad target");
             ins->targets.push_back((uint32_t)v);
         }
-        bool pair = ins->gate == PG_CX || ins->gate == PG_CZ || ins->gate == PG_DEP2;
+        bool pair = ins->gate == PG_CX || ins->gate == PG_CZ || ins->gate == PG_DEP2 || ins->gate == PG_PC2;
         if (pair) {
             if (ins->targets.size() % 2) fail(lo, "two-qubit gate needs an even number of targets");
             for (size_t k = 0; k < ins->targets.size(); k += 2) {
@@ -270,7 +284,8 @@ uint32_t opcode_of(int pg) {
         case PG_XERR: return OP_XERR;
         case PG_ZERR: return OP_ZERR;
         case PG_YERR: return OP_YERR;
-        case PG_DEP1: return OP_DEP1;
+        case PG_DEP1: case PG_PC1: return OP_DEP1;      // one-qubit Pauli channel
+        case PG_PC2: return OP_DEP2;                     // two-qubit Pauli channel
         case PG_X: return OP_X;
         case PG_Y: return OP_Y;
         case PG_Z: return OP_Z;
@@ -413,7 +428,7 @@ class Emitter {
                         instr++;
                         continue;
                     }
-                    table = table_for(in.p);
+                    table = table_for(in);
                 }
                 bool pair = op_is_pair(op);
                 size_t step = pair ? 2 : 1;
@@ -473,7 +488,7 @@ class Emitter {
     uint32_t seg_ = 0;
     std::vector<LayerBuild> layers_;
     uint32_t last_collapse_ = 0;      // layer index + 1 of the last collapsing op
-    std::map<uint64_t, uint32_t> tables_;
+    std::map<std::vector<uint64_t>, uint32_t> tables_;
 
     void begin_segment() {
         seg_++;
@@ -539,17 +554,51 @@ class Emitter {
         return n;
     }
 
-    uint32_t table_for(double p) {
-        uint64_t bits;
-        memcpy(&bits, &p, sizeof bits);
-        auto it = tables_.find(bits);
+    // Noise table of an instruction (kNoiseTableWords words): the 64 gap
+    // thresholds of its total probability p, then 15 Pauli-choice thresholds
+    // T[0..14] and T[15]. A hit's Pauli index is 1 + #{i : v >= T[i]} for a
+    // fresh 32-bit draw v (1 X, 2 Y, 3 Z; pairs 4a + b):
+    //   DEPOLARIZE1: T[i] = ceil((i + 1) 2^32 / 3), i < 2, so the index is 1 + floor(3v / 2^32);
+    //   DEPOLARIZE2: T[i] = ceil((i + 1) 2^32 / 15), i < 14, i.e. 1 + floor(15v / 2^32);
+    //   PAULI_CHANNEL_1/2 with probabilities q: T[i] = round-half-even(2^32 (q_1 + ... + q_{i+1}) / p);
+    //   every other threshold 2^32. T[15] = 3 or 15 for the depolarizing
+    //   channels (the kernel multiplies instead of scanning), else 0.
+    uint32_t table_for(const Instr &in) {
+        const uint64_t kind = in.gate == PG_DEP1 ? 1 : in.gate == PG_DEP2 ? 2 : in.gate == PG_PC1 ? 3
+                            : in.gate == PG_PC2 ? 4 : 0;
+        auto bits_of = [](double v) {
+            uint64_t b;
+            memcpy(&b, &v, sizeof b);
+            return b;
+        };
+        std::vector<uint64_t> key{kind, bits_of(in.p)};
+        for (double v : in.args) key.push_back(bits_of(v));
+        auto it = tables_.find(key);
         if (it != tables_.end()) return it->second;
         uint32_t id = (uint32_t)hp_->table_p.size();
-        if (id >= 256) throw ParseError{STIM_E_UNSUPPORTED, "more than 256 distinct noise probabilities"};
-        hp_->table_p.push_back(p);
-        hp_->geo.resize(hp_->geo.size() + 64);
-        geometric_table(p, &hp_->geo[hp_->geo.size() - 64]);
-        tables_[bits] = id;
+        if (id >= 256) throw ParseError{STIM_E_UNSUPPORTED, "more than 256 distinct noise tables"};
+        hp_->table_p.push_back(in.p);
+        hp_->geo.resize(hp_->geo.size() + kNoiseTableWords);
+        uint64_t *G = &hp_->geo[hp_->geo.size() - kNoiseTableWords];
+        geometric_table(in.p, G);
+        uint64_t *T = G + 64;
+        for (int i = 0; i < 15; i++) T[i] = 1ull << 32;
+        T[15] = 0;
+        if (kind == 1 || kind == 2) {
+            const uint64_t m = kind == 1 ? 3 : 15;
+            for (uint64_t i = 0; i + 1 < m; i++) T[i] = (((i + 1) << 32) + m - 1) / m;
+            T[15] = m;
+        } else if ((kind == 3 || kind == 4) && in.p > 0) {
+            double partial = 0;
+            for (size_t i = 0; i + 1 < in.args.size(); i++) {
+                partial += in.args[i];
+                long long t = llrint(ldexp(partial / in.p, 32));
+                if (t < 0) t = 0;
+                if (t > (1LL << 32)) t = 1LL << 32;
+                T[i] = (uint64_t)t;
+            }
+        }
+        tables_[key] = id;
         return id;
     }
 };

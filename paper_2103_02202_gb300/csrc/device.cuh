@@ -91,14 +91,30 @@ __device__ __forceinline__ int geo_gap(const uint64_t *__restrict__ G, uint32_t 
     return k;
 }
 
-// General procedure: exact geometric gaps. With G the threshold table of p, a
-// draw u gives the gap min{k : u < G[k]} to the next error; the error process
-// stops at the first draw with u >= G[remaining - 1] (next error beyond bit
-// 63). The caller has drawn block 0 and found an error: its first word, draw
-// 0, satisfies blk0.x < G[63]. X_ERROR, Y_ERROR and Z_ERROR put X, Y or Z at
-// each error; DEPOLARIZE1 spends one more draw v per error on the Pauli
-// 1 + floor(3v / 2^32) (1 X, 2 Y, 3 Z); DEPOLARIZE2 on c = 1 + floor(15v / 2^32),
-// first-qubit Pauli c >> 2, second c & 3.
+// Pauli index of a channel hit: 1 + #{i : v >= T[i]} over the table's 15
+// non-decreasing choice thresholds. A uniform (depolarizing) channel over m
+// Paulis stores m in T[15] and thresholds ceil(i 2^32 / m), for which the
+// count equals floor(m v / 2^32): one multiply instead of the scan.
+__device__ __forceinline__ uint32_t pauli_choice(const uint64_t *__restrict__ T, uint32_t v) {
+    const uint64_t m = __ldg(T + 15);
+    if (m) return 1u + (uint32_t)((m * v) >> 32);
+    uint32_t c = 1;
+#pragma unroll 1
+    while (c < 16u && (uint64_t)v >= __ldg(T + c - 1)) c++;
+    return c;
+}
+
+// General procedure: exact geometric gaps. With G the table of the channel
+// (kNoiseTableWords words: gap thresholds G[0..63], then Pauli-choice
+// thresholds T[0..14] and T[15]), a draw u gives the gap min{k : u < G[k]} to the next error;
+// the error process stops at the first draw with u >= G[remaining - 1] (next
+// error beyond bit 63). The caller has drawn block 0 and found an error: its
+// first word, draw 0, satisfies blk0.x < G[63]. X_ERROR, Y_ERROR and Z_ERROR
+// put X, Y or Z at each error; the one-qubit channels (DEPOLARIZE1,
+// PAULI_CHANNEL_1) spend one more draw v per error on the Pauli c =
+// pauli_choice(v) (1 X, 2 Y, 3 Z), the two-qubit channels (DEPOLARIZE2,
+// PAULI_CHANNEL_2) on c with first-qubit Pauli c >> 2 and second c & 3. For
+// the depolarizing channels c = 1 + floor(3v / 2^32) and 1 + floor(15v / 2^32).
 template <class K>
 __device__ __forceinline__ void noise_masks_slow(uint32_t opc, const uint64_t *__restrict__ G, K key, uint32_t instr,
                                                  uint32_t slot, uint32_t word, uint4 blk0, uint64_t &xa,
@@ -121,13 +137,9 @@ __device__ __forceinline__ void noise_masks_slow(uint32_t opc, const uint64_t *_
             xa |= bit;
         } else if (opc == OP_ZERR) {
             za |= bit;
-        } else if (opc == OP_DEP1) {
-            const uint32_t pa = 1u + (uint32_t)((3ull * next()) >> 32);
-            if (pa <= 2u) xa |= bit;
-            if (pa >= 2u) za |= bit;
-        } else if (opc == OP_DEP2) {
-            const uint32_t c = 1u + (uint32_t)((15ull * next()) >> 32);
-            const uint32_t pa = c >> 2, pb = c & 3u;
+        } else if (opc == OP_DEP1 || opc == OP_DEP2) {
+            const uint32_t c = pauli_choice(G + 64, next());
+            const uint32_t pa = opc == OP_DEP1 ? c : c >> 2, pb = opc == OP_DEP1 ? 0u : c & 3u;
             if (pa == 1u || pa == 2u) xa |= bit;
             if (pa >= 2u) za |= bit;
             if (pb == 1u || pb == 2u) xb |= bit;

@@ -221,7 +221,7 @@ __device__ __forceinline__ void noise_op(const FrameArgs &a, const SmemKeys key,
     const uint32_t tbl = pair ? (op.slot >> 24) : op.b;
     const uint32_t slot = pair ? (op.slot & 0xFFFFFFu) : op.slot;
     const uint32_t instr = op.instr + instr_off;
-    const uint64_t *G = a.geo + 64u * tbl;
+    const uint64_t *G = a.geo + kNoiseTableWords * tbl;
     const uint64_t g63 = __ldg(G + 63);
     uint4 blk[V];
     uint32_t hits = 0;
@@ -437,7 +437,7 @@ __device__ __forceinline__ uint32_t noise_hits(const FrameArgs &a, const SmemKey
     const uint32_t tbl = pair ? (op.slot >> 24) : op.b;
     const uint32_t slot = pair ? (op.slot & 0xFFFFFFu) : op.slot;
     const uint32_t ti = kTagNoise | (op.instr + instr_off);
-    const uint64_t g63 = __ldg(a.geo + 64u * tbl + 63u);
+    const uint64_t g63 = __ldg(a.geo + kNoiseTableWords * tbl + 63u);
     uint32_t hits = 0;
 #pragma unroll
     for (int i = 0; i < V; i++) {
@@ -463,7 +463,7 @@ __device__ __forceinline__ void deferred_hit(const FrameArgs &a, const SmemKeys 
     const uint32_t gw = (uint32_t)a.word0 + tile0 + w;
     const uint4 blk0 = philox_sched(make_uint4(0u, slot, kTagNoise | instr, gw), key);
     uint64_t mxa, mza, mxb, mzb;
-    noise_masks_slow(opc, a.geo + 64u * tbl, key, instr, slot, gw, blk0, mxa, mza, mxb, mzb);
+    noise_masks_slow(opc, a.geo + kNoiseTableWords * tbl, key, instr, slot, gw, blk0, mxa, mza, mxb, mzb);
     xor_qubit_word<W, C, GMEM>(t, ov.x & 0x0FFFFFFFu, w, mxa, mza);
     if (pair) xor_qubit_word<W, C, GMEM>(t, ov.y, w, mxb, mzb);
 }

@@ -51,6 +51,11 @@ inline uint32_t frame_opcode(uint32_t o) {
     }
 }
 
+// Words of one noise table: 64 geometric gap thresholds, then 15 cumulative
+// Pauli-choice thresholds of the channel and the Pauli count of a uniform
+// (depolarizing) channel, 0 for other channels.
+constexpr uint32_t kNoiseTableWords = 80;
+
 constexpr uint32_t kQubitBits = 24;
 constexpr uint32_t kQubitMask = (1u << kQubitBits) - 1;
 constexpr uint32_t kMaxInstr = 1u << 28;       // instruction ordinals share a counter word with a 4-bit tag
@@ -101,7 +106,7 @@ struct HostProgram {
     uint32_t max_loop_depth = 0;
     std::vector<ProgEntry> prog;
     std::vector<DevOp> ops;
-    std::vector<uint64_t> geo;              // [num_tables][64] geometric thresholds
+    std::vector<uint64_t> geo;              // [num_tables][kNoiseTableWords] noise tables
     std::vector<double> table_p;
     std::vector<uint64_t> det_ptr;          // num_det + 1 offsets into det_meas
     std::vector<uint32_t> det_meas;         // absolute measurement indices

@@ -15,7 +15,7 @@ struct FrameArgs {
     const uint32_t *rank_tab;  // per merged layer: C + 1 segment offsets
     const FrameSeg *segs;      // FrameProgram::segs
     const DevOp *ops;          // FrameProgram::ops (qubit references)
-    const uint64_t *geo;       // [tables][64]
+    const uint64_t *geo;       // [tables][kNoiseTableWords] noise tables
     const uint64_t *ref;       // packed reference sample (ceil(M/64) words)
     uint32_t n;                // qubits
     uint32_t Q;                // qubits per CTA slice

@@ -75,6 +75,8 @@ CIRCUITS = {
                     "CZ rec[-2] 0\nMR 1 2\nDETECTOR rec[-1]\n}\nM 3\n"),
     "observables": ("H 0\nM 0 1\nOBSERVABLE_INCLUDE(3) rec[-1]\nREPEAT 4 {\nMR 1\nDETECTOR rec[-1]\n"
                     "OBSERVABLE_INCLUDE(1) rec[-1] rec[-2]\n}\n"),
+    "pauli_channels": ("PAULI_CHANNEL_1(0.1, 0, 0.2) 0 1 2\nPAULI_CHANNEL_2(" + ", ".join(["0.01"] * 15) +
+                       ") 0 1 2 3\nDEPOLARIZE1(0.1) 3\nM 0 1 2 3\n"),
 }
 
 
@@ -142,6 +144,12 @@ BAD = [
     ("M 0\nOBSERVABLE_INCLUDE(0) rec[-2]\n", sg.STIM_E_PARSE),
     ("M 0\nOBSERVABLE_INCLUDE(1, 2) rec[-1]\n", sg.STIM_E_PARSE),
     ("M 0\nOBSERVABLE_INCLUDE(65536) rec[-1]\n", sg.STIM_E_PARSE),
+    ("PAULI_CHANNEL_1(0.1, 0.2) 0\n", sg.STIM_E_PARSE),
+    ("PAULI_CHANNEL_1(0.5, 0.4, 0.2) 0\n", sg.STIM_E_PARSE),
+    ("PAULI_CHANNEL_1(-0.1, 0.2, 0.1) 0\n", sg.STIM_E_PARSE),
+    ("PAULI_CHANNEL_2(0.1) 0 1\n", sg.STIM_E_PARSE),
+    ("PAULI_CHANNEL_2(" + ", ".join(["0.01"] * 15) + ") 0\n", sg.STIM_E_PARSE),
+    ("PAULI_CHANNEL_2(" + ", ".join(["0.01"] * 15) + ") 1 1\n", sg.STIM_E_PARSE),
 ]
 
 

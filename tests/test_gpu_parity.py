@@ -576,3 +576,69 @@ def test_observables_match_oracle(idx):
     np.testing.assert_array_equal(words_to_bits(dh, R), od)
     got = [list(dets[begin[s]:begin[s + 1]]) for s in range(shots)]
     assert got == [list(np.flatnonzero(row)) for row in od]
+
+
+def _dyadic_probs(rng, m, total):
+    """m probabilities k_i / 2^j * total with integer k_i summing to 2^j (so
+    the sum is exactly `total`, a power of two), about half of them zero."""
+    den = 16 if m == 3 else 32
+    k = rng.integers(0, 4, m) * (rng.random(m) < 0.6)
+    k[int(rng.integers(m))] += den - int(k.sum()) if k.sum() < den else 0
+    while k.sum() > den:
+        k[int(np.argmax(k))] -= 1
+    return [float(v) / den * total for v in k]
+
+
+def _channel_circuit(rng, n, L):
+    """Random Clifford layers mixed with PAULI_CHANNEL_1/2 (random, sparse and
+    probability-one distributions) and the depolarizing channels."""
+    lines = ["H " + " ".join(map(str, range(n)))]
+    for _ in range(L):
+        kind = rng.random()
+        if kind < 0.3:
+            a, b = rng.choice(n, 2, replace=False)
+            lines.append(f"{str(rng.choice(['CX', 'CZ']))} {a} {b}")
+        elif kind < 0.45:
+            lines.append(f"{str(rng.choice(WIDE_1Q))} {int(rng.integers(n))}")
+        elif kind < 0.65:
+            q = _dyadic_probs(rng, 3, float(rng.choice([0.0625, 0.5, 1.0])))
+            tg = " ".join(map(str, rng.choice(n, int(rng.integers(1, n + 1)), replace=False)))
+            lines.append("PAULI_CHANNEL_1(" + ", ".join(repr(float(v)) for v in q) + f") {tg}")
+        elif kind < 0.8:
+            q = _dyadic_probs(rng, 15, float(rng.choice([0.03125, 0.5, 1.0])))
+            if rng.random() < 0.3:
+                q = [v * 0.3 for v in q]     # a total that is not a power of two
+            a, b = rng.choice(n, 2, replace=False)
+            lines.append("PAULI_CHANNEL_2(" + ", ".join(repr(float(v)) for v in q) + f") {a} {b}")
+        elif kind < 0.9:
+            p = float(rng.choice([0.01, 0.3]))
+            a, b = rng.choice(n, 2, replace=False)
+            lines.append(f"DEPOLARIZE2({p}) {a} {b}" if rng.random() < 0.5 else f"DEPOLARIZE1({p}) {a}")
+        else:
+            k = int(rng.integers(1, n + 1))
+            lines.append("MR " + " ".join(map(str, rng.choice(n, k, replace=False))))
+            lines.append("DETECTOR rec[-1]")
+    lines.append(str(rng.choice(["M", "MX", "MY"])) + " " + " ".join(map(str, range(n))))
+    return "\n".join(lines) + "\n"
+
+
+def test_pauli_channels_match_oracle():
+    rng = np.random.default_rng(2300)
+    for it in range(20):
+        n = int(rng.integers(2, 30))
+        text = _channel_circuit(rng, n, int(rng.integers(5, 60)))
+        shots = int(rng.integers(1, 900))
+        mb, db = gpu_sample(text, shots, 500 + it)
+        om, od = oracle.Circuit(text).sample(np.arange(shots), 500 + it, threads=8)
+        np.testing.assert_array_equal(mb, om, err_msg=text)
+        np.testing.assert_array_equal(db, od, err_msg=text)
+
+
+@pytest.mark.parametrize("hint", [(1, 64, 0, 2), (4, 128, 0, 1), (8, 256, 0, 1), (2, 128, 1, 1)])
+def test_pauli_channels_tile_shapes(hint):
+    rng = np.random.default_rng(2301)
+    text = _channel_circuit(rng, 24, 150)
+    mb, db = gpu_sample(text, 1000, 6, hint=hint)
+    om, od = oracle.Circuit(text).sample(np.arange(1000), 6, threads=8)
+    np.testing.assert_array_equal(mb, om)
+    np.testing.assert_array_equal(db, od)
