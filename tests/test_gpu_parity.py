@@ -642,3 +642,15 @@ def test_pauli_channels_tile_shapes(hint):
     om, od = oracle.Circuit(text).sample(np.arange(1000), 6, threads=8)
     np.testing.assert_array_equal(mb, om)
     np.testing.assert_array_equal(db, od)
+
+
+@pytest.mark.parametrize("hint", [(1, 64, 0, 2), (2, 64, 0, 2), (4, 128, 0, 4), (1, 64, 0, 8), (8, 256, 0, 2)])
+def test_cluster_deferred_hits_on_one_remote_word(hint):
+    """A chain owned by one CTA of a cluster ends in several likely noise ops on
+    a qubit of another CTA: their deferred hits reach the same remote word in
+    one flush and must all land (XOR-merged per address within the warp)."""
+    text = ("H 0 1 2 3\nCZ 2 0\nCZ 1 3\nX_ERROR(0.5) 0\nX_ERROR(0.5) 0\nY_ERROR(0.5) 0\n"
+            "DEPOLARIZE1(0.5) 0\nCX 0 1\nM 0 1 2 3\n") * 3
+    mb, _ = gpu_sample(text, 3000, 17, hint=hint)
+    om, _ = oracle.Circuit(text).sample(np.arange(3000), 17, threads=8)
+    np.testing.assert_array_equal(mb, om)
