@@ -771,6 +771,20 @@ class FrameBuilder {
                     uint32_t d = (uint32_t)c0.size();
                     while (d > 0 && op_is_noise(c0[d - 1].a >> 24)) d--;
                     sg.defer_from = d;
+                    // a chain whose deferred tail names one qubit twice can send
+                    // two hits to one frame word in one flush
+                    bool dup = false;
+                    for (size_t k = i; k < j && !dup; k++) {
+                        const auto &ops = chains_[by_rank[r][k]].ops;
+                        std::vector<uint32_t> qs;
+                        for (size_t o = d; o < ops.size(); o++) {
+                            qs.push_back(op_q0(ops[o]));
+                            if (op_q1(ops[o]) != op_q0(ops[o])) qs.push_back(op_q1(ops[o]));
+                        }
+                        std::sort(qs.begin(), qs.end());
+                        dup = std::adjacent_find(qs.begin(), qs.end()) != qs.end();
+                    }
+                    if (dup) sg.defer_from |= kSegTailRepeatsQubit;
                 }
                 for (size_t k = i; k < j; k++)
                     for (const DevOp &d : chains_[by_rank[r][k]].ops) {

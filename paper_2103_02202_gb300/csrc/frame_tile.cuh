@@ -483,7 +483,10 @@ __device__ __forceinline__ void deferred_hit(const FrameArgs &a, const SmemKeys 
 // XOR of v into the shared::cluster address ca (ca = 0: nothing), issued by a
 // whole warp. Lanes naming the same address are merged first (their values
 // XORed into the group's lowest lane), so one red instruction never carries
-// two lanes with the same cluster address: such duplicates lost updates.
+// two lanes with the same cluster address: such duplicates lost updates. Used
+// only for flushes that hold hits of a segment flagged kSegTailRepeatsQubit
+// (hits of distinct chains, and of tails naming each qubit once, never share
+// a word).
 __device__ __forceinline__ void warp_red_xor_cluster(uint32_t ca, uint64_t v, uint32_t lane) {
     const uint32_t key = v ? ca : 0u;
     const uint32_t same = __match_any_sync(0xFFFFFFFFu, key);
@@ -602,19 +605,26 @@ __device__ __forceinline__ bool run_tile(const FrameArgs &a, unsigned char *dyn,
                 // warp and resolved 32 at a time, one per lane.
                 const uint32_t first = segs[sb].y;
                 uint32_t qn = 0;
+                bool qdup = false;      // queued hits may share a frame word (warp-uniform)
                 auto flush = [&](uint32_t n) {
                     __syncwarp();
-                    if constexpr (C > 1 && !GMEM)
-                        deferred_hits_cluster<W, C>(a, key, t, lane, n, qsa, first, tile0, instr_off);
-                    else if (lane < n)
+                    if constexpr (C > 1 && !GMEM) {
+                        if (qdup)
+                            deferred_hits_cluster<W, C>(a, key, t, lane, n, qsa, first, tile0, instr_off);
+                        else if (lane < n)
+                            deferred_hit<W, C, GMEM>(a, key, t, lds32(qsa + 4u * lane), first, tile0, instr_off);
+                    } else if (lane < n) {
                         deferred_hit<W, C, GMEM>(a, key, t, lds32(qsa + 4u * lane), first, tile0, instr_off);
+                    }
+                    qdup = false;
                     __syncwarp();
                 };
                 uint32_t g = threadIdx.x, seg_start = 0;
                 for (uint32_t s = sb; s < se; s++) {
                     const uint4 sv = segs[s];
                     const uint32_t len = sv.x, items = sv.z * (W / V), span = (items + 31u) & ~31u;
-                    const uint32_t dfrom = sv.w;
+                    const uint32_t dfrom = sv.w & ~kSegTailRepeatsQubit;
+                    const bool seg_dup = (sv.w & kSegTailRepeatsQubit) != 0u;
                     bool have_next = false;      // nxt holds this item's first op
                     uint4 nxt = make_uint4(0u, 0u, 0u, 0u);
                     for (; g < seg_start + span; g += blockDim.x) {
@@ -652,6 +662,7 @@ __device__ __forceinline__ bool run_tile(const FrameArgs &a, unsigned char *dyn,
                                             sts32(qsa + 4u * (qn + __popc(m & ((1u << lane) - 1u))),
                                                   (oi << 3) | (wo + (uint32_t)i));
                                         qn += cnt;
+                                        qdup |= seg_dup;
                                     }
                                 }
                             }

@@ -145,8 +145,12 @@ struct FrameSeg {
     uint32_t len;         // ops per chain
     uint32_t op_begin;    // first op of the first chain
     uint32_t count;       // chains
-    uint32_t defer_from;  // chain steps >= defer_from are all noise ops
+    uint32_t defer_from;  // chain steps >= defer_from are all noise ops; bit 31: kSegTailRepeatsQubit
 };
+
+// FrameSeg::defer_from flag: some chain's deferred tail names a qubit twice, so
+// its hits may meet in one frame word within one flush of the hit queue.
+constexpr uint32_t kSegTailRepeatsQubit = 1u << 31;
 
 struct FrameProgram {
     int C = 1;
