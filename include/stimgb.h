@@ -152,6 +152,20 @@ int stim_reference_sample(stim_circuit *c, uint64_t *ref_bits, uint64_t *det_bit
                           int flags, void *stream);
 
 /*
+ * stim_reference_many -- computes (and keeps on their handles) the reference
+ * samples of k circuits at once, as stim_reference_sample would one by one.
+ * Circuits of at most 4096 qubits each run the single-CTA inverse tableau
+ * (Section 4) on internal streams, side by side on the GPU; larger ones follow
+ * one at a time with the multi-CTA tableau. Handles whose reference is
+ * already computed are skipped unless flags is STIM_RECOMPUTE; a handle may
+ * appear more than once. Blocks until every reference is done.
+ * Errors: STIM_E_INVALID_ARG (null array or element, unknown flags),
+ * STIM_E_OOM, STIM_E_CUDA, STIM_E_TIMEOUT; references finished before the
+ * error stay valid.
+ */
+int stim_reference_many(stim_circuit *const *circuits, size_t k, int flags);
+
+/*
  * stim_frame_sample -- bulk Pauli-frame sampling (Section 3): num_shots shots
  * with global shot indices 0..num_shots-1 under `seed`.
  *

@@ -30,7 +30,7 @@ __all__ = [
     "stim_frame_sample_detections",
     "STIM_MEAS_MAJOR", "STIM_SHOT_MAJOR", "STIM_DEVICE", "STIM_HOST", "STIM_RECOMPUTE",
     "StimError", "library", "library_path", "stim_compile", "stim_info_get", "stim_free",
-    "stim_last_error", "stim_reference_sample", "stim_frame_sample", "stim_frame_sample_ex",
+    "stim_last_error", "stim_reference_sample", "stim_reference_many", "stim_frame_sample", "stim_frame_sample_ex",
     "Circuit", "EXPORTED_SYMBOLS", "stim_frame_sample_noalloc", "stim_batch_create", "stim_batch_sample",
     "stim_batch_info", "stim_batch_free", "Batch", "Server", "STIM_OUT_MEAS", "STIM_OUT_DET", "stim_profile", "stim_profile_read", "KERNEL_NAMES",
 ]
@@ -118,6 +118,7 @@ _SIGNATURES = {
     "stim_free": (None, [_VP]),
     "stim_last_error": (ctypes.c_int, [ctypes.c_char_p, ctypes.c_size_t]),
     "stim_reference_sample": (ctypes.c_int, [_VP, _VP, _VP, ctypes.c_int, _VP]),
+    "stim_reference_many": (ctypes.c_int, [ctypes.POINTER(_VP), ctypes.c_size_t, ctypes.c_int]),
     "stim_frame_sample": (ctypes.c_int, [_VP, _U64, _U64, _VP, _VP, ctypes.c_int, _VP]),
     "stim_frame_sample_ex": (ctypes.c_int, [_VP, _U64, _U64, _U64, _VP, _VP, ctypes.c_int,
                                             ctypes.POINTER(StimTileHint), _VP]),
@@ -202,6 +203,12 @@ def stim_reference_sample(handle: int, ref_bits: int, det_bits: int = 0, flags: 
                           stream: int = 0) -> None:
     _check(library().stim_reference_sample(handle, ref_bits or None, det_bits or None, flags,
                                            stream or None))
+
+
+def stim_reference_many(handles, flags: int = 0) -> None:
+    """Reference samples of several circuits at once (small ones side by side)."""
+    arr = (_VP * max(len(handles), 1))(*[h for h in handles])
+    _check(library().stim_reference_many(arr, len(handles), flags))
 
 
 def stim_frame_sample(handle: int, num_shots: int, seed: int, meas_out: int = 0, det_out: int = 0,

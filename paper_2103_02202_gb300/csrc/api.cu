@@ -182,16 +182,26 @@ int ensure_device(stim_circuit *c) {
     return frame_program(c, 1, &fp1);     // the single-CTA program is always resident
 }
 
-int compute_reference(stim_circuit *c, cudaStream_t st) {
+// One reference-sample computation in flight: its stream and tableau scratch.
+struct RefJob {
+    cudaStream_t st = nullptr;
+    char *blob = nullptr;
+    bool launched = false;
+};
+
+// Launches the inverse-tableau kernel of c on st with at most max_blocks CTAs
+// (0: the library's choice; 1: the single-CTA variant, which keeps the tableau
+// in its L1 and needs no grid barrier). Scratch comes from the stream-ordered
+// allocator, so launches on several streams do not serialize on allocation.
+int reference_launch(stim_circuit *c, cudaStream_t st, uint32_t max_blocks, RefJob *job) {
     const HostProgram &hp = c->hp;
     const uint32_t n = hp.num_qubits;
+    job->st = st;
+    job->blob = nullptr;
+    job->launched = false;
     STIMGB_CK(cudaMemsetAsync(c->d_ref, 0, c->ref_words * 8, st), "memset");
     STIMGB_CK(cudaMemsetAsync(c->d_detflag, 0, c->ref_words * 8, st), "memset");
-    if (n == 0 || hp.num_meas == 0) {
-        STIMGB_CK(cudaStreamSynchronize(st), "sync");
-        c->ref_valid = true;
-        return STIM_OK;
-    }
+    if (n == 0 || hp.num_meas == 0) return STIM_OK;
     const uint32_t nw = (n + 63) / 64;
     const size_t col_words = (size_t)2 * n * nw;
     TabArgs a{};
@@ -203,14 +213,13 @@ int compute_reference(stim_circuit *c, cudaStream_t st) {
     a.ref = c->d_ref;
     a.detflag = c->d_detflag;
     a.status = c->d_status;
-    char *blob = nullptr;
     const size_t bytes_tx = col_words * 8, bytes_sign = (size_t)2 * n * 4, bytes_klist = (size_t)n * 4 + 64;
     const size_t bytes_kmask = (size_t)nw * 8 + 64, bytes_rnd = (size_t)std::max<uint32_t>(hp.max_layer_ops, 1) * 4 + 64;
     const size_t total = 2 * bytes_tx + 2 * bytes_sign + bytes_klist + bytes_kmask + bytes_rnd + 256 + 1024;
-    STIMGB_CK(cudaMalloc((void **)&blob, total), "alloc tableau");
+    STIMGB_CK(cudaMallocAsync((void **)&job->blob, total, st), "alloc tableau");
     size_t off = 0;
     auto take = [&](size_t b) {
-        char *p = blob + off;
+        char *p = job->blob + off;
         off += (b + 255) & ~(size_t)255;
         return p;
     };
@@ -222,8 +231,7 @@ int compute_reference(stim_circuit *c, cudaStream_t st) {
     a.kmask = (uint64_t *)take(bytes_kmask);
     a.rnd = (uint32_t *)take(bytes_rnd);
     a.ctl = (TabCtl *)take(sizeof(TabCtl));
-    int rc = STIM_OK;
-    cudaError_t e = cudaMemsetAsync(blob, 0, total, st);
+    cudaError_t e = cudaMemsetAsync(job->blob, 0, total, st);
     if (e == cudaSuccess) e = cudaMemsetAsync(c->d_status, 0, sizeof(int), st);
     if (e == cudaSuccess) e = launch_tableau_init(a, st);
     if (e == cudaSuccess) {
@@ -232,19 +240,98 @@ int compute_reference(stim_circuit *c, cudaStream_t st) {
         // ~1024 column words per CTA (measured best for random circuits; d=100 uses all SMs either way)
         uint64_t want = (col_words + 1023) / 1024;
         if (want < 1) want = 1;
+        if (max_blocks && want > max_blocks) want = max_blocks;
         uint32_t blocks = (uint32_t)std::min<uint64_t>(want, (uint64_t)maxb);
         ProfScope ps(STIM_KERNEL_TABLEAU, st);
         e = launch_tableau(a, blocks, threads, st);
     }
-    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+    if (e != cudaSuccess) {
+        cudaFreeAsync(job->blob, st);
+        job->blob = nullptr;
+        return cuda_fail(e, "reference sample");
+    }
+    job->launched = true;
+    return STIM_OK;
+}
+
+// Waits for a launched job, checks the kernel's status word, frees the scratch
+// and marks the reference valid.
+int reference_finish(stim_circuit *c, RefJob *job) {
     int status = 0;
-    if (e == cudaSuccess) e = cudaMemcpy(&status, c->d_status, sizeof(int), cudaMemcpyDeviceToHost);
-    cudaFree(blob);
+    cudaError_t e = cudaSuccess;
+    if (job->launched) e = cudaMemcpyAsync(&status, c->d_status, sizeof(int), cudaMemcpyDeviceToHost, job->st);
+    if (job->blob) {
+        const cudaError_t f = cudaFreeAsync(job->blob, job->st);
+        if (e == cudaSuccess) e = f;
+        job->blob = nullptr;
+    }
+    const cudaError_t s = cudaStreamSynchronize(job->st);
+    if (e == cudaSuccess) e = s;
     if (e != cudaSuccess) return cuda_fail(e, "reference sample");
     if (status == DEV_TIMEOUT) return fail(STIM_E_TIMEOUT, "tableau grid barrier timed out");
     if (status != 0) return fail(STIM_E_CUDA, "tableau kernel reported a malformed program");
     c->ref_valid = true;
-    return rc;
+    return STIM_OK;
+}
+
+int compute_reference(stim_circuit *c, cudaStream_t st) {
+    RefJob job;
+    const int r = reference_launch(c, st, 0, &job);
+    if (r != STIM_OK) return r;
+    return reference_finish(c, &job);
+}
+
+// Circuits of at most this many qubits take the single-CTA tableau when many
+// references are computed together (they then run side by side, one SM each).
+constexpr uint32_t kConcurrentRefMaxQubits = 4096;
+constexpr size_t kConcurrentRefStreams = 64;
+
+int references_many(stim_circuit *const *cs, size_t k, bool recompute) {
+    std::vector<stim_circuit *> small, large;
+    for (size_t i = 0; i < k; i++) {
+        stim_circuit *c = cs[i];
+        if (!c) return fail(STIM_E_INVALID_ARG, "stim_reference_many: null circuit");
+        const int r = ensure_device(c);
+        if (r != STIM_OK) return r;
+        if (c->ref_valid && !recompute) continue;
+        if (std::find(small.begin(), small.end(), c) != small.end() ||
+            std::find(large.begin(), large.end(), c) != large.end())
+            continue;
+        (c->hp.num_qubits <= kConcurrentRefMaxQubits ? small : large).push_back(c);
+    }
+    int rc = STIM_OK;
+    if (!small.empty()) {
+        std::vector<cudaStream_t> streams(std::min(small.size(), kConcurrentRefStreams), nullptr);
+        for (cudaStream_t &st : streams)
+            if (cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking) != cudaSuccess) {
+                st = nullptr;
+                rc = fail(STIM_E_CUDA, "stim_reference_many: stream creation failed");
+            }
+        std::vector<RefJob> jobs(small.size());
+        std::vector<bool> ok(small.size(), false);
+        if (rc == STIM_OK)
+            for (size_t i = 0; i < small.size(); i++) {
+                const int r = reference_launch(small[i], streams[i % streams.size()], 1, &jobs[i]);
+                if (r != STIM_OK) {
+                    rc = r;
+                    break;
+                }
+                ok[i] = true;
+            }
+        for (size_t i = 0; i < small.size(); i++) {
+            if (!ok[i]) continue;
+            const int r = reference_finish(small[i], &jobs[i]);
+            if (rc == STIM_OK) rc = r;
+        }
+        for (cudaStream_t st : streams)
+            if (st) cudaStreamDestroy(st);
+        if (rc != STIM_OK) return rc;
+    }
+    for (stim_circuit *c : large) {
+        const int r = compute_reference(c, nullptr);
+        if (r != STIM_OK) return r;
+    }
+    return STIM_OK;
 }
 
 // Tile shape: the smallest cluster whose qubit slice fits shared memory, then
@@ -405,6 +492,8 @@ int stimgb_sample_into(stim_circuit *c, uint64_t num_shots, uint64_t seed, uint6
     return launch_sampling(c, num_shots, seed, shot_offset, tc, rec, det, gframe, st);
 }
 
+int stimgb_ensure_references(stim_circuit *const *cs, size_t k) { return references_many(cs, k, false); }
+
 int stimgb_ensure_reference(stim_circuit *c, cudaStream_t st) {
     int r = ensure_device(c);
     if (r != STIM_OK) return r;
@@ -508,6 +597,12 @@ int stim_reference_sample(stim_circuit *c, uint64_t *ref_bits, uint64_t *det_bit
     if (det_bits && words) STIMGB_CK(cudaMemcpyAsync(det_bits, c->d_detflag, words * 8, kind, st), "copy flags");
     if (flags & STIM_HOST) STIMGB_CK(cudaStreamSynchronize(st), "sync");
     return STIM_OK;
+}
+
+int stim_reference_many(stim_circuit *const *circuits, size_t k, int flags) {
+    if (!circuits && k) return fail(STIM_E_INVALID_ARG, "stim_reference_many: null array");
+    if (!valid_flags(flags, STIM_RECOMPUTE)) return fail(STIM_E_INVALID_ARG, "stim_reference_many: unknown flags");
+    return references_many(circuits, k, (flags & STIM_RECOMPUTE) != 0);
 }
 
 int stim_frame_sample_ex(stim_circuit *c, uint64_t num_shots, uint64_t seed, uint64_t shot_offset,

@@ -498,7 +498,11 @@ int stim_batch_create(stim_circuit *const *circuits, const uint64_t *num_shots, 
     for (size_t i = 0; i < k && r == STIM_OK; i++) {
         if (!circuits[i]) r = bfail(STIM_E_INVALID_ARG, "stim_batch_create: null circuit");
         else if ((num_shots[i] + 63) / 64 > (1ull << 31)) r = bfail(STIM_E_UNSUPPORTED, "stim_batch_create: too many shots");
-        else r = stimgb_ensure_reference(circuits[i], st);
+    }
+    // reference samples of all circuits, the small ones side by side
+    if (r == STIM_OK) r = stimgb_ensure_references(circuits, k);
+    for (size_t i = 0; i < k && r == STIM_OK; i++) {
+        r = stimgb_ensure_reference(circuits[i], st);
         if (r == STIM_OK) {
             maxn = std::max(maxn, circuits[i]->hp.num_qubits);
             ops += circuits[i]->hp.num_gate_targets + circuits[i]->hp.num_noise_targets;

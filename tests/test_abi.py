@@ -178,8 +178,11 @@ def test_invalid_arguments_without_gpu():
     lib = sg.library()
     assert lib.stim_reference_sample(None, None, None, 0, None) == sg.STIM_E_INVALID_ARG
     assert lib.stim_frame_sample(None, 10, 0, None, None, 0, None) == sg.STIM_E_INVALID_ARG
+    assert lib.stim_reference_many(None, 2, 0) == sg.STIM_E_INVALID_ARG
     h = sg.stim_compile("H 0\nM 0\n")
     try:
+        arr = (ctypes.c_void_p * 1)(h)
+        assert lib.stim_reference_many(arr, 1, 0x40) == sg.STIM_E_INVALID_ARG     # unknown flag
         rc = lib.stim_frame_sample_ex(h, 10, 0, 3, None, None, 0, None, None)
         assert rc == sg.STIM_E_INVALID_ARG      # shot_offset not a multiple of 64
         rc = lib.stim_frame_sample(h, 10, 0, None, None, 0x40, None)

@@ -654,3 +654,36 @@ def test_cluster_deferred_hits_on_one_remote_word(hint):
     mb, _ = gpu_sample(text, 3000, 17, hint=hint)
     om, _ = oracle.Circuit(text).sample(np.arange(3000), 17, threads=8)
     np.testing.assert_array_equal(mb, om)
+
+
+def test_reference_many_matches_oracle_and_one_by_one():
+    """stim_reference_many (single-CTA tableaus side by side for small
+    circuits, the multi-CTA path above 4096 qubits) gives the references the
+    oracle gives, and the ones the one-at-a-time path gives."""
+    rng = np.random.default_rng(2400)
+    texts = [W.random_clifford(int(n), int(dp), int(sd)) for n, dp, sd in
+             zip(rng.integers(20, 300, 10), rng.integers(10, 80, 10), rng.integers(0, 1000, 10))]
+    texts += [W.surface_code_memory(d, 3, 0.001) for d in (3, 5, 9)]
+    texts += [_wide_circuit(rng, 12, 40), _wide_circuit(rng, 25, 50, feedforward=True)]
+    texts.append(texts[0])
+    cs = [sg.Circuit(t) for t in texts]
+    sg.stim_reference_many([c.handle for c in cs] + [cs[1].handle])      # a repeated handle is fine
+    got = []
+    for c in cs:
+        r, d = c.reference()            # the cached sample
+        torch.cuda.synchronize()
+        got.append((words_to_bits(to_np(r)[None, :], c.num_measurements)[0],
+                    words_to_bits(to_np(d)[None, :], c.num_measurements)[0]))
+    for t, (r, d) in zip(texts, got):
+        orf, odf = oracle.Circuit(t).reference()
+        np.testing.assert_array_equal(r, orf, err_msg=t[:200])
+        np.testing.assert_array_equal(d, odf, err_msg=t[:200])
+    # recompute one by one (library's block count) and compare, plus a large circuit
+    big = sg.Circuit(W.surface_code_memory(47, 2, 0.001))     # 4417 qubits: multi-CTA path
+    sg.stim_reference_many([big.handle, cs[2].handle], sg.STIM_RECOMPUTE)
+    rb, db = big.reference()
+    rb2, db2 = big.reference(recompute=True)
+    torch.cuda.synchronize()
+    assert torch.equal(rb, rb2) and torch.equal(db, db2)
+    for c in cs + [big]:
+        c.close()
