@@ -485,6 +485,16 @@ def main():
     ref_dev, _ = circ.reference(recompute=True)
     torch.cuda.synchronize()
     ttfs = time.perf_counter() - t0
+    # the same experiment at another noise strength: compile, then the
+    # reference sample comes from the skeleton-keyed cache
+    ttfs_sweep = None
+    if "p" in wl:
+        t0 = time.perf_counter()
+        swept = sg.Circuit(circuit_text(dict(wl, p=wl["p"] * 2)))
+        swept.reference()
+        torch.cuda.synchronize()
+        ttfs_sweep = time.perf_counter() - t0
+        swept.close()
 
     det = torch.empty((D, nwords), dtype=torch.int64, device="cuda")
 
@@ -671,6 +681,7 @@ def main():
         "compile_s": compile_s,
         "time_to_first_sample_s": ttfs,
         "time_to_first_sample_cold_s": ttfs_cold,
+        "time_to_first_sample_noise_sweep_s": ttfs_sweep,
         "kernels": {k: {"launches": v[0], "avg_ms": v[1] / max(v[0], 1)} for k, v in prof.items() if v[0]},
         "roofline": {
             "bound": "hbm", "achieved": achieved, "peak": hbm_peak, "unit": "GB/s",

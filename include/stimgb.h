@@ -73,6 +73,9 @@ typedef struct {
     uint64_t num_layers;         /* fused layers executed per shot (loops unrolled) */
     uint64_t num_program_layers; /* fused layers stored (loop bodies once) */
     uint64_t num_observables;    /* K: largest OBSERVABLE_INCLUDE index + 1 (0 without any) */
+    uint64_t reference_key;      /* hash of the noiseless skeleton: circuits that differ only in
+                                    noise channels, DETECTORs and OBSERVABLE_INCLUDEs share it
+                                    (and their reference sample) */
 } stim_info;
 
 /* Tile choice for the frame kernel; zero fields mean "let the library pick". */
@@ -164,6 +167,26 @@ int stim_reference_sample(stim_circuit *c, uint64_t *ref_bits, uint64_t *det_bit
  * error stay valid.
  */
 int stim_reference_many(stim_circuit *const *circuits, size_t k, int flags);
+
+/*
+ * Reference-sample cache. Reference samples are kept process-wide, keyed by
+ * the circuit's noiseless skeleton (its gates, collapsing and classically
+ * controlled operations with their targets and REPEAT structure, in source
+ * order; noise channels, DETECTORs and OBSERVABLE_INCLUDEs do not change the
+ * reference sample): a circuit compiled after another one with the same
+ * skeleton -- the same experiment at another noise strength -- copies the
+ * cached sample instead of running the tableau, reusing work across slight
+ * variations of a circuit as the paper's conclusion (Section 7) suggests.
+ * STIM_RECOMPUTE bypasses it. Entries are compared in full, not by hash.
+ *
+ * stim_reference_cache_set: byte budget (default 256 MiB); least recently
+ *   used entries are dropped to fit; 0 turns the cache off and empties it.
+ * stim_reference_cache_stats: lookups that hit and missed, entries and bytes
+ *   held; any pointer may be NULL.
+ * Both are thread-safe and need no GPU.
+ */
+int stim_reference_cache_set(size_t budget_bytes);
+int stim_reference_cache_stats(uint64_t *hits, uint64_t *misses, uint64_t *entries, uint64_t *bytes);
 
 /*
  * stim_frame_sample -- bulk Pauli-frame sampling (Section 3): num_shots shots

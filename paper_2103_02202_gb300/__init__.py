@@ -30,7 +30,8 @@ __all__ = [
     "stim_frame_sample_detections",
     "STIM_MEAS_MAJOR", "STIM_SHOT_MAJOR", "STIM_DEVICE", "STIM_HOST", "STIM_RECOMPUTE",
     "StimError", "library", "library_path", "stim_compile", "stim_info_get", "stim_free",
-    "stim_last_error", "stim_reference_sample", "stim_reference_many", "stim_frame_sample", "stim_frame_sample_ex",
+    "stim_last_error", "stim_reference_sample", "stim_reference_many", "stim_reference_cache_set",
+    "stim_reference_cache_stats", "stim_frame_sample", "stim_frame_sample_ex",
     "Circuit", "EXPORTED_SYMBOLS", "stim_frame_sample_noalloc", "stim_batch_create", "stim_batch_sample",
     "stim_batch_info", "stim_batch_free", "Batch", "Server", "STIM_OUT_MEAS", "STIM_OUT_DET", "stim_profile", "stim_profile_read", "KERNEL_NAMES",
 ]
@@ -69,7 +70,7 @@ class StimInfo(ctypes.Structure):
                 ("num_detectors", ctypes.c_uint64), ("num_gate_targets", ctypes.c_uint64),
                 ("num_noise_targets", ctypes.c_uint64), ("num_instructions", ctypes.c_uint64),
                 ("num_layers", ctypes.c_uint64), ("num_program_layers", ctypes.c_uint64),
-                ("num_observables", ctypes.c_uint64)]
+                ("num_observables", ctypes.c_uint64), ("reference_key", ctypes.c_uint64)]
 
 
 class StimTileHint(ctypes.Structure):
@@ -119,6 +120,9 @@ _SIGNATURES = {
     "stim_last_error": (ctypes.c_int, [ctypes.c_char_p, ctypes.c_size_t]),
     "stim_reference_sample": (ctypes.c_int, [_VP, _VP, _VP, ctypes.c_int, _VP]),
     "stim_reference_many": (ctypes.c_int, [ctypes.POINTER(_VP), ctypes.c_size_t, ctypes.c_int]),
+    "stim_reference_cache_set": (ctypes.c_int, [ctypes.c_size_t]),
+    "stim_reference_cache_stats": (ctypes.c_int, [ctypes.POINTER(_U64), ctypes.POINTER(_U64),
+                                                  ctypes.POINTER(_U64), ctypes.POINTER(_U64)]),
     "stim_frame_sample": (ctypes.c_int, [_VP, _U64, _U64, _VP, _VP, ctypes.c_int, _VP]),
     "stim_frame_sample_ex": (ctypes.c_int, [_VP, _U64, _U64, _U64, _VP, _VP, ctypes.c_int,
                                             ctypes.POINTER(StimTileHint), _VP]),
@@ -209,6 +213,16 @@ def stim_reference_many(handles, flags: int = 0) -> None:
     """Reference samples of several circuits at once (small ones side by side)."""
     arr = (_VP * max(len(handles), 1))(*[h for h in handles])
     _check(library().stim_reference_many(arr, len(handles), flags))
+
+
+def stim_reference_cache_set(budget_bytes: int) -> None:
+    _check(library().stim_reference_cache_set(int(budget_bytes)))
+
+
+def stim_reference_cache_stats() -> dict:
+    v = [_U64() for _ in range(4)]
+    _check(library().stim_reference_cache_stats(*[ctypes.byref(x) for x in v]))
+    return dict(zip(("hits", "misses", "entries", "bytes"), (int(x.value) for x in v)))
 
 
 def stim_frame_sample(handle: int, num_shots: int, seed: int, meas_out: int = 0, det_out: int = 0,

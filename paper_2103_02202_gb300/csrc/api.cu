@@ -2,6 +2,7 @@
 #include <cuda_runtime.h>
 
 #include <algorithm>
+#include <map>
 #include <cstdio>
 #include <cstring>
 #include <mutex>
@@ -182,23 +183,103 @@ int ensure_device(stim_circuit *c) {
     return frame_program(c, 1, &fp1);     // the single-CTA program is always resident
 }
 
-// One reference-sample computation in flight: its stream and tableau scratch.
+// Reference samples by noiseless skeleton, process-wide: a circuit that
+// differs from an earlier one only in its noise channels, detectors or
+// observables (a sweep of noise strengths, say) takes the earlier reference
+// sample instead of running the tableau again -- the reuse of work across
+// slight variations of a circuit that the paper's conclusion (Section 7)
+// suggests. Least recently used entries leave first when the byte budget is
+// exceeded; a budget of 0 turns the cache off.
+struct RefCache {
+    struct Entry {
+        std::vector<uint32_t> skeleton;
+        std::vector<uint64_t> ref, detflag;
+        uint64_t last_use = 0;
+        size_t bytes() const { return skeleton.size() * 4 + (ref.size() + detflag.size()) * 8 + 64; }
+    };
+    std::mutex mu;
+    std::multimap<uint64_t, Entry> map;     // skeleton hash -> entries
+    size_t bytes = 0, cap = (size_t)256 << 20;
+    uint64_t clock = 0, hits = 0, misses = 0;
+
+    void evict_to(size_t limit) {          // lock held
+        while (bytes > limit && !map.empty()) {
+            auto old = map.begin();
+            for (auto it = map.begin(); it != map.end(); ++it)
+                if (it->second.last_use < old->second.last_use) old = it;
+            bytes -= old->second.bytes();
+            map.erase(old);
+        }
+    }
+    bool lookup(const HostProgram &hp, size_t words, std::vector<uint64_t> *ref, std::vector<uint64_t> *det) {
+        std::lock_guard<std::mutex> g(mu);
+        if (cap == 0) return false;
+        auto range = map.equal_range(hp.skeleton_hash);
+        for (auto it = range.first; it != range.second; ++it)
+            if (it->second.ref.size() == words && it->second.skeleton == hp.skeleton) {
+                it->second.last_use = ++clock;
+                *ref = it->second.ref;
+                *det = it->second.detflag;
+                hits++;
+                return true;
+            }
+        misses++;
+        return false;
+    }
+    void insert(const HostProgram &hp, std::vector<uint64_t> ref, std::vector<uint64_t> det) {
+        std::lock_guard<std::mutex> g(mu);
+        if (cap == 0) return;
+        auto range = map.equal_range(hp.skeleton_hash);
+        for (auto it = range.first; it != range.second; ++it)
+            if (it->second.skeleton == hp.skeleton) return;
+        Entry e;
+        e.skeleton = hp.skeleton;
+        e.ref = std::move(ref);
+        e.detflag = std::move(det);
+        e.last_use = ++clock;
+        if (e.bytes() > cap) return;
+        bytes += e.bytes();
+        map.emplace(hp.skeleton_hash, std::move(e));
+        evict_to(cap);
+    }
+};
+
+RefCache &ref_cache() {
+    static RefCache c;
+    return c;
+}
+
+// One reference-sample computation in flight: its stream and tableau scratch
+// (or the cached sample being copied in).
 struct RefJob {
     cudaStream_t st = nullptr;
     char *blob = nullptr;
     bool launched = false;
+    bool from_cache = false;
+    bool to_cache = false;
+    std::vector<uint64_t> ref, detflag;     // host copies (cache hit: source; miss: destination)
 };
 
 // Launches the inverse-tableau kernel of c on st with at most max_blocks CTAs
 // (0: the library's choice; 1: the single-CTA variant, which keeps the tableau
 // in its L1 and needs no grid barrier). Scratch comes from the stream-ordered
 // allocator, so launches on several streams do not serialize on allocation.
-int reference_launch(stim_circuit *c, cudaStream_t st, uint32_t max_blocks, RefJob *job) {
+int reference_launch(stim_circuit *c, cudaStream_t st, uint32_t max_blocks, bool use_cache, RefJob *job) {
     const HostProgram &hp = c->hp;
     const uint32_t n = hp.num_qubits;
     job->st = st;
     job->blob = nullptr;
     job->launched = false;
+    job->from_cache = false;
+    job->to_cache = false;
+    if (n > 0 && hp.num_meas > 0 && use_cache && ref_cache().lookup(hp, c->ref_words, &job->ref, &job->detflag)) {
+        STIMGB_CK(cudaMemcpyAsync(c->d_ref, job->ref.data(), c->ref_words * 8, cudaMemcpyHostToDevice, st), "copy reference");
+        STIMGB_CK(cudaMemcpyAsync(c->d_detflag, job->detflag.data(), c->ref_words * 8, cudaMemcpyHostToDevice, st),
+                  "copy reference");
+        job->from_cache = true;
+        return STIM_OK;
+    }
+    job->to_cache = use_cache;
     STIMGB_CK(cudaMemsetAsync(c->d_ref, 0, c->ref_words * 8, st), "memset");
     STIMGB_CK(cudaMemsetAsync(c->d_detflag, 0, c->ref_words * 8, st), "memset");
     if (n == 0 || hp.num_meas == 0) return STIM_OK;
@@ -260,6 +341,14 @@ int reference_finish(stim_circuit *c, RefJob *job) {
     int status = 0;
     cudaError_t e = cudaSuccess;
     if (job->launched) e = cudaMemcpyAsync(&status, c->d_status, sizeof(int), cudaMemcpyDeviceToHost, job->st);
+    const bool keep = job->launched && job->to_cache && ref_cache().cap > 0;
+    if (keep && e == cudaSuccess) {
+        job->ref.resize(c->ref_words);
+        job->detflag.resize(c->ref_words);
+        e = cudaMemcpyAsync(job->ref.data(), c->d_ref, c->ref_words * 8, cudaMemcpyDeviceToHost, job->st);
+        if (e == cudaSuccess)
+            e = cudaMemcpyAsync(job->detflag.data(), c->d_detflag, c->ref_words * 8, cudaMemcpyDeviceToHost, job->st);
+    }
     if (job->blob) {
         const cudaError_t f = cudaFreeAsync(job->blob, job->st);
         if (e == cudaSuccess) e = f;
@@ -270,13 +359,16 @@ int reference_finish(stim_circuit *c, RefJob *job) {
     if (e != cudaSuccess) return cuda_fail(e, "reference sample");
     if (status == DEV_TIMEOUT) return fail(STIM_E_TIMEOUT, "tableau grid barrier timed out");
     if (status != 0) return fail(STIM_E_CUDA, "tableau kernel reported a malformed program");
+    if (keep) ref_cache().insert(c->hp, std::move(job->ref), std::move(job->detflag));
     c->ref_valid = true;
     return STIM_OK;
 }
 
-int compute_reference(stim_circuit *c, cudaStream_t st) {
+// use_cache: take the sample of an equal noiseless skeleton when one is cached
+// (and cache a freshly computed one); false recomputes with the tableau.
+int compute_reference(stim_circuit *c, cudaStream_t st, bool use_cache) {
     RefJob job;
-    const int r = reference_launch(c, st, 0, &job);
+    const int r = reference_launch(c, st, 0, use_cache, &job);
     if (r != STIM_OK) return r;
     return reference_finish(c, &job);
 }
@@ -311,7 +403,7 @@ int references_many(stim_circuit *const *cs, size_t k, bool recompute) {
         std::vector<bool> ok(small.size(), false);
         if (rc == STIM_OK)
             for (size_t i = 0; i < small.size(); i++) {
-                const int r = reference_launch(small[i], streams[i % streams.size()], 1, &jobs[i]);
+                const int r = reference_launch(small[i], streams[i % streams.size()], 1, !recompute, &jobs[i]);
                 if (r != STIM_OK) {
                     rc = r;
                     break;
@@ -328,7 +420,7 @@ int references_many(stim_circuit *const *cs, size_t k, bool recompute) {
         if (rc != STIM_OK) return rc;
     }
     for (stim_circuit *c : large) {
-        const int r = compute_reference(c, nullptr);
+        const int r = compute_reference(c, nullptr, !recompute);
         if (r != STIM_OK) return r;
     }
     return STIM_OK;
@@ -497,7 +589,7 @@ int stimgb_ensure_references(stim_circuit *const *cs, size_t k) { return referen
 int stimgb_ensure_reference(stim_circuit *c, cudaStream_t st) {
     int r = ensure_device(c);
     if (r != STIM_OK) return r;
-    if (!c->ref_valid) return compute_reference(c, st);
+    if (!c->ref_valid) return compute_reference(c, st, true);
     return STIM_OK;
 }
 
@@ -543,6 +635,25 @@ int stim_info_get(const stim_circuit *c, stim_info *out) {
     out->num_instructions = hp.num_instr;
     out->num_layers = hp.num_layers_exec;
     out->num_program_layers = hp.num_layers_stored;
+    out->reference_key = hp.skeleton_hash;
+    return STIM_OK;
+}
+
+int stim_reference_cache_set(size_t budget_bytes) {
+    RefCache &rc = ref_cache();
+    std::lock_guard<std::mutex> g(rc.mu);
+    rc.cap = budget_bytes;
+    rc.evict_to(budget_bytes);
+    return STIM_OK;
+}
+
+int stim_reference_cache_stats(uint64_t *hits, uint64_t *misses, uint64_t *entries, uint64_t *bytes) {
+    RefCache &rc = ref_cache();
+    std::lock_guard<std::mutex> g(rc.mu);
+    if (hits) *hits = rc.hits;
+    if (misses) *misses = rc.misses;
+    if (entries) *entries = rc.map.size();
+    if (bytes) *bytes = rc.bytes;
     return STIM_OK;
 }
 
@@ -588,7 +699,7 @@ int stim_reference_sample(stim_circuit *c, uint64_t *ref_bits, uint64_t *det_bit
     int r = ensure_device(c);
     if (r != STIM_OK) return r;
     if (!c->ref_valid || (flags & STIM_RECOMPUTE)) {
-        r = compute_reference(c, st);
+        r = compute_reference(c, st, (flags & STIM_RECOMPUTE) == 0);
         if (r != STIM_OK) return r;
     }
     const size_t words = (c->hp.num_meas + 63) / 64;
@@ -618,7 +729,7 @@ int stim_frame_sample_ex(stim_circuit *c, uint64_t num_shots, uint64_t seed, uin
     int r = ensure_device(c);
     if (r != STIM_OK) return r;
     if (!c->ref_valid) {
-        r = compute_reference(c, st);
+        r = compute_reference(c, st, true);
         if (r != STIM_OK) return r;
     }
     if (num_shots == 0) return STIM_OK;

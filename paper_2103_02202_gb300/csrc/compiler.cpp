@@ -603,6 +603,30 @@ class Emitter {
     }
 };
 
+// The noiseless skeleton of a block: every instruction that acts on the
+// noiseless state (gates, collapsing ops, classically controlled ops) with its
+// targets, and REPEAT structure, in source order. Noise channels, DETECTOR and
+// OBSERVABLE_INCLUDE do not change the reference sample, so circuits with
+// equal skeletons have equal reference samples.
+void skeleton_of(const Block &b, std::vector<uint32_t> *out) {
+    for (const Node &nd : b.items) {
+        if (nd.block) {
+            out->push_back(0xFFFFFFFFu);
+            out->push_back((uint32_t)nd.block->reps);
+            out->push_back((uint32_t)(nd.block->reps >> 32));
+            skeleton_of(*nd.block, out);
+            out->push_back(0xFFFFFFFEu);
+            continue;
+        }
+        const Instr &in = nd.ins;
+        if (in.gate == PG_DET || in.gate == PG_OBS) continue;
+        if (op_is_noise(opcode_of(in.gate))) continue;
+        out->push_back((uint32_t)in.gate);
+        out->push_back((uint32_t)in.targets.size());
+        out->insert(out->end(), in.targets.begin(), in.targets.end());
+    }
+}
+
 // Flattened detector list: absolute measurement index of every rec[-k].
 // Observable lookbacks go to obs[k] (appended after the detectors by the caller).
 void collect_detectors(const Block &b, uint64_t *meas, HostProgram *hp, std::vector<std::vector<uint32_t>> *obs) {
@@ -889,6 +913,14 @@ int compile_circuit(const char *text, size_t len, HostProgram *out, std::string 
             hp.det_meas.insert(hp.det_meas.end(), o.begin(), o.end());
             hp.det_ptr.push_back(hp.det_meas.size());
         }
+        skeleton_of(root, &hp.skeleton);
+        uint64_t h = 1469598103934665603ull;        // FNV-1a over the skeleton's bytes
+        for (uint32_t v : hp.skeleton)
+            for (int k = 0; k < 4; k++) {
+                h ^= (v >> (8 * k)) & 0xFFu;
+                h *= 1099511628211ull;
+            }
+        hp.skeleton_hash = h;
         Emitter em(&hp, hp.num_qubits ? hp.num_qubits : 1);
         hp.num_layers_exec = em.emit(root, 0, 0, 0);
         *out = std::move(hp);

@@ -110,6 +110,11 @@ struct HostProgram {
     std::vector<double> table_p;
     std::vector<uint64_t> det_ptr;          // num_det + 1 offsets into det_meas
     std::vector<uint32_t> det_meas;         // absolute measurement indices
+    // noiseless skeleton (source-order gates, collapses and classically
+    // controlled ops with their targets, REPEAT structure) and its FNV-1a
+    // hash: equal skeletons give equal reference samples
+    std::vector<uint32_t> skeleton;
+    uint64_t skeleton_hash = 0;
     // per-op-type target counts with loops unrolled (for bench accounting)
     uint64_t exec_targets[OP_COUNT] = {0};
 };

@@ -189,3 +189,37 @@ def test_invalid_arguments_without_gpu():
         assert rc == sg.STIM_E_INVALID_ARG      # unknown flag
     finally:
         sg.stim_free(h)
+
+
+def _key(text):
+    h = sg.stim_compile(text)
+    try:
+        return sg.stim_info_get(h)["reference_key"]
+    finally:
+        sg.stim_free(h)
+
+
+def test_reference_key_ignores_noise_detectors_and_observables():
+    base = W.surface_code_memory(5, 4, 0.001)
+    same = [W.surface_code_memory(5, 4, 0.01), W.surface_code_memory(5, 4, 0.0),
+            W.surface_code_memory(5, 4, 0.001, observable=True),
+            "\n".join(l for l in base.splitlines() if not l.strip().startswith("DETECTOR")) + "\n",
+            base.replace("DEPOLARIZE1", "PAULI_CHANNEL_1(0.01, 0.02, 0.03) #")]
+    for t in same:
+        assert _key(t) == _key(base)
+    # anything the noiseless state sees changes the key
+    different = [W.surface_code_memory(5, 5, 0.001), W.surface_code_memory(7, 4, 0.001),
+                 base.replace("MR", "M", 1), base.replace("REPEAT 3", "REPEAT 7"),
+                 base + "H 0\n", base.replace("H ", "S ", 1), base + "CX rec[-1] 0\n"]
+    keys = {_key(t) for t in different}
+    assert _key(base) not in keys and len(keys) == len(different)
+    # equal skeletons written differently (rounds 5 = REPEAT 4) share the key
+    assert _key(W.surface_code_memory(5, 5, 0.02)) == _key(base.replace("REPEAT 3", "REPEAT 4"))
+
+
+def test_reference_cache_controls_without_gpu():
+    st = sg.stim_reference_cache_stats()
+    assert set(st) == {"hits", "misses", "entries", "bytes"}
+    sg.stim_reference_cache_set(0)
+    assert sg.stim_reference_cache_stats()["entries"] == 0
+    sg.stim_reference_cache_set(256 << 20)

@@ -687,3 +687,41 @@ def test_reference_many_matches_oracle_and_one_by_one():
     assert torch.equal(rb, rb2) and torch.equal(db, db2)
     for c in cs + [big]:
         c.close()
+
+
+def test_reference_cache_reuses_equal_skeletons():
+    """A circuit that differs from an earlier one only in noise, detectors and
+    observables takes the cached reference sample; it equals a recomputed one
+    and the oracle's, and STIM_RECOMPUTE bypasses the cache."""
+    sg.stim_reference_cache_set(256 << 20)
+    a = sg.Circuit(W.surface_code_memory(9, 6, 0.001))
+    a.reference()
+    torch.cuda.synchronize()
+    before = sg.stim_reference_cache_stats()
+    text_b = W.surface_code_memory(9, 6, 0.02, observable=True)
+    b = sg.Circuit(text_b)
+    assert b.info["reference_key"] == a.info["reference_key"]
+    rb, db = b.reference()
+    torch.cuda.synchronize()
+    after = sg.stim_reference_cache_stats()
+    assert after["hits"] == before["hits"] + 1
+    rb2, db2 = b.reference(recompute=True)
+    torch.cuda.synchronize()
+    assert sg.stim_reference_cache_stats()["hits"] == after["hits"]
+    assert torch.equal(rb, rb2) and torch.equal(db, db2)
+    orf, odf = oracle.Circuit(text_b).reference()
+    np.testing.assert_array_equal(words_to_bits(to_np(rb)[None, :], b.num_measurements)[0], orf)
+    # sampling with the cached reference matches the oracle
+    mb, dbits = gpu_sample(text_b, 700, 31)
+    om, od = oracle.Circuit(text_b).sample(np.arange(700), 31, threads=8)
+    np.testing.assert_array_equal(mb, om)
+    np.testing.assert_array_equal(dbits, od)
+    # with the cache off nothing is looked up
+    sg.stim_reference_cache_set(0)
+    c = sg.Circuit(W.surface_code_memory(9, 6, 0.005))
+    c.reference()
+    torch.cuda.synchronize()
+    assert sg.stim_reference_cache_stats()["entries"] == 0
+    sg.stim_reference_cache_set(256 << 20)
+    for h in (a, b, c):
+        h.close()
