@@ -280,11 +280,16 @@ def run_batch_workload(args):
     t0 = time.perf_counter()
     cs = [sg.Circuit(e["text"]) for e in spec]
     compile_s = time.perf_counter() - t0
-    # reference samples of all circuits at once (the small ones side by side)
+    # reference samples of all circuits at once, side by side on the GPU
     t0 = time.perf_counter()
     sg.stim_reference_many([c.handle for c in cs])
     torch.cuda.synchronize()
     ref_s = time.perf_counter() - t0
+    # again without the reference cache (circuits of equal skeleton reuse a sample)
+    t0 = time.perf_counter()
+    sg.stim_reference_many([c.handle for c in cs], sg.STIM_RECOMPUTE)
+    torch.cuda.synchronize()
+    ref_many_s = time.perf_counter() - t0
     # the same references one circuit at a time, for comparison
     t0 = time.perf_counter()
     for c in cs:
@@ -337,7 +342,8 @@ def run_batch_workload(args):
         "plain": {"value": gate_shots / (res["plain"] / 1000.0), "unit": "shot-gates/s",
                   "ms_per_step": res["plain"], "launches_per_step": 2 * len(cs)},
         "shots_per_s": sum(shots) / (res["batched"] / 1000.0),
-        "compile_s": compile_s, "reference_samples_s": ref_s, "reference_samples_one_by_one_s": ref_seq_s,
+        "compile_s": compile_s, "reference_samples_s": ref_s, "reference_samples_side_by_side_uncached_s": ref_many_s,
+        "reference_samples_one_by_one_s": ref_seq_s,
     }
     print(json.dumps(line), flush=True)
     sg.stim_batch_free(plan)

@@ -499,7 +499,7 @@ int stim_batch_create(stim_circuit *const *circuits, const uint64_t *num_shots, 
         if (!circuits[i]) r = bfail(STIM_E_INVALID_ARG, "stim_batch_create: null circuit");
         else if ((num_shots[i] + 63) / 64 > (1ull << 31)) r = bfail(STIM_E_UNSUPPORTED, "stim_batch_create: too many shots");
     }
-    // reference samples of all circuits, the small ones side by side
+    // reference samples of all circuits, side by side
     if (r == STIM_OK) r = stimgb_ensure_references(circuits, k);
     for (size_t i = 0; i < k && r == STIM_OK; i++) {
         r = stimgb_ensure_reference(circuits[i], st);

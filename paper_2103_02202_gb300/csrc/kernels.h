@@ -87,6 +87,8 @@ struct TabArgs {
     int *status;
 };
 
+constexpr uint32_t kTableauThreads = 512;     // threads per CTA of the tableau kernel
+
 cudaError_t launch_tableau_init(const TabArgs &a, cudaStream_t stream);
 // Cooperative launch; blocks * threads must be co-resident.
 cudaError_t launch_tableau(const TabArgs &a, uint32_t blocks, uint32_t threads, cudaStream_t stream);

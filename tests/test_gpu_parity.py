@@ -657,9 +657,9 @@ def test_cluster_deferred_hits_on_one_remote_word(hint):
 
 
 def test_reference_many_matches_oracle_and_one_by_one():
-    """stim_reference_many (single-CTA tableaus side by side for small
-    circuits, the multi-CTA path above 4096 qubits) gives the references the
-    oracle gives, and the ones the one-at-a-time path gives."""
+    """stim_reference_many (tableaus side by side within the co-resident CTA
+    limit) gives the references the oracle gives, and the ones the
+    one-at-a-time path gives."""
     rng = np.random.default_rng(2400)
     texts = [W.random_clifford(int(n), int(dp), int(sd)) for n, dp, sd in
              zip(rng.integers(20, 300, 10), rng.integers(10, 80, 10), rng.integers(0, 1000, 10))]
@@ -679,7 +679,7 @@ def test_reference_many_matches_oracle_and_one_by_one():
         np.testing.assert_array_equal(r, orf, err_msg=t[:200])
         np.testing.assert_array_equal(d, odf, err_msg=t[:200])
     # recompute one by one (library's block count) and compare, plus a large circuit
-    big = sg.Circuit(W.surface_code_memory(47, 2, 0.001))     # 4417 qubits: multi-CTA path
+    big = sg.Circuit(W.surface_code_memory(47, 2, 0.001))     # 4417 qubits
     sg.stim_reference_many([big.handle, cs[2].handle], sg.STIM_RECOMPUTE)
     rb, db = big.reference()
     rb2, db2 = big.reference(recompute=True)
