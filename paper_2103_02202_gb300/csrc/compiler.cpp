@@ -789,27 +789,30 @@ class FrameBuilder {
                 sg.op_begin = (uint32_t)fp_->ops.size();
                 sg.count = (uint32_t)(j - i);
                 // first chain step from which only noise ops follow: their
-                // error masks commute, so they may be applied after the chain
-                {
-                    const auto &c0 = chains_[by_rank[r][i]].ops;
-                    uint32_t d = (uint32_t)c0.size();
-                    while (d > 0 && op_is_noise(c0[d - 1].a >> 24)) d--;
-                    sg.defer_from = d;
-                    // a chain whose deferred tail names one qubit twice can send
-                    // two hits to one frame word in one flush
-                    bool dup = false;
-                    for (size_t k = i; k < j && !dup; k++) {
-                        const auto &ops = chains_[by_rank[r][k]].ops;
-                        std::vector<uint32_t> qs;
-                        for (size_t o = d; o < ops.size(); o++) {
-                            qs.push_back(op_q0(ops[o]));
-                            if (op_q1(ops[o]) != op_q0(ops[o])) qs.push_back(op_q1(ops[o]));
+                // error masks commute, so they may be applied after the chain.
+                // With a cluster (C > 1) the deferred tail must also name each
+                // qubit once: its hits are flushed as one warp-wide
+                // red.shared::cluster.xor, which lost updates when two lanes
+                // named the same address (a local red.shared.xor does not).
+                uint32_t dfrom = 0;
+                for (size_t k = i; k < j; k++) {
+                    const auto &ops = chains_[by_rank[r][k]].ops;
+                    uint32_t d = (uint32_t)ops.size();
+                    std::vector<uint32_t> seen;
+                    while (d > 0 && op_is_noise(ops[d - 1].a >> 24)) {
+                        if (C_ > 1) {
+                            const uint32_t qa = op_q0(ops[d - 1]), qb = op_q1(ops[d - 1]);
+                            if (std::find(seen.begin(), seen.end(), qa) != seen.end() ||
+                                std::find(seen.begin(), seen.end(), qb) != seen.end())
+                                break;
+                            seen.push_back(qa);
+                            if (qb != qa) seen.push_back(qb);
                         }
-                        std::sort(qs.begin(), qs.end());
-                        dup = std::adjacent_find(qs.begin(), qs.end()) != qs.end();
+                        d--;
                     }
-                    if (dup) sg.defer_from |= kSegTailRepeatsQubit;
+                    dfrom = std::max(dfrom, d);
                 }
+                sg.defer_from = dfrom;
                 for (size_t k = i; k < j; k++)
                     for (const DevOp &d : chains_[by_rank[r][k]].ops) {
                         fp_->ops.push_back(encode(d));

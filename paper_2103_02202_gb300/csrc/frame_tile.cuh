@@ -448,82 +448,24 @@ __device__ __forceinline__ uint32_t noise_hits(const FrameArgs &a, const SmemKey
 }
 
 // A deferred hit: entry = (op index within the CTA's layer) << 3 | word of the
-// tile. Redraws block 0 and runs the general procedure: the error masks of
-// qubit a (and b for a pair), refs ra, rb; false for a non-noise op.
-__device__ __forceinline__ bool deferred_masks(const FrameArgs &a, const SmemKeys key, uint32_t e, uint32_t first,
-                                               uint32_t tile0, uint32_t instr_off, uint32_t &ra, uint32_t &rb,
-                                               uint64_t &mxa, uint64_t &mza, uint64_t &mxb, uint64_t &mzb) {
+// tile. Redraws block 0, runs the general procedure and XORs the masks in.
+template <int W, int C, bool GMEM>
+__device__ __forceinline__ void deferred_hit(const FrameArgs &a, const SmemKeys key, const Tile<W, C, GMEM> &t,
+                                             uint32_t e, uint32_t first, uint32_t tile0, uint32_t instr_off) {
     const uint32_t oi = e >> 3, w = e & 7u;
     const uint4 ov = __ldg(reinterpret_cast<const uint4 *>(a.ops) + first + oi);
     const uint32_t opc = ov.x >> 28;
-    if (opc - OP_XERR > OP_YERR - OP_XERR) return false;      // only noise ops are queued
+    if (opc - OP_XERR > OP_YERR - OP_XERR) return;      // only noise ops are queued
     const bool pair = opc == OP_DEP2;
     const uint32_t tbl = pair ? (ov.w >> 24) : ov.y;
     const uint32_t slot = pair ? (ov.w & 0xFFFFFFu) : ov.w;
     const uint32_t instr = ov.z + instr_off;
     const uint32_t gw = (uint32_t)a.word0 + tile0 + w;
     const uint4 blk0 = philox_sched(make_uint4(0u, slot, kTagNoise | instr, gw), key);
-    noise_masks_slow(opc, a.geo + kNoiseTableWords * tbl, key, instr, slot, gw, blk0, mxa, mza, mxb, mzb);
-    ra = ov.x & 0x0FFFFFFFu;
-    rb = pair ? ov.y : ra;
-    if (!pair) mxb = mzb = 0;
-    return true;
-}
-
-template <int W, int C, bool GMEM>
-__device__ __forceinline__ void deferred_hit(const FrameArgs &a, const SmemKeys key, const Tile<W, C, GMEM> &t,
-                                             uint32_t e, uint32_t first, uint32_t tile0, uint32_t instr_off) {
-    uint32_t ra, rb;
     uint64_t mxa, mza, mxb, mzb;
-    if (!deferred_masks(a, key, e, first, tile0, instr_off, ra, rb, mxa, mza, mxb, mzb)) return;
-    xor_qubit_word<W, C, GMEM>(t, ra, e & 7u, mxa, mza);
-    if (mxb | mzb) xor_qubit_word<W, C, GMEM>(t, rb, e & 7u, mxb, mzb);
-}
-
-// XOR of v into the shared::cluster address ca (ca = 0: nothing), issued by a
-// whole warp. Lanes naming the same address are merged first (their values
-// XORed into the group's lowest lane), so one red instruction never carries
-// two lanes with the same cluster address: such duplicates lost updates. Used
-// only for flushes that hold hits of a segment flagged kSegTailRepeatsQubit
-// (hits of distinct chains, and of tails naming each qubit once, never share
-// a word).
-__device__ __forceinline__ void warp_red_xor_cluster(uint32_t ca, uint64_t v, uint32_t lane) {
-    const uint32_t key = v ? ca : 0u;
-    const uint32_t same = __match_any_sync(0xFFFFFFFFu, key);
-    if (__any_sync(0xFFFFFFFFu, key != 0u && (same & (same - 1u)) != 0u)) {
-        uint64_t acc = 0;
-#pragma unroll 1
-        for (uint32_t l = 0; l < 32u; l++) {
-            const uint64_t vl = __shfl_sync(0xFFFFFFFFu, v, (int)l);
-            if ((same >> l) & 1u) acc ^= vl;
-        }
-        v = acc;
-    }
-    if (key != 0u && lane == (uint32_t)(__ffs((int)same) - 1)) red_xor_cluster(ca, v);
-}
-
-// Deferred hits of a cluster tile, one queue entry per lane below n; every
-// lane of the warp calls this (the merged reductions are warp collectives).
-template <int W, int C>
-__device__ __forceinline__ void deferred_hits_cluster(const FrameArgs &a, const SmemKeys key,
-                                                      const Tile<W, C, false> &t, uint32_t lane, uint32_t n,
-                                                      uint32_t qsa, uint32_t first, uint32_t tile0,
-                                                      uint32_t instr_off) {
-    uint32_t ra = 0, rb = 0, w = 0;
-    uint64_t mxa = 0, mza = 0, mxb = 0, mzb = 0;
-    if (lane < n) {
-        const uint32_t e = lds32(qsa + 4u * lane);
-        w = e & 7u;
-        if (!deferred_masks(a, key, e, first, tile0, instr_off, ra, rb, mxa, mza, mxb, mzb)) mxa = mza = mxb = mzb = 0;
-    }
-    const uint32_t ax = mapa_rank(row_word<W>(t.fsa, ra & 0xFFFFFFu, w), ra >> 24);
-    const uint32_t az = mapa_rank(row_word<W>(t.fsa, ra & 0xFFFFFFu, W + w), ra >> 24);
-    warp_red_xor_cluster(ax, mxa, lane);
-    warp_red_xor_cluster(az, mza, lane);
-    const uint32_t bx = mapa_rank(row_word<W>(t.fsa, rb & 0xFFFFFFu, w), rb >> 24);
-    const uint32_t bz = mapa_rank(row_word<W>(t.fsa, rb & 0xFFFFFFu, W + w), rb >> 24);
-    warp_red_xor_cluster(bx, mxb, lane);
-    warp_red_xor_cluster(bz, mzb, lane);
+    noise_masks_slow(opc, a.geo + kNoiseTableWords * tbl, key, instr, slot, gw, blk0, mxa, mza, mxb, mzb);
+    xor_qubit_word<W, C, GMEM>(t, ov.x & 0x0FFFFFFFu, w, mxa, mza);
+    if (pair) xor_qubit_word<W, C, GMEM>(t, ov.y, w, mxb, mzb);
 }
 
 __device__ __forceinline__ uint64_t to_global(const void *p) {
@@ -605,26 +547,16 @@ __device__ __forceinline__ bool run_tile(const FrameArgs &a, unsigned char *dyn,
                 // warp and resolved 32 at a time, one per lane.
                 const uint32_t first = segs[sb].y;
                 uint32_t qn = 0;
-                bool qdup = false;      // queued hits may share a frame word (warp-uniform)
                 auto flush = [&](uint32_t n) {
                     __syncwarp();
-                    if constexpr (C > 1 && !GMEM) {
-                        if (qdup)
-                            deferred_hits_cluster<W, C>(a, key, t, lane, n, qsa, first, tile0, instr_off);
-                        else if (lane < n)
-                            deferred_hit<W, C, GMEM>(a, key, t, lds32(qsa + 4u * lane), first, tile0, instr_off);
-                    } else if (lane < n) {
-                        deferred_hit<W, C, GMEM>(a, key, t, lds32(qsa + 4u * lane), first, tile0, instr_off);
-                    }
-                    qdup = false;
+                    if (lane < n) deferred_hit<W, C, GMEM>(a, key, t, lds32(qsa + 4u * lane), first, tile0, instr_off);
                     __syncwarp();
                 };
                 uint32_t g = threadIdx.x, seg_start = 0;
                 for (uint32_t s = sb; s < se; s++) {
                     const uint4 sv = segs[s];
                     const uint32_t len = sv.x, items = sv.z * (W / V), span = (items + 31u) & ~31u;
-                    const uint32_t dfrom = sv.w & ~kSegTailRepeatsQubit;
-                    const bool seg_dup = (sv.w & kSegTailRepeatsQubit) != 0u;
+                    const uint32_t dfrom = sv.w;
                     bool have_next = false;      // nxt holds this item's first op
                     uint4 nxt = make_uint4(0u, 0u, 0u, 0u);
                     for (; g < seg_start + span; g += blockDim.x) {
@@ -662,7 +594,6 @@ __device__ __forceinline__ bool run_tile(const FrameArgs &a, unsigned char *dyn,
                                             sts32(qsa + 4u * (qn + __popc(m & ((1u << lane) - 1u))),
                                                   (oi << 3) | (wo + (uint32_t)i));
                                         qn += cnt;
-                                        qdup |= seg_dup;
                                     }
                                 }
                             }

@@ -130,7 +130,8 @@ struct HostProgram {
 // its slice; its chains of a merged layer are grouped into segments of equal
 // opcode signature (so warps run uniform code). Noise ops at the end of a
 // chain (defer_from onwards) touch nothing the chain reads later, and their
-// error masks commute, so the kernel may apply them after the chain. A layer
+// error masks commute, so the kernel may apply them after the chain; with a
+// cluster they also name distinct qubits, so their hits never meet in one word. A layer
 // holding a classically controlled op never folds into the open merged layer:
 // the record it reads was written by another thread, and the barrier that
 // ends the previous merged layer makes that write visible.
@@ -150,12 +151,8 @@ struct FrameSeg {
     uint32_t len;         // ops per chain
     uint32_t op_begin;    // first op of the first chain
     uint32_t count;       // chains
-    uint32_t defer_from;  // chain steps >= defer_from are all noise ops; bit 31: kSegTailRepeatsQubit
+    uint32_t defer_from;  // chain steps >= defer_from are all noise ops (C > 1: on distinct qubits)
 };
-
-// FrameSeg::defer_from flag: some chain's deferred tail names a qubit twice, so
-// its hits may meet in one frame word within one flush of the hit queue.
-constexpr uint32_t kSegTailRepeatsQubit = 1u << 31;
 
 struct FrameProgram {
     int C = 1;
