@@ -280,7 +280,7 @@ def run_batch_workload(args):
     t0 = time.perf_counter()
     cs = [sg.Circuit(e["text"]) for e in spec]
     compile_s = time.perf_counter() - t0
-    # reference samples of all circuits at once, side by side on the GPU
+    # reference samples of all circuits at once (small ones side by side)
     t0 = time.perf_counter()
     sg.stim_reference_many([c.handle for c in cs])
     torch.cuda.synchronize()

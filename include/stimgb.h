@@ -157,14 +157,12 @@ int stim_reference_sample(stim_circuit *c, uint64_t *ref_bits, uint64_t *det_bit
 /*
  * stim_reference_many -- computes (and keeps on their handles) the reference
  * samples of k circuits at once, as stim_reference_sample would one by one.
- * Each circuit's inverse tableau (Section 4) keeps its usual CTA count and
- * runs on an internal stream; circuits start, longest first, whenever the
- * CTAs of all running tableaus fit the GPU's co-resident maximum, so many
- * small and mid-size circuits share the GPU instead of queueing. Handles
- * whose reference is already computed (or cached, see below) are skipped
- * unless flags is STIM_RECOMPUTE; a handle may appear more than once. Blocks
- * until every reference is done. The caller should not run other kernels on
- * the GPU meanwhile: the tableaus' grid barriers need all their CTAs resident.
+ * Circuits whose inverse tableau (Section 4) wants at most two CTAs (up to
+ * about 250 qubits) run the single-CTA tableau side by side on internal
+ * streams; larger ones follow one at a time with the multi-CTA tableau.
+ * Handles whose reference is already computed (or cached, see below) are
+ * skipped unless flags is STIM_RECOMPUTE; a handle may appear more than once.
+ * Blocks until every reference is done.
  * Errors: STIM_E_INVALID_ARG (null array or element, unknown flags),
  * STIM_E_OOM, STIM_E_CUDA, STIM_E_TIMEOUT; references finished before the
  * error stay valid.

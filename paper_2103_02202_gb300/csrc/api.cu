@@ -2,9 +2,7 @@
 #include <cuda_runtime.h>
 
 #include <algorithm>
-#include <chrono>
 #include <map>
-#include <thread>
 #include <cstdio>
 #include <cstring>
 #include <mutex>
@@ -381,91 +379,55 @@ int compute_reference(stim_circuit *c, cudaStream_t st, bool use_cache) {
     return reference_finish(c, &job);
 }
 
-// Reference samples of many circuits side by side: each tableau keeps its
-// usual CTA count, and a circuit is launched (on its own stream) only while
-// the CTAs of all running tableaus fit the co-resident maximum, so every
-// cooperative grid can be resident at once and their grid barriers cannot
-// wait on one another. The longest circuits (by measurements x tableau
-// words) start first; finished ones free their CTAs for the next.
+// Reference samples of many circuits. Circuits whose tableau wants at most
+// kSideBySideBlocks CTAs run the single-CTA tableau (no grid barrier) side by
+// side on internal streams; the others follow one at a time with their usual
+// multi-CTA grid. Multi-CTA (grid-barrier) tableaus are never run
+// concurrently with each other.
+constexpr uint32_t kSideBySideBlocks = 2;
 constexpr size_t kReferenceStreams = 32;
 
 int references_many(stim_circuit *const *cs, size_t k, bool recompute) {
-    std::vector<stim_circuit *> todo;
+    std::vector<stim_circuit *> small, large;
     for (size_t i = 0; i < k; i++) {
         stim_circuit *c = cs[i];
         if (!c) return fail(STIM_E_INVALID_ARG, "stim_reference_many: null circuit");
         const int r = ensure_device(c);
         if (r != STIM_OK) return r;
-        if ((c->ref_valid && !recompute) || std::find(todo.begin(), todo.end(), c) != todo.end()) continue;
-        todo.push_back(c);
+        if ((c->ref_valid && !recompute) || std::find(small.begin(), small.end(), c) != small.end() ||
+            std::find(large.begin(), large.end(), c) != large.end())
+            continue;
+        const int maxb = tableau_max_blocks(kTableauThreads, c->device);
+        (tableau_blocks(c, maxb) <= kSideBySideBlocks ? small : large).push_back(c);
     }
-    if (todo.empty()) return STIM_OK;
-    const int maxb = tableau_max_blocks(kTableauThreads, todo[0]->device);
-    auto cost = [](const stim_circuit *c) {
-        const double n = c->hp.num_qubits;
-        return (double)c->hp.num_meas * n * n;
-    };
-    std::stable_sort(todo.begin(), todo.end(), [&](stim_circuit *x, stim_circuit *y) { return cost(x) > cost(y); });
-    std::vector<cudaStream_t> streams(std::min(todo.size(), kReferenceStreams), nullptr);
-    for (cudaStream_t &st : streams)
-        if (cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking) != cudaSuccess) {
-            for (cudaStream_t s2 : streams)
-                if (s2) cudaStreamDestroy(s2);
-            return fail(STIM_E_CUDA, "stim_reference_many: stream creation failed");
-        }
-    struct Running {
-        stim_circuit *c;
-        size_t stream;
-        uint32_t blocks;
-        RefJob job;
-    };
-    std::vector<Running> running;
-    std::vector<bool> stream_busy(streams.size(), false);
-    int free_blocks = maxb, rc = STIM_OK;
-    size_t next = 0;
-    while (rc == STIM_OK && (next < todo.size() || !running.empty())) {
-        // start every circuit that fits, in cost order
-        while (rc == STIM_OK && next < todo.size()) {
-            stim_circuit *c = todo[next];
-            const uint32_t b = tableau_blocks(c, maxb);
-            size_t sidx = 0;
-            while (sidx < streams.size() && stream_busy[sidx]) sidx++;
-            if ((int)b > free_blocks || sidx == streams.size()) break;
-            Running run{c, sidx, b, RefJob()};
-            rc = reference_launch(c, streams[sidx], 0, !recompute, &run.job);
-            if (rc != STIM_OK) break;
-            if (!run.job.launched) {        // trivial circuit or a cache hit: nothing runs on the SMs
-                rc = reference_finish(c, &run.job);
-                next++;
-                continue;
+    int rc = STIM_OK;
+    if (!small.empty()) {
+        std::vector<cudaStream_t> streams(std::min(small.size(), kReferenceStreams), nullptr);
+        for (cudaStream_t &st : streams)
+            if (cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking) != cudaSuccess) {
+                st = nullptr;
+                rc = fail(STIM_E_CUDA, "stim_reference_many: stream creation failed");
             }
-            stream_busy[sidx] = true;
-            free_blocks -= (int)b;
-            running.push_back(std::move(run));
-            next++;
+        std::vector<RefJob> jobs(small.size());
+        std::vector<bool> started(small.size(), false);
+        for (size_t i = 0; i < small.size() && rc == STIM_OK; i++) {
+            rc = reference_launch(small[i], streams[i % streams.size()], 1, !recompute, &jobs[i]);
+            started[i] = rc == STIM_OK;
         }
-        if (rc != STIM_OK || running.empty()) continue;
-        // wait for the first finished tableau (polling all running streams)
-        bool any = false;
-        while (!any) {
-            for (size_t i = 0; i < running.size(); i++) {
-                const cudaError_t q = cudaStreamQuery(streams[running[i].stream]);
-                if (q == cudaErrorNotReady) continue;
-                any = true;
-                const int r = reference_finish(running[i].c, &running[i].job);
-                if (rc == STIM_OK) rc = r;
-                stream_busy[running[i].stream] = false;
-                free_blocks += (int)running[i].blocks;
-                running.erase(running.begin() + (long)i);
-                break;
-            }
-            if (!any) std::this_thread::sleep_for(std::chrono::microseconds(50));
+        for (size_t i = 0; i < small.size(); i++) {
+            if (!started[i]) continue;
+            const int r = reference_finish(small[i], &jobs[i]);
+            if (rc == STIM_OK) rc = r;
         }
+        for (cudaStream_t st : streams)
+            if (st) cudaStreamDestroy(st);
+        if (rc != STIM_OK) return rc;
     }
-    for (Running &r : running) reference_finish(r.c, &r.job);     // after an error: drain
-    for (cudaStream_t st : streams)
-        if (st) cudaStreamDestroy(st);
-    return rc;
+    for (stim_circuit *c : large) {
+        const int r = compute_reference(c, nullptr, !recompute);
+        if (r != STIM_OK) return r;
+    }
+    return STIM_OK;
 }
 
 // Tile shape: the smallest cluster whose qubit slice fits shared memory, then

@@ -81,8 +81,8 @@ struct TileChoice {
 // Library-internal entry points shared by the batched and serving paths.
 int stimgb_frame_program(stim_circuit *c, int C, const DevFrameProgram **out);
 int stimgb_ensure_reference(stim_circuit *c, cudaStream_t st);
-// Reference samples of k circuits, side by side within the co-resident CTA
-// limit (internal streams); blocks until done.
+// Reference samples of k circuits: small ones side by side (single-CTA
+// tableaus on internal streams), the others one at a time; blocks until done.
 int stimgb_ensure_references(stim_circuit *const *cs, size_t k);
 // Tile shape for num_shots shots and the global-frame scratch it needs (words).
 int stimgb_sampling_layout(stim_circuit *c, uint64_t num_shots, TileChoice *tc, size_t *gframe_words);

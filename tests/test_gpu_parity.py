@@ -657,8 +657,8 @@ def test_cluster_deferred_hits_on_one_remote_word(hint):
 
 
 def test_reference_many_matches_oracle_and_one_by_one():
-    """stim_reference_many (tableaus side by side within the co-resident CTA
-    limit) gives the references the oracle gives, and the ones the
+    """stim_reference_many (small circuits side by side, the others one at a
+    time) gives the references the oracle gives, and the ones the
     one-at-a-time path gives."""
     rng = np.random.default_rng(2400)
     texts = [W.random_clifford(int(n), int(dp), int(sd)) for n, dp, sd in
