@@ -271,13 +271,14 @@ uint32_t tableau_blocks(const stim_circuit *c, int maxb) {
     return (uint32_t)std::min<uint64_t>(want, (uint64_t)std::max(maxb, 1));
 }
 
-// Launches the inverse-tableau kernel of c on st with at most max_blocks CTAs
-// (0: the library's choice; 1: the single-CTA variant, which keeps the tableau
-// in its L1 and needs no grid barrier). Scratch comes from the stream-ordered
-// allocator, so launches on several streams do not serialize on allocation.
-int reference_launch(stim_circuit *c, cudaStream_t st, uint32_t max_blocks, bool use_cache, RefJob *job) {
+// First half of a reference computation on st: a cached sample of an equal
+// skeleton is copied in (job->from_cache), or the tableau scratch is
+// allocated, cleared and initialised into *a (*needs_kernel = true). Trivial
+// circuits (no qubits or no measurements) need neither.
+int reference_prepare(stim_circuit *c, cudaStream_t st, bool use_cache, RefJob *job, TabArgs *a, bool *needs_kernel) {
     const HostProgram &hp = c->hp;
     const uint32_t n = hp.num_qubits;
+    *needs_kernel = false;
     job->st = st;
     job->blob = nullptr;
     job->launched = false;
@@ -296,15 +297,15 @@ int reference_launch(stim_circuit *c, cudaStream_t st, uint32_t max_blocks, bool
     if (n == 0 || hp.num_meas == 0) return STIM_OK;
     const uint32_t nw = (n + 63) / 64;
     const size_t col_words = (size_t)2 * n * nw;
-    TabArgs a{};
-    a.prog = c->d_prog;
-    a.nprog = (uint32_t)hp.prog.size();
-    a.ops = c->d_ops;
-    a.n = n;
-    a.nw = nw;
-    a.ref = c->d_ref;
-    a.detflag = c->d_detflag;
-    a.status = c->d_status;
+    *a = TabArgs{};
+    a->prog = c->d_prog;
+    a->nprog = (uint32_t)hp.prog.size();
+    a->ops = c->d_ops;
+    a->n = n;
+    a->nw = nw;
+    a->ref = c->d_ref;
+    a->detflag = c->d_detflag;
+    a->status = c->d_status;
     const size_t bytes_tx = col_words * 8, bytes_sign = (size_t)2 * n * 4, bytes_klist = (size_t)n * 4 + 64;
     const size_t bytes_kmask = (size_t)nw * 8 + 64, bytes_rnd = (size_t)std::max<uint32_t>(hp.max_layer_ops, 1) * 4 + 64;
     const size_t total = 2 * bytes_tx + 2 * bytes_sign + bytes_klist + bytes_kmask + bytes_rnd + 256 + 1024;
@@ -315,20 +316,39 @@ int reference_launch(stim_circuit *c, cudaStream_t st, uint32_t max_blocks, bool
         off += (b + 255) & ~(size_t)255;
         return p;
     };
-    a.tx = (uint64_t *)take(bytes_tx);
-    a.tz = (uint64_t *)take(bytes_tx);
-    a.sign = (uint32_t *)take(bytes_sign);
-    a.perm = (uint32_t *)take(bytes_sign);
-    a.klist = (uint32_t *)take(bytes_klist);
-    a.kmask = (uint64_t *)take(bytes_kmask);
-    a.rnd = (uint32_t *)take(bytes_rnd);
-    a.ctl = (TabCtl *)take(sizeof(TabCtl));
+    a->tx = (uint64_t *)take(bytes_tx);
+    a->tz = (uint64_t *)take(bytes_tx);
+    a->sign = (uint32_t *)take(bytes_sign);
+    a->perm = (uint32_t *)take(bytes_sign);
+    a->klist = (uint32_t *)take(bytes_klist);
+    a->kmask = (uint64_t *)take(bytes_kmask);
+    a->rnd = (uint32_t *)take(bytes_rnd);
+    a->ctl = (TabCtl *)take(sizeof(TabCtl));
     cudaError_t e = cudaMemsetAsync(job->blob, 0, total, st);
     if (e == cudaSuccess) e = cudaMemsetAsync(c->d_status, 0, sizeof(int), st);
-    if (e == cudaSuccess) e = launch_tableau_init(a, st);
-    if (e == cudaSuccess) {
-        uint32_t blocks = tableau_blocks(c, tableau_max_blocks(kTableauThreads, c->device));
-        if (max_blocks && blocks > max_blocks) blocks = max_blocks;
+    if (e == cudaSuccess) e = launch_tableau_init(*a, st);
+    if (e != cudaSuccess) {
+        cudaFreeAsync(job->blob, st);
+        job->blob = nullptr;
+        return cuda_fail(e, "reference sample");
+    }
+    *needs_kernel = true;
+    return STIM_OK;
+}
+
+// Launches the inverse-tableau kernel of c on st with at most max_blocks CTAs
+// (0: the library's choice; 1: the single-CTA variant, which keeps the tableau
+// in its L1 and needs no grid barrier). Scratch comes from the stream-ordered
+// allocator, so launches on several streams do not serialize on allocation.
+int reference_launch(stim_circuit *c, cudaStream_t st, uint32_t max_blocks, bool use_cache, RefJob *job) {
+    TabArgs a;
+    bool needs_kernel = false;
+    const int r = reference_prepare(c, st, use_cache, job, &a, &needs_kernel);
+    if (r != STIM_OK || !needs_kernel) return r;
+    uint32_t blocks = tableau_blocks(c, tableau_max_blocks(kTableauThreads, c->device));
+    if (max_blocks && blocks > max_blocks) blocks = max_blocks;
+    cudaError_t e;
+    {
         ProfScope ps(STIM_KERNEL_TABLEAU, st);
         e = launch_tableau(a, blocks, kTableauThreads, st);
     }
@@ -379,11 +399,74 @@ int compute_reference(stim_circuit *c, cudaStream_t st, bool use_cache) {
     return reference_finish(c, &job);
 }
 
+// Multi-CTA tableaus of several circuits in one cooperative launch on st:
+// circuit i gets blocks[i] CTAs (the sum co-resident), meeting only at its
+// own barrier. One launch, so no two cooperative grids run side by side.
+int reference_batch(const std::vector<stim_circuit *> &cs, const std::vector<uint32_t> &blocks, bool use_cache,
+                    cudaStream_t st) {
+    std::vector<RefJob> jobs(cs.size());
+    std::vector<TabArgs> args;
+    std::vector<size_t> which;       // index into cs of each args entry
+    std::vector<uint32_t> first, job_of;
+    size_t prepared = 0;             // cs[0 .. prepared) went through reference_prepare
+    int rc = STIM_OK;
+    for (size_t i = 0; i < cs.size() && rc == STIM_OK; i++) {
+        TabArgs a;
+        bool needs = false;
+        rc = reference_prepare(cs[i], st, use_cache, &jobs[i], &a, &needs);
+        if (rc != STIM_OK) break;
+        prepared = i + 1;
+        if (!needs) continue;
+        a.nblk = blocks[i];
+        first.push_back((uint32_t)job_of.size());
+        for (uint32_t b = 0; b < blocks[i]; b++) job_of.push_back((uint32_t)args.size());
+        args.push_back(a);
+        which.push_back(i);
+    }
+    char *dev = nullptr;
+    if (rc == STIM_OK && !args.empty()) {
+        const size_t b_args = args.size() * sizeof(TabArgs), b_first = first.size() * 4, b_of = job_of.size() * 4;
+        const size_t o_first = (b_args + 255) & ~(size_t)255, o_of = o_first + ((b_first + 255) & ~(size_t)255);
+        cudaError_t e = cudaMallocAsync((void **)&dev, o_of + b_of, st);
+        if (e == cudaSuccess) e = cudaMemcpyAsync(dev, args.data(), b_args, cudaMemcpyHostToDevice, st);
+        if (e == cudaSuccess) e = cudaMemcpyAsync(dev + o_first, first.data(), b_first, cudaMemcpyHostToDevice, st);
+        if (e == cudaSuccess) e = cudaMemcpyAsync(dev + o_of, job_of.data(), b_of, cudaMemcpyHostToDevice, st);
+        if (e == cudaSuccess) {
+            ProfScope ps(STIM_KERNEL_TABLEAU, st);
+            e = launch_tableau_batch(reinterpret_cast<const TabArgs *>(dev), reinterpret_cast<const uint32_t *>(dev + o_of),
+                                     reinterpret_cast<const uint32_t *>(dev + o_first), (uint32_t)job_of.size(),
+                                     kTableauThreads, st);
+        }
+        if (e == cudaSuccess)
+            for (size_t k : which) jobs[k].launched = true;
+        else
+            rc = cuda_fail(e, "reference sample (batched tableau)");
+    }
+    // prepared circuits: the launched ones and those that needed no kernel are
+    // finished (and become valid); a tableau that never ran only frees its scratch
+    std::vector<bool> needs_kernel(cs.size(), false);
+    for (size_t k : which) needs_kernel[k] = true;
+    for (size_t i = 0; i < prepared; i++) {
+        if (needs_kernel[i] && !jobs[i].launched) {
+            if (jobs[i].blob) cudaFreeAsync(jobs[i].blob, st);
+            jobs[i].blob = nullptr;
+            continue;
+        }
+        const int r = reference_finish(cs[i], &jobs[i]);
+        if (rc == STIM_OK) rc = r;
+    }
+    if (dev) {
+        cudaFreeAsync(dev, st);
+        cudaStreamSynchronize(st);
+    }
+    return rc;
+}
+
 // Reference samples of many circuits. Circuits whose tableau wants at most
 // kSideBySideBlocks CTAs run the single-CTA tableau (no grid barrier) side by
-// side on internal streams; the others follow one at a time with their usual
-// multi-CTA grid. Multi-CTA (grid-barrier) tableaus are never run
-// concurrently with each other.
+// side on internal streams; the others share batched cooperative launches
+// (reference_batch), each circuit with CTAs in proportion to what it wants,
+// the total within the co-resident maximum.
 constexpr uint32_t kSideBySideBlocks = 2;
 constexpr size_t kReferenceStreams = 32;
 
@@ -423,8 +506,32 @@ int references_many(stim_circuit *const *cs, size_t k, bool recompute) {
             if (st) cudaStreamDestroy(st);
         if (rc != STIM_OK) return rc;
     }
-    for (stim_circuit *c : large) {
-        const int r = compute_reference(c, nullptr, !recompute);
+    if (large.empty()) return STIM_OK;
+    const int maxb = tableau_batch_max_blocks(kTableauThreads, large[0]->device);
+    // waves of at most maxb circuits; CTAs in proportion to each circuit's want
+    for (size_t w0 = 0; w0 < large.size(); w0 += (size_t)maxb) {
+        const size_t w1 = std::min(large.size(), w0 + (size_t)maxb);
+        std::vector<stim_circuit *> wave(large.begin() + (long)w0, large.begin() + (long)w1);
+        std::vector<uint32_t> want(wave.size());
+        uint64_t sum = 0;
+        for (size_t i = 0; i < wave.size(); i++) sum += (want[i] = tableau_blocks(wave[i], maxb));
+        std::vector<uint32_t> blocks(wave.size());
+        uint64_t used = 0;
+        for (size_t i = 0; i < wave.size(); i++) {
+            blocks[i] = sum <= (uint64_t)maxb ? want[i]
+                                              : std::max<uint32_t>(1, (uint32_t)((uint64_t)want[i] * (uint64_t)maxb / sum));
+            used += blocks[i];
+        }
+        // rounding up to one CTA each can exceed maxb by a little: trim the largest
+        while (used > (uint64_t)maxb) {
+            size_t big = 0;
+            for (size_t i = 1; i < wave.size(); i++)
+                if (blocks[i] > blocks[big]) big = i;
+            if (blocks[big] <= 1) break;
+            blocks[big]--;
+            used--;
+        }
+        const int r = reference_batch(wave, blocks, !recompute, nullptr);
         if (r != STIM_OK) return r;
     }
     return STIM_OK;

@@ -85,6 +85,7 @@ struct TabArgs {
     uint32_t *rnd;             // [max collapse ops per layer] scratch: random flags
     TabCtl *ctl;               // zeroed before launch
     int *status;
+    uint32_t nblk;             // CTAs working on this circuit (set by the launchers)
 };
 
 constexpr uint32_t kTableauThreads = 512;     // threads per CTA of the tableau kernel
@@ -93,6 +94,12 @@ cudaError_t launch_tableau_init(const TabArgs &a, cudaStream_t stream);
 // Cooperative launch; blocks * threads must be co-resident.
 cudaError_t launch_tableau(const TabArgs &a, uint32_t blocks, uint32_t threads, cudaStream_t stream);
 int tableau_max_blocks(uint32_t threads, int device);
+// One cooperative launch for several circuits: jobs[j] (device array, nblk set)
+// gets CTAs first[j] .. first[j] + jobs[j].nblk - 1; job_of[b] names CTA b's
+// circuit. blocks (the sum) must be co-resident: tableau_batch_max_blocks.
+cudaError_t launch_tableau_batch(const TabArgs *jobs, const uint32_t *job_of, const uint32_t *first, uint32_t blocks,
+                                 uint32_t threads, cudaStream_t stream);
+int tableau_batch_max_blocks(uint32_t threads, int device);
 
 // det[k][w] = XOR over m in D_k of rec[m][w] ^ ref(m), padding bits cleared.
 cudaError_t launch_detectors(const uint64_t *rec, uint64_t rec_stride, const uint64_t *det_ptr,

@@ -45,8 +45,10 @@ namespace {
 constexpr uint64_t kBarrierTimeoutNs = 2000000000ull;   // 2 s per wait
 constexpr uint32_t kListLimit = 16;                     // CNOT targets handled by list, else by mask
 
+// Barrier over the a.nblk CTAs of one tableau (the whole grid, or one
+// circuit's CTA range of a batched launch).
 __device__ __forceinline__ bool tab_barrier(const TabArgs &a) {
-    if (gridDim.x == 1) {
+    if (a.nblk == 1) {
         __syncthreads();
         return true;
     }
@@ -56,7 +58,7 @@ __device__ __forceinline__ bool tab_barrier(const TabArgs &a) {
         const unsigned g = *gen;
         __threadfence();
         const unsigned arrived = atomicAdd(&a.ctl->bar_count, 1u);
-        if (arrived == gridDim.x - 1) {
+        if (arrived == a.nblk - 1) {
             atomicExch(&a.ctl->bar_count, 0u);
             __threadfence();
             atomicAdd(&a.ctl->bar_gen, 1u);
@@ -317,15 +319,16 @@ __global__ void tableau_init_kernel(TabArgs a) {
     }
 }
 
+// The inverse-tableau walk of one circuit by CTA bid of its a.nblk CTAs.
 template <bool L1>
-__global__ void __launch_bounds__(512) tableau_kernel(TabArgs a) {
+__device__ __forceinline__ void tableau_body(const TabArgs &a, uint32_t bid) {
     const uint32_t lane = threadIdx.x & 31;
     const uint32_t wpb = blockDim.x >> 5;
-    const uint32_t gwarp = blockIdx.x * wpb + (threadIdx.x >> 5);
-    const uint32_t nwarps = gridDim.x * wpb;
-    const uint32_t gtid = blockIdx.x * blockDim.x + threadIdx.x;
-    const uint32_t nthreads = gridDim.x * blockDim.x;
-    const bool leader = blockIdx.x == 0 && threadIdx.x < 32;
+    const uint32_t gwarp = bid * wpb + (threadIdx.x >> 5);
+    const uint32_t nwarps = a.nblk * wpb;
+    const uint32_t gtid = bid * blockDim.x + threadIdx.x;
+    const uint32_t nthreads = a.nblk * blockDim.x;
+    const bool leader = bid == 0 && threadIdx.x < 32;
     __shared__ uint32_t s_first;
 
     uint32_t meas_off = 0;
@@ -483,6 +486,21 @@ __global__ void __launch_bounds__(512) tableau_kernel(TabArgs a) {
     }
 }
 
+template <bool L1>
+__global__ void __launch_bounds__(512) tableau_kernel(TabArgs a) {
+    tableau_body<L1>(a, blockIdx.x);
+}
+
+// Several circuits in one cooperative launch: CTA b works for circuit
+// job_of[b] as its CTA b - first[job_of[b]]; each circuit's CTAs meet only at
+// that circuit's barrier.
+__global__ void __launch_bounds__(512) tableau_batch_kernel(const TabArgs *jobs, const uint32_t *job_of,
+                                                            const uint32_t *first) {
+    const uint32_t j = job_of[blockIdx.x];
+    const TabArgs a = jobs[j];
+    tableau_body<false>(a, blockIdx.x - first[j]);
+}
+
 cudaError_t launch_tableau_init(const TabArgs &a, cudaStream_t stream) {
     const uint32_t threads = 256;
     uint32_t blocks = (a.n + threads - 1) / threads;
@@ -490,6 +508,24 @@ cudaError_t launch_tableau_init(const TabArgs &a, cudaStream_t stream) {
     if (blocks > 4096) blocks = 4096;
     tableau_init_kernel<<<blocks, threads, 0, stream>>>(a);
     return cudaGetLastError();
+}
+
+cudaError_t launch_tableau_batch(const TabArgs *jobs, const uint32_t *job_of, const uint32_t *first, uint32_t blocks,
+                                 uint32_t threads, cudaStream_t stream) {
+    const TabArgs *j = jobs;
+    const uint32_t *o = job_of, *f = first;
+    void *params[] = {(void *)&j, (void *)&o, (void *)&f};
+    return cudaLaunchCooperativeKernel((const void *)tableau_batch_kernel, dim3(blocks), dim3(threads), params, 0,
+                                       stream);
+}
+
+int tableau_batch_max_blocks(uint32_t threads, int device) {
+    int per_sm = 0, sms = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, tableau_batch_kernel, (int)threads, 0) != cudaSuccess)
+        return 1;
+    if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, device) != cudaSuccess) return 1;
+    const int b = per_sm * sms;
+    return b > 0 ? b : 1;
 }
 
 int tableau_max_blocks(uint32_t threads, int device) {
@@ -504,6 +540,7 @@ int tableau_max_blocks(uint32_t threads, int device) {
 
 cudaError_t launch_tableau(const TabArgs &a, uint32_t blocks, uint32_t threads, cudaStream_t stream) {
     TabArgs args = a;
+    args.nblk = blocks;
     void *params[] = {&args};
     if (blocks == 1)    // one CTA: the tableau stays in its L1, no grid barrier
         return cudaLaunchCooperativeKernel((const void *)tableau_kernel<true>, dim3(1), dim3(threads), params, 0,

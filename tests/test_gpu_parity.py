@@ -725,3 +725,25 @@ def test_reference_cache_reuses_equal_skeletons():
     sg.stim_reference_cache_set(256 << 20)
     for h in (a, b, c):
         h.close()
+
+
+def test_reference_many_batched_launch_with_scaled_ctas():
+    """Mid-size circuits whose tableaus together want more CTAs than can be
+    co-resident share batched cooperative launches with scaled-down CTA
+    counts; their references equal the one-at-a-time ones."""
+    rng = np.random.default_rng(2500)
+    texts = [W.random_clifford(int(n), 30, int(sd)) for n, sd in
+             zip(rng.integers(900, 1600, 14), rng.integers(0, 1000, 14))]
+    texts += [W.surface_code_memory(21, 4, 0.001), W.random_clifford(300, 60, 9)]
+    cs = [sg.Circuit(t) for t in texts]
+    sg.stim_reference_many([c.handle for c in cs], sg.STIM_RECOMPUTE)
+    batched = []
+    for c in cs:
+        r, d = c.reference()
+        batched.append((r.clone(), d.clone()))
+    for c, (r, d) in zip(cs, batched):
+        r2, d2 = c.reference(recompute=True)
+        torch.cuda.synchronize()
+        assert torch.equal(r, r2) and torch.equal(d, d2)
+    for c in cs:
+        c.close()
