@@ -497,8 +497,7 @@ __global__ void __launch_bounds__(512) tableau_kernel(TabArgs a) {
 __global__ void __launch_bounds__(512) tableau_batch_kernel(const TabArgs *jobs, const uint32_t *job_of,
                                                             const uint32_t *first) {
     const uint32_t j = job_of[blockIdx.x];
-    const TabArgs a = jobs[j];
-    tableau_body<false>(a, blockIdx.x - first[j]);
+    tableau_body<false>(jobs[j], blockIdx.x - first[j]);     // arguments read in place (global, cached)
 }
 
 cudaError_t launch_tableau_init(const TabArgs &a, cudaStream_t stream) {
