@@ -747,3 +747,35 @@ def test_reference_many_batched_launch_with_scaled_ctas():
         assert torch.equal(r, r2) and torch.equal(d, d2)
     for c in cs:
         c.close()
+
+
+def test_reference_cache_budget_evicts_least_recent():
+    """The cache keeps within its byte budget by dropping the least recently
+    used samples; dropped skeletons are computed again (a miss)."""
+    sg.stim_reference_cache_set(0)                 # empty
+    texts = [W.surface_code_memory(d, 4, 0.001) for d in (5, 7, 9)]
+    cs = [sg.Circuit(t) for t in texts]
+    sg.stim_reference_cache_set(256 << 20)
+    for c in cs:
+        c.reference()
+    torch.cuda.synchronize()
+    st = sg.stim_reference_cache_stats()
+    assert st["entries"] == 3
+    # one byte less than held: exactly the least recently used entry (d=5) goes
+    sg.stim_reference_cache_set(st["bytes"] - 1)
+    st2 = sg.stim_reference_cache_stats()
+    assert st2["entries"] == 2 and st2["bytes"] < st["bytes"]
+    # a new handle of the evicted skeleton misses; one of a kept skeleton hits
+    before = sg.stim_reference_cache_stats()
+    again = sg.Circuit(W.surface_code_memory(5, 4, 0.02))
+    again.reference()
+    torch.cuda.synchronize()
+    mid = sg.stim_reference_cache_stats()
+    assert mid["misses"] == before["misses"] + 1 and mid["hits"] == before["hits"]
+    kept = sg.Circuit(W.surface_code_memory(9, 4, 0.02))
+    kept.reference()
+    torch.cuda.synchronize()
+    assert sg.stim_reference_cache_stats()["hits"] == mid["hits"] + 1
+    sg.stim_reference_cache_set(256 << 20)
+    for c in cs + [again, kept]:
+        c.close()
