@@ -5,8 +5,7 @@
 // Dynamic shared memory of one tile (byte offsets from the region start;
 // H = kTileHeaderBytes):
 //   [0, 80)                  Philox round keys of the seed
-//   [256, H)                 per-warp queues of deferred noise hits: 32 entries of
-//                            (op, word) per warp, then their first Philox blocks
+//   [256, H)                 per-warp queues of deferred noise hits
 //   [H, H + R)               program metadata (prog | rank_tab | segs) when it
 //                            fits the R = meta_region bytes reserved for it
 //   [H + R, ...)             frame rows (shared-memory layout)
@@ -429,35 +428,30 @@ __device__ __forceinline__ void xor_qubit_word(const Tile<W, C, GMEM> &t, uint32
     }
 }
 
-// Key material of a noise op's first draws: slot, tag | instruction ordinal,
-// and G[63] (block 0's first word below it: some error in the 64 shots).
-struct NoiseDraw {
-    uint32_t slot, ti;
-    uint64_t g63;
-};
-__device__ __forceinline__ NoiseDraw noise_draw(const FrameArgs &a, const DevOp op, uint32_t instr_off) {
+// First draws of a noise op on V words: bit i set when word i has an error.
+template <int V>
+__device__ __forceinline__ uint32_t noise_hits(const FrameArgs &a, const SmemKeys key, const DevOp op, uint32_t gw0,
+                                               uint32_t instr_off) {
     const uint32_t opc = op.a >> 28;
     const bool pair = opc == OP_DEP2;
     const uint32_t tbl = pair ? (op.slot >> 24) : op.b;
-    NoiseDraw d;
-    d.slot = pair ? (op.slot & 0xFFFFFFu) : op.slot;
-    d.ti = kTagNoise | (op.instr + instr_off);
-    d.g63 = __ldg(a.geo + kNoiseTableWords * tbl + 63u);
-    return d;
-}
-
-__device__ __forceinline__ void sts128(uint32_t a, uint4 v) {
-    asm volatile("st.shared.v4.u32 [%0], {%1, %2, %3, %4};" ::"r"(a), "r"(v.x), "r"(v.y), "r"(v.z), "r"(v.w)
-                 : "memory");
+    const uint32_t slot = pair ? (op.slot & 0xFFFFFFu) : op.slot;
+    const uint32_t ti = kTagNoise | (op.instr + instr_off);
+    const uint64_t g63 = __ldg(a.geo + kNoiseTableWords * tbl + 63u);
+    uint32_t hits = 0;
+#pragma unroll
+    for (int i = 0; i < V; i++) {
+        const uint4 blk = philox_sched(make_uint4(0u, slot, ti, gw0 + (uint32_t)i), key);
+        if ((uint64_t)blk.x < g63) hits |= 1u << i;
+    }
+    return hits;
 }
 
 // A deferred hit: entry = (op index within the CTA's layer) << 3 | word of the
-// tile, blk0 = the first Philox block that found it (kept in the queue, so it
-// is not drawn twice). Runs the general procedure and XORs the masks in.
+// tile. Redraws block 0, runs the general procedure and XORs the masks in.
 template <int W, int C, bool GMEM>
 __device__ __forceinline__ void deferred_hit(const FrameArgs &a, const SmemKeys key, const Tile<W, C, GMEM> &t,
-                                             uint32_t e, uint4 blk0, uint32_t first, uint32_t tile0,
-                                             uint32_t instr_off) {
+                                             uint32_t e, uint32_t first, uint32_t tile0, uint32_t instr_off) {
     const uint32_t oi = e >> 3, w = e & 7u;
     const uint4 ov = __ldg(reinterpret_cast<const uint4 *>(a.ops) + first + oi);
     const uint32_t opc = ov.x >> 28;
@@ -467,6 +461,7 @@ __device__ __forceinline__ void deferred_hit(const FrameArgs &a, const SmemKeys 
     const uint32_t slot = pair ? (ov.w & 0xFFFFFFu) : ov.w;
     const uint32_t instr = ov.z + instr_off;
     const uint32_t gw = (uint32_t)a.word0 + tile0 + w;
+    const uint4 blk0 = philox_sched(make_uint4(0u, slot, kTagNoise | instr, gw), key);
     uint64_t mxa, mza, mxb, mzb;
     noise_masks_slow(opc, a.geo + kNoiseTableWords * tbl, key, instr, slot, gw, blk0, mxa, mza, mxb, mzb);
     xor_qubit_word<W, C, GMEM>(t, ov.x & 0x0FFFFFFFu, w, mxa, mza);
@@ -494,7 +489,6 @@ __device__ __forceinline__ bool run_tile(const FrameArgs &a, unsigned char *dyn,
     const SmemKeys key{sbase};
     const uint32_t lane = threadIdx.x & 31u;
     const uint32_t qsa = sbase + kHitQueueOffset + (threadIdx.x >> 5) * (4u * kHitQueueCap);   // this warp's queue
-    const uint32_t qba = sbase + kHitBlockOffset + (threadIdx.x >> 5) * (16u * kHitQueueCap);  // and its blocks
     const uint32_t qlo = rank * a.Q;
     const uint32_t nq = a.n > qlo ? min(a.Q, a.n - qlo) : 0u;
     Tile<W, C, GMEM> t;
@@ -555,9 +549,7 @@ __device__ __forceinline__ bool run_tile(const FrameArgs &a, unsigned char *dyn,
                 uint32_t qn = 0;
                 auto flush = [&](uint32_t n) {
                     __syncwarp();
-                    if (lane < n)
-                        deferred_hit<W, C, GMEM>(a, key, t, lds32(qsa + 4u * lane), lds128(qba + 16u * lane), first,
-                                                 tile0, instr_off);
+                    if (lane < n) deferred_hit<W, C, GMEM>(a, key, t, lds32(qsa + 4u * lane), first, tile0, instr_off);
                     __syncwarp();
                 };
                 uint32_t g = threadIdx.x, seg_start = 0;
@@ -584,15 +576,13 @@ __device__ __forceinline__ bool run_tile(const FrameArgs &a, unsigned char *dyn,
                             if (j < dfrom) {
                                 if (act) frame_op<W, C, GMEM>(a, key, t, as_op(ov), wo, tile0, instr_off, meas_off);
                             } else {
-                                // padding lanes hold chain 0's op: a valid noise op
-                                const NoiseDraw nd = noise_draw(a, as_op(ov), instr_off);
-                                const uint32_t gw0 = (uint32_t)a.word0 + tile0 + wo;
+                                const uint32_t hits =
+                                    act ? noise_hits<V>(a, key, as_op(ov), (uint32_t)a.word0 + tile0 + wo, instr_off)
+                                        : 0u;
                                 const uint32_t oi = op0 + j - first;       // index within the CTA's layer
 #pragma unroll
                                 for (int i = 0; i < V; i++) {
-                                    uint4 blk = make_uint4(0u, 0u, 0u, 0u);
-                                    if (act) blk = philox_sched(make_uint4(0u, nd.slot, nd.ti, gw0 + (uint32_t)i), key);
-                                    const bool h = act && (uint64_t)blk.x < nd.g63;
+                                    const bool h = (hits >> i) & 1u;
                                     const uint32_t m = __ballot_sync(0xFFFFFFFFu, h);
                                     if (m) {
                                         const uint32_t cnt = __popc(m);
@@ -600,11 +590,9 @@ __device__ __forceinline__ bool run_tile(const FrameArgs &a, unsigned char *dyn,
                                             flush(qn);
                                             qn = 0;
                                         }
-                                        if (h) {
-                                            const uint32_t pos = qn + __popc(m & ((1u << lane) - 1u));
-                                            sts32(qsa + 4u * pos, (oi << 3) | (wo + (uint32_t)i));
-                                            sts128(qba + 16u * pos, blk);
-                                        }
+                                        if (h)
+                                            sts32(qsa + 4u * (qn + __popc(m & ((1u << lane) - 1u))),
+                                                  (oi << 3) | (wo + (uint32_t)i));
                                         qn += cnt;
                                     }
                                 }

@@ -33,14 +33,12 @@ struct FrameArgs {
 };
 
 // Dynamic shared memory of a frame tile: a header (round keys, then 32
-// queues of 32 deferred noise hits, one per warp: the hits' (op, word)
-// entries, then their first Philox blocks), the program metadata
+// queues of 32 deferred noise hits, one per warp), the program metadata
 // (meta_region bytes), then (shared layout) the frame rows of Q qubits x 2W
 // words.
 constexpr uint32_t kHitQueueOffset = 256;
 constexpr uint32_t kHitQueueCap = 32;          // entries per warp
-constexpr uint32_t kHitBlockOffset = kHitQueueOffset + 32 * kHitQueueCap * 4;
-constexpr uint32_t kTileHeaderBytes = kHitBlockOffset + 32 * kHitQueueCap * 16;
+constexpr uint32_t kTileHeaderBytes = kHitQueueOffset + 32 * kHitQueueCap * 4;
 
 // Largest CTA of a frame kernel with W words per tile: threads that apply ops
 // to two or four words at once need more registers. One-word tiles are sized
