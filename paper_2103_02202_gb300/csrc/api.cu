@@ -202,6 +202,10 @@ struct RefCache {
     size_t bytes = 0, cap = (size_t)256 << 20;
     uint64_t clock = 0, hits = 0, misses = 0;
 
+    bool enabled() {
+        std::lock_guard<std::mutex> g(mu);
+        return cap > 0;
+    }
     void evict_to(size_t limit) {          // lock held
         while (bytes > limit && !map.empty()) {
             auto old = map.begin();
@@ -367,7 +371,7 @@ int reference_finish(stim_circuit *c, RefJob *job) {
     int status = 0;
     cudaError_t e = cudaSuccess;
     if (job->launched) e = cudaMemcpyAsync(&status, c->d_status, sizeof(int), cudaMemcpyDeviceToHost, job->st);
-    const bool keep = job->launched && job->to_cache && ref_cache().cap > 0;
+    const bool keep = job->launched && job->to_cache && ref_cache().enabled();
     if (keep && e == cudaSuccess) {
         job->ref.resize(c->ref_words);
         job->detflag.resize(c->ref_words);
