@@ -779,3 +779,19 @@ def test_reference_cache_budget_evicts_least_recent():
     sg.stim_reference_cache_set(256 << 20)
     for c in cs + [again, kept]:
         c.close()
+
+
+def test_paper_teleportation_example_on_the_gpu():
+    """The paper's teleportation example (golden fixture): the final bit is
+    False in every GPU shot and the records equal the oracle's."""
+    import os
+    gold = {}
+    for line in open(os.path.join(os.path.dirname(__file__), "golden", "teleportation.txt")):
+        if line.strip() and line[0] != "#":
+            k, v = line.rstrip("\n").split(" ", 1)
+            gold[k] = v
+    txt = gold["circuit"].replace(";", "\n") + "\n"
+    mb, _ = gpu_sample(txt, 10000, 12)
+    assert np.all(mb[:, -1] == int(gold["final_measurement"]))
+    om, _ = oracle.Circuit(txt).sample(np.arange(10000), 12, threads=8)
+    np.testing.assert_array_equal(mb, om)

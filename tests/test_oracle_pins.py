@@ -798,3 +798,30 @@ def test_pauli_channel_parse_errors():
                 "PAULI_CHANNEL_2(" + ", ".join(["0.01"] * 15) + ") 1 1\n"):
         with pytest.raises(ValueError):
             oracle.Circuit(bad)
+
+
+def _teleportation_golden():
+    gold = {}
+    for line in open(os.path.join(GOLD, "teleportation.txt")):
+        if line.strip() and line[0] != "#":
+            k, v = line.rstrip("\n").split(" ", 1)
+            gold[k] = v
+    return gold["circuit"].replace(";", "\n") + "\n", int(gold["final_measurement"])
+
+
+def test_paper_teleportation_example_golden():
+    """The paper's teleportation example: with Bob's corrections applied from
+    Alice's two records, the uncomputed qubit always measures False, while
+    Alice's bits are random. Checked on the reference, the frame shots and the
+    state vector (which also confirms the final bit is deterministic)."""
+    txt, final = _teleportation_golden()
+    ref, det = oracle.Circuit(txt).reference()
+    assert int(ref[-1]) == final and int(det[-1]) == 1
+    meas, _ = oracle.Circuit(txt).sample(np.arange(4096), seed=11, threads=4)
+    assert np.all(meas[:, -1] == final)
+    assert 0.45 < meas[:, 0].mean() < 0.55 and 0.45 < meas[:, 1].mean() < 0.55
+    br = sv.branches(txt)
+    assert len(br) == 4 and all(k[-1] == final for k in br)
+    # without Bob's corrections the final bit is random
+    bare = txt.replace("CX rec[-2] 9\n", "").replace("CZ rec[-1] 9\n", "")
+    assert {k[-1] for k in sv.branches(bare)} == {0, 1}
