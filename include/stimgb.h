@@ -55,7 +55,8 @@ extern "C" {
 #define STIM_SHOT_MAJOR   0x1  /* row s = shot s; bit r = measurement/detector r */
 #define STIM_DEVICE       0x0  /* output pointers are device memory */
 #define STIM_HOST         0x2  /* output pointers are host memory */
-#define STIM_RECOMPUTE    0x4  /* stim_reference_sample: ignore the cached sample */
+#define STIM_RECOMPUTE    0x4  /* stim_reference_sample, stim_reference_many: run the tableau
+                                  again (ignore the handle's sample and the reference cache) */
 #define STIM_ASYNC        0x8  /* stim_frame_sample(_ex): return once the work and the host
                                   copies are enqueued on the stream; see stim_frame_sample_ex */
 
