@@ -126,6 +126,28 @@ int stim_compile(const char *text, size_t len, stim_circuit **out);
 /* Counts of a compiled circuit. */
 int stim_info_get(const stim_circuit *c, stim_info *out);
 
+/* Shape of the frame-kernel program of a circuit for a cluster of
+ * cluster_size CTAs (1, 2, 4 or 8), as the frame sampler builds it: fused
+ * layers folded into merged layers of per-thread op chains, grouped into
+ * segments of equal op signature (host-only, no GPU). */
+typedef struct {
+    uint32_t cluster_size;
+    uint32_t qubits_per_cta;       /* Q = ceil(num_qubits / cluster_size) */
+    uint64_t merged_layers;        /* merged layers executed per shot (loops unrolled) */
+    uint64_t stored_layers;        /* merged layers stored (loop bodies once) */
+    uint64_t segments, chains, ops;
+    uint32_t max_chain_ops;        /* longest chain (ops one thread runs between barriers) */
+    uint32_t max_cta_ops;          /* largest op range of one CTA in one merged layer */
+    uint64_t deferred_ops;         /* trailing noise ops applied after their chain */
+    uint64_t tails_repeating_qubit;/* chains whose deferred tail names a qubit twice
+                                      (always 0 when cluster_size > 1) */
+    uint64_t feedforward_not_first;/* classically controlled ops that are not the first op
+                                      of their chain (always 0) */
+} stim_frame_program_info;
+
+/* Errors: STIM_E_INVALID_ARG (NULL argument, cluster_size not 1, 2, 4 or 8), STIM_E_OOM. */
+int stim_frame_program_info_get(const stim_circuit *c, int cluster_size, stim_frame_program_info *out);
+
 /* Frees the handle and its device memory (synchronizes the device first). */
 void stim_free(stim_circuit *c);
 

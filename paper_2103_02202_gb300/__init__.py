@@ -29,7 +29,8 @@ __all__ = [
     "STIM_E_TIMEOUT", "STIM_E_BUSY", "STIM_E_UNSUPPORTED", "STIM_E_CAPACITY", "STIM_ASYNC",
     "stim_frame_sample_detections",
     "STIM_MEAS_MAJOR", "STIM_SHOT_MAJOR", "STIM_DEVICE", "STIM_HOST", "STIM_RECOMPUTE",
-    "StimError", "library", "library_path", "stim_compile", "stim_info_get", "stim_free",
+    "StimError", "library", "library_path", "stim_compile", "stim_info_get", "stim_frame_program_info_get",
+    "stim_free",
     "stim_last_error", "stim_reference_sample", "stim_reference_many", "stim_reference_cache_set",
     "stim_reference_cache_stats", "stim_frame_sample", "stim_frame_sample_ex",
     "Circuit", "EXPORTED_SYMBOLS", "stim_frame_sample_noalloc", "stim_batch_create", "stim_batch_sample",
@@ -71,6 +72,15 @@ class StimInfo(ctypes.Structure):
                 ("num_noise_targets", ctypes.c_uint64), ("num_instructions", ctypes.c_uint64),
                 ("num_layers", ctypes.c_uint64), ("num_program_layers", ctypes.c_uint64),
                 ("num_observables", ctypes.c_uint64), ("reference_key", ctypes.c_uint64)]
+
+
+class StimFrameProgramInfo(ctypes.Structure):
+    _fields_ = [("cluster_size", ctypes.c_uint32), ("qubits_per_cta", ctypes.c_uint32),
+                ("merged_layers", ctypes.c_uint64), ("stored_layers", ctypes.c_uint64),
+                ("segments", ctypes.c_uint64), ("chains", ctypes.c_uint64), ("ops", ctypes.c_uint64),
+                ("max_chain_ops", ctypes.c_uint32), ("max_cta_ops", ctypes.c_uint32),
+                ("deferred_ops", ctypes.c_uint64), ("tails_repeating_qubit", ctypes.c_uint64),
+                ("feedforward_not_first", ctypes.c_uint64)]
 
 
 class StimTileHint(ctypes.Structure):
@@ -116,6 +126,7 @@ _U64 = ctypes.c_uint64
 _SIGNATURES = {
     "stim_compile": (ctypes.c_int, [ctypes.c_char_p, ctypes.c_size_t, ctypes.POINTER(_VP)]),
     "stim_info_get": (ctypes.c_int, [_VP, ctypes.POINTER(StimInfo)]),
+    "stim_frame_program_info_get": (ctypes.c_int, [_VP, ctypes.c_int, ctypes.POINTER(StimFrameProgramInfo)]),
     "stim_free": (None, [_VP]),
     "stim_last_error": (ctypes.c_int, [ctypes.c_char_p, ctypes.c_size_t]),
     "stim_reference_sample": (ctypes.c_int, [_VP, _VP, _VP, ctypes.c_int, _VP]),
@@ -196,6 +207,13 @@ def stim_info_get(handle: int) -> dict:
     info = StimInfo()
     _check(library().stim_info_get(handle, ctypes.byref(info)))
     return {k: int(getattr(info, k)) for k, _ in StimInfo._fields_}
+
+
+def stim_frame_program_info_get(handle: int, cluster_size: int) -> dict:
+    """Shape of the frame-kernel program for a cluster of cluster_size CTAs (host only)."""
+    info = StimFrameProgramInfo()
+    _check(library().stim_frame_program_info_get(handle, int(cluster_size), ctypes.byref(info)))
+    return {name: getattr(info, name) for name, _ in StimFrameProgramInfo._fields_}
 
 
 def stim_free(handle: int) -> None:

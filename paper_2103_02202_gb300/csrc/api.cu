@@ -754,6 +754,46 @@ int stim_info_get(const stim_circuit *c, stim_info *out) {
     return STIM_OK;
 }
 
+int stim_frame_program_info_get(const stim_circuit *c, int cluster_size, stim_frame_program_info *out) {
+    if (!c || !out) return fail(STIM_E_INVALID_ARG, "stim_frame_program_info_get: null argument");
+    if (cluster_size != 1 && cluster_size != 2 && cluster_size != 4 && cluster_size != 8)
+        return fail(STIM_E_INVALID_ARG, "stim_frame_program_info_get: cluster_size must be 1, 2, 4 or 8");
+    FrameProgram fp;
+    try {
+        build_frame_program(c->hp, cluster_size, &fp);
+    } catch (const std::bad_alloc &) {
+        return fail(STIM_E_OOM, "out of host memory building the frame program");
+    }
+    *out = stim_frame_program_info{};
+    out->cluster_size = (uint32_t)cluster_size;
+    out->qubits_per_cta = fp.Q;
+    out->merged_layers = fp.merged_layers_exec;
+    for (const ProgEntry &e : fp.prog) out->stored_layers += e.kind == ENT_LAYER;
+    out->segments = fp.segs.size();
+    out->ops = fp.ops.size();
+    out->max_cta_ops = fp.max_rank_ops;
+    auto global_q = [&](uint32_t ref) { return (ref >> 24) * fp.Q + (ref & 0xFFFFFFu); };
+    for (const FrameSeg &sg : fp.segs) {
+        out->chains += sg.count;
+        out->max_chain_ops = std::max(out->max_chain_ops, sg.len);
+        out->deferred_ops += (uint64_t)sg.count * (sg.len - sg.defer_from);
+        for (uint32_t k = 0; k < sg.count; k++) {
+            const DevOp *ch = fp.ops.data() + sg.op_begin + (size_t)k * sg.len;
+            std::vector<uint32_t> qs;
+            for (uint32_t j = 0; j < sg.len; j++) {
+                const uint32_t opc = ch[j].a >> 28;
+                if ((opc == OP_FFX || opc == OP_FFZ) && j > 0) out->feedforward_not_first++;
+                if (j < sg.defer_from) continue;
+                qs.push_back(global_q(ch[j].a & 0x0FFFFFFFu));
+                if (opc == OP_DEP2) qs.push_back(global_q(ch[j].b));
+            }
+            std::sort(qs.begin(), qs.end());
+            if (std::adjacent_find(qs.begin(), qs.end()) != qs.end()) out->tails_repeating_qubit++;
+        }
+    }
+    return STIM_OK;
+}
+
 int stim_reference_cache_set(size_t budget_bytes) {
     RefCache &rc = ref_cache();
     std::lock_guard<std::mutex> g(rc.mu);

@@ -689,11 +689,19 @@ class FrameBuilder {
             const uint32_t tot = e.n_gate + e.n_noise + e.n_collapse;
             const DevOp *ops = hp_.ops.data() + e.op_begin;
             bool fold = !chains_.empty();
+            std::vector<uint32_t> grow;      // ops this layer would append to each open chain
             for (uint32_t i = 0; i < tot && fold; i++) {
                 if (op_is_feedforward(ops[i].a >> 24)) fold = false;       // reads a record of another thread
                 if (frame_opcode(ops[i].a >> 24) == OP_COUNT) continue;     // no frame action
                 const int own = chain_of(ops[i]);
-                if (own == -2 || (own >= 0 && chains_[own].ops.size() >= kMaxChainOps)) fold = false;
+                if (own == -2) {
+                    fold = false;
+                } else if (own >= 0) {
+                    // several targets of one instruction may join one chain
+                    if (grow.empty()) grow.assign(chains_.size(), 0);
+                    grow[own] += frame_opcode(ops[i].a >> 24) == OP_SX ? 3u : 1u;
+                    if (chains_[own].ops.size() + grow[own] > kMaxChainOps) fold = false;
+                }
             }
             if (!fold && !chains_.empty()) emitted += emit();
             for (uint32_t i = 0; i < tot; i++) {

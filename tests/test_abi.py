@@ -2,6 +2,8 @@
 declares; the host compiler (no GPU needed) agrees with the oracle's counts
 and rejects malformed circuits."""
 import ctypes
+
+import numpy as np
 import os
 import re
 
@@ -223,3 +225,65 @@ def test_reference_cache_controls_without_gpu():
     sg.stim_reference_cache_set(0)
     assert sg.stim_reference_cache_stats()["entries"] == 0
     sg.stim_reference_cache_set(256 << 20)
+
+
+def _fp(text, C):
+    h = sg.stim_compile(text)
+    try:
+        return sg.stim_frame_program_info_get(h, C)
+    finally:
+        sg.stim_free(h)
+
+
+def _noisy_wide(rng, n, L):
+    """Random circuits whose chains end in several noise ops on shared qubits."""
+    lines = []
+    nmeas = 0
+    for _ in range(L):
+        k = rng.random()
+        if k < 0.25:
+            a, b = rng.choice(n, 2, replace=False)
+            lines.append(f"{str(rng.choice(['CX', 'CZ']))} {a} {b}")
+        elif k < 0.6:
+            ch = str(rng.choice(["X_ERROR", "Y_ERROR", "DEPOLARIZE1"]))
+            lines.append(f"{ch}(0.1) " + " ".join(map(str, rng.choice(n, int(rng.integers(1, n + 1)), replace=False))))
+        elif k < 0.75:
+            a, b = rng.choice(n, 2, replace=False)
+            lines.append(f"DEPOLARIZE2(0.1) {a} {b}")
+        elif k < 0.85 and nmeas:
+            lines.append(f"CX rec[-{int(rng.integers(1, nmeas + 1))}] {int(rng.integers(n))}")
+        else:
+            q = int(rng.integers(n))
+            lines.append(f"M {q}")
+            nmeas += 1
+    return "\n".join(lines) + "\nM " + " ".join(map(str, range(n))) + "\n"
+
+
+def test_frame_program_invariants():
+    """Host-only checks of the frame builder: chain structure does not depend
+    on the cluster size; chains stay within 12 ops; with a cluster no
+    deferred tail names a qubit twice (duplicate addresses in one cluster
+    reduction lost updates); classically controlled ops always start their
+    chain (they read a record written before the previous barrier)."""
+    rng = np.random.default_rng(2600)
+    single_repeats = 0
+    for _ in range(40):
+        n = int(rng.integers(3, 40))
+        text = _noisy_wide(rng, n, int(rng.integers(10, 80)))
+        infos = {C: _fp(text, C) for C in (1, 2, 4, 8)}
+        for C, inf in infos.items():
+            assert inf["chains"] == infos[1]["chains"] and inf["ops"] == infos[1]["ops"]
+            assert inf["max_chain_ops"] <= 12
+            assert inf["feedforward_not_first"] == 0
+            assert inf["deferred_ops"] <= infos[1]["deferred_ops"]
+            if C > 1:
+                assert inf["tails_repeating_qubit"] == 0
+        single_repeats += infos[1]["tails_repeating_qubit"]
+    assert single_repeats > 0      # single CTAs keep long tails (their local reductions merge duplicates)
+    dup = ("H 0 1 2 3\nCZ 2 0\nCZ 1 3\nX_ERROR(0.5) 0\nX_ERROR(0.5) 0\nY_ERROR(0.5) 0\n"
+           "DEPOLARIZE1(0.5) 0\nCX 0 1\nM 0 1 2 3\n")
+    one, two = _fp(dup, 1), _fp(dup, 2)
+    assert one["tails_repeating_qubit"] == 1 and two["tails_repeating_qubit"] == 0
+    assert two["deferred_ops"] == one["deferred_ops"] - 3
+    with pytest.raises(sg.StimError):
+        _fp(dup, 3)
