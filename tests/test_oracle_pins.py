@@ -825,3 +825,82 @@ def test_paper_teleportation_example_golden():
     # without Bob's corrections the final bit is random
     bare = txt.replace("CX rec[-2] 9\n", "").replace("CZ rec[-1] 9\n", "")
     assert {k[-1] for k in sv.branches(bare)} == {0, 1}
+
+
+# ---------------------------------------------------------------------------
+# Section 2.3, "Inverting Tableaus": the terms on qubit b of T(X_a), T(Z_a)
+# determine the terms on qubit a of T^-1(X_b), T^-1(Z_b): x(T^-1 X_b)_a =
+# z(T Z_a)_b, z(T^-1 X_b)_a = z(T X_a)_b, x(T^-1 Z_b)_a = x(T Z_a)_b,
+# z(T^-1 Z_b)_a = x(T X_a)_b (the symplectic transpose).
+# ---------------------------------------------------------------------------
+_TERM = {"I": (0, 0), "X": (1, 0), "Y": (1, 1), "Z": (0, 1)}
+_NAME = {v: k for k, v in _TERM.items()}
+
+
+def _inverse_terms(tx_a_b, tz_a_b):
+    """(term of T(X_a) on b, term of T(Z_a) on b) -> (term of T^-1(X_b) on a, of T^-1(Z_b) on a)."""
+    (xx, xz), (zx, zz) = _TERM[tx_a_b], _TERM[tz_a_b]
+    return _NAME[(zz, xz)], _NAME[(zx, xx)]
+
+
+def test_inverse_locality_golden():
+    """The paper's worked example of inverting a tableau locally: the rule
+    above turns its four given terms of T into the four terms of T^-1 it
+    prints."""
+    rows = [l.split() for l in open(os.path.join(GOLD, "inverse_locality.txt")) if l.strip() and l[0] != "#"]
+    given = {r[1]: r[3] for r in rows if r[0] == "given"}
+    derived = {r[1]: r[3] for r in rows if r[0] == "derived"}
+    inv_x, inv_z = _inverse_terms(given["X3"], given["Z3"])
+    assert (inv_x, inv_z) == (derived["X4"], derived["Z4"])
+
+
+_DAGGER = {"H": "H", "S": "S_DAG", "S_DAG": "S", "SQRT_X": "SQRT_X_DAG", "SQRT_X_DAG": "SQRT_X",
+           "SQRT_Y": "SQRT_Y_DAG", "SQRT_Y_DAG": "SQRT_Y", "X": "X", "Y": "Y", "Z": "Z", "CX": "CX", "CZ": "CZ"}
+
+
+def _propagate(gates, n, x, z):
+    """Pauli terms (no sign) of a generator pushed through the gate list with
+    the oracle's per-gate conjugation tables."""
+    x, z = list(x), list(z)
+    for name, qs in gates:
+        lx = sum(x[q] << i for i, q in enumerate(qs))
+        lz = sum(z[q] << i for i, q in enumerate(qs))
+        ox, oz, _ = oracle.conj_local(name, lx, lz)
+        for i, q in enumerate(qs):
+            x[q], z[q] = (ox >> i) & 1, (oz >> i) & 1
+    return x, z
+
+
+def test_inverse_tableau_terms_are_the_local_transpose():
+    """For random Clifford circuits, the tableau of the reversed, daggered
+    circuit (built from the oracle's gate tables) has exactly the Pauli terms
+    the paper's local rule derives from the circuit's own tableau. The oracle
+    itself never inverts a tableau; what this checks of it is that every
+    per-gate term table preserves commutation and undoes its dagger's at the
+    term level (a non-symplectic table entry fails). Signs are not compared:
+    a dagger pair has the same terms."""
+    rng = np.random.default_rng(2800)
+    one = [g for g in _DAGGER if g not in ("CX", "CZ")]
+    for _ in range(30):
+        n = int(rng.integers(2, 7))
+        gates = []
+        for _ in range(int(rng.integers(5, 40))):
+            if rng.random() < 0.4:
+                a, b = (int(v) for v in rng.choice(n, 2, replace=False))
+                gates.append((str(rng.choice(["CX", "CZ"])), (a, b)))
+            else:
+                gates.append((str(rng.choice(one)), (int(rng.integers(n)),)))
+        inverse = [(_DAGGER[g], qs) for g, qs in reversed(gates)]
+        unit = [[int(i == j) for j in range(n)] for i in range(n)]
+        zero = [0] * n
+        T = {("X", a): _propagate(gates, n, unit[a], zero) for a in range(n)}
+        T.update({("Z", a): _propagate(gates, n, zero, unit[a]) for a in range(n)})
+        Ti = {("X", b): _propagate(inverse, n, unit[b], zero) for b in range(n)}
+        Ti.update({("Z", b): _propagate(inverse, n, zero, unit[b]) for b in range(n)})
+        for a in range(n):
+            for b in range(n):
+                tx = _NAME[(T[("X", a)][0][b], T[("X", a)][1][b])]
+                tz = _NAME[(T[("Z", a)][0][b], T[("Z", a)][1][b])]
+                want_x, want_z = _inverse_terms(tx, tz)
+                assert _NAME[(Ti[("X", b)][0][a], Ti[("X", b)][1][a])] == want_x
+                assert _NAME[(Ti[("Z", b)][0][a], Ti[("Z", b)][1][a])] == want_z
