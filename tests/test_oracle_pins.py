@@ -904,3 +904,34 @@ def test_inverse_tableau_terms_are_the_local_transpose():
                 want_x, want_z = _inverse_terms(tx, tz)
                 assert _NAME[(Ti[("X", b)][0][a], Ti[("X", b)][1][a])] == want_x
                 assert _NAME[(Ti[("Z", b)][0][a], Ti[("Z", b)][1][a])] == want_z
+
+
+def test_stabilizer_facts_from_the_paper():
+    """Section 2.2's examples: +Z stabilizes |0> but not |1>, +X stabilizes
+    |0> + |1>, -YY stabilizes |00> + |11>, and |000> is the state stabilized
+    by ZII, IZI, IIZ. As matrices, and as
+    what the oracle's tableau reports for the matching measurements: a fresh
+    qubit measures 0 in Z deterministically; on the Bell pair the two Y-basis
+    outcomes have odd parity (eigenvalue -1 of YY), the second one fixed by
+    the first."""
+    P = {"I": np.eye(2), "X": np.array([[0, 1], [1, 0]]), "Y": np.array([[0, -1j], [1j, 0]]),
+         "Z": np.diag([1, -1])}
+    zero, one, plus = np.array([1, 0]), np.array([0, 1]), np.array([1, 1]) / math.sqrt(2)
+    np.testing.assert_allclose(P["Z"] @ zero, zero)
+    assert not np.allclose(P["Z"] @ one, one)                  # +Z does not stabilize |1>
+    np.testing.assert_allclose(P["X"] @ plus, plus)            # +X stabilizes |0> + |1>
+    bell = np.array([1, 0, 0, 1]) / math.sqrt(2)
+    np.testing.assert_allclose(-np.kron(P["Y"], P["Y"]) @ bell, bell)
+    z3 = np.zeros(8)
+    z3[0] = 1
+    for k in range(3):
+        ops = [P["Z"] if i == k else P["I"] for i in range(3)]
+        np.testing.assert_allclose(np.kron(np.kron(ops[0], ops[1]), ops[2]) @ z3, z3)
+    ref, det = oracle.Circuit("H 0\nMX 0\nX 1\nM 1\n").reference()
+    assert list(ref) == [0, 1] and list(det) == [1, 1]         # |0> + |1> reads +1 in X; |1> reads 1 in Z
+    ref, det = oracle.Circuit("M 0 1 2\n").reference()
+    assert list(ref) == [0, 0, 0] and list(det) == [1, 1, 1]
+    ref, det = oracle.Circuit("H 0\nCX 0 1\nMY 0 1\n").reference()
+    assert list(det) == [0, 1] and int(ref[0]) ^ int(ref[1]) == 1
+    meas, _ = oracle.Circuit("H 0\nCX 0 1\nMY 0 1\n").sample(np.arange(512), seed=2)
+    assert np.all(meas[:, 0] ^ meas[:, 1] == 1) and 0.4 < meas[:, 0].mean() < 0.6
