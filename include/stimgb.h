@@ -213,6 +213,19 @@ int stim_reference_cache_set(size_t budget_bytes);
 int stim_reference_cache_stats(uint64_t *hits, uint64_t *misses, uint64_t *entries, uint64_t *bytes);
 
 /*
+ * stim_debug_fail_allocations -- fault injection for tests: of the device
+ * allocations the single-circuit paths make next (upload of a compiled
+ * circuit, staging buffers of stim_frame_sample_ex, tableau scratch of the
+ * reference sample), the first `skip` succeed and the following `count` fail
+ * as if the device were out of memory, so the calls that make them return
+ * STIM_E_OOM. A failed call leaves its handle usable; a later call allocates
+ * afresh. count = 0 turns injection off. Process-wide, thread-safe; no GPU
+ * needed to set it.
+ * Errors: STIM_E_INVALID_ARG (a negative argument).
+ */
+int stim_debug_fail_allocations(int skip, int count);
+
+/*
  * stim_frame_sample -- bulk Pauli-frame sampling (Section 3): num_shots shots
  * with global shot indices 0..num_shots-1 under `seed`.
  *

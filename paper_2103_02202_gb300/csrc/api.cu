@@ -2,6 +2,7 @@
 #include <cuda_runtime.h>
 
 #include <algorithm>
+#include <atomic>
 #include <map>
 #include <cstdio>
 #include <cstring>
@@ -37,10 +38,47 @@ int cuda_fail(cudaError_t e, const char *what) {
         if (_e != cudaSuccess) return cuda_fail(_e, what); \
     } while (0)
 
+// Device allocations of the single-circuit paths go through dev_malloc, so a
+// test can make the next few fail as if the device were out of memory
+// (stim_debug_fail_allocations) and check that every error path leaves the
+// handle usable.
+std::mutex g_inject_mu;
+int g_inject_skip = 0, g_inject_fail = 0;
+std::atomic<bool> g_inject_armed{false};
+
+bool injected_failure() {
+    if (!g_inject_armed.load()) return false;
+    std::lock_guard<std::mutex> g(g_inject_mu);
+    if (g_inject_skip > 0) {
+        g_inject_skip--;
+        return false;
+    }
+    if (g_inject_fail > 0) {
+        g_inject_fail--;
+        if (g_inject_fail == 0) g_inject_armed.store(false);
+        return true;
+    }
+    return false;
+}
+
+cudaError_t dev_malloc(void **p, size_t bytes) {
+    if (injected_failure()) return cudaErrorMemoryAllocation;
+    return cudaMalloc(p, bytes);
+}
+
+cudaError_t dev_malloc_async(void **p, size_t bytes, cudaStream_t st) {
+    if (injected_failure()) return cudaErrorMemoryAllocation;
+    return cudaMallocAsync(p, bytes, st);
+}
+
 template <typename T>
 int upload(T **dst, const std::vector<T> &src, const char *what) {
     size_t bytes = std::max<size_t>(src.size(), 1) * sizeof(T);
-    STIMGB_CK(cudaMalloc((void **)dst, bytes), what);
+    if (*dst) {         // left by an earlier attempt that failed part way
+        cudaFree(*dst);
+        *dst = nullptr;
+    }
+    STIMGB_CK(dev_malloc((void **)dst, bytes), what);
     if (!src.empty()) STIMGB_CK(cudaMemcpy(*dst, src.data(), src.size() * sizeof(T), cudaMemcpyHostToDevice), what);
     return STIM_OK;
 }
@@ -53,7 +91,7 @@ int grow(uint64_t **p, size_t *cap, size_t words, const char *what) {
         *p = nullptr;
         *cap = 0;
     }
-    STIMGB_CK(cudaMalloc((void **)p, std::max<size_t>(words, 1) * 8), what);
+    STIMGB_CK(dev_malloc((void **)p, std::max<size_t>(words, 1) * 8), what);
     *cap = words;
     return STIM_OK;
 }
@@ -162,22 +200,34 @@ int ensure_device(stim_circuit *c) {
     STIMGB_CK(cudaGetDevice(&dev), "cudaGetDevice");
     if (c->device >= 0) {
         if (c->device != dev) return fail(STIM_E_INVALID_ARG, "circuit handle was uploaded to another device");
-        return STIM_OK;
+        if (c->fprog[0].C == 1) return STIM_OK;
+        const DevFrameProgram *fp1;     // an earlier upload stopped before the single-CTA program
+        return frame_program(c, 1, &fp1);
     }
     const HostProgram &hp = c->hp;
+    // a failure part way frees what was uploaded, so a later call starts afresh
+    auto drop = [&](int r) {
+        for (void **p : {(void **)&c->d_prog, (void **)&c->d_ops, (void **)&c->d_geo, (void **)&c->d_det_ptr,
+                         (void **)&c->d_det_meas, (void **)&c->d_ref, (void **)&c->d_detflag, (void **)&c->d_status}) {
+            cudaFree(*p);
+            *p = nullptr;
+        }
+        return r;
+    };
     int r;
-    if ((r = upload(&c->d_prog, hp.prog, "upload program")) != STIM_OK) return r;
-    if ((r = upload(&c->d_ops, hp.ops, "upload ops")) != STIM_OK) return r;
-    if ((r = upload(&c->d_geo, hp.geo, "upload noise tables")) != STIM_OK) return r;
-    if ((r = upload(&c->d_det_ptr, hp.det_ptr, "upload detectors")) != STIM_OK) return r;
-    if ((r = upload(&c->d_det_meas, hp.det_meas, "upload detectors")) != STIM_OK) return r;
+    if ((r = upload(&c->d_prog, hp.prog, "upload program")) != STIM_OK) return drop(r);
+    if ((r = upload(&c->d_ops, hp.ops, "upload ops")) != STIM_OK) return drop(r);
+    if ((r = upload(&c->d_geo, hp.geo, "upload noise tables")) != STIM_OK) return drop(r);
+    if ((r = upload(&c->d_det_ptr, hp.det_ptr, "upload detectors")) != STIM_OK) return drop(r);
+    if ((r = upload(&c->d_det_meas, hp.det_meas, "upload detectors")) != STIM_OK) return drop(r);
     c->ref_words = std::max<size_t>((hp.num_meas + 63) / 64, 1);
-    STIMGB_CK(cudaMalloc((void **)&c->d_ref, c->ref_words * 8), "alloc reference");
-    STIMGB_CK(cudaMalloc((void **)&c->d_detflag, c->ref_words * 8), "alloc reference");
-    STIMGB_CK(cudaMalloc((void **)&c->d_status, sizeof(int)), "alloc status");
-    STIMGB_CK(cudaMemset(c->d_ref, 0, c->ref_words * 8), "memset");
-    STIMGB_CK(cudaMemset(c->d_detflag, 0, c->ref_words * 8), "memset");
-    STIMGB_CK(cudaMemset(c->d_status, 0, sizeof(int)), "memset");
+    cudaError_t e = dev_malloc((void **)&c->d_ref, c->ref_words * 8);
+    if (e == cudaSuccess) e = dev_malloc((void **)&c->d_detflag, c->ref_words * 8);
+    if (e == cudaSuccess) e = dev_malloc((void **)&c->d_status, sizeof(int));
+    if (e == cudaSuccess) e = cudaMemset(c->d_ref, 0, c->ref_words * 8);
+    if (e == cudaSuccess) e = cudaMemset(c->d_detflag, 0, c->ref_words * 8);
+    if (e == cudaSuccess) e = cudaMemset(c->d_status, 0, sizeof(int));
+    if (e != cudaSuccess) return drop(cuda_fail(e, "alloc reference"));
     c->device = dev;
     const DevFrameProgram *fp1;
     return frame_program(c, 1, &fp1);     // the single-CTA program is always resident
@@ -313,7 +363,7 @@ int reference_prepare(stim_circuit *c, cudaStream_t st, bool use_cache, RefJob *
     const size_t bytes_tx = col_words * 8, bytes_sign = (size_t)2 * n * 4, bytes_klist = (size_t)n * 4 + 64;
     const size_t bytes_kmask = (size_t)nw * 8 + 64, bytes_rnd = (size_t)std::max<uint32_t>(hp.max_layer_ops, 1) * 4 + 64;
     const size_t total = 2 * bytes_tx + 2 * bytes_sign + bytes_klist + bytes_kmask + bytes_rnd + 256 + 1024;
-    STIMGB_CK(cudaMallocAsync((void **)&job->blob, total, st), "alloc tableau");
+    STIMGB_CK(dev_malloc_async((void **)&job->blob, total, st), "alloc tableau");
     size_t off = 0;
     auto take = [&](size_t b) {
         char *p = job->blob + off;
@@ -431,7 +481,7 @@ int reference_batch(const std::vector<stim_circuit *> &cs, const std::vector<uin
     if (rc == STIM_OK && !args.empty()) {
         const size_t b_args = args.size() * sizeof(TabArgs), b_first = first.size() * 4, b_of = job_of.size() * 4;
         const size_t o_first = (b_args + 255) & ~(size_t)255, o_of = o_first + ((b_first + 255) & ~(size_t)255);
-        cudaError_t e = cudaMallocAsync((void **)&dev, o_of + b_of, st);
+        cudaError_t e = dev_malloc_async((void **)&dev, o_of + b_of, st);
         if (e == cudaSuccess) e = cudaMemcpyAsync(dev, args.data(), b_args, cudaMemcpyHostToDevice, st);
         if (e == cudaSuccess) e = cudaMemcpyAsync(dev + o_first, first.data(), b_first, cudaMemcpyHostToDevice, st);
         if (e == cudaSuccess) e = cudaMemcpyAsync(dev + o_of, job_of.data(), b_of, cudaMemcpyHostToDevice, st);
@@ -791,6 +841,15 @@ int stim_frame_program_info_get(const stim_circuit *c, int cluster_size, stim_fr
             if (std::adjacent_find(qs.begin(), qs.end()) != qs.end()) out->tails_repeating_qubit++;
         }
     }
+    return STIM_OK;
+}
+
+int stim_debug_fail_allocations(int skip, int count) {
+    if (skip < 0 || count < 0) return fail(STIM_E_INVALID_ARG, "stim_debug_fail_allocations: negative argument");
+    std::lock_guard<std::mutex> g(g_inject_mu);
+    g_inject_skip = skip;
+    g_inject_fail = count;
+    g_inject_armed.store(count > 0);
     return STIM_OK;
 }
 

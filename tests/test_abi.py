@@ -287,3 +287,11 @@ def test_frame_program_invariants():
     assert two["deferred_ops"] == one["deferred_ops"] - 3
     with pytest.raises(sg.StimError):
         _fp(dup, 3)
+
+
+def test_fault_injection_controls_without_gpu():
+    lib = sg.library()
+    assert lib.stim_debug_fail_allocations(-1, 1) == sg.STIM_E_INVALID_ARG
+    assert lib.stim_debug_fail_allocations(0, -1) == sg.STIM_E_INVALID_ARG
+    sg.stim_debug_fail_allocations(3, 1)
+    sg.stim_debug_fail_allocations(0, 0)          # off again

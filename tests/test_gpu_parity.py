@@ -795,3 +795,33 @@ def test_paper_teleportation_example_on_the_gpu():
     assert np.all(mb[:, -1] == int(gold["final_measurement"]))
     om, _ = oracle.Circuit(txt).sample(np.arange(10000), 12, threads=8)
     np.testing.assert_array_equal(mb, om)
+
+
+def test_failed_device_allocations_leave_handles_usable():
+    """Fault injection: each device allocation of compile-upload, reference
+    and sampling fails in turn (STIM_E_OOM); the same handle then samples
+    bit-exactly once injection is off."""
+    text = W.surface_code_memory(5, 4, 0.01)
+    om, od = oracle.Circuit(text).sample(np.arange(300), 4, threads=8)
+    sg.stim_reference_cache_set(0)             # every reference runs the tableau (its scratch is allocated)
+    failed_sites = 0
+    try:
+        for skip in range(14):
+            c = sg.Circuit(text)
+            sg.stim_debug_fail_allocations(skip, 1)
+            try:
+                c.sample_host(300, 4, shot_major=False)
+            except sg.StimError as e:
+                assert e.code == sg.STIM_E_OOM, (skip, e)
+                failed_sites += 1
+            sg.stim_debug_fail_allocations(0, 0)
+            m, d = c.sample_host(300, 4, shot_major=False)
+            mb = words_to_bits(m, 300).T
+            db = words_to_bits(d, 300).T
+            np.testing.assert_array_equal(mb, om, err_msg=f"skip={skip}")
+            np.testing.assert_array_equal(db, od, err_msg=f"skip={skip}")
+            c.close()
+    finally:
+        sg.stim_debug_fail_allocations(0, 0)
+        sg.stim_reference_cache_set(256 << 20)
+    assert failed_sites >= 8
