@@ -46,6 +46,11 @@
  *     probability p (gap sampling as above) and pick the Pauli of each hit
  *     by a fresh draw against the cumulative thresholds
  *     round-half-even(2^32 * partial sum / p).
+ *
+ * Parity unpinned: which Philox draw feeds which shot bit (the keying above)
+ * is a convention of this implementation, not the paper's; Philox itself, the
+ * geometric tables and every noise distribution are pinned, the exact bit
+ * pattern of the keying only by agreement with the GPU path.
  */
 #include <math.h>
 #include <pthread.h>
