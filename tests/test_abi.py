@@ -295,3 +295,26 @@ def test_fault_injection_controls_without_gpu():
     assert lib.stim_debug_fail_allocations(0, -1) == sg.STIM_E_INVALID_ARG
     sg.stim_debug_fail_allocations(3, 1)
     sg.stim_debug_fail_allocations(0, 0)          # off again
+
+
+@pytest.mark.parametrize("d,rounds,qubits,meas,dets", [(3, 3, 17, 33, 24), (25, 25, 1249, 16225, 15600),
+                                                       (100, 100, 19999, 1009900, 999901)])
+def test_surface_code_workload_sizes(d, rounds, qubits, meas, dets):
+    """The seeded surface-code generator produces the sizes the benchmark
+    configurations are stated with (gate and noise targets too at d=100)."""
+    h = sg.stim_compile(W.surface_code_memory(d, rounds, 1e-3))
+    try:
+        info = sg.stim_info_get(h)
+    finally:
+        sg.stim_free(h)
+    assert (info["num_qubits"], info["num_measurements"], info["num_detectors"]) == (qubits, meas, dets)
+    if d == 100:
+        assert info["num_gate_targets"] == 5989699 and info["num_noise_targets"] == 5969700
+
+
+def test_workload_generators_are_seeded():
+    a = W.batch_circuits()
+    b = W.batch_circuits()
+    assert [e["text"] for e in a] == [e["text"] for e in b] and len(a) == 64
+    assert W.random_clifford(50, 10, 3) == W.random_clifford(50, 10, 3)
+    assert W.random_clifford(50, 10, 3) != W.random_clifford(50, 10, 4)
