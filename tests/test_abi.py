@@ -77,6 +77,7 @@ CIRCUITS = {
                     "CZ rec[-2] 0\nMR 1 2\nDETECTOR rec[-1]\n}\nM 3\n"),
     "observables": ("H 0\nM 0 1\nOBSERVABLE_INCLUDE(3) rec[-1]\nREPEAT 4 {\nMR 1\nDETECTOR rec[-1]\n"
                     "OBSERVABLE_INCLUDE(1) rec[-1] rec[-2]\n}\n"),
+    "observable_without_targets": "M 0\nOBSERVABLE_INCLUDE(5)\nDETECTOR rec[-1]\n",
     "pauli_channels": ("PAULI_CHANNEL_1(0.1, 0, 0.2) 0 1 2\nPAULI_CHANNEL_2(" + ", ".join(["0.01"] * 15) +
                        ") 0 1 2 3\nDEPOLARIZE1(0.1) 3\nM 0 1 2 3\n"),
 }
