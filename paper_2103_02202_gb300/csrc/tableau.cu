@@ -14,9 +14,9 @@
 //   CZ: X_a <- X_a Z_b,  X_b <- X_b Z_a
 //   X, Y, Z negate the anticommuting columns; SQRT_Y(_DAG) swap the two
 //   columns (like H) and negate one of them.
-// each a column product whose phase is accumulated with the two-bit-counter
-// method of the paper's Pauli-multiplication figure (one warp per product,
-// warp-reduced popcounts).
+// each a column product (one warp per product) whose phase is the sum, over
+// qubit positions, of the +-i factors of the single-qubit products (popcounts
+// of the +i and -i position masks, warp-reduced).
 //
 // A measurement of Z_q is deterministic when column Z_q has no X/Y term; the
 // outcome is its sign. Otherwise a pivot p (lowest X/Y row) is chosen, CNOTs
@@ -42,11 +42,14 @@ namespace stimgb {
 
 namespace {
 
-constexpr uint64_t kBarrierTimeoutNs = 2000000000ull;   // 2 s per wait
 constexpr uint32_t kListLimit = 16;                     // CNOT targets handled by list, else by mask
 
 // Barrier over the a.nblk CTAs of one tableau (the whole grid, or one
-// circuit's CTA range of a batched launch).
+// circuit's CTA range of a batched launch). A wait gives up after
+// a.bar_timeout_ns: it sets the circuit's abort flag and DEV_TIMEOUT, every
+// CTA then leaves the kernel at its next barrier, and the host reports
+// STIM_E_TIMEOUT. (a.bar_extra > 0, a test knob, makes the barrier wait for
+// arrivals that never come.)
 __device__ __forceinline__ bool tab_barrier(const TabArgs &a) {
     if (a.nblk == 1) {
         __syncthreads();
@@ -58,7 +61,7 @@ __device__ __forceinline__ bool tab_barrier(const TabArgs &a) {
         const unsigned g = *gen;
         __threadfence();
         const unsigned arrived = atomicAdd(&a.ctl->bar_count, 1u);
-        if (arrived == a.nblk - 1) {
+        if (arrived == a.nblk + a.bar_extra - 1) {
             atomicExch(&a.ctl->bar_count, 0u);
             __threadfence();
             atomicAdd(&a.ctl->bar_gen, 1u);
@@ -67,7 +70,7 @@ __device__ __forceinline__ bool tab_barrier(const TabArgs &a) {
             while (*gen == g) {
                 if (*(volatile int *)&a.ctl->abort) break;
                 __nanosleep(64);
-                if (globaltimer_ns() - t0 > kBarrierTimeoutNs) {
+                if (globaltimer_ns() - t0 > a.bar_timeout_ns) {
                     atomicExch(&a.ctl->abort, 1);
                     atomicExch(a.status, DEV_TIMEOUT);
                     break;
@@ -100,24 +103,30 @@ __device__ __forceinline__ void st_tab(T *p, T v) {
 }
 
 // dst column := dst * src (logical columns); extra = additional power of i.
+//
+// Phase of a product of two Pauli strings (Section 2, xz encoding): per qubit
+// position the single-qubit product P1 P2 contributes i^g, with g = +1 for the
+// cyclic pairs XY, YZ, ZX, g = -1 (i^3) for YX, ZY, XZ, and g = 0 when the two
+// commute. Each lane classifies its words into X-only, Y and Z-only masks for
+// both factors, forms the +i and -i position masks and adds their popcounts
+// into one integer exponent (mod 4), which the warp then sums.
 template <bool L1>
 __device__ void column_product(const TabArgs &a, uint32_t dst, uint32_t src, uint32_t extra, uint32_t lane) {
     const uint32_t pd = ld_u32<L1>(a.perm + dst), ps = ld_u32<L1>(a.perm + src);
     uint64_t *dx = a.tx + (uint64_t)pd * a.nw, *dz = a.tz + (uint64_t)pd * a.nw;
     const uint64_t *sx = a.tx + (uint64_t)ps * a.nw, *sz = a.tz + (uint64_t)ps * a.nw;
-    uint64_t c1 = 0, c2 = 0;   // per-bit two-bit counters of the phase exponent
+    uint32_t ph = 0;      // this lane's exponent of i
     for (uint32_t w = lane; w < a.nw; w += 32) {
-        const uint64_t x1 = ld_u64<L1>(dx + w), z1 = ld_u64<L1>(dz + w);
-        const uint64_t x2 = ld_u64<L1>(sx + w), z2 = ld_u64<L1>(sz + w);
-        const uint64_t nx = x1 ^ x2, nz = z1 ^ z2;
-        const uint64_t x1z2 = x1 & z2;
-        const uint64_t anti = (x2 & z1) ^ x1z2;            // positions that anticommute
-        c2 ^= (c1 ^ nx ^ nz ^ x1z2) & anti;               // +1 or -1 per anticommuting position
-        c1 ^= anti;
-        st_tab<L1>(dx + w, nx);
-        st_tab<L1>(dz + w, nz);
+        const uint64_t ax = ld_u64<L1>(dx + w), az = ld_u64<L1>(dz + w);
+        const uint64_t bx = ld_u64<L1>(sx + w), bz = ld_u64<L1>(sz + w);
+        const uint64_t a_x = ax & ~az, a_y = ax & az, a_z = az & ~ax;    // left factor: X, Y, Z
+        const uint64_t b_x = bx & ~bz, b_y = bx & bz, b_z = bz & ~bx;    // right factor: X, Y, Z
+        const uint64_t up = (a_x & b_y) | (a_y & b_z) | (a_z & b_x);    // XY = iZ, YZ = iX, ZX = iY
+        const uint64_t dn = (a_y & b_x) | (a_z & b_y) | (a_x & b_z);    // YX = -iZ, ZY = -iX, XZ = -iY
+        ph += (uint32_t)__popcll(up) + 3u * (uint32_t)__popcll(dn);
+        st_tab<L1>(dx + w, ax ^ bx);
+        st_tab<L1>(dz + w, az ^ bz);
     }
-    uint32_t ph = (uint32_t)(__popcll(c1) + 2 * __popcll(c2));
     for (int d = 16; d > 0; d >>= 1) ph += __shfl_xor_sync(0xffffffffu, ph, d);
     if (lane == 0) {
         const uint32_t tot = (ph + extra + 2u * ld_u32<L1>(a.sign + pd) + 2u * ld_u32<L1>(a.sign + ps)) & 3u;
