@@ -226,6 +226,22 @@ int stim_reference_cache_stats(uint64_t *hits, uint64_t *misses, uint64_t *entri
 int stim_debug_fail_allocations(int skip, int count);
 
 /*
+ * stim_debug_tableau_barrier -- failure-detection knob for tests (no
+ * counterpart in the paper). The reference-sample kernel separates its
+ * phases with a software grid barrier whose waits are bounded: a wait that
+ * lasts longer than timeout_ns (0 = the default, 2 s) gives up, every CTA of
+ * the tableau leaves the kernel, and stim_reference_sample returns
+ * STIM_E_TIMEOUT with the handle still usable. extra_arrivals > 0 makes
+ * every barrier of multi-CTA tableaus launched afterwards wait for that many
+ * arrivals beyond its CTAs, which never come, so the wait runs out; 0
+ * restores normal operation. Single-CTA tableaus use the CTA barrier and are
+ * not affected. Applies to tableau launches prepared after the call;
+ * process-wide.
+ * Errors: none.
+ */
+int stim_debug_tableau_barrier(uint32_t extra_arrivals, uint64_t timeout_ns);
+
+/*
  * stim_frame_sample -- bulk Pauli-frame sampling (Section 3): num_shots shots
  * with global shot indices 0..num_shots-1 under `seed`.
  *

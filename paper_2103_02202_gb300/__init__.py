@@ -32,7 +32,7 @@ __all__ = [
     "StimError", "library", "library_path", "stim_compile", "stim_info_get", "stim_frame_program_info_get",
     "stim_free",
     "stim_last_error", "stim_reference_sample", "stim_reference_many", "stim_reference_cache_set",
-    "stim_reference_cache_stats", "stim_debug_fail_allocations", "stim_frame_sample", "stim_frame_sample_ex",
+    "stim_reference_cache_stats", "stim_debug_fail_allocations", "stim_debug_tableau_barrier", "stim_frame_sample", "stim_frame_sample_ex",
     "Circuit", "EXPORTED_SYMBOLS", "stim_frame_sample_noalloc", "stim_batch_create", "stim_batch_sample",
     "stim_batch_info", "stim_batch_free", "Batch", "Server", "STIM_OUT_MEAS", "STIM_OUT_DET", "stim_profile", "stim_profile_read", "KERNEL_NAMES",
 ]
@@ -133,6 +133,7 @@ _SIGNATURES = {
     "stim_reference_many": (ctypes.c_int, [ctypes.POINTER(_VP), ctypes.c_size_t, ctypes.c_int]),
     "stim_reference_cache_set": (ctypes.c_int, [ctypes.c_size_t]),
     "stim_debug_fail_allocations": (ctypes.c_int, [ctypes.c_int, ctypes.c_int]),
+    "stim_debug_tableau_barrier": (ctypes.c_int, [ctypes.c_uint32, ctypes.c_uint64]),
     "stim_reference_cache_stats": (ctypes.c_int, [ctypes.POINTER(_U64), ctypes.POINTER(_U64),
                                                   ctypes.POINTER(_U64), ctypes.POINTER(_U64)]),
     "stim_frame_sample": (ctypes.c_int, [_VP, _U64, _U64, _VP, _VP, ctypes.c_int, _VP]),
@@ -232,6 +233,11 @@ def stim_reference_many(handles, flags: int = 0) -> None:
     """Reference samples of several circuits at once (small ones side by side)."""
     arr = (_VP * max(len(handles), 1))(*[h for h in handles])
     _check(library().stim_reference_many(arr, len(handles), flags))
+
+
+def stim_debug_tableau_barrier(extra_arrivals: int, timeout_ns: int) -> None:
+    """Test knob: bounded tableau grid-barrier waits (see include/stimgb.h)."""
+    _check(library().stim_debug_tableau_barrier(int(extra_arrivals), int(timeout_ns)))
 
 
 def stim_debug_fail_allocations(skip: int, count: int) -> None:

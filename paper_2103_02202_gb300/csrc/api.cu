@@ -61,6 +61,12 @@ bool injected_failure() {
     return false;
 }
 
+// Tableau grid-barrier settings (stim_debug_tableau_barrier): the limit of
+// one wait and, for tests, arrivals the barrier waits for beyond its CTAs.
+constexpr uint64_t kBarrierTimeoutNs = 2000000000ull;   // 2 s per wait
+std::atomic<uint32_t> g_bar_extra{0};
+std::atomic<uint64_t> g_bar_timeout_ns{kBarrierTimeoutNs};
+
 cudaError_t dev_malloc(void **p, size_t bytes) {
     if (injected_failure()) return cudaErrorMemoryAllocation;
     return cudaMalloc(p, bytes);
@@ -360,6 +366,8 @@ int reference_prepare(stim_circuit *c, cudaStream_t st, bool use_cache, RefJob *
     a->ref = c->d_ref;
     a->detflag = c->d_detflag;
     a->status = c->d_status;
+    a->bar_extra = g_bar_extra.load();
+    a->bar_timeout_ns = g_bar_timeout_ns.load();
     const size_t bytes_tx = col_words * 8, bytes_sign = (size_t)2 * n * 4, bytes_klist = (size_t)n * 4 + 64;
     const size_t bytes_kmask = (size_t)nw * 8 + 64, bytes_rnd = (size_t)std::max<uint32_t>(hp.max_layer_ops, 1) * 4 + 64;
     const size_t total = 2 * bytes_tx + 2 * bytes_sign + bytes_klist + bytes_kmask + bytes_rnd + 256 + 1024;
@@ -850,6 +858,12 @@ int stim_debug_fail_allocations(int skip, int count) {
     g_inject_skip = skip;
     g_inject_fail = count;
     g_inject_armed.store(count > 0);
+    return STIM_OK;
+}
+
+int stim_debug_tableau_barrier(uint32_t extra_arrivals, uint64_t timeout_ns) {
+    g_bar_extra.store(extra_arrivals);
+    g_bar_timeout_ns.store(timeout_ns ? timeout_ns : kBarrierTimeoutNs);
     return STIM_OK;
 }
 

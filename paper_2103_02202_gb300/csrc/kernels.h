@@ -86,6 +86,8 @@ struct TabArgs {
     TabCtl *ctl;               // zeroed before launch
     int *status;
     uint32_t nblk;             // CTAs working on this circuit (set by the launchers)
+    uint32_t bar_extra;        // test knob: arrivals a barrier waits for beyond nblk (0 in normal use)
+    uint64_t bar_timeout_ns;   // limit of one barrier wait
 };
 
 constexpr uint32_t kTableauThreads = 512;     // threads per CTA of the tableau kernel
