@@ -83,8 +83,12 @@ extern "C" int stim_frame_sample_noalloc(stim_circuit *c, uint64_t num_shots, ui
     e = cudaDeviceGetAttribute(&smem_optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
     if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
     if (e != cudaSuccess) return fail(STIM_E_CUDA, std::string("attribute: ") + cudaGetErrorString(e));
-    const size_t per_word = (size_t)n * 16;
-    if (per_word + kTileHeaderBytes > (size_t)smem_optin)
+    const DevFrameProgram &fp = c->fprog[0];    // single-CTA program, uploaded with the circuit
+    if (fp.C != 1) return fail(STIM_E_INVALID_ARG, "stim_frame_sample_noalloc: circuit not uploaded");
+    // the launch asks for exactly tile_smem_bytes(...) of shared memory, so
+    // both the rejection and the tile width are decided on that figure
+    const uint32_t meta_region = meta_region_for(fp.meta_bytes);
+    if (tile_smem_bytes(fp.Q, 1, false, meta_region) > (size_t)smem_optin)
         return fail(STIM_E_UNSUPPORTED,
                     "stim_frame_sample_noalloc: one 64-shot frame tile does not fit shared memory");
     uint64_t *rec = nullptr;
@@ -96,13 +100,12 @@ extern "C" int stim_frame_sample_noalloc(stim_circuit *c, uint64_t num_shots, ui
     if (n > 0 && M > 0) {
         int W = 1;
         for (int w : {8, 4, 2}) {
-            if (per_word * w + 256 <= (size_t)smem_optin / 2 && (nwords + w - 1) / w >= (uint64_t)sms * 2) {
+            if (tile_smem_bytes(fp.Q, w, false, meta_region) <= (size_t)smem_optin / 2 &&
+                (nwords + w - 1) / w >= (uint64_t)sms * 2) {
                 W = w;
                 break;
             }
         }
-        const DevFrameProgram &fp = c->fprog[0];    // single-CTA program, uploaded with the circuit
-        if (fp.C != 1) return fail(STIM_E_INVALID_ARG, "stim_frame_sample_noalloc: circuit not uploaded");
         FrameArgs a{};
         a.prog = fp.prog;
         a.nprog = fp.nprog;
@@ -122,7 +125,7 @@ extern "C" int stim_frame_sample_noalloc(stim_circuit *c, uint64_t num_shots, ui
         a.status = c->d_status;
         const uint64_t grid = (nwords + W - 1) / W;
         a.meta_bytes = fp.meta_bytes;
-        a.meta_region = meta_region_for(fp.meta_bytes);
+        a.meta_region = meta_region;
         e = launch_frame(a, W, 1, false, (uint32_t)grid, 256, tile_smem_bytes(fp.Q, W, false, a.meta_region), st);
         if (e != cudaSuccess) return fail(STIM_E_CUDA, std::string("frame kernel: ") + cudaGetErrorString(e));
     }

@@ -96,3 +96,53 @@ def test_noalloc_with_classically_controlled_ops():
     torch.cuda.synchronize()
     assert torch.equal(want, got)
     c.close()
+
+
+@pytest.mark.parametrize("shots", [40000, 80000, 160000])
+def test_noalloc_wide_tiles_match(shots):
+    """Shot counts large enough that the no-allocation call picks tiles of 2,
+    4 and 8 words per CTA (on a 152-SM GB300: at least 2 x 152 x W words);
+    the results still equal the allocating entry point's bit for bit."""
+    c = sg.Circuit(W.surface_code_memory(3, 3, 0.01))
+    lib = sg.library()
+    stream = torch.cuda.current_stream().cuda_stream
+    c.reference()
+    nw = (shots + 63) // 64
+    want = torch.full((c.num_detectors, nw), -1, dtype=torch.int64, device="cuda")
+    got = torch.full((c.num_detectors, nw), -1, dtype=torch.int64, device="cuda")
+    rc = lib.stim_frame_sample_ex(c.handle, shots, 5, 128, None, want.data_ptr(), sg.STIM_DEVICE, None, stream)
+    assert rc == sg.STIM_OK, sg.stim_last_error()
+    rc = lib.stim_frame_sample_noalloc(c.handle, shots, 5, 128, got.data_ptr(), stream)
+    assert rc == sg.STIM_OK, sg.stim_last_error()
+    torch.cuda.synchronize()
+    assert torch.equal(want, got)
+    c.close()
+
+
+def test_noalloc_runs_with_every_library_allocation_failing():
+    """With the library's device-allocation fault injector failing every
+    allocation, the no-allocation call still succeeds and returns the same
+    bits as the allocating entry point (which ran before the injector was
+    armed): no library allocation is on its path."""
+    c = sg.Circuit(W.surface_code_memory(5, 5, 0.02))
+    lib = sg.library()
+    stream = torch.cuda.current_stream().cuda_stream
+    c.reference()
+    shots = 5000
+    nw = (shots + 63) // 64
+    want = torch.full((c.num_detectors, nw), -1, dtype=torch.int64, device="cuda")
+    got = torch.full((c.num_detectors, nw), -1, dtype=torch.int64, device="cuda")
+    rc = lib.stim_frame_sample_ex(c.handle, shots, 9, 0, None, want.data_ptr(), sg.STIM_DEVICE, None, stream)
+    assert rc == sg.STIM_OK, sg.stim_last_error()
+    torch.cuda.synchronize()
+    assert lib.stim_debug_fail_allocations(0, 1 << 30) == sg.STIM_OK
+    try:
+        for _ in range(2):
+            got.fill_(-1)
+            rc = lib.stim_frame_sample_noalloc(c.handle, shots, 9, 0, got.data_ptr(), stream)
+            assert rc == sg.STIM_OK, sg.stim_last_error()
+            torch.cuda.synchronize()
+            assert torch.equal(want, got)
+    finally:
+        assert lib.stim_debug_fail_allocations(0, 0) == sg.STIM_OK
+    c.close()
