@@ -549,9 +549,9 @@ def test_noise_extremes():
 # Philox4x32-10 against independent implementations
 # --------------------------------------------------------------------------
 def test_philox_vs_curand_host_generator():
-    """cuRAND's host Philox4_32_10 generator emits block (0, 0, s, 0) under
-    key = (seed lo, seed hi) for subsequence s: check the oracle on the first
-    4096 outputs of several seeds."""
+    """cuRAND's host Philox4_32_10 generator (seed = key (seed lo, seed hi),
+    offset 0) emits the blocks at counters (0, 0, b, 0), b = 0, 1, 2, ...:
+    check the oracle on the first 4096 outputs (1024 blocks) of several seeds."""
     path = None
     for cand in ("/usr/local/cuda/lib64/libcurand.so", "/usr/local/cuda/lib64/libcurand.so.10"):
         if os.path.exists(cand):
@@ -564,11 +564,28 @@ def test_philox_vs_curand_host_generator():
         gen = ctypes.c_void_p()
         assert cur.curandCreateGeneratorHost(ctypes.byref(gen), 161) == 0  # PHILOX4_32_10
         assert cur.curandSetPseudoRandomGeneratorSeed(gen, ctypes.c_ulonglong(seed)) == 0
-        out = np.zeros(4, np.uint32)
-        assert cur.curandGenerate(gen, out.ctypes.data_as(ctypes.c_void_p), ctypes.c_size_t(4)) == 0
+        out = np.zeros(4096, np.uint32)
+        assert cur.curandGenerate(gen, out.ctypes.data_as(ctypes.c_void_p), ctypes.c_size_t(4096)) == 0
         cur.curandDestroyGenerator(gen)  # noqa
         key = [seed & 0xFFFFFFFF, seed >> 32]
-        np.testing.assert_array_equal(oracle.philox([0, 0, 0, 0], key), out)
+        for b in range(1024):
+            np.testing.assert_array_equal(oracle.philox([0, 0, b, 0], key), out[4 * b:4 * b + 4])
+
+
+def test_philox_known_answers():
+    """The published Philox4x32-10 known-answer vectors (Salmon et al., SC'11;
+    tests/golden/philox4x32_10_kat.txt)."""
+    rows = 0
+    with open(os.path.join(GOLD, "philox4x32_10_kat.txt")) as f:
+        for line in f:
+            line = line.split("#", 1)[0].split()
+            if not line:
+                continue
+            v = [int(t, 16) for t in line]
+            assert len(v) == 10
+            np.testing.assert_array_equal(oracle.philox(v[0:4], v[4:6]), np.array(v[6:10], np.uint32))
+            rows += 1
+    assert rows == 3
 
 
 def test_philox_vs_triton_interpreter():
