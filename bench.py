@@ -38,7 +38,9 @@ WORKLOADS = {
     "surface_d3": dict(d=3, rounds=3, p=1e-3, shots=1024),
 }
 BITS_PER_TARGET = {   # algorithmic frame bits read + written per shot per target
-    "H": 4, "S": 3, "CX": 6, "CZ": 6, "M": 4, "MR": 4, "R": 2,
+    # M: x read, record written, z read and written; MR adds x := 0 and the
+    # z write of its reset; R writes x and z
+    "H": 4, "S": 3, "CX": 6, "CZ": 6, "M": 4, "MR": 6, "R": 2,
 }
 THROTTLE_BITS = {0x8: "hw_slowdown", 0x20: "sw_thermal_slowdown", 0x40: "hw_thermal_slowdown",
                  0x80: "hw_power_brake_slowdown", 0x4: "sw_power_cap", 0x1: "gpu_idle",
@@ -59,6 +61,10 @@ def parse_args():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--shots", type=int, default=0, help="shots per step (0 = the workload's)")
     ap.add_argument("--tile", default="", help="frame tile hint W,threads,global,cluster (default: library's)")
+    ap.add_argument("--no-c3", action="store_true", help="skip the 64-circuit batch sub-result")
+    ap.add_argument("--no-c5", action="store_true", help="skip the serving sub-result")
+    ap.add_argument("--c3-steps", type=int, default=3, help="timed steps of the 64-circuit batch sub-result")
+    ap.add_argument("--c5-requests", type=int, default=3000, help="requests of the serving sub-result")
     return ap.parse_args()
 
 
@@ -250,7 +256,8 @@ def run_reference_arm(args, wl, text):
         "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
         "ms_per_step": 1000 * tot / args.steps, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "u8", "data": "synthetic",
-        "config": {"workload": workload_name(wl), "shots_per_step": per_step,
+        "config": {"workload": workload_name(dict(wl, shots=per_step)), "shots_per_step": per_step,
+                   "full_workload": workload_name(wl),
                    "note": "oracle per-shot frame sampler on host cores; each step samples "
                            "%d shots of the workload" % per_step},
         "shots_per_s": shots / tot,
@@ -267,15 +274,16 @@ def workload_name(wl):
             % (wl["d"], wl["rounds"], wl["p"], wl["shots"]))
 
 
-def run_batch_workload(args):
-    """64 heterogeneous circuits: one persistent batched launch vs a plain
-    launch per circuit, same shots, same outputs."""
+C3_NAME = ("64 circuits: 32 rotated surface codes d in 3..31, rounds d..2d, p log-uniform [1e-4, 1e-2]; "
+           "32 random Clifford n in [50, 2000], depth [100, 1000]; shots log-uniform [1e3, 1e6] (seeded)")
+
+
+def measure_c3(steps, warmup, one_by_one_refs=False):
+    """64 heterogeneous circuits: one persistent batched launch per step vs a
+    plain launch per circuit, same shots, same outputs (device-resident)."""
     import torch
     import paper_2103_02202_gb300 as sg
-    from paper_2103_02202_gb300 import build as sgbuild
     from paper_2103_02202_gb300 import workloads as W
-    torch.cuda.set_device(0)
-    sgbuild.build()
     spec = W.batch_circuits()
     t0 = time.perf_counter()
     cs = [sg.Circuit(e["text"]) for e in spec]
@@ -290,12 +298,13 @@ def run_batch_workload(args):
     sg.stim_reference_many([c.handle for c in cs], sg.STIM_RECOMPUTE)
     torch.cuda.synchronize()
     ref_many_s = time.perf_counter() - t0
-    # the same references one circuit at a time, for comparison
-    t0 = time.perf_counter()
-    for c in cs:
-        c.reference(recompute=True)
-    torch.cuda.synchronize()
-    ref_seq_s = time.perf_counter() - t0
+    ref_seq_s = None
+    if one_by_one_refs:
+        t0 = time.perf_counter()
+        for c in cs:
+            c.reference(recompute=True)
+        torch.cuda.synchronize()
+        ref_seq_s = time.perf_counter() - t0
     shots = [e["shots"] for e in spec]
     seeds = [e["seed"] for e in spec]
     stream = torch.cuda.current_stream()
@@ -321,44 +330,63 @@ def run_batch_workload(args):
 
     res = {}
     for name, fn in (("plain", plain_step), ("batched", batch_step)):
-        for _ in range(max(args.warmup, 1)):
+        for _ in range(max(warmup, 1)):
             fn()
         torch.cuda.synchronize()
         e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         e0.record(stream)
-        for _ in range(args.steps):
+        for _ in range(steps):
             fn()
         e1.record(stream)
         torch.cuda.synchronize()
-        res[name] = e0.elapsed_time(e1) / args.steps
-    line = {
-        "metric": METRIC, "value": gate_shots / (res["batched"] / 1000.0), "unit": "shot-gates/s",
-        "n_gpus": 1, "steps": args.steps, "warmup": args.warmup, "ms_per_step": res["batched"],
-        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "u64", "data": "synthetic",
-        "config": {"workload": "64 circuits: 32 rotated surface codes d in 3..31, rounds d..2d, p log-uniform "
-                               "[1e-4, 1e-2]; 32 random Clifford n in [50, 2000], depth [100, 1000]; shots "
-                               "log-uniform [1e3, 1e6] (seeded)", "total_shots": sum(shots),
-                   "tile": sg.stim_batch_info(plan)},
-        "plain": {"value": gate_shots / (res["plain"] / 1000.0), "unit": "shot-gates/s",
-                  "ms_per_step": res["plain"], "launches_per_step": 2 * len(cs)},
-        "shots_per_s": sum(shots) / (res["batched"] / 1000.0),
-        "compile_s": compile_s, "reference_samples_s": ref_s, "reference_samples_side_by_side_uncached_s": ref_many_s,
+        res[name] = e0.elapsed_time(e1) / steps
+    out = {
+        "workload": C3_NAME, "steps": steps, "total_shots_per_step": sum(shots),
+        "batched": {"shot_gates_per_s": gate_shots / (res["batched"] / 1000.0),
+                    "shots_per_s": sum(shots) / (res["batched"] / 1000.0), "ms_per_step": res["batched"],
+                    "launches_per_step": 1, "tile": sg.stim_batch_info(plan)},
+        "plain": {"shot_gates_per_s": gate_shots / (res["plain"] / 1000.0),
+                  "shots_per_s": sum(shots) / (res["plain"] / 1000.0), "ms_per_step": res["plain"],
+                  "launches_per_step": "one frame launch (plus a detector launch where the circuit has "
+                                       "detectors) per circuit"},
+        "batched_over_plain": res["plain"] / res["batched"],
+        "compile_s": compile_s, "reference_samples_s": ref_s,
+        "reference_samples_side_by_side_uncached_s": ref_many_s,
         "reference_samples_one_by_one_s": ref_seq_s,
     }
-    print(json.dumps(line), flush=True)
     sg.stim_batch_free(plan)
+    for c in cs:
+        c.close()
+    return out
 
 
-def run_serve_workload(args):
-    """Poisson stream of sampling requests through the continuous-batching
-    server (150 GB budget); rate set to 80% of the measured capacity."""
-    import threading
+def run_batch_workload(args):
     import torch
-    import paper_2103_02202_gb300 as sg
     from paper_2103_02202_gb300 import build as sgbuild
-    from paper_2103_02202_gb300 import workloads as W
     torch.cuda.set_device(0)
     sgbuild.build()
+    r = measure_c3(args.steps, args.warmup, one_by_one_refs=True)
+    line = {
+        "metric": METRIC, "value": r["batched"]["shot_gates_per_s"], "unit": "shot-gates/s",
+        "n_gpus": 1, "steps": args.steps, "warmup": args.warmup, "ms_per_step": r["batched"]["ms_per_step"],
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "u64", "data": "synthetic",
+        "config": {"workload": C3_NAME, "total_shots": r["total_shots_per_step"], "tile": r["batched"]["tile"]},
+        "plain": r["plain"], "shots_per_s": r["batched"]["shots_per_s"],
+        "batched_over_plain": r["batched_over_plain"], "compile_s": r["compile_s"],
+        "reference_samples_s": r["reference_samples_s"],
+        "reference_samples_side_by_side_uncached_s": r["reference_samples_side_by_side_uncached_s"],
+        "reference_samples_one_by_one_s": r["reference_samples_one_by_one_s"],
+    }
+    print(json.dumps(line), flush=True)
+
+
+def measure_c5(requests, streams=16, budget=150 << 30):
+    """Poisson stream of sampling requests through the continuous-batching
+    server (150 GB budget, rate 80% of the measured burst capacity), then the
+    same requests as plain back-to-back calls on one stream."""
+    import torch
+    import paper_2103_02202_gb300 as sg
+    from paper_2103_02202_gb300 import workloads as W
     catalogue, _ = W.serve_requests(count=1)
     t0 = time.perf_counter()
     cs = [sg.Circuit(W.catalogue_text(e)) for e in catalogue]
@@ -368,13 +396,13 @@ def run_serve_workload(args):
     sg.stim_reference_many([c.handle for c in cs])
     torch.cuda.synchronize()
     ref_s = time.perf_counter() - t0
-    srv = sg.Server(150 << 30, streams=16)
+    srv = sg.Server(budget, streams=streams)
 
     def outputs(c):
         return sg.STIM_OUT_DET if c.num_detector_rows else sg.STIM_OUT_MEAS
 
     # capacity: a burst of requests drawn like the stream, all submitted at once
-    _, probe = W.serve_requests(seed=99, count=min(600, args.requests))
+    _, probe = W.serve_requests(seed=99, count=min(600, requests))
     for r in probe[:50]:
         rid = srv.submit(cs[r["circuit"]], r["shots"], r["seed"], 0, outputs(cs[r["circuit"]]))
         srv.wait(rid, 600)
@@ -389,8 +417,8 @@ def run_serve_workload(args):
     rate = 0.8 * capacity
     srv.close()
 
-    srv = sg.Server(150 << 30, streams=16)
-    _, reqs = W.serve_requests(seed=5, count=args.requests, rate_hz=rate)
+    srv = sg.Server(budget, streams=streams)
+    _, reqs = W.serve_requests(seed=5, count=requests, rate_hz=rate)
     done_ids = []
     lock = threading.Lock()
 
@@ -423,19 +451,73 @@ def run_serve_workload(args):
     wall = time.perf_counter() - t0
     st = srv.stats()
     srv.close()
-    line = {
-        "metric": METRIC, "value": st["gate_shots"] / st["wall_s"], "unit": "shot-gates/s",
-        "n_gpus": 1, "steps": 1, "warmup": 0, "ms_per_step": 1000 * wall, "higher_is_better": True,
-        "scaling": "weak", "vs_baseline": None, "dtype": "u64", "data": "synthetic",
-        "config": {"workload": "serving: %d Poisson requests over %d resident circuits (rotated surface codes "
-                               "d=3..51 x p in {1e-4,1e-3,1e-2}, 8 random Clifford), shots log-uniform "
-                               "[1e3, 1e5], HBM budget 150 GB, 16 streams" % (len(reqs), len(cs)),
-                   "arrival_rate_hz": rate, "capacity_hz": capacity},
-        "shots_per_s": st["shots"] / st["wall_s"], "requests": st["completed"], "failed": st["failed"],
+
+    # aggregate capacity on these same requests: all submitted at once
+    srv = sg.Server(budget, streams=streams)
+    t0 = time.perf_counter()
+    ids = [srv.submit(cs[r["circuit"]], r["shots"], r["seed"], 0, outputs(cs[r["circuit"]])) for r in reqs]
+    for rid in ids:
+        srv.wait(rid, 600)
+        srv.release(rid)
+    served_burst_s = time.perf_counter() - t0
+    srv.close()
+
+    # the same requests as plain calls, back to back on one stream (device
+    # outputs in one reused buffer; no server, no arrivals)
+    stream = torch.cuda.current_stream()
+    maxw = max((r["shots"] + 63) // 64 for r in reqs)
+    maxrows = max(c.num_detector_rows or c.num_measurements for c in cs)
+    buf = torch.empty(maxrows * maxw, dtype=torch.int64, device="cuda")
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    plain_shots = plain_gate_shots = 0
+    for r in reqs:
+        c = cs[r["circuit"]]
+        ptr = buf.data_ptr()
+        sg.stim_frame_sample_ex(c.handle, r["shots"], r["seed"], 0, 0 if c.num_detector_rows else ptr,
+                                ptr if c.num_detector_rows else 0, 0, None, stream.cuda_stream)
+        plain_shots += r["shots"]
+        plain_gate_shots += r["shots"] * c.info["num_gate_targets"]
+    torch.cuda.synchronize()
+    plain_s = time.perf_counter() - t0
+    out = {
+        "workload": "serving: %d Poisson requests over %d resident circuits (rotated surface codes d=3..51 x "
+                    "p in {1e-4,1e-3,1e-2}, 8 random Clifford), shots log-uniform [1e3, 1e5], HBM budget "
+                    "150 GB, %d streams" % (len(reqs), len(cs), streams),
+        "requests": st["completed"], "failed": st["failed"], "arrival_rate_hz": rate, "capacity_hz": capacity,
+        "served": {"shot_gates_per_s": st["gate_shots"] / st["wall_s"], "shots_per_s": st["shots"] / st["wall_s"],
+                   "wall_s": wall},
         "p50_latency_s": st["p50_latency_s"], "p99_latency_s": st["p99_latency_s"],
         "max_latency_s": st["max_latency_s"], "peak_hbm_bytes": st["peak_bytes_in_use"],
+        "plain": {"shot_gates_per_s": plain_gate_shots / plain_s, "shots_per_s": plain_shots / plain_s,
+                  "wall_s": plain_s,
+                  "how": "the same requests as back-to-back stim_frame_sample_ex calls on one stream"},
+        "served_burst": {"shot_gates_per_s": plain_gate_shots / served_burst_s,
+                         "shots_per_s": plain_shots / served_burst_s, "wall_s": served_burst_s,
+                         "how": "the same requests, all submitted to the server at once"},
+        "served_over_plain": plain_s / served_burst_s,
         "compile_s": compile_s, "reference_samples_s": ref_s,
     }
+    for c in cs:
+        c.close()
+    return out
+
+
+def run_serve_workload(args):
+    import torch
+    from paper_2103_02202_gb300 import build as sgbuild
+    torch.cuda.set_device(0)
+    sgbuild.build()
+    r = measure_c5(args.requests)
+    line = {
+        "metric": METRIC, "value": r["served"]["shot_gates_per_s"], "unit": "shot-gates/s",
+        "n_gpus": 1, "steps": 1, "warmup": 0, "ms_per_step": 1000 * r["served"]["wall_s"],
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "u64", "data": "synthetic",
+        "config": {"workload": r["workload"], "arrival_rate_hz": r["arrival_rate_hz"],
+                   "capacity_hz": r["capacity_hz"]},
+        "shots_per_s": r["served"]["shots_per_s"],
+    }
+    line.update({k: v for k, v in r.items() if k not in ("workload", "served")})
     print(json.dumps(line), flush=True)
 
 
@@ -543,9 +625,12 @@ def main():
     value = total_shots * gate_targets / sec
 
     # ---- batched: the same shots, several batches per persistent launch ----
+    # B batches per launch (at most the step count); floor(steps / B) launches
+    # are timed, and the rate is taken over the shots they sample.
     batched = None
-    B = args.batch_per_launch
-    if B > 0 and args.steps % B == 0:
+    B = min(args.batch_per_launch, args.steps)
+    if B > 0:
+        launches = args.steps // B
         plan = sg.stim_batch_create([circ.handle] * B, [shots] * B, None, stream.cuda_stream)
         dets_b = [torch.empty((D, nwords), dtype=torch.int64, device="cuda") for _ in range(B)]
 
@@ -553,7 +638,8 @@ def main():
             offs = [shard_offset(rank, world, j * B + i, shots) for i in range(B)]
             sg.stim_batch_sample(plan, [2021] * B, offs, None, [t.data_ptr() for t in dets_b], stream.cuda_stream)
 
-        for j in range(max(1, args.warmup // B + 1)):
+        wl_launches = max(1, -(-args.warmup // B))
+        for j in range(wl_launches):
             bstep(j)
         torch.cuda.synchronize()
         if dist:
@@ -561,8 +647,8 @@ def main():
         b0 = torch.cuda.Event(enable_timing=True)
         b1 = torch.cuda.Event(enable_timing=True)
         b0.record(stream)
-        for j in range(args.steps // B):
-            bstep(args.warmup // B + 1 + j)
+        for j in range(launches):
+            bstep(wl_launches + j)
         b1.record(stream)
         torch.cuda.synchronize()
         bms = b0.elapsed_time(b1)
@@ -571,9 +657,11 @@ def main():
             dist.all_reduce(t, op=dist.ReduceOp.MAX)
             bms = float(t.item())
         binfo = sg.stim_batch_info(plan)
-        batched = {"value": total_shots * gate_targets / (bms / 1000.0), "unit": "shot-gates/s",
-                   "ms_per_step": bms / args.steps, "batches_per_launch": B,
-                   "launches": args.steps // B, "tile": binfo}
+        bshots = shots * B * launches * world
+        batched = {"value": bshots * gate_targets / (bms / 1000.0), "unit": "shot-gates/s",
+                   "shots_per_s": bshots / (bms / 1000.0),
+                   "ms_per_batch": bms / (B * launches), "batches_per_launch": B,
+                   "launches": launches, "warmup_launches": wl_launches, "tile": binfo}
         sg.stim_batch_free(plan)
         del dets_b
 
@@ -710,6 +798,12 @@ def main():
         "paper_context": "Stim (paper abstract): d=100 surface code sampled at ~1 kHz on one laptop "
                          "CPU core (i7-8650U) after 15 s of analysis",
     }
+    # ---- rows a9 and a10 on the same box: the 64-circuit batch (batched vs
+    # plain) and the serving loop (served vs plain), device-resident outputs ----
+    if world == 1 and not args.no_c3:
+        line["c3_batch"] = measure_c3(args.c3_steps, 1)
+    if world == 1 and not args.no_c5:
+        line["c5_serve"] = measure_c5(args.c5_requests)
     if not args.no_cpu_baseline:
         threads = os.cpu_count() or 1
         k = args.cpu_shots or max(threads, 8)
