@@ -314,25 +314,37 @@ def test_edge_cases():
 @pytest.mark.slow
 def test_surface_d100_bench_configuration_sampled_parity():
     """d=100, 100 rounds, p=1e-3, 16384 shots at shot offset 16384 (step 1
-    of the benchmark), default launch (thread-block clusters): sampled shots
-    vs the oracle, and the full reference sample vs the oracle's tableau."""
+    of the benchmark), default launch (thread-block clusters): the first and
+    last shots, a word boundary and 256 random shots vs the oracle, and the
+    full reference sample vs the oracle's tableau. A second call of 16377
+    shots (a partial last word) gives the same bits on every shared shot and
+    zero padding, and its last shot matches the oracle too."""
     text = W.surface_code_memory(100, 100, 1e-3)
     S, off = 16384, 16384
     c = sg.Circuit(text)
     ref, det = c.reference()
     _, d = c.sample(S, 2021, shot_offset=off, meas=False)
+    Sp = S - 7
+    _, dp = c.sample(Sp, 2021, shot_offset=off, meas=False)
     torch.cuda.synchronize()
     o = oracle.Circuit(text)
     oref, odet = o.reference()
     M = c.num_measurements
     np.testing.assert_array_equal(words_to_bits(to_np(ref)[None, :], M)[0], oref)
     np.testing.assert_array_equal(words_to_bits(to_np(det)[None, :], M)[0], odet)
-    pick = np.array([0, 1, 63, 64, 8191, S - 1] + list(np.random.default_rng(3).choice(S, 10, replace=False)))
+    rnd = np.random.default_rng(3).choice(S, 256, replace=False)
+    pick = np.unique(np.concatenate([[0, 1, 63, 64, 8191, Sp - 1, S - 1], rnd]))
     cols = torch.as_tensor(pick // 64, device="cuda")
     bits = torch.as_tensor(pick % 64, device="cuda")
     gd = ((d[:, cols] >> bits) & 1).cpu().numpy().astype(np.uint8).T
     _, od = o.sample(pick, 2021, shot_offset=off, threads=16, ref=oref)
     np.testing.assert_array_equal(gd, od)
+    # partial last word: same bits on shared shots, padding bits zero
+    nw = (Sp + 63) // 64
+    assert torch.equal(dp[:, :nw - 1], d[:, :nw - 1])
+    keep = (1 << (Sp % 64)) - 1
+    assert torch.equal(dp[:, nw - 1] & ~keep, torch.zeros_like(dp[:, nw - 1]))
+    assert torch.equal(dp[:, nw - 1] & keep, d[:, nw - 1] & keep)
     c.close()
 
 
