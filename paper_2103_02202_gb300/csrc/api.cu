@@ -370,12 +370,17 @@ int reference_prepare(stim_circuit *c, cudaStream_t st, bool use_cache, RefJob *
     a->bar_timeout_ns = g_bar_timeout_ns.load();
     const size_t bytes_tx = col_words * 8, bytes_sign = (size_t)2 * n * 4, bytes_klist = (size_t)n * 4 + 64;
     const size_t bytes_kmask = (size_t)nw * 8 + 64, bytes_rnd = (size_t)std::max<uint32_t>(hp.max_layer_ops, 1) * 4 + 64;
-    const size_t total = 2 * bytes_tx + 2 * bytes_sign + bytes_klist + bytes_kmask + bytes_rnd + 256 + 1024;
+    // Every part starts on a 256-byte boundary; the allocation is the sum of
+    // the rounded part sizes, so the last part (the control words, which the
+    // memset below must clear) lies wholly inside it.
+    auto round256 = [](size_t b) { return (b + 255) & ~(size_t)255; };
+    const size_t total = 2 * round256(bytes_tx) + 2 * round256(bytes_sign) + round256(bytes_klist) +
+                         round256(bytes_kmask) + round256(bytes_rnd) + round256(sizeof(TabCtl));
     STIMGB_CK(dev_malloc_async((void **)&job->blob, total, st), "alloc tableau");
     size_t off = 0;
     auto take = [&](size_t b) {
         char *p = job->blob + off;
-        off += (b + 255) & ~(size_t)255;
+        off += round256(b);
         return p;
     };
     a->tx = (uint64_t *)take(bytes_tx);
@@ -386,6 +391,11 @@ int reference_prepare(stim_circuit *c, cudaStream_t st, bool use_cache, RefJob *
     a->kmask = (uint64_t *)take(bytes_kmask);
     a->rnd = (uint32_t *)take(bytes_rnd);
     a->ctl = (TabCtl *)take(sizeof(TabCtl));
+    if (off != total) {
+        cudaFreeAsync(job->blob, st);
+        job->blob = nullptr;
+        return fail(STIM_E_CUDA, "reference sample: tableau scratch layout mismatch");
+    }
     cudaError_t e = cudaMemsetAsync(job->blob, 0, total, st);
     if (e == cudaSuccess) e = cudaMemsetAsync(c->d_status, 0, sizeof(int), st);
     if (e == cudaSuccess) e = launch_tableau_init(*a, st);
