@@ -399,7 +399,9 @@ int stim_server_cancel(stim_server *s, stim_request_id id);
 int stim_server_release(stim_server *s, stim_request_id id);
 /* Copies a finished request's outputs into caller buffers (either may be
  * NULL): flags STIM_HOST or STIM_DEVICE; MEAS_MAJOR layout. Host copies return
- * when done; device copies are asynchronous on `stream`. */
+ * when done; device copies are asynchronous on `stream`, and a later
+ * stim_server_release of the request waits for them before its buffers go
+ * back to the arena. */
 int stim_server_copy_result(stim_server *s, stim_request_id id, uint64_t *meas_dst, uint64_t *det_dst,
                             int flags, void *stream);
 int stim_server_stats(stim_server *s, stim_server_statistics *out);

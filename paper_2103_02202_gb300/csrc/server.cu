@@ -114,6 +114,7 @@ struct Request {
     size_t off_meas = SIZE_MAX, off_det = SIZE_MAX, off_rec = SIZE_MAX, off_gframe = SIZE_MAX;
     int slot = -1;
     cudaEvent_t ev = nullptr;
+    cudaEvent_t copy_ev = nullptr;      // after the last device copy out of the result buffers
     Clock::time_point t_submit, t_start, t_done;
 };
 
@@ -421,6 +422,14 @@ int stim_server_release(stim_server *s, stim_request_id id) {
     Request *r = it->second;
     if (r->state == RQ_QUEUED || r->state == RQ_RUNNING)
         return sfail(STIM_E_BUSY, "stim_server_release: request still in progress");
+    // an asynchronous device copy out of the result buffers may still be in
+    // flight on the caller's stream: the buffers return to the arena (and to
+    // the next request's kernels) only once it is done
+    if (r->copy_ev) {
+        cudaEventSynchronize(r->copy_ev);
+        cudaEventDestroy(r->copy_ev);
+        r->copy_ev = nullptr;
+    }
     free_outputs(s, r);
     if (r->ev) cudaEventDestroy(r->ev);
     s->reqs.erase(it);
@@ -454,6 +463,18 @@ int stim_server_copy_result(stim_server *s, stim_request_id id, uint64_t *meas_d
         return sfail(STIM_E_CUDA, "stim_server_copy_result: copy failed");
     if ((flags & STIM_HOST) && cudaStreamSynchronize(st) != cudaSuccess)
         return sfail(STIM_E_CUDA, "stim_server_copy_result: sync failed");
+    if (!(flags & STIM_HOST)) {
+        // remember where the copy ends, so that stim_server_release waits for it
+        std::lock_guard<std::mutex> lk(s->mu);
+        auto it = s->reqs.find(id);
+        if (it != s->reqs.end()) {
+            Request *r = it->second;
+            if (!r->copy_ev && cudaEventCreateWithFlags(&r->copy_ev, cudaEventDisableTiming) != cudaSuccess)
+                return sfail(STIM_E_CUDA, "stim_server_copy_result: event creation failed");
+            if (cudaEventRecord(r->copy_ev, st) != cudaSuccess)
+                return sfail(STIM_E_CUDA, "stim_server_copy_result: event record failed");
+        }
+    }
     return STIM_OK;
 }
 
@@ -494,6 +515,7 @@ void stim_server_destroy(stim_server *s) {
     cudaDeviceSynchronize();
     for (auto &kv : s->reqs) {
         if (kv.second->ev) cudaEventDestroy(kv.second->ev);
+        if (kv.second->copy_ev) cudaEventDestroy(kv.second->copy_ev);
         delete kv.second;
     }
     for (cudaStream_t st : s->streams) cudaStreamDestroy(st);

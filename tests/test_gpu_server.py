@@ -154,3 +154,28 @@ def test_observable_rows_in_server_results():
     srv.release(rid)
     srv.close()
     c.close()
+
+
+def test_release_right_after_device_copy_keeps_the_copy():
+    """A device copy out of a request's result buffers is asynchronous; a
+    release right after it must not hand the buffers to queued requests
+    before the copy has read them. With a small budget every release lets the
+    next queued request reuse the same arena bytes at once."""
+    cs = _circuits()
+    c = cs[3]
+    srv = sg.Server(3 << 20, streams=2)      # room for about two of these requests at a time
+    reqs = [(5000 + 37 * k, 1000 + k) for k in range(24)]
+    ids = [srv.submit(c, shots, seed) for shots, seed in reqs]
+    side = torch.cuda.Stream()
+    got = []
+    with torch.cuda.stream(side):
+        for rid, (shots, seed) in zip(ids, reqs):
+            srv.wait(rid)
+            got.append(srv.fetch(c, rid, shots))
+            srv.release(rid)
+    torch.cuda.synchronize()
+    for (shots, seed), (m, d) in zip(reqs, got):
+        pm, pd = c.sample(shots, seed)
+        torch.cuda.synchronize()
+        assert torch.equal(pm, m) and torch.equal(pd, d)
+    srv.close()
