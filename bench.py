@@ -142,6 +142,30 @@ def profiled_traffic(shots):
     return int(b.group(1)) * shots / int(cs.group(1))
 
 
+def profiled_issue(shots, frame_avg_ms, clk, sms):
+    """Issue-slot use of the frame kernel: warp instructions per launch (from
+    the committed ncu capture, scaled by shots, while the kernel sources are
+    unchanged) over the slots available in the measured launch time (SMs x 4
+    schedulers x SM clock). None without a valid capture."""
+    try:
+        txt = open(TRAFFIC_PROFILE).read()
+    except OSError:
+        return None
+    import re
+    sha = re.search(r"kernel_sources_sha256:\s*([0-9a-f]{64})", txt)
+    inst = re.search(r"warp_instructions_per_launch:\s*(\d+)", txt)
+    cs = re.search(r"captured_shots:\s*(\d+)", txt)
+    if not (sha and inst and cs) or sha.group(1) != frame_sources_sha256():
+        return None
+    mhz = clk.get("sm_mhz") or 0
+    if not mhz:
+        return None
+    w = int(inst.group(1)) * shots / int(cs.group(1))
+    slots = sms * 4 * mhz * 1e6 * frame_avg_ms / 1e3
+    return {"warp_instructions": w, "slots": slots, "frac": w / slots,
+            "source": "ncu smsp__inst_executed.sum of the committed capture, scaled by shots"}
+
+
 def algorithmic_frame_bytes_per_shot(counts, n):
     bits = sum(BITS_PER_TARGET.get(g, 0) * k for g, k in counts.items())
     bits += 2 * n          # frame initialisation writes x and z
@@ -734,6 +758,12 @@ def main():
             dist.destroy_process_group()
         return
 
+    # ---- shared-memory bandwidth of this GPU (the frame's own resource) ----
+    try:
+        smem_local_gbs, smem_cluster_gbs = sg.stim_probe_smem_bandwidth()
+    except sg.StimError:
+        smem_local_gbs = smem_cluster_gbs = None
+
     # ---- roofline of the dominant (frame) kernel ----
     peaks = {}
     try:
@@ -783,6 +813,16 @@ def main():
             "frac": achieved / hbm_peak, "traffic": profiled_traffic(shots),
             "kernel": "frame", "peak_source": peak_src,
             "algorithmic_bytes_per_launch": frame_bytes,
+            "note": "the survey's roofline for this kernel: algorithmic frame bytes against measured HBM "
+                    "bandwidth; the frame itself stays in shared memory (see smem) and the kernel is "
+                    "limited by instruction issue (see issue)",
+            "smem": None if not smem_local_gbs else {
+                "achieved": achieved, "peak": smem_cluster_gbs, "unit": "GB/s",
+                "frac": achieved / smem_cluster_gbs, "peak_local": smem_local_gbs,
+                "peak_source": "measured on this GPU by stim_probe_smem_bandwidth (16-byte loads and stores; "
+                               "the cluster figure, since the frame is spread over a cluster)"},
+            "issue": profiled_issue(shots, frame_avg_ms, clocks.summary(),
+                                    torch.cuda.get_device_properties(local).multi_processor_count),
         },
         "batched": batched,
         "e2e": {"value": e2e_dense_value, "unit": "shot-gates/s", "h2d_bytes_per_step": 0,

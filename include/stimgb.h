@@ -468,6 +468,19 @@ typedef struct {
 int stim_profile(int enable);
 int stim_profile_read(stim_kernel_stat *out, int n);
 
+/*
+ * stim_probe_smem_bandwidth -- measured shared-memory bandwidth of the current
+ * device (measurement support; no counterpart in the paper), the roofline
+ * denominator of the frame kernel, whose frames live in shared memory. Every
+ * CTA streams 16-byte loads and stores (the frame kernel's access width) over
+ * its own 64 KiB buffer (local_gbs), or over the buffer of the other CTA of a
+ * 2-CTA cluster through distributed shared memory (cluster_gbs); bytes are
+ * loads plus stores, timed with CUDA events (best of three after a warm-up).
+ * Allocates a small device buffer; synchronizes.
+ * Errors: STIM_E_INVALID_ARG (NULL argument), STIM_E_CUDA.
+ */
+int stim_probe_smem_bandwidth(double *local_gbs, double *cluster_gbs);
+
 #ifdef __cplusplus
 }
 #endif

@@ -32,7 +32,7 @@ __all__ = [
     "StimError", "library", "library_path", "stim_compile", "stim_info_get", "stim_frame_program_info_get",
     "stim_free",
     "stim_last_error", "stim_reference_sample", "stim_reference_many", "stim_reference_cache_set",
-    "stim_reference_cache_stats", "stim_debug_fail_allocations", "stim_debug_tableau_barrier", "stim_frame_sample", "stim_frame_sample_ex",
+    "stim_reference_cache_stats", "stim_debug_fail_allocations", "stim_debug_tableau_barrier", "stim_probe_smem_bandwidth", "stim_frame_sample", "stim_frame_sample_ex",
     "Circuit", "EXPORTED_SYMBOLS", "stim_frame_sample_noalloc", "stim_batch_create", "stim_batch_sample",
     "stim_batch_info", "stim_batch_free", "Batch", "Server", "STIM_OUT_MEAS", "STIM_OUT_DET", "stim_profile", "stim_profile_read", "KERNEL_NAMES",
 ]
@@ -134,6 +134,7 @@ _SIGNATURES = {
     "stim_reference_cache_set": (ctypes.c_int, [ctypes.c_size_t]),
     "stim_debug_fail_allocations": (ctypes.c_int, [ctypes.c_int, ctypes.c_int]),
     "stim_debug_tableau_barrier": (ctypes.c_int, [ctypes.c_uint32, ctypes.c_uint64]),
+    "stim_probe_smem_bandwidth": (ctypes.c_int, [ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_double)]),
     "stim_reference_cache_stats": (ctypes.c_int, [ctypes.POINTER(_U64), ctypes.POINTER(_U64),
                                                   ctypes.POINTER(_U64), ctypes.POINTER(_U64)]),
     "stim_frame_sample": (ctypes.c_int, [_VP, _U64, _U64, _VP, _VP, ctypes.c_int, _VP]),
@@ -233,6 +234,13 @@ def stim_reference_many(handles, flags: int = 0) -> None:
     """Reference samples of several circuits at once (small ones side by side)."""
     arr = (_VP * max(len(handles), 1))(*[h for h in handles])
     _check(library().stim_reference_many(arr, len(handles), flags))
+
+
+def stim_probe_smem_bandwidth() -> tuple:
+    """(local, cluster) shared-memory GB/s of the current device (see include/stimgb.h)."""
+    lo, cl = ctypes.c_double(), ctypes.c_double()
+    _check(library().stim_probe_smem_bandwidth(ctypes.byref(lo), ctypes.byref(cl)))
+    return lo.value, cl.value
 
 
 def stim_debug_tableau_barrier(extra_arrivals: int, timeout_ns: int) -> None:

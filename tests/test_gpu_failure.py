@@ -67,3 +67,13 @@ def test_batched_tableau_barrier_timeout_returns_error():
         torch.cuda.synchronize()
         np.testing.assert_array_equal(_bits(ref, c.num_measurements), oracle.Circuit(t).reference()[0])
         c.close()
+
+
+def test_smem_bandwidth_probe_is_plausible():
+    """The shared-memory bandwidth probe (the frame kernel's roofline
+    denominator) returns positive figures of the right order: between 1 and
+    200 TB/s for local shared memory, and a cluster figure no larger than
+    twice the local one."""
+    lo, cl = sg.stim_probe_smem_bandwidth()
+    assert 1e3 < lo < 2e5
+    assert 0 < cl < 2 * lo
