@@ -59,6 +59,11 @@ extern "C" {
                                   again (ignore the handle's sample and the reference cache) */
 #define STIM_ASYNC        0x8  /* stim_frame_sample(_ex): return once the work and the host
                                   copies are enqueued on the stream; see stim_frame_sample_ex */
+#define STIM_EVENTS_IN_KERNEL 0x10 /* stim_frame_sample(_ex) with detection events only: compute
+                                  them inside the frame kernel from a ring of the most recent
+                                  measurement flips (stim_info.flip_ring_rows rows) instead of
+                                  writing the measurement records and running the detector
+                                  kernel; see stim_frame_sample_ex */
 
 typedef struct stim_circuit stim_circuit;
 
@@ -77,6 +82,11 @@ typedef struct {
     uint64_t reference_key;      /* hash of the noiseless skeleton: circuits that differ only in
                                     noise channels, DETECTORs and OBSERVABLE_INCLUDEs share it
                                     (and their reference sample) */
+    uint64_t flip_ring_rows;     /* R: rows of the ring of recent measurement flips from which
+                                    the frame kernel computes detection events when only those
+                                    are asked for (used when 4 R <= M and the circuit has no
+                                    classically controlled ops); 0 without DETECTOR or
+                                    OBSERVABLE_INCLUDE */
 } stim_info;
 
 /* Tile choice for the frame kernel; zero fields mean "let the library pick". */
@@ -273,6 +283,19 @@ int stim_frame_sample(stim_circuit *c, uint64_t num_shots, uint64_t seed,
  * kernels of the next; a call that reuses a set waits on the GPU for that
  * set's previous copies.
  * Calls on one handle must still come from one host thread at a time.
+ *
+ * Detection events without records (survey NEXT-1, Section 5.6): when only
+ * det_out is given and either STIM_EVENTS_IN_KERNEL is set or the records
+ * would take more than 8 GiB, and the circuit has no classically controlled
+ * ops and 4 x stim_info.flip_ring_rows <= M, the frame kernel keeps each
+ * measurement's flip in a ring of flip_ring_rows rows and evaluates the
+ * detectors and observables of each straight-line stretch itself: no record
+ * buffer (ring: flip_ring_rows x ceil(num_shots/64) words instead of M x
+ * ceil(num_shots/64)) and no detector kernel; the same bits either way.
+ * With one 64-shot word per tile (the default for circuits that need thread-
+ * block clusters) the ring reads are 8-byte loads from L2 on the kernel's
+ * critical path, so that form is slower than the record path (the d=100
+ * surface code: about 32 ms against 25 ms per 16384 shots); its gain is memory.
  */
 int stim_frame_sample_ex(stim_circuit *c, uint64_t num_shots, uint64_t seed,
                          uint64_t shot_offset, uint64_t *meas_out, uint64_t *det_out,

@@ -26,7 +26,7 @@ from . import workloads  # noqa: F401  (seeded input generators)
 
 __all__ = [
     "STIM_OK", "STIM_E_PARSE", "STIM_E_INVALID_ARG", "STIM_E_OOM", "STIM_E_CUDA",
-    "STIM_E_TIMEOUT", "STIM_E_BUSY", "STIM_E_UNSUPPORTED", "STIM_E_CAPACITY", "STIM_ASYNC",
+    "STIM_E_TIMEOUT", "STIM_E_BUSY", "STIM_E_UNSUPPORTED", "STIM_E_CAPACITY", "STIM_ASYNC", "STIM_EVENTS_IN_KERNEL",
     "stim_frame_sample_detections",
     "STIM_MEAS_MAJOR", "STIM_SHOT_MAJOR", "STIM_DEVICE", "STIM_HOST", "STIM_RECOMPUTE",
     "StimError", "library", "library_path", "stim_compile", "stim_info_get", "stim_frame_program_info_get",
@@ -53,6 +53,7 @@ STIM_DEVICE = 0x0
 STIM_HOST = 0x2
 STIM_RECOMPUTE = 0x4
 STIM_ASYNC = 0x8
+STIM_EVENTS_IN_KERNEL = 0x10
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
 _LIB_PATH = os.path.join(_HERE, "_build", "libstimgb.so")
@@ -71,7 +72,8 @@ class StimInfo(ctypes.Structure):
                 ("num_detectors", ctypes.c_uint64), ("num_gate_targets", ctypes.c_uint64),
                 ("num_noise_targets", ctypes.c_uint64), ("num_instructions", ctypes.c_uint64),
                 ("num_layers", ctypes.c_uint64), ("num_program_layers", ctypes.c_uint64),
-                ("num_observables", ctypes.c_uint64), ("reference_key", ctypes.c_uint64)]
+                ("num_observables", ctypes.c_uint64), ("reference_key", ctypes.c_uint64),
+                ("flip_ring_rows", ctypes.c_uint64)]
 
 
 class StimFrameProgramInfo(ctypes.Structure):
@@ -397,8 +399,9 @@ class Circuit:
         return ref, det
 
     def sample(self, num_shots: int, seed: int, *, shot_offset: int = 0, shot_major: bool = False,
-               meas: bool = True, dets: bool = True, hint=None, stream=None):
-        """Sample on the device; returns (meas, dets) int64 tensors (None when not asked)."""
+               meas: bool = True, dets: bool = True, hint=None, stream=None, events_in_kernel: bool = False):
+        """Sample on the device; returns (meas, dets) int64 tensors (None when not asked).
+        events_in_kernel: with dets only, ask for STIM_EVENTS_IN_KERNEL."""
         import torch
         M, D = self.num_measurements, self.num_detector_rows
         if shot_major:
@@ -411,6 +414,8 @@ class Circuit:
         dt = torch.empty(ds, dtype=torch.int64, device="cuda") if dets else None
         s = stream if stream is not None else torch.cuda.current_stream()
         flags = STIM_SHOT_MAJOR if shot_major else STIM_MEAS_MAJOR
+        if events_in_kernel:
+            flags |= STIM_EVENTS_IN_KERNEL
         stim_frame_sample_ex(self.handle, num_shots, seed, shot_offset,
                              mt.data_ptr() if mt is not None and mt.numel() else 0,
                              dt.data_ptr() if dt is not None and dt.numel() else 0,

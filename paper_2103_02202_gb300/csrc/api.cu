@@ -214,7 +214,8 @@ int ensure_device(stim_circuit *c) {
     // a failure part way frees what was uploaded, so a later call starts afresh
     auto drop = [&](int r) {
         for (void **p : {(void **)&c->d_prog, (void **)&c->d_ops, (void **)&c->d_geo, (void **)&c->d_det_ptr,
-                         (void **)&c->d_det_meas, (void **)&c->d_ref, (void **)&c->d_detflag, (void **)&c->d_status}) {
+                         (void **)&c->d_det_meas, (void **)&c->d_det_items, (void **)&c->d_det_looks,
+                         (void **)&c->d_ref, (void **)&c->d_detflag, (void **)&c->d_status}) {
             cudaFree(*p);
             *p = nullptr;
         }
@@ -226,6 +227,8 @@ int ensure_device(stim_circuit *c) {
     if ((r = upload(&c->d_geo, hp.geo, "upload noise tables")) != STIM_OK) return drop(r);
     if ((r = upload(&c->d_det_ptr, hp.det_ptr, "upload detectors")) != STIM_OK) return drop(r);
     if ((r = upload(&c->d_det_meas, hp.det_meas, "upload detectors")) != STIM_OK) return drop(r);
+    if ((r = upload(&c->d_det_items, hp.det_items, "upload detectors")) != STIM_OK) return drop(r);
+    if ((r = upload(&c->d_det_looks, hp.det_looks, "upload detectors")) != STIM_OK) return drop(r);
     c->ref_words = std::max<size_t>((hp.num_meas + 63) / 64, 1);
     cudaError_t e = dev_malloc((void **)&c->d_ref, c->ref_words * 8);
     if (e == cudaSuccess) e = dev_malloc((void **)&c->d_detflag, c->ref_words * 8);
@@ -685,9 +688,11 @@ int choose_tile(uint32_t n, uint64_t nwords, int sms, size_t smem_optin, const s
 }
 
 // Frame kernel (records into rec, may be null) and detector kernel (events
-// into det, may be null) for one call, with caller-provided buffers.
+// into det, may be null) for one call, with caller-provided buffers. With a
+// ring (stimgb_ring_words words), detection events are computed inside the
+// frame kernel from the ring of recent flips instead, and rec may be null.
 int launch_sampling(stim_circuit *c, uint64_t num_shots, uint64_t seed, uint64_t shot_offset, const TileChoice &tc,
-                    uint64_t *rec, uint64_t *det, uint64_t *gframe, cudaStream_t st) {
+                    uint64_t *rec, uint64_t *det, uint64_t *gframe, uint64_t *ring, cudaStream_t st) {
     const HostProgram &hp = c->hp;
     const uint32_t n = hp.num_qubits;
     const uint64_t D = hp.num_det;
@@ -717,17 +722,30 @@ int launch_sampling(stim_circuit *c, uint64_t num_shots, uint64_t seed, uint64_t
         a.last_mask = last_mask;
         a.rec = hp.num_meas ? rec : nullptr;
         a.rec_stride = nwords;
+        a.rec_mask = 0xFFFFFFFFu;
         a.gframe = gframe;
         a.gstride = gstride;
         a.status = c->d_status;
         a.seed = seed;
         a.meta_bytes = fp->meta_bytes;
         a.meta_region = meta_region_for(fp->meta_bytes);
+        if (ring && det && D > 0) {
+            a.rec = ring;
+            a.rec_mask = (uint32_t)(hp.ring_len - 1);
+            a.num_dets = (uint32_t)(D - hp.num_obs);
+            a.det = det;
+            a.det_stride = nwords;
+            a.det_items = c->d_det_items;
+            a.det_looks = c->d_det_looks;
+            if (hp.num_obs)      // observables accumulate over the whole circuit
+                STIMGB_CK(cudaMemsetAsync(det + (D - hp.num_obs) * nwords, 0, hp.num_obs * nwords * 8, st),
+                          "clear observables");
+        }
         ProfScope ps(STIM_KERNEL_FRAME, st);
         STIMGB_CK(launch_frame(a, W, C, gmem, (uint32_t)grid, threads, tile_smem_bytes(fp->Q, W, gmem, a.meta_region), st),
                   "frame kernel");
     }
-    if (det && D > 0) {
+    if (det && D > 0 && !(ring && n > 0)) {
         ProfScope ps(STIM_KERNEL_DETECTORS, st);
         STIMGB_CK(launch_detectors(rec, nwords, c->d_det_ptr, c->d_det_meas, c->d_ref, D, nwords, last_mask, det,
                                    nwords, st),
@@ -739,6 +757,17 @@ int launch_sampling(stim_circuit *c, uint64_t num_shots, uint64_t seed, uint64_t
 bool valid_flags(int flags, int allowed) { return (flags & ~allowed) == 0; }
 
 }  // namespace
+
+size_t stimgb_ring_words(const stim_circuit *c, uint64_t num_shots, const TileChoice &tc) {
+    const HostProgram &hp = c->hp;
+    if (hp.ring_len == 0 || hp.num_det == 0 || hp.num_feedforward > 0 || hp.num_qubits == 0) return 0;
+    if (hp.ring_len > (1ull << 31)) return 0;
+    if (tc.gmem || (tc.W != 1 && tc.W != 8)) return 0;      // the frame kernel shapes that evaluate DETS entries
+    const uint64_t nwords = (num_shots + 63) / 64;
+    const uint64_t ring = nwords * hp.ring_len;
+    if (ring * 4 > hp.num_meas * nwords) return 0;     // a ring is worth it only when far smaller than the records
+    return (size_t)ring;
+}
 
 // Used by the batched launch (batch.cu).
 int stimgb_frame_program(stim_circuit *c, int C, const DevFrameProgram **out) {
@@ -764,7 +793,7 @@ int stimgb_sampling_layout(stim_circuit *c, uint64_t num_shots, TileChoice *tc, 
 
 int stimgb_sample_into(stim_circuit *c, uint64_t num_shots, uint64_t seed, uint64_t shot_offset, const TileChoice &tc,
                        uint64_t *rec, uint64_t *det, uint64_t *gframe, cudaStream_t st) {
-    return launch_sampling(c, num_shots, seed, shot_offset, tc, rec, det, gframe, st);
+    return launch_sampling(c, num_shots, seed, shot_offset, tc, rec, det, gframe, nullptr, st);
 }
 
 int stimgb_ensure_references(stim_circuit *const *cs, size_t k) { return references_many(cs, k, false); }
@@ -819,6 +848,7 @@ int stim_info_get(const stim_circuit *c, stim_info *out) {
     out->num_layers = hp.num_layers_exec;
     out->num_program_layers = hp.num_layers_stored;
     out->reference_key = hp.skeleton_hash;
+    out->flip_ring_rows = hp.ring_len;
     return STIM_OK;
 }
 
@@ -907,6 +937,8 @@ void stim_free(stim_circuit *c) {
         cudaFree(c->d_geo);
         cudaFree(c->d_det_ptr);
         cudaFree(c->d_det_meas);
+        cudaFree(c->d_det_items);
+        cudaFree(c->d_det_looks);
         cudaFree(c->d_ref);
         cudaFree(c->d_detflag);
         cudaFree(c->d_status);
@@ -918,6 +950,7 @@ void stim_free(stim_circuit *c) {
             cudaFree(sc.gframe);
             cudaFree(sc.hits);
             cudaFree(sc.hits_out);
+            cudaFree(sc.ring);
             if (sc.done) cudaEventDestroy(sc.done);
         }
         for (DevFrameProgram &d : c->fprog) {
@@ -958,7 +991,7 @@ int stim_frame_sample_ex(stim_circuit *c, uint64_t num_shots, uint64_t seed, uin
                          uint64_t *meas_out, uint64_t *det_out, int flags, const stim_tile_hint *hint,
                          void *stream) {
     if (!c) return fail(STIM_E_INVALID_ARG, "stim_frame_sample: null handle");
-    if (!valid_flags(flags, STIM_HOST | STIM_SHOT_MAJOR | STIM_ASYNC))
+    if (!valid_flags(flags, STIM_HOST | STIM_SHOT_MAJOR | STIM_ASYNC | STIM_EVENTS_IN_KERNEL))
         return fail(STIM_E_INVALID_ARG, "stim_frame_sample: unknown flags");
     if (shot_offset % 64) return fail(STIM_E_INVALID_ARG, "stim_frame_sample: shot_offset must be a multiple of 64");
     if ((shot_offset + num_shots + 63) / 64 > (1ull << 32))
@@ -1004,8 +1037,13 @@ int stim_frame_sample_ex(stim_circuit *c, uint64_t num_shots, uint64_t seed, uin
 
     // ---- record buffers ----
     const bool meas_direct = meas_out && !shot_major && !host;
+    // detection events alone: computed inside the frame kernel from a ring of
+    // recent flips when the circuit allows it, so no record buffer is written
+    constexpr uint64_t kRecordBytesForRing = 8ull << 30;     // records above this take the ring by themselves
+    const bool want_ring = (flags & STIM_EVENTS_IN_KERNEL) || M * nwords * 8 > kRecordBytesForRing;
+    const size_t ring_words = (det_out && !meas_out && D > 0 && want_ring) ? stimgb_ring_words(c, num_shots, tc) : 0;
     // classically controlled ops read the records back inside the frame kernel
-    const bool need_rec = (meas_out || det_out || hp.num_feedforward > 0) && M > 0;
+    const bool need_rec = (meas_out || (det_out && !ring_words) || hp.num_feedforward > 0) && M > 0;
     uint64_t *rec = nullptr;
     if (need_rec) {
         if (meas_direct) {
@@ -1032,7 +1070,12 @@ int stim_frame_sample_ex(stim_circuit *c, uint64_t num_shots, uint64_t seed, uin
             det = sc.det;
         }
     }
-    if ((r = launch_sampling(c, num_shots, seed, shot_offset, tc, rec, det, gframe, st)) != STIM_OK) return r;
+    uint64_t *ring = nullptr;
+    if (ring_words) {
+        if ((r = grow(&sc.ring, &sc.ring_cap, ring_words, "alloc flip ring")) != STIM_OK) return r;
+        ring = sc.ring;
+    }
+    if ((r = launch_sampling(c, num_shots, seed, shot_offset, tc, rec, det, gframe, ring, st)) != STIM_OK) return r;
     if (async) {
         STIMGB_CK(cudaEventRecord(c->kernels_done, st), "record kernels");
         c->kernels_pending = true;

@@ -81,7 +81,7 @@ __global__ void __launch_bounds__(frame_max_threads(W), frame_min_ctas(W)) batch
         for (uint32_t i = threadIdx.x; i < sizeof(FrameArgs) / 4; i += blockDim.x)
             reinterpret_cast<uint32_t *>(sa)[i] = __ldg(src + i);
         __syncthreads();
-        frame_detail::run_tile<W, C, false>(*sa, tile_dyn, rank, it.tile);
+        frame_detail::run_tile<W, C, false, false>(*sa, tile_dyn, rank, it.tile);
         __syncthreads();
     }
 }
@@ -345,6 +345,7 @@ int fill_descs(stim_batch *b, const uint64_t *seeds, const uint64_t *offsets, ui
         a.last_mask = last_mask;
         a.rec = hp.num_meas ? rec : nullptr;
         a.rec_stride = nwords;
+        a.rec_mask = 0xFFFFFFFFu;
         a.status = c->d_status;
         a.seed = seeds[i];
         a.meta_bytes = fp->meta_bytes;

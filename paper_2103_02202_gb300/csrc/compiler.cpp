@@ -383,15 +383,18 @@ class Emitter {
     Emitter(HostProgram *hp, uint32_t n) : hp_(hp), stamp_(n, 0), last_(n, 0) {}
 
     // Emit the body of `b` for its first iteration, with the given starting
-    // instruction ordinal and measurement index. Returns layer executions.
-    uint64_t emit(const Block &b, uint64_t instr, uint64_t meas, uint32_t depth) {
+    // instruction ordinal, measurement index and detector index. Returns
+    // layer executions.
+    uint64_t emit(const Block &b, uint64_t instr, uint64_t meas, uint64_t det, uint32_t depth) {
         if (depth > hp_->max_loop_depth) hp_->max_loop_depth = depth;
         if (depth > (uint32_t)kMaxLoopDepth) throw ParseError{STIM_E_UNSUPPORTED, "REPEAT nested more than 16 deep"};
         uint64_t exec = 0;
         begin_segment();
+        uint64_t seg_meas0 = meas;
         for (const Node &nd : b.items) {
             if (nd.block) {
                 exec += flush();
+                flush_dets(meas, meas - seg_meas0);
                 Counts inner;
                 uint32_t mq = 0;
                 bool any = false;
@@ -402,8 +405,9 @@ class Emitter {
                 e.reps = (uint32_t)nd.block->reps;
                 e.instr_stride = (uint32_t)inner.instr;
                 e.meas_stride = (uint32_t)inner.meas;
+                e.n_noise = (uint32_t)inner.det;        // detector stride
                 hp_->prog.push_back(e);
-                uint64_t body = emit(*nd.block, instr, meas, depth + 1);
+                uint64_t body = emit(*nd.block, instr, meas, det, depth + 1);
                 if (hp_->prog.size() == begin_idx + 1) {
                     hp_->prog.pop_back();       // body without layers: nothing to repeat
                 } else {
@@ -416,11 +420,21 @@ class Emitter {
                 exec += body * nd.block->reps;
                 instr += inner.instr * nd.block->reps;
                 meas += inner.meas * nd.block->reps;
+                det += inner.det * nd.block->reps;
                 begin_segment();
+                seg_meas0 = meas;
                 continue;
             }
             const Instr &in = nd.ins;
-            if (in.gate != PG_DET && in.gate != PG_OBS) {
+            if (in.gate == PG_DET || in.gate == PG_OBS) {
+                // record lookbacks were validated when the detectors were collected
+                DetItem it{};
+                it.row = in.gate == PG_DET ? (uint32_t)det++ : (kObsRow | (uint32_t)in.p);
+                it.look_begin = (uint32_t)hp_->det_looks.size();
+                it.look_count = (uint32_t)in.targets.size();
+                for (uint32_t k : in.targets) hp_->det_looks.push_back((uint32_t)(meas - k));
+                seg_dets_.push_back(it);
+            } else {
                 uint32_t op = opcode_of(in.gate);
                 uint32_t table = 0;
                 if (op_is_noise(op)) {
@@ -475,7 +489,16 @@ class Emitter {
             instr++;
         }
         exec += flush();
+        flush_dets(meas, meas - seg_meas0);
         return exec;
+    }
+
+    // Ring length for the DETS entries emitted (0 without any).
+    uint64_t ring_len() const {
+        if (!any_dets_) return 0;
+        uint64_t r = 1;
+        while (r <= max_det_dist_ + max_seg_meas_) r <<= 1;
+        return r;
     }
 
   private:
@@ -489,6 +512,29 @@ class Emitter {
     std::vector<LayerBuild> layers_;
     uint32_t last_collapse_ = 0;      // layer index + 1 of the last collapsing op
     std::map<std::vector<uint64_t>, uint32_t> tables_;
+    std::vector<DetItem> seg_dets_;   // detectors and observables of the open stretch
+    bool any_dets_ = false;
+    uint64_t max_det_dist_ = 0;       // farthest lookback of a DETS entry from its position
+    uint64_t max_seg_meas_ = 0;       // most measurements of one straight-line stretch
+
+    // A DETS entry for the detectors and observables of the stretch that ends
+    // here (meas measurements made so far, seg_meas of them in the stretch).
+    void flush_dets(uint64_t meas, uint64_t seg_meas) {
+        max_seg_meas_ = std::max(max_seg_meas_, seg_meas);
+        if (seg_dets_.empty()) return;
+        ProgEntry e{};
+        e.kind = ENT_DETS;
+        e.op_begin = (uint32_t)hp_->det_items.size();
+        e.n_gate = (uint32_t)seg_dets_.size();
+        e.meas_stride = (uint32_t)meas;
+        for (const DetItem &it : seg_dets_)
+            for (uint32_t k = 0; k < it.look_count; k++)
+                max_det_dist_ = std::max<uint64_t>(max_det_dist_, meas - hp_->det_looks[it.look_begin + k]);
+        hp_->det_items.insert(hp_->det_items.end(), seg_dets_.begin(), seg_dets_.end());
+        hp_->prog.push_back(e);
+        seg_dets_.clear();
+        any_dets_ = true;
+    }
 
     void begin_segment() {
         seg_++;
@@ -872,7 +918,9 @@ void build_frame_program(const HostProgram &hp, int C, FrameProgram *out) {
             k = j;
             continue;
         }
-        if (e.kind == ENT_LOOP_BEGIN) {
+        if (e.kind == ENT_DETS) {
+            fp.prog.push_back(e);       // evaluated between merged layers; indexes HostProgram::det_items
+        } else if (e.kind == ENT_LOOP_BEGIN) {
             open.push_back(fp.prog.size());
             layer_count.push_back(0);
             fp.prog.push_back(e);
@@ -933,7 +981,8 @@ int compile_circuit(const char *text, size_t len, HostProgram *out, std::string 
             }
         hp.skeleton_hash = h;
         Emitter em(&hp, hp.num_qubits ? hp.num_qubits : 1);
-        hp.num_layers_exec = em.emit(root, 0, 0, 0);
+        hp.num_layers_exec = em.emit(root, 0, 0, 0, 0);
+        hp.ring_len = em.ring_len();
         *out = std::move(hp);
         return 0;
     } catch (const ParseError &e) {

@@ -31,17 +31,21 @@
 
 namespace stimgb {
 
-template <int W, int C, bool GMEM>
+template <int W, int C, bool GMEM, bool DETS>
 __global__ void __launch_bounds__(frame_max_threads(W), frame_min_ctas(W)) frame_kernel(const __grid_constant__ FrameArgs a) {
     extern __shared__ __align__(128) unsigned char dyn_smem[];
     const uint32_t rank = C > 1 ? (uint32_t)(blockIdx.x % C) : 0u;
-    frame_detail::run_tile<W, C, GMEM>(a, dyn_smem, rank, blockIdx.x / C);
+    frame_detail::run_tile<W, C, GMEM, DETS>(a, dyn_smem, rank, blockIdx.x / C);
 }
 
 template <int W, int C, bool GMEM>
 static cudaError_t launch_frame_t(const FrameArgs &a, uint32_t tiles, uint32_t threads, size_t smem,
                                   cudaStream_t stream) {
-    auto kern = frame_kernel<W, C, GMEM>;
+    // detection events in the kernel: shared-memory frames of 1 or 8 words
+    // per tile only (the shapes the tile chooser picks by itself)
+    constexpr bool kDets = !GMEM && (W == 1 || W == 8);
+    if (a.det != nullptr && !kDets) return cudaErrorInvalidValue;
+    auto kern = a.det != nullptr ? frame_kernel<W, C, GMEM, kDets> : frame_kernel<W, C, GMEM, false>;
     if (smem > 48 * 1024) {
         cudaError_t err = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         if (err != cudaSuccess) return err;

@@ -265,8 +265,9 @@ __device__ __forceinline__ void noise_op(const FrameArgs &a, const SmemKeys key,
 }
 
 // Applies one op to the V words at word offset wo of the tile (word tile0 + wo
-// of the call).
-template <int W, int C, bool GMEM>
+// of the call). DETS: detection events are computed in the kernel, so
+// measurements write their flips into the ring rows of a.rec.
+template <int W, int C, bool GMEM, bool DETS>
 __device__ __forceinline__ void frame_op(const FrameArgs &a, const SmemKeys key, const Tile<W, C, GMEM> &t,
                                          const DevOp op, uint32_t wo, uint32_t tile0, uint32_t instr_off,
                                          uint32_t meas_off) {
@@ -332,9 +333,17 @@ __device__ __forceinline__ void frame_op(const FrameArgs &a, const SmemKeys key,
         case OP_R: {
             if (opc != OP_R) qa.load(t, pa);
             if (opc != OP_R && a.rec != nullptr) {
+                // the record (reference xor flip), or with in-kernel detection
+                // events the flip alone, in ring row m & rec_mask
                 const uint32_t m = op.b + meas_off;
-                const uint64_t refm = 0ull - ((__ldg(a.ref + (m >> 6)) >> (m & 63)) & 1ull);
-                uint64_t *row = a.rec + (uint64_t)m * a.rec_stride;
+                uint64_t refm = 0;
+                uint64_t *row;
+                if constexpr (DETS) {
+                    row = a.rec + (uint64_t)(m & a.rec_mask) * a.rec_stride;
+                } else {
+                    refm = 0ull - ((__ldg(a.ref + (m >> 6)) >> (m & 63)) & 1ull);
+                    row = a.rec + (uint64_t)m * a.rec_stride;
+                }
 #pragma unroll
                 for (int i = 0; i < V; i++) {
                     const uint32_t lw = lw0 + i;
@@ -468,6 +477,58 @@ __device__ __forceinline__ void deferred_hit(const FrameArgs &a, const SmemKeys 
     if (pair) xor_qubit_word<W, C, GMEM>(t, ov.y, w, mxb, mzb);
 }
 
+// Detection events of the DETS entry items [first, first + n) for this tile:
+// each detector is the XOR of its records' flips, read from the ring rows of
+// a.rec (written by every CTA of the tile before the barrier this follows);
+// observables XOR into their rows. The tile's items x words are spread over
+// the cluster's CTAs and their threads, four items per thread at a time so
+// that their ring loads (L2: other SMs wrote them) are in flight together.
+// Padding bits of the last word are cleared.
+template <int W, int C>
+__device__ __forceinline__ void eval_dets(const FrameArgs &a, uint32_t rank, uint32_t tile0, uint32_t first,
+                                          uint32_t n, uint32_t meas_off, uint32_t det_off) {
+    constexpr uint32_t kBatch = 4;
+    const uint32_t total = n * W, stride = C * blockDim.x;
+    const uint4 *items = reinterpret_cast<const uint4 *>(a.det_items) + first;
+    const unsigned long long *ring = reinterpret_cast<const unsigned long long *>(a.rec);
+    for (uint32_t u0 = rank * blockDim.x + threadIdx.x; u0 < total; u0 += kBatch * stride) {
+        uint4 it[kBatch];
+        uint64_t lw[kBatch], v[kBatch];
+        bool ok[kBatch];
+        uint32_t maxl = 0;
+#pragma unroll
+        for (uint32_t b = 0; b < kBatch; b++) {
+            const uint32_t u = u0 + b * stride;
+            lw[b] = (uint64_t)tile0 + u % W;
+            ok[b] = u < total && lw[b] < a.nwords;
+            it[b] = ok[b] ? __ldg(items + u / W) : make_uint4(0u, 0u, 0u, 0u);
+            v[b] = 0;
+            maxl = max(maxl, it[b].z);
+        }
+        for (uint32_t j = 0; j < maxl; j++) {
+#pragma unroll
+            for (uint32_t b = 0; b < kBatch; b++) {
+                if (j < it[b].z) {
+                    const uint32_t m = __ldg(a.det_looks + it[b].y + j) + meas_off;
+                    v[b] ^= __ldcg(ring + (uint64_t)(m & a.rec_mask) * a.rec_stride + lw[b]);
+                }
+            }
+        }
+#pragma unroll
+        for (uint32_t b = 0; b < kBatch; b++) {
+            if (!ok[b]) continue;
+            uint64_t x = v[b];
+            if (lw[b] == a.nwords - 1) x &= a.last_mask;
+            if (it[b].x & kObsRow)
+                atomicXor(reinterpret_cast<unsigned long long *>(
+                              a.det + (a.num_dets + (uint64_t)(it[b].x & ~kObsRow)) * a.det_stride + lw[b]),
+                          (unsigned long long)x);
+            else
+                a.det[(uint64_t)(it[b].x + det_off) * a.det_stride + lw[b]] = x;
+        }
+    }
+}
+
 __device__ __forceinline__ uint64_t to_global(const void *p) {
     uint64_t g;
     asm("cvta.to.global.u64 %0, %1;" : "=l"(g) : "l"(p));
@@ -476,8 +537,9 @@ __device__ __forceinline__ uint64_t to_global(const void *p) {
 
 // Propagates the frames of one tile (W words, this CTA's qubit slice) through
 // the whole program. dyn = start of the tile's dynamic shared memory (layout
-// above). Returns false on a malformed program.
-template <int W, int C, bool GMEM>
+// above). DETS: evaluate the program's DETS entries from the flip ring
+// (a.det set); otherwise they are skipped. Returns false on a malformed program.
+template <int W, int C, bool GMEM, bool DETS>
 __device__ __forceinline__ bool run_tile(const FrameArgs &a, unsigned char *dyn, uint32_t rank, uint64_t tile) {
     constexpr int V = VecWidth<W>::V;
     if (blockDim.x % 32u != 0u) {       // partial warps would stall the hit-queue ballots
@@ -527,6 +589,15 @@ __device__ __forceinline__ bool run_tile(const FrameArgs &a, unsigned char *dyn,
     const uint4 *ops = reinterpret_cast<const uint4 *>(a.ops);
     bool ok = true;
     uint32_t instr_off = 0, meas_off = 0;
+    // a DETS entry waiting for the next barrier: its item count here, its
+    // first item and the offsets of its loop iteration in shared memory (the
+    // same values in every thread). Two slots (header bytes 80..103), used in
+    // turn: with a cluster the end-of-layer arrive does not wait, so a fast
+    // thread may record the next DETS entry while a slow one still evaluates
+    // the pending one -- never further ahead, since the next layer's wait
+    // needs the slow thread's arrive.
+    uint32_t dets_n = 0, dets_slot = 0;
+#define STIMGB_DETS_AT (reinterpret_cast<uint32_t *>(dyn + 80 + 12 * dets_slot))
     uint32_t loop_pc[kMaxLoopDepth];
     uint32_t loop_iter[kMaxLoopDepth];
     int sp = 0;
@@ -574,7 +645,7 @@ __device__ __forceinline__ bool run_tile(const FrameArgs &a, unsigned char *dyn,
                             if (j + 1 < len) nxt = __ldg(ops + op0 + j + 1);     // one op ahead
                             else if (have_next) nxt = __ldg(ops + op2);         // across items
                             if (j < dfrom) {
-                                if (act) frame_op<W, C, GMEM>(a, key, t, as_op(ov), wo, tile0, instr_off, meas_off);
+                                if (act) frame_op<W, C, GMEM, DETS>(a, key, t, as_op(ov), wo, tile0, instr_off, meas_off);
                             } else {
                                 const uint32_t hits =
                                     act ? noise_hits<V>(a, key, as_op(ov), (uint32_t)a.word0 + tile0 + wo, instr_off)
@@ -603,7 +674,31 @@ __device__ __forceinline__ bool run_tile(const FrameArgs &a, unsigned char *dyn,
                 }
                 if (qn) flush(qn);
             }
+            if (DETS && dets_n) {
+                // the last stretch's flips were in the ring at this layer's
+                // barrier; this layer's measurements do not reach their rows
+                eval_dets<W, C>(a, rank, tile0, STIMGB_DETS_AT[0], dets_n, STIMGB_DETS_AT[1], STIMGB_DETS_AT[2]);
+                dets_n = 0;
+            }
             tile_arrive<C>();
+            pc++;
+        } else if (e.kind == ENT_DETS) {
+            if constexpr (DETS) {
+                if (dets_n) {       // two DETS entries without a layer between: a barrier of its own
+                    tile_wait<C>();
+                    eval_dets<W, C>(a, rank, tile0, STIMGB_DETS_AT[0], dets_n, STIMGB_DETS_AT[1], STIMGB_DETS_AT[2]);
+                    tile_arrive<C>();
+                }
+                // detector offset of this loop iteration: iterations so far
+                // times each enclosing loop's detector count
+                uint32_t det_off = 0;
+                for (int k = 0; k < sp; k++) det_off += loop_iter[k] * prog[loop_pc[k]].n_noise;
+                dets_slot ^= 1u;
+                STIMGB_DETS_AT[0] = e.op_begin;
+                STIMGB_DETS_AT[1] = meas_off;
+                STIMGB_DETS_AT[2] = det_off;
+                dets_n = e.n_gate;
+            }
             pc++;
         } else if (e.kind == ENT_LOOP_BEGIN) {
             if (sp >= kMaxLoopDepth) {
@@ -635,6 +730,8 @@ __device__ __forceinline__ bool run_tile(const FrameArgs &a, unsigned char *dyn,
         }
     }
     tile_wait<C>();
+    if (DETS && dets_n && ok) eval_dets<W, C>(a, rank, tile0, STIMGB_DETS_AT[0], dets_n, STIMGB_DETS_AT[1], STIMGB_DETS_AT[2]);
+#undef STIMGB_DETS_AT
     return ok;
 }
 

@@ -35,6 +35,8 @@ struct stim_circuit {
     uint64_t *d_geo = nullptr;
     uint64_t *d_det_ptr = nullptr;
     uint32_t *d_det_meas = nullptr;
+    stimgb::DetItem *d_det_items = nullptr;    // DETS entries' detectors (see HostProgram)
+    uint32_t *d_det_looks = nullptr;
     uint64_t *d_ref = nullptr;
     uint64_t *d_detflag = nullptr;
     int *d_status = nullptr;
@@ -57,6 +59,8 @@ struct stim_circuit {
         size_t hits_cap = 0;
         uint64_t *hits_out = nullptr;     // per-shot event lists: host-bound detector indices
         size_t hits_out_cap = 0;
+        uint64_t *ring = nullptr;         // recent measurement flips (detection events in the frame kernel)
+        size_t ring_cap = 0;
         cudaEvent_t done = nullptr;
         bool used = false;
     } scratch[2];
@@ -90,3 +94,7 @@ int stimgb_sampling_layout(stim_circuit *c, uint64_t num_shots, TileChoice *tc, 
 // ceil(num_shots/64) words, required when det is given; any may be null).
 int stimgb_sample_into(stim_circuit *c, uint64_t num_shots, uint64_t seed, uint64_t shot_offset, const TileChoice &tc,
                        uint64_t *rec, uint64_t *det, uint64_t *gframe, cudaStream_t st);
+// Words of the flip ring for detection events computed inside the frame
+// kernel, or 0 when that path does not apply (no detectors, classically
+// controlled ops, or a ring no smaller than a quarter of the records).
+size_t stimgb_ring_words(const stim_circuit *c, uint64_t num_shots, const TileChoice &tc);

@@ -76,15 +76,29 @@ struct DevOp {
 // Device status words written by kernels (read by the host after a sync).
 enum : int { DEV_OK = 0, DEV_TIMEOUT = 1, DEV_BAD_PROGRAM = 2 };
 
-enum : uint32_t { ENT_LAYER = 0, ENT_LOOP_BEGIN = 1, ENT_LOOP_END = 2 };
+enum : uint32_t { ENT_LAYER = 0, ENT_LOOP_BEGIN = 1, ENT_LOOP_END = 2, ENT_DETS = 3 };
+
+// One DETECTOR or OBSERVABLE_INCLUDE of a straight-line stretch of the
+// program (between REPEAT boundaries): its detection-event row (detector
+// index of the first loop iteration, or kObsRow | observable index) and the
+// absolute measurement indices (first iteration) of its records,
+// looks[look_begin .. look_begin + look_count).
+struct DetItem {
+    uint32_t row, look_begin, look_count, pad;
+};
+constexpr uint32_t kObsRow = 0x80000000u;
 
 // Program entry (32 bytes).
 //   LAYER:      ops [op_begin, op_begin + n_gate + n_noise + n_collapse), stored
 //               as gates, then noise, then collapsing ops in source order.
 //   LOOP_BEGIN: reps iterations of the entries up to the matching LOOP_END;
-//               each iteration advances instruction ordinals by instr_stride
-//               and measurement indices by meas_stride.
-//   LOOP_END:   op_begin = index of the matching LOOP_BEGIN.
+//               each iteration advances instruction ordinals by instr_stride,
+//               measurement indices by meas_stride and detector indices by
+//               n_noise (the loop body's DETECTOR count).
+//   LOOP_END:   op_begin = index of the matching LOOP_BEGIN (strides as above).
+//   DETS:       the detectors and observables of the straight-line stretch
+//               that ends here: det_items [op_begin, op_begin + n_gate);
+//               meas_stride = measurements made so far (first iteration).
 struct ProgEntry {
     uint32_t kind;
     uint32_t op_begin;
@@ -110,6 +124,14 @@ struct HostProgram {
     std::vector<double> table_p;
     std::vector<uint64_t> det_ptr;          // num_det + 1 offsets into det_meas
     std::vector<uint32_t> det_meas;         // absolute measurement indices
+    // the same detectors and observables as DETS entries of the program
+    // (loop bodies once), for evaluation inside the frame kernel from a ring
+    // of recent measurement flips; ring_len is a power of two larger than the
+    // farthest a DETS entry looks back plus the measurements of one
+    // straight-line stretch (0 when the program has no DETS entry)
+    std::vector<DetItem> det_items;
+    std::vector<uint32_t> det_looks;
+    uint64_t ring_len = 0;
     // noiseless skeleton (source-order gates, collapses and classically
     // controlled ops with their targets, REPEAT structure) and its FNV-1a
     // hash: equal skeletons give equal reference samples

@@ -30,6 +30,19 @@ struct FrameArgs {
     uint64_t seed;             // Philox key = (seed lo, seed hi)
     uint32_t meta_bytes;       // bytes of prog + rank_tab + segs (one buffer starting at prog)
     uint32_t meta_region;      // shared bytes reserved for them; copied there when meta_bytes fits
+    // Detection events inside the frame kernel (det null: DETS entries are
+    // skipped and the detector kernel reads the records instead). With det
+    // set, rec holds each measurement's flip (x before the collapse; the
+    // record xor the reference) in a ring of the rec_mask + 1 most recent
+    // measurements, row m & rec_mask; a DETS entry XORs its detectors' ring
+    // words into det rows [num_dets][det_stride] (observables XOR into rows
+    // num_dets + k, cleared before the launch). rec_mask is all ones otherwise.
+    uint32_t rec_mask;
+    uint32_t num_dets;         // DETECTOR rows (observables follow)
+    uint64_t *det;
+    uint64_t det_stride;
+    const DetItem *det_items;
+    const uint32_t *det_looks;
 };
 
 // Dynamic shared memory of a frame tile: a header (round keys, then 32

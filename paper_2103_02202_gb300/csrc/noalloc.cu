@@ -122,6 +122,7 @@ extern "C" int stim_frame_sample_noalloc(stim_circuit *c, uint64_t num_shots, ui
         a.last_mask = (num_shots % 64) ? ((1ull << (num_shots % 64)) - 1) : ~0ull;
         a.rec = rec;
         a.rec_stride = nwords;
+        a.rec_mask = 0xFFFFFFFFu;
         a.status = c->d_status;
         const uint64_t grid = (nwords + W - 1) / W;
         a.meta_bytes = fp.meta_bytes;

@@ -358,6 +358,10 @@ __device__ __forceinline__ void tableau_body(const TabArgs &a, uint32_t bid) {
             pc++;
             continue;
         }
+        if (e.kind == ENT_DETS) {       // detectors do not act on the tableau
+            pc++;
+            continue;
+        }
         if (e.kind == ENT_LOOP_END) {
             if (sp <= 0) {
                 if (gtid == 0) atomicExch(a.status, DEV_BAD_PROGRAM);
