@@ -62,6 +62,7 @@ def parse_args():
     ap.add_argument("--shots", type=int, default=0, help="shots per step (0 = the workload's)")
     ap.add_argument("--tile", default="", help="frame tile hint W,threads,global,cluster (default: library's)")
     ap.add_argument("--no-c3", action="store_true", help="skip the 64-circuit batch sub-result")
+    ap.add_argument("--no-ttfs", action="store_true", help="skip the Bacon-Shor / random-circuit time to first sample")
     ap.add_argument("--no-c5", action="store_true", help="skip the serving sub-result")
     ap.add_argument("--c3-steps", type=int, default=3, help="timed steps of the 64-circuit batch sub-result")
     ap.add_argument("--c5-requests", type=int, default=3000, help="requests of the serving sub-result")
@@ -296,6 +297,30 @@ def run_reference_arm(args, wl, text):
 def workload_name(wl):
     return ("rotated surface-code memory d=%d, %d rounds, p=%g, %d shots per step"
             % (wl["d"], wl["rounds"], wl["p"], wl["shots"]))
+
+
+def measure_ttfs():
+    """Time to first sample (compile + inverse-tableau reference sample, the
+    tableau's random-measurement path) on the paper's Section 6 workload
+    families: Bacon-Shor memories (rounds = d, p = 1e-3) and random Clifford
+    circuits (depth = n)."""
+    import torch
+    import paper_2103_02202_gb300 as sg
+    from paper_2103_02202_gb300 import workloads as W
+    cases = [("bacon_shor", d, W.bacon_shor(d, d, 1e-3)) for d in (10, 20, 40, 60)]
+    cases += [("random_clifford", n, W.random_clifford(n, n, 7)) for n in (250, 500, 1000, 2000)]
+    out = []
+    for fam, size, text in cases:
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        c = sg.Circuit(text)
+        c.reference(recompute=True)
+        torch.cuda.synchronize()
+        dt = time.perf_counter() - t0
+        out.append({"family": fam, "size": size, "qubits": c.num_qubits, "measurements": c.num_measurements,
+                    "time_to_first_sample_s": dt})
+        c.close()
+    return out
 
 
 C3_NAME = ("64 circuits: 32 rotated surface codes d in 3..31, rounds d..2d, p log-uniform [1e-4, 1e-2]; "
@@ -689,6 +714,30 @@ def main():
         sg.stim_batch_free(plan)
         del dets_b
 
+    # ---- the same steps with detection events computed inside the frame
+    # kernel (STIM_EVENTS_IN_KERNEL: flip ring, no record buffer) ----
+    in_kernel = None
+    if world == 1:
+        def kstep(i):
+            sg.stim_frame_sample_ex(circ.handle, shots, 2021, shard_offset(rank, world, i, shots), 0, det.data_ptr(),
+                                    sg.STIM_DEVICE | sg.STIM_EVENTS_IN_KERNEL, hint, stream.cuda_stream)
+
+        for i in range(2):
+            kstep(i)
+        torch.cuda.synchronize()
+        k0 = torch.cuda.Event(enable_timing=True)
+        k1 = torch.cuda.Event(enable_timing=True)
+        k0.record(stream)
+        for i in range(args.steps):
+            kstep(args.warmup + i)
+        k1.record(stream)
+        torch.cuda.synchronize()
+        kms = k0.elapsed_time(k1) / args.steps
+        in_kernel = {"value": shots * gate_targets / (kms / 1000.0), "unit": "shot-gates/s", "ms_per_step": kms,
+                     "flip_ring_rows": info.get("flip_ring_rows"),
+                     "record_bytes_avoided_per_step": M * nwords * 8,
+                     "ring_bytes": (info.get("flip_ring_rows") or 0) * nwords * 8}
+
     # ---- end to end: same steps through the public API with host output ----
     # Asynchronous host copies (STIM_ASYNC) on two alternating streams: step
     # i's detection events travel to pinned host memory while step i+1's
@@ -825,6 +874,7 @@ def main():
                                     torch.cuda.get_device_properties(local).multi_processor_count),
         },
         "batched": batched,
+        "events_in_kernel": in_kernel,
         "e2e": {"value": e2e_dense_value, "unit": "shot-gates/s", "h2d_bytes_per_step": 0,
                 "d2h_bytes_per_step": D * nwords * 8, "steps": e2e_steps,
                 "output": "bit-packed detection events in host memory via stim_frame_sample_ex "
@@ -840,6 +890,8 @@ def main():
     }
     # ---- rows a9 and a10 on the same box: the 64-circuit batch (batched vs
     # plain) and the serving loop (served vs plain), device-resident outputs ----
+    if world == 1 and not args.no_ttfs:
+        line["time_to_first_sample_section6"] = measure_ttfs()
     if world == 1 and not args.no_c3:
         line["c3_batch"] = measure_c3(args.c3_steps, 1)
     if world == 1 and not args.no_c5:

@@ -259,6 +259,93 @@ def repetition_code(distance: int, rounds: int, p: float) -> str:
     return "REPEAT %d {\n%s\n}\n" % (rounds, "\n".join("    " + b for b in body))
 
 
+def bacon_shor(d: int, rounds: int, p: float, observable: bool = False) -> str:
+    """Memory experiment on the distance-d Bacon-Shor code (the subsystem
+    code of the paper's time-to-first-sample benchmarks, Section 6): data
+    qubits on a d x d grid, q(r, c) = r * d + c; two-qubit gauge operators
+    X(r, c) X(r + 1, c) on vertical pairs and Z(r, c) Z(r, c + 1) on
+    horizontal pairs, each measured through an ancilla (X gauges: H, CX
+    ancilla -> data twice, H, MR; Z gauges: CX data -> ancilla twice, MR),
+    X gauges first each round. The gauges do not commute with each other, so
+    most gauge outcomes are random and the inverse-tableau reference sample
+    spends its time on random measurements. Noise as in the surface-code
+    memory: DEPOLARIZE1 after H layers, DEPOLARIZE2 after CX layers, X_ERROR
+    before measurements.
+
+    Detectors compare the stabilizers (products of gauges) between rounds:
+    the Z stabilizer of columns (c, c + 1) is the product of the d Z gauges of
+    that column pair, the X stabilizer of rows (r, r + 1) that of the d X
+    gauges of that row pair; round 1 has Z-stabilizer detectors only, and the
+    final Z-basis data measurement closes each Z stabilizer. With
+    observable=True the data of column 0 (a logical Z) is observable 0."""
+    if d < 2 or rounds < 1:
+        raise ValueError("need d >= 2 and rounds >= 1")
+    nd = d * d
+    xg = [(r, c) for r in range(d - 1) for c in range(d)]        # X(r,c) X(r+1,c)
+    zg = [(r, c) for r in range(d) for c in range(d - 1)]        # Z(r,c) Z(r,c+1)
+    xa = {g: nd + k for k, g in enumerate(xg)}
+    za = {g: nd + len(xg) + k for k, g in enumerate(zg)}
+    q = lambda r, c: r * d + c   # noqa: E731
+    pp = _fmt_p(p) if p > 0 else None
+    xs = " ".join(str(xa[g]) for g in xg)
+    zs = " ".join(str(za[g]) for g in zg)
+    rnd = [f"H {xs}"]
+    if pp:
+        rnd.append(f"DEPOLARIZE1({pp}) {xs}")
+    for dr in (0, 1):
+        pairs = " ".join(f"{xa[(r, c)]} {q(r + dr, c)}" for (r, c) in xg)
+        rnd.append(f"CX {pairs}")
+        if pp:
+            rnd.append(f"DEPOLARIZE2({pp}) {pairs}")
+    rnd.append(f"H {xs}")
+    if pp:
+        rnd.append(f"DEPOLARIZE1({pp}) {xs}")
+        rnd.append(f"X_ERROR({pp}) {xs}")
+    rnd.append(f"MR {xs}")
+    for dc in (0, 1):
+        pairs = " ".join(f"{q(r, c + dc)} {za[(r, c)]}" for (r, c) in zg)
+        rnd.append(f"CX {pairs}")
+        if pp:
+            rnd.append(f"DEPOLARIZE2({pp}) {pairs}")
+    if pp:
+        rnd.append(f"X_ERROR({pp}) {zs}")
+    rnd.append(f"MR {zs}")
+    nx, nz = len(xg), len(zg)
+    per_round = nx + nz
+    # record offsets (rec[-k]) of a round's gauges, counted back from the end of the round
+    xrec = {g: per_round - k for k, g in enumerate(xg)}
+    zrec = {g: nz - k for k, g in enumerate(zg)}
+
+    def zstab(c, back):
+        return " ".join(f"rec[-{zrec[(r, c)] + back}]" for r in range(d))
+
+    def xstab(r, back):
+        return " ".join(f"rec[-{xrec[(r, c)] + back}]" for c in range(d))
+
+    lines = [f"# Bacon-Shor memory, d={d}, rounds={rounds}, p={p}", "R " + " ".join(map(str, range(nd + nx + nz)))]
+    lines += rnd
+    for c in range(d - 1):
+        lines.append(f"DETECTOR {zstab(c, 0)}")
+    if rounds > 1:
+        lines.append(f"REPEAT {rounds - 1} {{")
+        lines += ["    " + x for x in rnd]
+        for c in range(d - 1):
+            lines.append(f"    DETECTOR {zstab(c, 0)} {zstab(c, per_round)}")
+        for r in range(d - 1):
+            lines.append(f"    DETECTOR {xstab(r, 0)} {xstab(r, per_round)}")
+        lines.append("}")
+    data = " ".join(map(str, range(nd)))
+    if pp:
+        lines.append(f"X_ERROR({pp}) {data}")
+    lines.append(f"M {data}")
+    for c in range(d - 1):
+        dat = " ".join(f"rec[-{nd - q(r, cc)}]" for r in range(d) for cc in (c, c + 1))
+        lines.append(f"DETECTOR {dat} {zstab(c, nd)}")
+    if observable:
+        lines.append("OBSERVABLE_INCLUDE(0) " + " ".join(f"rec[-{nd - q(r, 0)}]" for r in range(d)))
+    return "\n".join(lines) + "\n"
+
+
 def _log_uniform_int(rng, lo: float, hi: float) -> int:
     return int(round(math.exp(rng.uniform(math.log(lo), math.log(hi)))))
 

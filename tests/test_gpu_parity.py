@@ -326,7 +326,10 @@ def test_surface_d100_bench_configuration_sampled_parity():
     _, d = c.sample(S, 2021, shot_offset=off, meas=False)
     Sp = S - 7
     _, dp = c.sample(Sp, 2021, shot_offset=off, meas=False)
+    # the same events computed inside the frame kernel (flip ring, no records)
+    _, dk = c.sample(S, 2021, shot_offset=off, meas=False, events_in_kernel=True)
     torch.cuda.synchronize()
+    assert torch.equal(dk, d)
     o = oracle.Circuit(text)
     oref, odet = o.reference()
     M = c.num_measurements
@@ -837,3 +840,23 @@ def test_failed_device_allocations_leave_handles_usable():
         sg.stim_debug_fail_allocations(0, 0)
         sg.stim_reference_cache_set(256 << 20)
     assert failed_sites >= 8
+
+
+@pytest.mark.parametrize("d", [3, 8, 20, 30])
+def test_bacon_shor_reference_matches_oracle(d):
+    """Bacon-Shor memory (a random-measurement workload for the tableau):
+    reference sample and deterministic flags equal the oracle's, and sampled
+    detection events equal the oracle's on a few hundred shots."""
+    text = W.bacon_shor(d, d, 1e-3, observable=True)
+    ref, det = gpu_reference(text)
+    o = oracle.Circuit(text)
+    oref, odet = o.reference()
+    np.testing.assert_array_equal(ref, oref)
+    np.testing.assert_array_equal(det, odet)
+    c = sg.Circuit(text)
+    _, d_ev = c.sample(300, 17, meas=False)
+    torch.cuda.synchronize()
+    gd = words_to_bits(to_np(d_ev), 300).T
+    _, od = o.sample(np.arange(300), 17, threads=8, ref=oref)
+    np.testing.assert_array_equal(gd, od)
+    c.close()
