@@ -377,8 +377,13 @@ int reference_prepare(stim_circuit *c, cudaStream_t st, bool use_cache, RefJob *
     // the rounded part sizes, so the last part (the control words, which the
     // memset below must clear) lies wholly inside it.
     auto round256 = [](size_t b) { return (b + 255) & ~(size_t)255; };
+    // row-major copy for bursts of random measurements (circuits of 256 qubits or more)
+    const uint32_t nw2 = (2 * n + 63) / 64;
+    const bool rows = n >= 256;
+    const size_t bytes_rows = rows ? (size_t)n * nw2 * 8 : 0, bytes_rsign = rows ? (size_t)nw2 * 8 : 0;
     const size_t total = 2 * round256(bytes_tx) + 2 * round256(bytes_sign) + round256(bytes_klist) +
-                         round256(bytes_kmask) + round256(bytes_rnd) + round256(sizeof(TabCtl));
+                         round256(bytes_kmask) + round256(bytes_rnd) + round256(sizeof(TabCtl)) +
+                         (rows ? 2 * round256(bytes_rows) + round256(bytes_rsign) : 0);
     STIMGB_CK(dev_malloc_async((void **)&job->blob, total, st), "alloc tableau");
     size_t off = 0;
     auto take = [&](size_t b) {
@@ -394,6 +399,12 @@ int reference_prepare(stim_circuit *c, cudaStream_t st, bool use_cache, RefJob *
     a->kmask = (uint64_t *)take(bytes_kmask);
     a->rnd = (uint32_t *)take(bytes_rnd);
     a->ctl = (TabCtl *)take(sizeof(TabCtl));
+    if (rows) {
+        a->rx = (uint64_t *)take(bytes_rows);
+        a->rz = (uint64_t *)take(bytes_rows);
+        a->rsign = (uint64_t *)take(bytes_rsign);
+        a->nw2 = nw2;
+    }
     if (off != total) {
         cudaFreeAsync(job->blob, st);
         job->blob = nullptr;

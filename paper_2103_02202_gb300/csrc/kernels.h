@@ -81,6 +81,7 @@ struct TabCtl {
     uint32_t pivot_is_y;
     uint32_t fix_x;
     uint32_t use_mask;
+    uint32_t nk_sum, nk_cnt;   // CNOT targets of the random measurements resolved so far (burst choice)
 };
 
 struct TabArgs {
@@ -99,6 +100,11 @@ struct TabArgs {
     TabCtl *ctl;               // zeroed before launch
     int *status;
     uint32_t nblk;             // CTAs working on this circuit (set by the launchers)
+    // Row-major copy for bursts of random measurements (null: bursts off):
+    // rx/rz[row k][nw2 words], bit c = the x/z bit of physical column c at
+    // start-of-time qubit k; rsign[nw2] the column signs. nw2 = ceil(2n / 64).
+    uint64_t *rx, *rz, *rsign;
+    uint32_t nw2;
     uint32_t bar_extra;        // test knob: arrivals a barrier waits for beyond nblk (0 in normal use)
     uint64_t bar_timeout_ns;   // limit of one barrier wait
 };

@@ -214,6 +214,8 @@ __device__ void leader_walk(const TabArgs &a, const DevOp *cops, uint32_t nc, ui
             a.ctl->use_mask = cnt > kListLimit ? 1u : 0u;
             a.ctl->next_j = j;
             a.ctl->has_random = 1u;
+            a.ctl->nk_sum += cnt;
+            a.ctl->nk_cnt += 1u;
             // outcome 0 and not deterministic: nothing to set in ref / detflag
         }
         __syncwarp();
@@ -317,6 +319,157 @@ __device__ void column_pass_mask(const TabArgs &a, uint32_t p, uint32_t py, uint
     }
 }
 
+// ---------------------------------------------------------------------------
+// Bursts of random measurements in row-major form (Section 5's data layout:
+// the tableau is transposed while random measurements are resolved). Appending
+// a CNOT p -> k to the tableau touches every column at rows p and k; with
+// columns stored contiguously that is a pass over all 2n columns, with rows
+// stored contiguously it is a few words of rows p and k. A layer with many
+// random measurements, in a circuit whose random measurements have had few
+// CNOT targets, is transposed to rows by the whole grid, walked by CTA 0
+// (one measurement at a time, CTA barriers only), and transposed back.
+// ---------------------------------------------------------------------------
+constexpr uint32_t kBurstMinRandom = 16;    // random measurements in the layer
+constexpr uint32_t kBurstMaxMeanTargets = 32;
+// the other CTAs wait out a burst at one bounded barrier wait: cap its length
+constexpr uint32_t kBurstMaxOps = 20000;
+
+// rows <- columns: word cw of row k holds bit k of physical columns 64cw .. 64cw + 63.
+__device__ void to_rows(const TabArgs &a, uint32_t gtid, uint32_t nthreads) {
+    const uint64_t total = (uint64_t)a.n * a.nw2;
+    for (uint64_t i = gtid; i < total; i += nthreads) {
+        const uint32_t k = (uint32_t)(i % a.n), cw = (uint32_t)(i / a.n);   // consecutive threads: consecutive rows
+        const uint32_t kw = k >> 6, kb = k & 63;
+        uint64_t vx = 0, vz = 0;
+        for (uint32_t j = 0; j < 64; j++) {
+            const uint32_t c = 64 * cw + j;
+            if (c >= 2 * a.n) break;
+            vx |= ((__ldcg(a.tx + (uint64_t)c * a.nw + kw) >> kb) & 1ull) << j;
+            vz |= ((__ldcg(a.tz + (uint64_t)c * a.nw + kw) >> kb) & 1ull) << j;
+        }
+        __stcg(a.rx + (uint64_t)k * a.nw2 + cw, vx);
+        __stcg(a.rz + (uint64_t)k * a.nw2 + cw, vz);
+    }
+    for (uint32_t cw = gtid; cw < a.nw2; cw += nthreads) {
+        uint64_t v = 0;
+        for (uint32_t j = 0; j < 64 && 64 * cw + j < 2 * a.n; j++)
+            v |= (uint64_t)(__ldcg(a.sign + 64 * cw + j) & 1u) << j;
+        __stcg(a.rsign + cw, v);
+    }
+}
+
+// columns <- rows: word w of column c holds bit c of rows 64w .. 64w + 63.
+__device__ void to_cols(const TabArgs &a, uint32_t gtid, uint32_t nthreads) {
+    const uint64_t total = (uint64_t)2 * a.n * a.nw;
+    for (uint64_t i = gtid; i < total; i += nthreads) {
+        const uint32_t c = (uint32_t)(i % (2 * a.n)), w = (uint32_t)(i / (2 * a.n));
+        const uint32_t cw = c >> 6, cb = c & 63;
+        uint64_t vx = 0, vz = 0;
+        for (uint32_t j = 0; j < 64; j++) {
+            const uint32_t k = 64 * w + j;
+            if (k >= a.n) break;
+            vx |= ((__ldcg(a.rx + (uint64_t)k * a.nw2 + cw) >> cb) & 1ull) << j;
+            vz |= ((__ldcg(a.rz + (uint64_t)k * a.nw2 + cw) >> cb) & 1ull) << j;
+        }
+        __stcg(a.tx + (uint64_t)c * a.nw + w, vx);
+        __stcg(a.tz + (uint64_t)c * a.nw + w, vz);
+    }
+    for (uint32_t c = gtid; c < 2 * a.n; c += nthreads)
+        __stcg(a.sign + c, (uint32_t)((__ldcg(a.rsign + (c >> 6)) >> (c & 63)) & 1ull));
+}
+
+
+// The collapsing ops j .. nc - 1 of a layer in row-major form, by one CTA in
+// source order (the same results as the leader walk plus column passes):
+// a measurement of Z_q reads column pc = perm(Z_q); rows with an X/Y bit there
+// are found; none: deterministic, the outcome is the column's sign (a reset
+// then clears it); else the lowest such row p is the pivot, the CNOT fan-out
+// p -> k over the other rows k updates x_k ^= x_p, z_p ^= XOR of z_k and every
+// column's sign by the closed form of the column pass, and the pivot collapse
+// (S if the pivot term is Y, H, X when the sign is -) makes the outcome 0.
+__device__ void burst_walk(const TabArgs &a, const DevOp *cops, uint32_t nc, uint32_t j, uint32_t meas_off) {
+    __shared__ uint32_t s_pivot, s_cnt, s_py, s_fx;
+    const uint32_t tid = threadIdx.x, B = blockDim.x;
+    for (; j < nc; j++) {
+        const DevOp op = cops[j];
+        const uint32_t opc = op.a >> 24, q = op.a & kQubitMask;
+        const uint32_t pc = __ldcg(a.perm + 2 * q + 1);
+        const uint32_t cwp = pc >> 6;
+        const uint64_t bitp = 1ull << (pc & 63);
+        if (tid == 0) {
+            s_pivot = a.n;
+            s_cnt = 0;
+        }
+        __syncthreads();
+        for (uint32_t k = tid; k < a.n; k += B) {
+            if (__ldcg(a.rx + (uint64_t)k * a.nw2 + cwp) & bitp) {
+                atomicMin(&s_pivot, k);
+                __stcg(a.klist + atomicAdd(&s_cnt, 1u), k);
+            }
+        }
+        __syncthreads();
+        const uint32_t p = s_pivot, cnt = s_cnt;
+        if (cnt == 0) {     // deterministic: the outcome is the sign of column Z_q
+            if (tid == 0) {
+                const uint64_t sw = __ldcg(a.rsign + cwp);
+                write_outcome(a, opc, op.b + meas_off, (uint32_t)((sw & bitp) != 0), 1);
+                if (opc != OP_M) __stcg(a.rsign + cwp, sw & ~bitp);
+            }
+            __syncthreads();
+            continue;
+        }
+        if (tid == 0) {
+            a.ctl->nk_sum += cnt - 1;
+            a.ctl->nk_cnt += 1;
+        }
+        // CNOT fan-out p -> k, k in K \ {p}, word by word over the columns
+        for (uint32_t w = tid; w < a.nw2; w += B) {
+            const uint64_t xp = __ldcg(a.rx + (uint64_t)p * a.nw2 + w);
+            uint64_t zp = __ldcg(a.rz + (uint64_t)p * a.nw2 + w);
+            uint64_t apar = 0, b0 = 0, b1 = 0;
+            for (uint32_t t = 0; t < cnt; t++) {
+                const uint32_t k = __ldcg(a.klist + t);
+                if (k == p) continue;
+                const uint64_t xk = __ldcg(a.rx + (uint64_t)k * a.nw2 + w);
+                const uint64_t zk = __ldcg(a.rz + (uint64_t)k * a.nw2 + w);
+                apar ^= zk & ~(zp ^ xk);
+                b1 ^= b0 & zk;
+                b0 ^= zk;
+                __stcg(a.rx + (uint64_t)k * a.nw2 + w, xk ^ xp);
+            }
+            const uint64_t s = __ldcg(a.rsign + w) ^ (xp & (apar ^ b1));
+            zp ^= b0;
+            __stcg(a.rz + (uint64_t)p * a.nw2 + w, zp);
+            __stcg(a.rsign + w, s);
+            if (w == cwp) {
+                s_py = (uint32_t)((zp & bitp) != 0);     // the pivot term of Z_q is Y
+                s_fx = (uint32_t)((s & bitp) != 0);      // its sign is -
+            }
+        }
+        __syncthreads();
+        const bool py = s_py != 0, fx = s_fx != 0;
+        for (uint32_t w = tid; w < a.nw2; w += B) {      // pivot collapse on row p
+            uint64_t xp = __ldcg(a.rx + (uint64_t)p * a.nw2 + w);
+            uint64_t zp = __ldcg(a.rz + (uint64_t)p * a.nw2 + w);
+            uint64_t s = __ldcg(a.rsign + w);
+            if (py) {        // S: X -> -Y, Y -> X
+                s ^= xp & ~zp;
+                zp ^= xp;
+            }
+            s ^= xp & zp;    // H: Y -> -Y, X <-> Z
+            const uint64_t t = xp;
+            xp = zp;
+            zp = t;
+            if (fx) s ^= zp; // X: Z -> -Z, Y -> -Y
+            __stcg(a.rx + (uint64_t)p * a.nw2 + w, xp);
+            __stcg(a.rz + (uint64_t)p * a.nw2 + w, zp);
+            __stcg(a.rsign + w, s);
+        }
+        __syncthreads();
+        // a random outcome is 0: nothing to write (reference and flags start cleared)
+    }
+}
+
 }  // namespace
 
 __global__ void tableau_init_kernel(TabArgs a) {
@@ -338,7 +491,7 @@ __device__ __forceinline__ void tableau_body(const TabArgs &a, uint32_t bid) {
     const uint32_t gtid = bid * blockDim.x + threadIdx.x;
     const uint32_t nthreads = a.nblk * blockDim.x;
     const bool leader = bid == 0 && threadIdx.x < 32;
-    __shared__ uint32_t s_first;
+    __shared__ uint32_t s_first, s_nrand;
 
     uint32_t meas_off = 0;
     uint32_t loop_pc[kMaxLoopDepth];
@@ -467,12 +620,25 @@ __device__ __forceinline__ void tableau_body(const TabArgs &a, uint32_t bid) {
         }
         if (!tab_barrier(a)) return;
         // (B) first random op; everything before it is deterministic and independent
-        if (threadIdx.x == 0) s_first = nc;
+        if (threadIdx.x == 0) {
+            s_first = nc;
+            s_nrand = 0;
+        }
         __syncthreads();
         for (uint32_t j = threadIdx.x; j < nc; j += blockDim.x)
-            if (ld_u32<L1>(a.rnd + j)) atomicMin(&s_first, j);
+            if (ld_u32<L1>(a.rnd + j)) {
+                atomicMin(&s_first, j);
+                atomicAdd(&s_nrand, 1u);
+            }
         __syncthreads();
         const uint32_t first = s_first;
+        // row-major burst for this layer's random measurements: the same
+        // choice in every CTA (the statistics last changed before the barrier above)
+        bool burst = false;
+        if (!L1 && a.rx != nullptr && s_nrand >= kBurstMinRandom && nc - s_first <= kBurstMaxOps) {
+            const uint32_t kc = ld_u32<L1>(&a.ctl->nk_cnt), ks = ld_u32<L1>(&a.ctl->nk_sum);
+            burst = kc >= 4 && ks <= kBurstMaxMeanTargets * kc;
+        }
         for (uint32_t j = gtid; j < first; j += nthreads) {
             const DevOp op = cops[j];
             const uint32_t opc = op.a >> 24, q = op.a & kQubitMask;
@@ -482,6 +648,15 @@ __device__ __forceinline__ void tableau_body(const TabArgs &a, uint32_t bid) {
         }
         if (!tab_barrier(a)) return;
         if (first >= nc) continue;
+        if (burst) {
+            to_rows(a, gtid, nthreads);
+            if (!tab_barrier(a)) return;
+            if (bid == 0) burst_walk(a, cops, nc, first, meas_off);
+            if (!tab_barrier(a)) return;
+            to_cols(a, gtid, nthreads);
+            if (!tab_barrier(a)) return;
+            continue;
+        }
         // (C) sequential from the first random op
         uint32_t j = first;
         for (;;) {
