@@ -323,6 +323,40 @@ def measure_ttfs():
     return out
 
 
+def measure_rounds_sweep():
+    """Reference samples of a sweep over the number of rounds (rotated surface
+    code memories, d fixed, rounds d..4d): each computed from scratch, then
+    the same sweep with the tableau prefix states, where each memory resumes
+    inside its REPEAT block from the state the previous one stored."""
+    import torch
+    import paper_2103_02202_gb300 as sg
+    from paper_2103_02202_gb300 import workloads as W
+    out = []
+    for d in (25, 50):
+        rounds = [d, 2 * d, 3 * d, 4 * d]
+        texts = [W.surface_code_memory(d, r, 1e-3) for r in rounds]
+        res = {}
+        for mode in ("cold", "prefix_reuse"):
+            sg.stim_reference_cache_set(0)
+            sg.stim_reference_cache_set(256 << 20)
+            sg.stim_prefix_cache_set(0)
+            sg.stim_prefix_cache_set(1 << 30)
+            times = []
+            for t in texts:
+                c = sg.Circuit(t)
+                torch.cuda.synchronize()
+                t0 = time.perf_counter()
+                c.reference(recompute=mode == "cold")
+                torch.cuda.synchronize()
+                times.append(time.perf_counter() - t0)
+                c.close()
+            res[mode] = times
+        st = sg.stim_prefix_cache_stats()
+        out.append({"d": d, "rounds": rounds, "cold_s": res["cold"], "prefix_reuse_s": res["prefix_reuse"],
+                    "speedup": sum(res["cold"]) / sum(res["prefix_reuse"]), "resumes": st["resumes"]})
+    return out
+
+
 C3_NAME = ("64 circuits: 32 rotated surface codes d in 3..31, rounds d..2d, p log-uniform [1e-4, 1e-2]; "
            "32 random Clifford n in [50, 2000], depth [100, 1000]; shots log-uniform [1e3, 1e6] (seeded)")
 
@@ -892,6 +926,7 @@ def main():
     # plain) and the serving loop (served vs plain), device-resident outputs ----
     if world == 1 and not args.no_ttfs:
         line["time_to_first_sample_section6"] = measure_ttfs()
+        line["reference_rounds_sweep"] = measure_rounds_sweep()
     if world == 1 and not args.no_c3:
         line["c3_batch"] = measure_c3(args.c3_steps, 1)
     if world == 1 and not args.no_c5:

@@ -223,6 +223,32 @@ int stim_reference_cache_set(size_t budget_bytes);
 int stim_reference_cache_stats(uint64_t *hits, uint64_t *misses, uint64_t *entries, uint64_t *bytes);
 
 /*
+ * Tableau prefix states. A circuit with top-level REPEAT blocks has a cut
+ * point before and after each; the inverse tableau there (Section 3's state,
+ * with the reference bits of the measurements before it) depends only on the
+ * noiseless skeleton of the source before the cut and on the qubit count. A
+ * reference computation that misses the reference-sample cache and finds a
+ * stored state for one of its cuts -- same qubit count, same skeleton prefix,
+ * compared in full -- resumes there (the latest such cut) instead of at the
+ * identity; a computation that reaches its last cut with no state stored for
+ * it stores one (the tableau then runs as two launches with a device copy
+ * between them). Memories that differ only after their REPEAT block, e.g. in
+ * the final readout, then recompute only that part. States live in device
+ * memory: 2n columns of ceil(n/64) words for each of the X and Z planes plus
+ * signs, permutation and the reference words before the cut (about 200 MB at
+ * 20,000 qubits). STIM_RECOMPUTE neither reads nor stores them.
+ *
+ * stim_prefix_cache_set: device-byte budget (default 1 GiB); least recently
+ *   used states are freed to fit (after the copies out of them finish); 0
+ *   turns storing and resuming off and frees every state.
+ * stim_prefix_cache_stats: computations resumed from a stored state, states
+ *   stored, states and device bytes held; any pointer may be NULL.
+ * Both are thread-safe; they touch the GPU only to free evicted states.
+ */
+int stim_prefix_cache_set(size_t budget_bytes);
+int stim_prefix_cache_stats(uint64_t *resumes, uint64_t *saves, uint64_t *entries, uint64_t *bytes);
+
+/*
  * stim_debug_fail_allocations -- fault injection for tests: of the device
  * allocations the single-circuit paths make next (upload of a compiled
  * circuit, staging buffers of stim_frame_sample_ex, tableau scratch of the

@@ -32,7 +32,7 @@ __all__ = [
     "StimError", "library", "library_path", "stim_compile", "stim_info_get", "stim_frame_program_info_get",
     "stim_free",
     "stim_last_error", "stim_reference_sample", "stim_reference_many", "stim_reference_cache_set",
-    "stim_reference_cache_stats", "stim_debug_fail_allocations", "stim_debug_tableau_barrier", "stim_probe_smem_bandwidth", "stim_frame_sample", "stim_frame_sample_ex",
+    "stim_reference_cache_stats", "stim_prefix_cache_set", "stim_prefix_cache_stats", "stim_debug_fail_allocations", "stim_debug_tableau_barrier", "stim_probe_smem_bandwidth", "stim_frame_sample", "stim_frame_sample_ex",
     "Circuit", "EXPORTED_SYMBOLS", "stim_frame_sample_noalloc", "stim_batch_create", "stim_batch_sample",
     "stim_batch_info", "stim_batch_free", "Batch", "Server", "STIM_OUT_MEAS", "STIM_OUT_DET", "stim_profile", "stim_profile_read", "KERNEL_NAMES",
 ]
@@ -134,6 +134,9 @@ _SIGNATURES = {
     "stim_reference_sample": (ctypes.c_int, [_VP, _VP, _VP, ctypes.c_int, _VP]),
     "stim_reference_many": (ctypes.c_int, [ctypes.POINTER(_VP), ctypes.c_size_t, ctypes.c_int]),
     "stim_reference_cache_set": (ctypes.c_int, [ctypes.c_size_t]),
+    "stim_prefix_cache_set": (ctypes.c_int, [ctypes.c_size_t]),
+    "stim_prefix_cache_stats": (ctypes.c_int, [ctypes.POINTER(_U64), ctypes.POINTER(_U64),
+                                               ctypes.POINTER(_U64), ctypes.POINTER(_U64)]),
     "stim_debug_fail_allocations": (ctypes.c_int, [ctypes.c_int, ctypes.c_int]),
     "stim_debug_tableau_barrier": (ctypes.c_int, [ctypes.c_uint32, ctypes.c_uint64]),
     "stim_probe_smem_bandwidth": (ctypes.c_int, [ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_double)]),
@@ -264,6 +267,17 @@ def stim_reference_cache_stats() -> dict:
     v = [_U64() for _ in range(4)]
     _check(library().stim_reference_cache_stats(*[ctypes.byref(x) for x in v]))
     return dict(zip(("hits", "misses", "entries", "bytes"), (int(x.value) for x in v)))
+
+
+def stim_prefix_cache_set(budget_bytes: int) -> None:
+    """Device-byte budget of the stored tableau prefix states (0: off)."""
+    _check(library().stim_prefix_cache_set(int(budget_bytes)))
+
+
+def stim_prefix_cache_stats() -> dict:
+    v = [_U64() for _ in range(4)]
+    _check(library().stim_prefix_cache_stats(*[ctypes.byref(x) for x in v]))
+    return dict(zip(("resumes", "saves", "entries", "bytes"), (int(x.value) for x in v)))
 
 
 def stim_frame_sample(handle: int, num_shots: int, seed: int, meas_out: int = 0, det_out: int = 0,

@@ -312,6 +312,101 @@ RefCache &ref_cache() {
     return c;
 }
 
+// Device-resident inverse-tableau states at top-level REPEAT boundaries (the
+// cut points of HostProgram). The state there is a function of the noiseless
+// skeleton of the source before the cut and of the qubit count alone, so a
+// circuit sharing that skeleton prefix resumes its tableau there instead of
+// at the identity: memories that differ only in what follows their REPEAT
+// block (the final readout, extra rounds of a different kind) recompute only
+// that part. An entry holds the tableau columns, signs and permutation, the
+// control words, and the reference and determinism words of the measurements
+// before the cut. Entries are taken in least-recently-used order under a
+// device-memory budget; copies out of an entry are ordered by events that
+// eviction waits for.
+struct PrefixCache {
+    struct Entry {
+        std::vector<uint32_t> skeleton;   // skeleton words of the prefix
+        uint32_t n = 0;
+        uint64_t meas = 0;
+        int device = -1;
+        char *buf = nullptr;              // state | control words | ref words | detflag words
+        size_t state_bytes = 0, ctl_off = 0, ref_off = 0, det_off = 0, words = 0, bytes = 0;
+        // stored after a top-level REPEAT block (see HostProgram::CutPoint)
+        bool after_loop = false;
+        uint64_t loop_hash = 0, loop_reps = 0, reps_pos = 0;
+        uint64_t last_use = 0;
+        std::vector<cudaEvent_t> reads;   // copies out of buf that may still be in flight
+    };
+    std::mutex mu;
+    std::multimap<uint64_t, Entry> map;   // prefix hash -> entries
+    size_t bytes = 0, cap = (size_t)1 << 30;
+    uint64_t clock = 0, resumes = 0, saves = 0;
+
+    static void release(Entry &e) {
+        int cur = -1;
+        cudaGetDevice(&cur);
+        if (e.device >= 0 && e.device != cur) cudaSetDevice(e.device);
+        for (cudaEvent_t ev : e.reads) {
+            cudaEventSynchronize(ev);
+            cudaEventDestroy(ev);
+        }
+        e.reads.clear();
+        if (e.buf) cudaFreeAsync(e.buf, nullptr);
+        e.buf = nullptr;
+        if (e.device >= 0 && e.device != cur) cudaSetDevice(cur);
+    }
+    void evict_to(size_t limit) {          // lock held
+        while (bytes > limit && !map.empty()) {
+            auto old = map.begin();
+            for (auto it = map.begin(); it != map.end(); ++it)
+                if (it->second.last_use < old->second.last_use) old = it;
+            bytes -= old->second.bytes;
+            release(old->second);
+            map.erase(old);
+        }
+    }
+    // Entry for cut k of hp on device, or nullptr (lock held).
+    Entry *find(const HostProgram &hp, size_t k, int device) {
+        const HostProgram::CutPoint &ct = hp.cuts[k];
+        auto range = map.equal_range(ct.prefix_hash);
+        for (auto it = range.first; it != range.second; ++it) {
+            Entry &e = it->second;
+            if (e.device != device || e.n != hp.num_qubits || e.meas != ct.meas ||
+                e.skeleton.size() != ct.skeleton_len ||
+                !std::equal(e.skeleton.begin(), e.skeleton.end(), hp.skeleton.begin()))
+                continue;
+            return &e;
+        }
+        return nullptr;
+    }
+    // Entry holding the state after the most iterations (fewer than the
+    // circuit's own) of the REPEAT block before cut k of hp, with the same
+    // body and the same source before it; nullptr if none (lock held).
+    Entry *find_in_loop(const HostProgram &hp, size_t k, int device) {
+        const HostProgram::CutPoint &ct = hp.cuts[k];
+        if (ct.loop_begin == UINT32_MAX) return nullptr;
+        const uint64_t meas0 = ct.meas - ct.loop_reps * ct.loop_meas;     // before the block
+        Entry *best = nullptr;
+        for (auto &kv : map) {
+            Entry &e = kv.second;
+            if (!e.after_loop || e.loop_hash != ct.loop_hash || e.loop_reps == 0 || e.loop_reps >= ct.loop_reps ||
+                e.device != device || e.n != hp.num_qubits || e.reps_pos != ct.reps_pos ||
+                e.meas != meas0 + e.loop_reps * ct.loop_meas || e.skeleton.size() != ct.skeleton_len)
+                continue;
+            bool same = true;
+            for (size_t i = 0; i < e.skeleton.size() && same; i++)
+                same = i == ct.reps_pos || i == ct.reps_pos + 1 || e.skeleton[i] == hp.skeleton[i];
+            if (same && (!best || e.loop_reps > best->loop_reps)) best = &e;
+        }
+        return best;
+    }
+};
+
+PrefixCache &prefix_cache() {
+    static PrefixCache c;
+    return c;
+}
+
 // One reference-sample computation in flight: its stream and tableau scratch
 // (or the cached sample being copied in).
 struct RefJob {
@@ -321,7 +416,115 @@ struct RefJob {
     bool from_cache = false;
     bool to_cache = false;
     std::vector<uint64_t> ref, detflag;     // host copies (cache hit: source; miss: destination)
+    size_t state_bytes = 0;     // tableau columns, signs and permutation at the front of blob
+    int resume_cut = -1;        // cut of the circuit the tableau resumed at (a stored prefix state)
+    int save_cut = -1;          // cut whose state this computation stores
+    char *snap = nullptr;       // that state, until the kernel has succeeded (see PrefixCache)
+    size_t snap_ctl = 0, snap_ref = 0, snap_det = 0, snap_words = 0, snap_bytes = 0;
 };
+
+// Resumes the tableau of c at the latest cut whose prefix state is stored,
+// or part way through the REPEAT block before a cut when a circuit with the
+// same source before the block and the same body stored its state after
+// fewer iterations: copies the state into the scratch behind a and sets
+// a->pc_begin (and a->iter_begin). Leaves a untouched when none is stored.
+cudaError_t prefix_resume(stim_circuit *c, RefJob *job, TabArgs *a, cudaStream_t st, bool *resumed) {
+    *resumed = false;
+    PrefixCache &pc = prefix_cache();
+    std::lock_guard<std::mutex> g(pc.mu);
+    if (pc.cap == 0) return cudaSuccess;
+    const HostProgram &hp = c->hp;
+    for (size_t k = hp.cuts.size(); k-- > 0;) {
+        const HostProgram::CutPoint &ct = hp.cuts[k];
+        // the state at the cut itself, else part way through the block before it
+        uint32_t pc_begin = ct.prog_index, iter_begin = 0;
+        PrefixCache::Entry *en = ct.prog_index > 0 ? pc.find(hp, k, c->device) : nullptr;
+        if (!en && (en = pc.find_in_loop(hp, k, c->device)) != nullptr) {
+            pc_begin = ct.loop_begin;
+            iter_begin = (uint32_t)en->loop_reps;
+        }
+        if (!en || en->state_bytes != job->state_bytes) continue;
+        cudaError_t e = cudaMemcpyAsync(job->blob, en->buf, en->state_bytes, cudaMemcpyDeviceToDevice, st);
+        if (e == cudaSuccess) e = cudaMemcpyAsync(a->ctl, en->buf + en->ctl_off, sizeof(TabCtl), cudaMemcpyDeviceToDevice, st);
+        if (e == cudaSuccess && en->words)
+            e = cudaMemcpyAsync(c->d_ref, en->buf + en->ref_off, en->words * 8, cudaMemcpyDeviceToDevice, st);
+        if (e == cudaSuccess && en->words)
+            e = cudaMemcpyAsync(c->d_detflag, en->buf + en->det_off, en->words * 8, cudaMemcpyDeviceToDevice, st);
+        cudaEvent_t ev = nullptr;
+        if (e == cudaSuccess) e = cudaEventCreateWithFlags(&ev, cudaEventDisableTiming);
+        if (e == cudaSuccess) e = cudaEventRecord(ev, st);
+        if (ev) {
+            for (size_t i = 0; i < en->reads.size();) {
+                if (cudaEventQuery(en->reads[i]) == cudaSuccess) {
+                    cudaEventDestroy(en->reads[i]);
+                    en->reads[i] = en->reads.back();
+                    en->reads.pop_back();
+                } else {
+                    i++;
+                }
+            }
+            en->reads.push_back(ev);
+        }
+        if (e != cudaSuccess) return e;
+        en->last_use = ++pc.clock;
+        pc.resumes++;
+        a->pc_begin = pc_begin;
+        a->iter_begin = iter_begin;
+        job->resume_cut = (int)k;
+        *resumed = true;
+        return cudaSuccess;
+    }
+    return cudaSuccess;
+}
+
+// The cut whose state a computation of c starting at pc_begin stores: the
+// last one after pc_begin, unless it is stored already (-1: none).
+int prefix_save_choice(const stim_circuit *c, uint32_t pc_begin) {
+    const HostProgram &hp = c->hp;
+    if (hp.cuts.empty() || hp.cuts.back().prog_index <= pc_begin) return -1;
+    PrefixCache &pc = prefix_cache();
+    std::lock_guard<std::mutex> g(pc.mu);
+    if (pc.cap == 0) return -1;
+    const size_t k = hp.cuts.size() - 1;
+    return pc.find(hp, k, c->device) ? -1 : (int)k;
+}
+
+// Moves the state a successful computation stored (job->snap) into the
+// prefix cache, or frees it when an equal one got there first or it exceeds
+// the budget.
+void prefix_store(stim_circuit *c, RefJob *job) {
+    PrefixCache &pc = prefix_cache();
+    std::lock_guard<std::mutex> g(pc.mu);
+    const HostProgram &hp = c->hp;
+    const HostProgram::CutPoint &ct = hp.cuts[(size_t)job->save_cut];
+    if (pc.cap == 0 || job->snap_bytes > pc.cap || pc.find(hp, (size_t)job->save_cut, c->device)) {
+        cudaFreeAsync(job->snap, job->st);
+        job->snap = nullptr;
+        return;
+    }
+    PrefixCache::Entry en;
+    en.skeleton.assign(hp.skeleton.begin(), hp.skeleton.begin() + (long)ct.skeleton_len);
+    en.n = hp.num_qubits;
+    en.meas = ct.meas;
+    en.device = c->device;
+    en.buf = job->snap;
+    en.state_bytes = job->state_bytes;
+    en.ctl_off = job->snap_ctl;
+    en.ref_off = job->snap_ref;
+    en.det_off = job->snap_det;
+    en.words = job->snap_words;
+    en.bytes = job->snap_bytes;
+    en.after_loop = ct.loop_begin != UINT32_MAX;
+    en.loop_hash = ct.loop_hash;
+    en.loop_reps = ct.loop_reps;
+    en.reps_pos = ct.reps_pos;
+    en.last_use = ++pc.clock;
+    job->snap = nullptr;
+    pc.evict_to(pc.cap - en.bytes);
+    pc.bytes += en.bytes;
+    pc.saves++;
+    pc.map.emplace(ct.prefix_hash, std::move(en));
+}
 
 // CTAs of the inverse-tableau kernel for c: ~1024 column words per CTA
 // (measured best for random circuits; d=100 uses all SMs either way), at most
@@ -347,6 +550,9 @@ int reference_prepare(stim_circuit *c, cudaStream_t st, bool use_cache, RefJob *
     job->launched = false;
     job->from_cache = false;
     job->to_cache = false;
+    job->resume_cut = -1;
+    job->save_cut = -1;
+    job->snap = nullptr;
     if (n > 0 && hp.num_meas > 0 && use_cache && ref_cache().lookup(hp, c->ref_words, &job->ref, &job->detflag)) {
         STIMGB_CK(cudaMemcpyAsync(c->d_ref, job->ref.data(), c->ref_words * 8, cudaMemcpyHostToDevice, st), "copy reference");
         STIMGB_CK(cudaMemcpyAsync(c->d_detflag, job->detflag.data(), c->ref_words * 8, cudaMemcpyHostToDevice, st),
@@ -363,6 +569,8 @@ int reference_prepare(stim_circuit *c, cudaStream_t st, bool use_cache, RefJob *
     *a = TabArgs{};
     a->prog = c->d_prog;
     a->nprog = (uint32_t)hp.prog.size();
+    a->pc_begin = 0;
+    a->pc_end = a->nprog;
     a->ops = c->d_ops;
     a->n = n;
     a->nw = nw;
@@ -410,9 +618,14 @@ int reference_prepare(stim_circuit *c, cudaStream_t st, bool use_cache, RefJob *
         job->blob = nullptr;
         return fail(STIM_E_CUDA, "reference sample: tableau scratch layout mismatch");
     }
+    job->state_bytes = 2 * round256(bytes_tx) + 2 * round256(bytes_sign);
     cudaError_t e = cudaMemsetAsync(job->blob, 0, total, st);
     if (e == cudaSuccess) e = cudaMemsetAsync(c->d_status, 0, sizeof(int), st);
-    if (e == cudaSuccess) e = launch_tableau_init(*a, st);
+    // a stored state of the longest shared skeleton prefix, else the identity
+    bool resumed = false;
+    if (e == cudaSuccess && use_cache) e = prefix_resume(c, job, a, st, &resumed);
+    if (e == cudaSuccess && !resumed) e = launch_tableau_init(*a, st);
+    if (e == cudaSuccess && use_cache) job->save_cut = prefix_save_choice(c, a->pc_begin);
     if (e != cudaSuccess) {
         cudaFreeAsync(job->blob, st);
         job->blob = nullptr;
@@ -420,6 +633,42 @@ int reference_prepare(stim_circuit *c, cudaStream_t st, bool use_cache, RefJob *
     }
     *needs_kernel = true;
     return STIM_OK;
+}
+
+// The tableau of c in two launches split at cut job->save_cut, with the
+// state at the cut copied into job->snap between them (when the allocation
+// fails the computation goes on without storing it).
+cudaError_t launch_tableau_saving(stim_circuit *c, RefJob *job, const TabArgs &a, uint32_t blocks, cudaStream_t st) {
+    const HostProgram::CutPoint &ct = c->hp.cuts[(size_t)job->save_cut];
+    TabArgs head = a;
+    head.pc_end = ct.prog_index;
+    cudaError_t e = launch_tableau(head, blocks, kTableauThreads, st);
+    if (e != cudaSuccess) return e;
+    auto round256 = [](size_t b) { return (b + 255) & ~(size_t)255; };
+    const size_t words = (size_t)((ct.meas + 63) / 64);
+    job->snap_words = words;
+    job->snap_ctl = round256(job->state_bytes);
+    job->snap_ref = job->snap_ctl + round256(sizeof(TabCtl));
+    job->snap_det = job->snap_ref + round256(words * 8);
+    job->snap_bytes = job->snap_det + round256(words * 8);
+    if (dev_malloc_async((void **)&job->snap, job->snap_bytes, st) != cudaSuccess) {
+        cudaGetLastError();
+        job->snap = nullptr;
+    } else {
+        e = cudaMemcpyAsync(job->snap, job->blob, job->state_bytes, cudaMemcpyDeviceToDevice, st);
+        if (e == cudaSuccess)
+            e = cudaMemcpyAsync(job->snap + job->snap_ctl, a.ctl, sizeof(TabCtl), cudaMemcpyDeviceToDevice, st);
+        if (e == cudaSuccess && words)
+            e = cudaMemcpyAsync(job->snap + job->snap_ref, c->d_ref, words * 8, cudaMemcpyDeviceToDevice, st);
+        if (e == cudaSuccess && words)
+            e = cudaMemcpyAsync(job->snap + job->snap_det, c->d_detflag, words * 8, cudaMemcpyDeviceToDevice, st);
+        if (e != cudaSuccess) return e;
+    }
+    if (ct.prog_index >= a.nprog) return cudaSuccess;
+    TabArgs tail = a;
+    tail.pc_begin = ct.prog_index;
+    tail.iter_begin = 0;
+    return launch_tableau(tail, blocks, kTableauThreads, st);
 }
 
 // Launches the inverse-tableau kernel of c on st with at most max_blocks CTAs
@@ -436,11 +685,13 @@ int reference_launch(stim_circuit *c, cudaStream_t st, uint32_t max_blocks, bool
     cudaError_t e;
     {
         ProfScope ps(STIM_KERNEL_TABLEAU, st);
-        e = launch_tableau(a, blocks, kTableauThreads, st);
+        e = job->save_cut >= 0 ? launch_tableau_saving(c, job, a, blocks, st) : launch_tableau(a, blocks, kTableauThreads, st);
     }
     if (e != cudaSuccess) {
         cudaFreeAsync(job->blob, st);
         job->blob = nullptr;
+        if (job->snap) cudaFreeAsync(job->snap, st);
+        job->snap = nullptr;
         return cuda_fail(e, "reference sample");
     }
     job->launched = true;
@@ -468,6 +719,14 @@ int reference_finish(stim_circuit *c, RefJob *job) {
     }
     const cudaError_t s = cudaStreamSynchronize(job->st);
     if (e == cudaSuccess) e = s;
+    if (job->snap) {        // the state stored at a cut is kept only from a kernel that succeeded
+        if (e == cudaSuccess && status == 0) {
+            prefix_store(c, job);
+        } else {
+            cudaFreeAsync(job->snap, job->st);
+            job->snap = nullptr;
+        }
+    }
     if (e != cudaSuccess) return cuda_fail(e, "reference sample");
     if (status == DEV_TIMEOUT) return fail(STIM_E_TIMEOUT, "tableau grid barrier timed out");
     if (status != 0) return fail(STIM_E_CUDA, "tableau kernel reported a malformed program");
@@ -923,6 +1182,24 @@ int stim_reference_cache_set(size_t budget_bytes) {
     std::lock_guard<std::mutex> g(rc.mu);
     rc.cap = budget_bytes;
     rc.evict_to(budget_bytes);
+    return STIM_OK;
+}
+
+int stim_prefix_cache_set(size_t budget_bytes) {
+    PrefixCache &pc = prefix_cache();
+    std::lock_guard<std::mutex> g(pc.mu);
+    pc.cap = budget_bytes;
+    pc.evict_to(budget_bytes);
+    return STIM_OK;
+}
+
+int stim_prefix_cache_stats(uint64_t *resumes, uint64_t *saves, uint64_t *entries, uint64_t *bytes) {
+    PrefixCache &pc = prefix_cache();
+    std::lock_guard<std::mutex> g(pc.mu);
+    if (resumes) *resumes = pc.resumes;
+    if (saves) *saves = pc.saves;
+    if (entries) *entries = pc.map.size();
+    if (bytes) *bytes = pc.bytes;
     return STIM_OK;
 }
 

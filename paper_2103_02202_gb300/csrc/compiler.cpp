@@ -406,6 +406,7 @@ class Emitter {
                 e.instr_stride = (uint32_t)inner.instr;
                 e.meas_stride = (uint32_t)inner.meas;
                 e.n_noise = (uint32_t)inner.det;        // detector stride
+                if (depth == 0) cut_at(meas, (size_t)(&nd - b.items.data()));
                 hp_->prog.push_back(e);
                 uint64_t body = emit(*nd.block, instr, meas, det, depth + 1);
                 if (hp_->prog.size() == begin_idx + 1) {
@@ -421,6 +422,10 @@ class Emitter {
                 instr += inner.instr * nd.block->reps;
                 meas += inner.meas * nd.block->reps;
                 det += inner.det * nd.block->reps;
+                if (depth == 0)
+                    cut_at(meas, (size_t)(&nd - b.items.data()) + 1,
+                           hp_->prog.size() == begin_idx ? UINT32_MAX : (uint32_t)begin_idx, nd.block->reps,
+                           inner.meas);
                 begin_segment();
                 seg_meas0 = meas;
                 continue;
@@ -491,6 +496,21 @@ class Emitter {
         exec += flush();
         flush_dets(meas, meas - seg_meas0);
         return exec;
+    }
+
+    // Top-level cut points recorded while emitting; the caller adds the
+    // prefix hashes of the items before each.
+    struct Cut {
+        uint32_t prog_index;     // first program entry after the cut
+        uint64_t meas;           // measurements before it
+        size_t items_before;     // top-level source items before it
+        uint32_t loop_begin;     // after a REPEAT block: its LOOP_BEGIN entry (UINT32_MAX: none emitted)
+        uint64_t loop_reps, loop_meas;
+    };
+    std::vector<Cut> cuts;
+    void cut_at(uint64_t meas, size_t items_before, uint32_t loop_begin = UINT32_MAX, uint64_t loop_reps = 0,
+                uint64_t loop_meas = 0) {
+        cuts.push_back(Cut{(uint32_t)hp_->prog.size(), meas, items_before, loop_begin, loop_reps, loop_meas});
     }
 
     // Ring length for the DETS entries emitted (0 without any).
@@ -654,23 +674,40 @@ class Emitter {
 // targets, and REPEAT structure, in source order. Noise channels, DETECTOR and
 // OBSERVABLE_INCLUDE do not change the reference sample, so circuits with
 // equal skeletons have equal reference samples.
+void skeleton_node(const Node &nd, std::vector<uint32_t> *out);
+
 void skeleton_of(const Block &b, std::vector<uint32_t> *out) {
-    for (const Node &nd : b.items) {
-        if (nd.block) {
-            out->push_back(0xFFFFFFFFu);
-            out->push_back((uint32_t)nd.block->reps);
-            out->push_back((uint32_t)(nd.block->reps >> 32));
-            skeleton_of(*nd.block, out);
-            out->push_back(0xFFFFFFFEu);
-            continue;
-        }
-        const Instr &in = nd.ins;
-        if (in.gate == PG_DET || in.gate == PG_OBS) continue;
-        if (op_is_noise(opcode_of(in.gate))) continue;
-        out->push_back((uint32_t)in.gate);
-        out->push_back((uint32_t)in.targets.size());
-        out->insert(out->end(), in.targets.begin(), in.targets.end());
+    for (const Node &nd : b.items) skeleton_node(nd, out);
+}
+
+// One item's part of the skeleton: a REPEAT block is bracketed by two marker
+// words with its repetition count; noise channels, DETECTOR and
+// OBSERVABLE_INCLUDE add nothing.
+void skeleton_node(const Node &nd, std::vector<uint32_t> *out) {
+    if (nd.block) {
+        out->push_back(0xFFFFFFFFu);
+        out->push_back((uint32_t)nd.block->reps);
+        out->push_back((uint32_t)(nd.block->reps >> 32));
+        skeleton_of(*nd.block, out);
+        out->push_back(0xFFFFFFFEu);
+        return;
     }
+    const Instr &in = nd.ins;
+    if (in.gate == PG_DET || in.gate == PG_OBS) return;
+    if (op_is_noise(opcode_of(in.gate))) return;
+    out->push_back((uint32_t)in.gate);
+    out->push_back((uint32_t)in.targets.size());
+    out->insert(out->end(), in.targets.begin(), in.targets.end());
+}
+
+// FNV-1a over the bytes of v, continuing from h.
+uint64_t fnv_words(uint64_t h, const std::vector<uint32_t> &v, size_t begin = 0) {
+    for (size_t i = begin; i < v.size(); i++)
+        for (int k = 0; k < 4; k++) {
+            h ^= (v[i] >> (8 * k)) & 0xFFu;
+            h *= 1099511628211ull;
+        }
+    return h;
 }
 
 // Flattened detector list: absolute measurement index of every rec[-k].
@@ -972,17 +1009,44 @@ int compile_circuit(const char *text, size_t len, HostProgram *out, std::string 
             hp.det_meas.insert(hp.det_meas.end(), o.begin(), o.end());
             hp.det_ptr.push_back(hp.det_meas.size());
         }
-        skeleton_of(root, &hp.skeleton);
-        uint64_t h = 1469598103934665603ull;        // FNV-1a over the skeleton's bytes
-        for (uint32_t v : hp.skeleton)
-            for (int k = 0; k < 4; k++) {
-                h ^= (v >> (8 * k)) & 0xFFu;
-                h *= 1099511628211ull;
-            }
+        // skeleton item by item, with the FNV-1a hash of every prefix
+        std::vector<uint64_t> prefix_hash(root.items.size() + 1);
+        std::vector<size_t> prefix_len(root.items.size() + 1);
+        uint64_t h = 1469598103934665603ull;
+        prefix_hash[0] = h;
+        prefix_len[0] = 0;
+        for (size_t i = 0; i < root.items.size(); i++) {
+            const size_t before = hp.skeleton.size();
+            skeleton_node(root.items[i], &hp.skeleton);
+            h = fnv_words(h, hp.skeleton, before);
+            prefix_hash[i + 1] = h;
+            prefix_len[i + 1] = hp.skeleton.size();
+        }
         hp.skeleton_hash = h;
         Emitter em(&hp, hp.num_qubits ? hp.num_qubits : 1);
         hp.num_layers_exec = em.emit(root, 0, 0, 0, 0);
         hp.ring_len = em.ring_len();
+        for (const Emitter::Cut &ct : em.cuts) {
+            HostProgram::CutPoint cp{};
+            cp.prog_index = ct.prog_index;
+            cp.meas = ct.meas;
+            cp.prefix_hash = prefix_hash[ct.items_before];
+            cp.skeleton_len = prefix_len[ct.items_before];
+            cp.loop_begin = ct.loop_begin;
+            if (ct.loop_begin != UINT32_MAX) {
+                // the same prefix hashed with the block's repetition count (the
+                // two words after its opening marker) taken as zero
+                const size_t at = prefix_len[ct.items_before - 1];
+                uint64_t lh = prefix_hash[ct.items_before - 1];
+                std::vector<uint32_t> part(hp.skeleton.begin() + (long)at, hp.skeleton.begin() + (long)cp.skeleton_len);
+                part[1] = part[2] = 0;
+                cp.loop_hash = fnv_words(lh, part);
+                cp.loop_reps = ct.loop_reps;
+                cp.loop_meas = ct.loop_meas;
+                cp.reps_pos = at + 1;
+            }
+            hp.cuts.push_back(cp);
+        }
         *out = std::move(hp);
         return 0;
     } catch (const ParseError &e) {

@@ -132,6 +132,28 @@ struct HostProgram {
     std::vector<DetItem> det_items;
     std::vector<uint32_t> det_looks;
     uint64_t ring_len = 0;
+    // Top-level boundaries of REPEAT blocks, where the program has no open
+    // loop: the tableau state there depends only on the noiseless skeleton
+    // of the source before it (prefix_hash, FNV-1a like skeleton_hash) and
+    // on num_qubits, so a circuit sharing that prefix may resume from it.
+    struct CutPoint {
+        uint32_t prog_index;     // first program entry after the boundary
+        uint64_t meas;           // measurements before it
+        uint64_t prefix_hash;
+        uint64_t skeleton_len;   // skeleton words of that prefix
+        // A cut right after a top-level REPEAT block that emitted entries:
+        // the state there is also the state after loop_reps iterations of
+        // any block with the same body and the same source before it, so a
+        // circuit repeating that body at least as often resumes inside its
+        // loop. loop_hash is prefix_hash with the repetition count (the
+        // skeleton words reps_pos and reps_pos + 1) taken as zero.
+        uint32_t loop_begin;     // the block's LOOP_BEGIN entry (UINT32_MAX: not such a cut)
+        uint64_t loop_reps;
+        uint64_t loop_meas;      // measurements per iteration
+        uint64_t loop_hash;
+        uint64_t reps_pos;
+    };
+    std::vector<CutPoint> cuts;
     // noiseless skeleton (source-order gates, collapses and classically
     // controlled ops with their targets, REPEAT structure) and its FNV-1a
     // hash: equal skeletons give equal reference samples

@@ -105,6 +105,11 @@ struct TabArgs {
     // start-of-time qubit k; rsign[nw2] the column signs. nw2 = ceil(2n / 64).
     uint64_t *rx, *rz, *rsign;
     uint32_t nw2;
+    // program entries [pc_begin, pc_end) are walked (a top-level stretch: the
+    // tableau of an earlier prefix may be resumed, or saved part way); with
+    // iter_begin > 0, pc_begin is a top-level LOOP_BEGIN entered at that
+    // iteration (the state of the earlier iterations resumed)
+    uint32_t pc_begin, pc_end, iter_begin;
     uint32_t bar_extra;        // test knob: arrivals a barrier waits for beyond nblk (0 in normal use)
     uint64_t bar_timeout_ns;   // limit of one barrier wait
 };

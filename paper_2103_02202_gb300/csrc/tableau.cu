@@ -497,16 +497,25 @@ __device__ __forceinline__ void tableau_body(const TabArgs &a, uint32_t bid) {
     uint32_t loop_pc[kMaxLoopDepth];
     uint32_t loop_iter[kMaxLoopDepth];
     int sp = 0;
-    uint32_t pc = 0;
-    while (pc < a.nprog) {
+    uint32_t pc = a.pc_begin;
+    const uint32_t pc_end = a.pc_end < a.nprog ? a.pc_end : a.nprog;
+    // a computation resumed inside a loop enters it at iteration iter_begin
+    uint32_t enter_iter = a.iter_begin;
+    if (enter_iter && (pc >= pc_end || a.prog[pc].kind != ENT_LOOP_BEGIN)) {
+        if (gtid == 0) atomicExch(a.status, DEV_BAD_PROGRAM);
+        return;
+    }
+    while (pc < pc_end) {
         const ProgEntry e = a.prog[pc];
         if (e.kind == ENT_LOOP_BEGIN) {
-            if (sp >= kMaxLoopDepth) {
+            if (sp >= kMaxLoopDepth || enter_iter >= (e.reps > 0 ? e.reps : 1u)) {
                 if (gtid == 0) atomicExch(a.status, DEV_BAD_PROGRAM);
                 return;
             }
             loop_pc[sp] = pc;
-            loop_iter[sp] = 0;
+            loop_iter[sp] = enter_iter;
+            meas_off += enter_iter * e.meas_stride;
+            enter_iter = 0;
             sp++;
             pc++;
             continue;
