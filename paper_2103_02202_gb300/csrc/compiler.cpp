@@ -627,8 +627,9 @@ class Emitter {
     //   DEPOLARIZE1: T[i] = ceil((i + 1) 2^32 / 3), i < 2, so the index is 1 + floor(3v / 2^32);
     //   DEPOLARIZE2: T[i] = ceil((i + 1) 2^32 / 15), i < 14, i.e. 1 + floor(15v / 2^32);
     //   PAULI_CHANNEL_1/2 with probabilities q: T[i] = round-half-even(2^32 (q_1 + ... + q_{i+1}) / p);
-    //   every other threshold 2^32. T[15] = 3 or 15 for the depolarizing
-    //   channels (the kernel multiplies instead of scanning), else 0.
+    //   every other threshold 2^32. T[15]'s low half = 3 or 15 for the
+    //   depolarizing channels (the kernel multiplies instead of scanning),
+    //   else 0; its high half a gap estimate constant (below).
     uint32_t table_for(const Instr &in) {
         const uint64_t kind = in.gate == PG_DEP1 ? 1 : in.gate == PG_DEP2 ? 2 : in.gate == PG_PC1 ? 3
                             : in.gate == PG_PC2 ? 4 : 0;
@@ -663,6 +664,19 @@ class Emitter {
                 if (t > (1LL << 32)) t = 1LL << 32;
                 T[i] = (uint64_t)t;
             }
+        }
+        // T[15]'s upper half: the float 1 / log2(1 - q) of the table's
+        // per-shot probability q = t / 2^32, from which the kernel estimates
+        // a gap before checking it against G (0 when q is 0 or 1)
+        {
+            long long t = llrint(ldexp(in.p, 32));
+            if (t < 0) t = 0;
+            if (t > (1LL << 32)) t = 1LL << 32;
+            float inv = 0.0f;
+            if (t > 0 && t < (1LL << 32)) inv = (float)(1.0 / log2(1.0 - ldexp((double)t, -32)));
+            uint32_t bits;
+            memcpy(&bits, &inv, sizeof bits);
+            T[15] |= (uint64_t)bits << 32;
         }
         tables_[key] = id;
         return id;

@@ -29,6 +29,9 @@ __device__ __forceinline__ uint64_t lds64(uint32_t a) {
 __device__ __forceinline__ void sts64(uint32_t a, uint64_t v) {
     asm volatile("st.shared.u64 [%0], %1;" ::"r"(a), "l"(v) : "memory");
 }
+__device__ __forceinline__ void sts128(uint32_t a, uint4 v) {
+    asm volatile("st.shared.v4.u32 [%0], {%1, %2, %3, %4};" ::"r"(a), "r"(v.x), "r"(v.y), "r"(v.z), "r"(v.w) : "memory");
+}
 __device__ __forceinline__ uint4 lds128(uint32_t a) {
     uint4 v;
     asm volatile("ld.shared.v4.u32 {%0, %1, %2, %3}, [%4];" : "=r"(v.x), "=r"(v.y), "=r"(v.z), "=r"(v.w) : "r"(a));
@@ -81,13 +84,25 @@ __device__ __forceinline__ uint64_t half_mask(K key, uint32_t tag_instr, uint32_
     return (uint64_t)r.x | ((uint64_t)r.y << 32);
 }
 
-// Gap to the next error for a draw u with u < G[63]: min{k : u < G[k]}, by a
-// branch-free binary search over the 64 monotone thresholds.
-__device__ __forceinline__ int geo_gap(const uint64_t *__restrict__ G, uint32_t u) {
-    int k = 0;
-#pragma unroll
-    for (int step = 32; step >= 1; step >>= 1)
-        if ((uint64_t)u >= __ldg(G + k + step - 1)) k += step;
+// Gap to the next error for a draw u with u < G[63]: min{k : u < G[k]}.
+// With the channel's per-shot probability q, G[k] is about
+// 2^32 (1 - (1 - q)^(k + 1)), so k is about floor(log2(1 - u / 2^32) /
+// log2(1 - q)); inv = 1 / log2(1 - q) comes with the table. The estimate
+// is checked against G[k - 1] <= u < G[k] (two independent loads) and moved
+// a step at a time until it holds, so the result is the table's exactly;
+// float rounding only decides how many steps that takes (almost always 0).
+__device__ __forceinline__ int geo_gap(const uint64_t *__restrict__ G, uint32_t u, float inv) {
+    const float y = __log2f(1.0f - (float)u * 2.3283064365386963e-10f) * inv;
+    int k = (int)y;             // y >= 0; saturates for infinities
+    k = k < 0 ? 0 : k > 63 ? 63 : k;
+    const uint64_t lo = k > 0 ? __ldg(G + k - 1) : 0ull, hi = __ldg(G + k);
+    if ((uint64_t)u < lo) {
+        do k--;
+        while (k > 0 && (uint64_t)u < __ldg(G + k - 1));
+    } else if ((uint64_t)u >= hi) {
+        do k++;
+        while ((uint64_t)u >= __ldg(G + k));     // ends by k = 63: u < G[63]
+    }
     return k;
 }
 
@@ -96,7 +111,7 @@ __device__ __forceinline__ int geo_gap(const uint64_t *__restrict__ G, uint32_t 
 // Paulis stores m in T[15] and thresholds ceil(i 2^32 / m), for which the
 // count equals floor(m v / 2^32): one multiply instead of the scan.
 __device__ __forceinline__ uint32_t pauli_choice(const uint64_t *__restrict__ T, uint32_t v) {
-    const uint64_t m = __ldg(T + 15);
+    const uint64_t m = __ldg(T + 15) & 0xFFFFFFFFull;
     if (m) return 1u + (uint32_t)((m * v) >> 32);
     uint32_t c = 1;
 #pragma unroll 1
@@ -115,23 +130,26 @@ __device__ __forceinline__ uint32_t pauli_choice(const uint64_t *__restrict__ T,
 // pauli_choice(v) (1 X, 2 Y, 3 Z), the two-qubit channels (DEPOLARIZE2,
 // PAULI_CHANNEL_2) on c with first-qubit Pauli c >> 2 and second c & 3. For
 // the depolarizing channels c = 1 + floor(3v / 2^32) and 1 + floor(15v / 2^32).
+// have_w: blk0.w holds draw 3 (a queued hit carries draws 0..2 only; block 0
+// is drawn again if the process gets that far).
 template <class K>
 __device__ __forceinline__ void noise_masks_slow(uint32_t opc, const uint64_t *__restrict__ G, K key, uint32_t instr,
-                                                 uint32_t slot, uint32_t word, uint4 blk0, uint64_t &xa,
+                                                 uint32_t slot, uint32_t word, uint4 blk0, bool have_w, uint64_t &xa,
                                                  uint64_t &za, uint64_t &xb, uint64_t &zb) {
     uint4 blk = blk0;
     uint32_t j = 1;                       // index of the next draw
     auto next = [&]() -> uint32_t {
         const uint32_t l = j & 3u;
-        if (l == 0u) blk = philox_sched(make_uint4(j >> 2, slot, kTagNoise | instr, word), key);
+        if (l == 0u || (j == 3u && !have_w)) blk = philox_sched(make_uint4(j >> 2, slot, kTagNoise | instr, word), key);
         j++;
         return l == 0u ? blk.x : l == 1u ? blk.y : l == 2u ? blk.z : blk.w;
     };
+    const float inv = __uint_as_float((uint32_t)(__ldg(G + 79) >> 32));    // T[15]'s high half
     xa = za = xb = zb = 0;
     uint32_t u = blk0.x;
     int pos = -1;
     for (;;) {
-        pos += geo_gap(G, u) + 1;
+        pos += geo_gap(G, u, inv) + 1;
         const uint64_t bit = 1ull << pos;
         if (opc == OP_XERR) {
             xa |= bit;
