@@ -996,7 +996,7 @@ int launch_sampling(stim_circuit *c, uint64_t num_shots, uint64_t seed, uint64_t
         a.gframe = gframe;
         a.gstride = gstride;
         a.status = c->d_status;
-        a.seed = seed;
+        set_seed(a, seed);
         a.meta_bytes = fp->meta_bytes;
         a.meta_region = meta_region_for(fp->meta_bytes);
         if (ring && det && D > 0) {

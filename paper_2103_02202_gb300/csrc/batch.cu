@@ -49,7 +49,7 @@ struct DetDesc {
     uint64_t row_begin;    // detector rows of earlier circuits
 };
 
-constexpr uint32_t kDescBytes = 256;   // FrameArgs copy at the start of dynamic smem
+constexpr uint32_t kDescBytes = 384;   // FrameArgs copy at the start of dynamic smem
 static_assert(sizeof(FrameArgs) <= kDescBytes, "descriptor does not fit its slot");
 
 template <int W, int C>
@@ -347,7 +347,7 @@ int fill_descs(stim_batch *b, const uint64_t *seeds, const uint64_t *offsets, ui
         a.rec_stride = nwords;
         a.rec_mask = 0xFFFFFFFFu;
         a.status = c->d_status;
-        a.seed = seeds[i];
+        set_seed(a, seeds[i]);
         a.meta_bytes = fp->meta_bytes;
         a.meta_region = b->meta_region;
         b->h_descs[i] = a;

@@ -45,6 +45,16 @@ struct SmemKeys {
     __device__ __forceinline__ uint4 pair(int i) const { return lds128(sa + 16u * (uint32_t)i); }
 };
 
+// Round keys in the kernel's parameter space (constant bank): with the index
+// known at compile time they are operands of the round's instructions, no
+// loads at all.
+struct ParamKeys {
+    const uint32_t *rk;
+    __device__ __forceinline__ uint4 pair(int i) const {
+        return make_uint4(rk[4 * i], rk[4 * i + 1], rk[4 * i + 2], rk[4 * i + 3]);
+    }
+};
+
 __device__ __forceinline__ void write_round_keys(uint32_t *dst, Key k) {
     // called by threads 0..9 of a CTA: dst[2r] = k0 + r W0, dst[2r + 1] = k1 + r W1
     const uint32_t r = threadIdx.x;
@@ -61,7 +71,8 @@ __device__ __forceinline__ uint4 philox_round(uint4 c, uint32_t k0, uint32_t k1)
                       (uint32_t)p0);
 }
 
-__device__ __forceinline__ uint4 philox_sched(uint4 c, SmemKeys k) {
+template <class K>
+__device__ __forceinline__ uint4 philox_sched(uint4 c, K k) {
 #pragma unroll
     for (int i = 0; i < 5; i++) {
         const uint4 kk = k.pair(i);

@@ -35,7 +35,7 @@ template <int W, int C, bool GMEM, bool DETS>
 __global__ void __launch_bounds__(frame_max_threads(W), frame_min_ctas(W)) frame_kernel(const __grid_constant__ FrameArgs a) {
     extern __shared__ __align__(128) unsigned char dyn_smem[];
     const uint32_t rank = C > 1 ? (uint32_t)(blockIdx.x % C) : 0u;
-    frame_detail::run_tile<W, C, GMEM, DETS>(a, dyn_smem, rank, blockIdx.x / C);
+    frame_detail::run_tile<W, C, GMEM, DETS, ParamKeys>(a, dyn_smem, rank, blockIdx.x / C);
 }
 
 template <int W, int C, bool GMEM>

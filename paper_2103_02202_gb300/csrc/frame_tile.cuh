@@ -212,8 +212,8 @@ struct Qubit<W, C, true> {
 // One noise op on V words. Every word draws block 0 of its stream; only a
 // word whose first draw shows an error in its 64 shots (probability about
 // 64p) runs the general gap procedure, one word at a time.
-template <int W, int C, bool GMEM>
-__device__ __forceinline__ void noise_op(const FrameArgs &a, const SmemKeys key, const Tile<W, C, GMEM> &t,
+template <int W, int C, bool GMEM, class K>
+__device__ __forceinline__ void noise_op(const FrameArgs &a, const K key, const Tile<W, C, GMEM> &t,
                                          const DevOp op, uint32_t wo, uint32_t gw0, uint32_t instr_off) {
     constexpr int V = VecWidth<W>::V;
     const uint32_t opc = op.a >> 28;
@@ -267,8 +267,8 @@ __device__ __forceinline__ void noise_op(const FrameArgs &a, const SmemKeys key,
 // Applies one op to the V words at word offset wo of the tile (word tile0 + wo
 // of the call). DETS: detection events are computed in the kernel, so
 // measurements write their flips into the ring rows of a.rec.
-template <int W, int C, bool GMEM, bool DETS>
-__device__ __forceinline__ void frame_op(const FrameArgs &a, const SmemKeys key, const Tile<W, C, GMEM> &t,
+template <int W, int C, bool GMEM, bool DETS, class K>
+__device__ __forceinline__ void frame_op(const FrameArgs &a, const K key, const Tile<W, C, GMEM> &t,
                                          const DevOp op, uint32_t wo, uint32_t tile0, uint32_t instr_off,
                                          uint32_t meas_off) {
     constexpr int V = VecWidth<W>::V;
@@ -276,7 +276,7 @@ __device__ __forceinline__ void frame_op(const FrameArgs &a, const SmemKeys key,
     const uint32_t lw0 = tile0 + wo;                   // first word within the call
     const uint32_t gw0 = (uint32_t)a.word0 + lw0;      // first global 64-shot word (RNG counter)
     if (opc - OP_XERR <= OP_YERR - OP_XERR) {      // noise channels
-        noise_op<W, C, GMEM>(a, key, t, op, wo, gw0, instr_off);
+        noise_op<W, C, GMEM, K>(a, key, t, op, wo, gw0, instr_off);
         return;
     }
     const Qubit<W, C, GMEM> qa(t, op.a & 0x0FFFFFFFu, wo);
@@ -439,8 +439,8 @@ __device__ __forceinline__ void xor_qubit_word(const Tile<W, C, GMEM> &t, uint32
 
 // First draws of a noise op on V words: bit i set when word i has an error;
 // blk[i] is word i's block 0 (its draws 0..3).
-template <int V>
-__device__ __forceinline__ uint32_t noise_hits(const FrameArgs &a, const SmemKeys key, const DevOp op, uint32_t gw0,
+template <int V, class K>
+__device__ __forceinline__ uint32_t noise_hits(const FrameArgs &a, const K key, const DevOp op, uint32_t gw0,
                                                uint32_t instr_off, uint4 (&blk)[V]) {
     const uint32_t opc = op.a >> 28;
     const bool pair = opc == OP_DEP2;
@@ -460,8 +460,8 @@ __device__ __forceinline__ uint32_t noise_hits(const FrameArgs &a, const SmemKey
 // A deferred hit: q = ((op index within the CTA's layer) << 3 | word of the
 // tile, draws 0..2 of the word's block 0). Runs the general procedure and
 // XORs the masks in.
-template <int W, int C, bool GMEM>
-__device__ __forceinline__ void deferred_hit(const FrameArgs &a, const SmemKeys key, const Tile<W, C, GMEM> &t,
+template <int W, int C, bool GMEM, class K>
+__device__ __forceinline__ void deferred_hit(const FrameArgs &a, const K key, const Tile<W, C, GMEM> &t,
                                              uint4 q, uint32_t first, uint32_t tile0, uint32_t instr_off) {
     const uint32_t oi = q.x >> 3, w = q.x & 7u;
     const uint4 ov = __ldg(reinterpret_cast<const uint4 *>(a.ops) + first + oi);
@@ -541,7 +541,20 @@ __device__ __forceinline__ uint64_t to_global(const void *p) {
 // the whole program. dyn = start of the tile's dynamic shared memory (layout
 // above). DETS: evaluate the program's DETS entries from the flip ring
 // (a.det set); otherwise they are skipped. Returns false on a malformed program.
-template <int W, int C, bool GMEM, bool DETS>
+template <class K>
+__device__ __forceinline__ K tile_keys(const FrameArgs &a, uint32_t sbase);
+template <>
+__device__ __forceinline__ SmemKeys tile_keys<SmemKeys>(const FrameArgs &, uint32_t sbase) {
+    return SmemKeys{sbase};
+}
+template <>
+__device__ __forceinline__ ParamKeys tile_keys<ParamKeys>(const FrameArgs &a, uint32_t) {
+    return ParamKeys{a.rk};
+}
+
+// K: where the Philox round keys are read (SmemKeys: the tile header, written
+// at the start; ParamKeys: a.rk in the kernel's parameter space).
+template <int W, int C, bool GMEM, bool DETS, class K = SmemKeys>
 __device__ __forceinline__ bool run_tile(const FrameArgs &a, unsigned char *dyn, uint32_t rank, uint64_t tile) {
     constexpr int V = VecWidth<W>::V;
     if (blockDim.x % 32u != 0u) {       // partial warps would stall the hit-queue ballots
@@ -550,7 +563,7 @@ __device__ __forceinline__ bool run_tile(const FrameArgs &a, unsigned char *dyn,
     }
     const uint32_t tile0 = (uint32_t)(tile * W);
     const uint32_t sbase = smem_addr(dyn);
-    const SmemKeys key{sbase};
+    const K key = tile_keys<K>(a, sbase);
     const uint32_t lane = threadIdx.x & 31u;
     const uint32_t qsa = sbase + kHitQueueOffset + (threadIdx.x >> 5) * (16u * kHitQueueCap);   // this warp's queue
     const uint32_t qlo = rank * a.Q;
@@ -622,7 +635,7 @@ __device__ __forceinline__ bool run_tile(const FrameArgs &a, unsigned char *dyn,
                 uint32_t qn = 0;
                 auto flush = [&](uint32_t n) {
                     __syncwarp();
-                    if (lane < n) deferred_hit<W, C, GMEM>(a, key, t, lds128(qsa + 16u * lane), first, tile0, instr_off);
+                    if (lane < n) deferred_hit<W, C, GMEM, K>(a, key, t, lds128(qsa + 16u * lane), first, tile0, instr_off);
                     __syncwarp();
                 };
                 uint32_t g = threadIdx.x, seg_start = 0;
@@ -647,11 +660,11 @@ __device__ __forceinline__ bool run_tile(const FrameArgs &a, unsigned char *dyn,
                             if (j + 1 < len) nxt = __ldg(ops + op0 + j + 1);     // one op ahead
                             else if (have_next) nxt = __ldg(ops + op2);         // across items
                             if (j < dfrom) {
-                                if (act) frame_op<W, C, GMEM, DETS>(a, key, t, as_op(ov), wo, tile0, instr_off, meas_off);
+                                if (act) frame_op<W, C, GMEM, DETS, K>(a, key, t, as_op(ov), wo, tile0, instr_off, meas_off);
                             } else {
                                 uint4 blk[V];
                                 const uint32_t hits =
-                                    act ? noise_hits<V>(a, key, as_op(ov), (uint32_t)a.word0 + tile0 + wo, instr_off, blk)
+                                    act ? noise_hits<V, K>(a, key, as_op(ov), (uint32_t)a.word0 + tile0 + wo, instr_off, blk)
                                         : 0u;
                                 const uint32_t oi = op0 + j - first;       // index within the CTA's layer
 #pragma unroll

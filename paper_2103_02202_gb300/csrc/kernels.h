@@ -28,6 +28,7 @@ struct FrameArgs {
     uint64_t gstride;
     int *status;
     uint64_t seed;             // Philox key = (seed lo, seed hi)
+    uint32_t rk[20];           // its round keys: rk[2r] = lo + r 0x9E3779B9, rk[2r + 1] = hi + r 0xBB67AE85 (set_seed)
     uint32_t meta_bytes;       // bytes of prog + rank_tab + segs (one buffer starting at prog)
     uint32_t meta_region;      // shared bytes reserved for them; copied there when meta_bytes fits
     // Detection events inside the frame kernel (det null: DETS entries are
@@ -44,6 +45,15 @@ struct FrameArgs {
     const DetItem *det_items;
     const uint32_t *det_looks;
 };
+
+// Sets a.seed and the round keys derived from it.
+inline void set_seed(FrameArgs &a, uint64_t seed) {
+    a.seed = seed;
+    for (uint32_t r = 0; r < 10; r++) {
+        a.rk[2 * r] = (uint32_t)seed + r * 0x9E3779B9u;
+        a.rk[2 * r + 1] = (uint32_t)(seed >> 32) + r * 0xBB67AE85u;
+    }
+}
 
 // Dynamic shared memory of a frame tile: a header (round keys, then 32
 // queues of 32 deferred noise hits, one per warp), the program metadata

@@ -116,7 +116,7 @@ extern "C" int stim_frame_sample_noalloc(stim_circuit *c, uint64_t num_shots, ui
         a.ref = c->d_ref;
         a.n = n;
         a.Q = fp.Q;
-        a.seed = seed;
+        set_seed(a, seed);
         a.word0 = shot_offset / 64;
         a.nwords = nwords;
         a.last_mask = (num_shots % 64) ? ((1ull << (num_shots % 64)) - 1) : ~0ull;
