@@ -29,9 +29,6 @@ __device__ __forceinline__ uint64_t lds64(uint32_t a) {
 __device__ __forceinline__ void sts64(uint32_t a, uint64_t v) {
     asm volatile("st.shared.u64 [%0], %1;" ::"r"(a), "l"(v) : "memory");
 }
-__device__ __forceinline__ void sts128(uint32_t a, uint4 v) {
-    asm volatile("st.shared.v4.u32 [%0], {%1, %2, %3, %4};" ::"r"(a), "r"(v.x), "r"(v.y), "r"(v.z), "r"(v.w) : "memory");
-}
 __device__ __forceinline__ uint4 lds128(uint32_t a) {
     uint4 v;
     asm volatile("ld.shared.v4.u32 {%0, %1, %2, %3}, [%4];" : "=r"(v.x), "=r"(v.y), "=r"(v.z), "=r"(v.w) : "r"(a));
@@ -141,17 +138,15 @@ __device__ __forceinline__ uint32_t pauli_choice(const uint64_t *__restrict__ T,
 // pauli_choice(v) (1 X, 2 Y, 3 Z), the two-qubit channels (DEPOLARIZE2,
 // PAULI_CHANNEL_2) on c with first-qubit Pauli c >> 2 and second c & 3. For
 // the depolarizing channels c = 1 + floor(3v / 2^32) and 1 + floor(15v / 2^32).
-// have_w: blk0.w holds draw 3 (a queued hit carries draws 0..2 only; block 0
-// is drawn again if the process gets that far).
 template <class K>
 __device__ __forceinline__ void noise_masks_slow(uint32_t opc, const uint64_t *__restrict__ G, K key, uint32_t instr,
-                                                 uint32_t slot, uint32_t word, uint4 blk0, bool have_w, uint64_t &xa,
+                                                 uint32_t slot, uint32_t word, uint4 blk0, uint64_t &xa,
                                                  uint64_t &za, uint64_t &xb, uint64_t &zb) {
     uint4 blk = blk0;
     uint32_t j = 1;                       // index of the next draw
     auto next = [&]() -> uint32_t {
         const uint32_t l = j & 3u;
-        if (l == 0u || (j == 3u && !have_w)) blk = philox_sched(make_uint4(j >> 2, slot, kTagNoise | instr, word), key);
+        if (l == 0u) blk = philox_sched(make_uint4(j >> 2, slot, kTagNoise | instr, word), key);
         j++;
         return l == 0u ? blk.x : l == 1u ? blk.y : l == 2u ? blk.z : blk.w;
     };

@@ -246,7 +246,7 @@ __device__ __forceinline__ void noise_op(const FrameArgs &a, const K key, const 
         for (int i = 1; i < V; i++)
             if (w == i) b0 = blk[i];
         uint64_t mxa, mza, mxb, mzb;
-        noise_masks_slow(opc, G, key, instr, slot, gw0 + (uint32_t)w, b0, true, mxa, mza, mxb, mzb);
+        noise_masks_slow(opc, G, key, instr, slot, gw0 + (uint32_t)w, b0, mxa, mza, mxb, mzb);
 #pragma unroll
         for (int i = 0; i < V; i++) {
             if (w == i) {
@@ -437,11 +437,10 @@ __device__ __forceinline__ void xor_qubit_word(const Tile<W, C, GMEM> &t, uint32
     }
 }
 
-// First draws of a noise op on V words: bit i set when word i has an error;
-// blk[i] is word i's block 0 (its draws 0..3).
+// First draws of a noise op on V words: bit i set when word i has an error.
 template <int V, class K>
 __device__ __forceinline__ uint32_t noise_hits(const FrameArgs &a, const K key, const DevOp op, uint32_t gw0,
-                                               uint32_t instr_off, uint4 (&blk)[V]) {
+                                               uint32_t instr_off) {
     const uint32_t opc = op.a >> 28;
     const bool pair = opc == OP_DEP2;
     const uint32_t tbl = pair ? (op.slot >> 24) : op.b;
@@ -451,19 +450,18 @@ __device__ __forceinline__ uint32_t noise_hits(const FrameArgs &a, const K key, 
     uint32_t hits = 0;
 #pragma unroll
     for (int i = 0; i < V; i++) {
-        blk[i] = philox_sched(make_uint4(0u, slot, ti, gw0 + (uint32_t)i), key);
-        if ((uint64_t)blk[i].x < g63) hits |= 1u << i;
+        const uint4 blk = philox_sched(make_uint4(0u, slot, ti, gw0 + (uint32_t)i), key);
+        if ((uint64_t)blk.x < g63) hits |= 1u << i;
     }
     return hits;
 }
 
-// A deferred hit: q = ((op index within the CTA's layer) << 3 | word of the
-// tile, draws 0..2 of the word's block 0). Runs the general procedure and
-// XORs the masks in.
+// A deferred hit: entry = (op index within the CTA's layer) << 3 | word of the
+// tile. Redraws block 0, runs the general procedure and XORs the masks in.
 template <int W, int C, bool GMEM, class K>
 __device__ __forceinline__ void deferred_hit(const FrameArgs &a, const K key, const Tile<W, C, GMEM> &t,
-                                             uint4 q, uint32_t first, uint32_t tile0, uint32_t instr_off) {
-    const uint32_t oi = q.x >> 3, w = q.x & 7u;
+                                             uint32_t e, uint32_t first, uint32_t tile0, uint32_t instr_off) {
+    const uint32_t oi = e >> 3, w = e & 7u;
     const uint4 ov = __ldg(reinterpret_cast<const uint4 *>(a.ops) + first + oi);
     const uint32_t opc = ov.x >> 28;
     if (opc - OP_XERR > OP_YERR - OP_XERR) return;      // only noise ops are queued
@@ -472,9 +470,9 @@ __device__ __forceinline__ void deferred_hit(const FrameArgs &a, const K key, co
     const uint32_t slot = pair ? (ov.w & 0xFFFFFFu) : ov.w;
     const uint32_t instr = ov.z + instr_off;
     const uint32_t gw = (uint32_t)a.word0 + tile0 + w;
+    const uint4 blk0 = philox_sched(make_uint4(0u, slot, kTagNoise | instr, gw), key);
     uint64_t mxa, mza, mxb, mzb;
-    noise_masks_slow(opc, a.geo + kNoiseTableWords * tbl, key, instr, slot, gw, make_uint4(q.y, q.z, q.w, 0u), false,
-                     mxa, mza, mxb, mzb);
+    noise_masks_slow(opc, a.geo + kNoiseTableWords * tbl, key, instr, slot, gw, blk0, mxa, mza, mxb, mzb);
     xor_qubit_word<W, C, GMEM>(t, ov.x & 0x0FFFFFFFu, w, mxa, mza);
     if (pair) xor_qubit_word<W, C, GMEM>(t, ov.y, w, mxb, mzb);
 }
@@ -565,7 +563,7 @@ __device__ __forceinline__ bool run_tile(const FrameArgs &a, unsigned char *dyn,
     const uint32_t sbase = smem_addr(dyn);
     const K key = tile_keys<K>(a, sbase);
     const uint32_t lane = threadIdx.x & 31u;
-    const uint32_t qsa = sbase + kHitQueueOffset + (threadIdx.x >> 5) * (16u * kHitQueueCap);   // this warp's queue
+    const uint32_t qsa = sbase + kHitQueueOffset + (threadIdx.x >> 5) * (4u * kHitQueueCap);   // this warp's queue
     const uint32_t qlo = rank * a.Q;
     const uint32_t nq = a.n > qlo ? min(a.Q, a.n - qlo) : 0u;
     Tile<W, C, GMEM> t;
@@ -635,7 +633,7 @@ __device__ __forceinline__ bool run_tile(const FrameArgs &a, unsigned char *dyn,
                 uint32_t qn = 0;
                 auto flush = [&](uint32_t n) {
                     __syncwarp();
-                    if (lane < n) deferred_hit<W, C, GMEM, K>(a, key, t, lds128(qsa + 16u * lane), first, tile0, instr_off);
+                    if (lane < n) deferred_hit<W, C, GMEM, K>(a, key, t, lds32(qsa + 4u * lane), first, tile0, instr_off);
                     __syncwarp();
                 };
                 uint32_t g = threadIdx.x, seg_start = 0;
@@ -662,9 +660,8 @@ __device__ __forceinline__ bool run_tile(const FrameArgs &a, unsigned char *dyn,
                             if (j < dfrom) {
                                 if (act) frame_op<W, C, GMEM, DETS, K>(a, key, t, as_op(ov), wo, tile0, instr_off, meas_off);
                             } else {
-                                uint4 blk[V];
                                 const uint32_t hits =
-                                    act ? noise_hits<V, K>(a, key, as_op(ov), (uint32_t)a.word0 + tile0 + wo, instr_off, blk)
+                                    act ? noise_hits<V, K>(a, key, as_op(ov), (uint32_t)a.word0 + tile0 + wo, instr_off)
                                         : 0u;
                                 const uint32_t oi = op0 + j - first;       // index within the CTA's layer
 #pragma unroll
@@ -678,9 +675,8 @@ __device__ __forceinline__ bool run_tile(const FrameArgs &a, unsigned char *dyn,
                                             qn = 0;
                                         }
                                         if (h)
-                                            sts128(qsa + 16u * (qn + __popc(m & ((1u << lane) - 1u))),
-                                                   make_uint4((oi << 3) | (wo + (uint32_t)i), blk[i].x, blk[i].y,
-                                                              blk[i].z));
+                                            sts32(qsa + 4u * (qn + __popc(m & ((1u << lane) - 1u))),
+                                                  (oi << 3) | (wo + (uint32_t)i));
                                         qn += cnt;
                                     }
                                 }

@@ -60,8 +60,8 @@ inline void set_seed(FrameArgs &a, uint64_t seed) {
 // (meta_region bytes), then (shared layout) the frame rows of Q qubits x 2W
 // words.
 constexpr uint32_t kHitQueueOffset = 256;
-constexpr uint32_t kHitQueueCap = 32;          // entries per warp, 16 bytes each
-constexpr uint32_t kTileHeaderBytes = kHitQueueOffset + 32 * kHitQueueCap * 16;
+constexpr uint32_t kHitQueueCap = 32;          // entries per warp
+constexpr uint32_t kTileHeaderBytes = kHitQueueOffset + 32 * kHitQueueCap * 4;
 
 // Largest CTA of a frame kernel with W words per tile: threads that apply ops
 // to two or four words at once need more registers. One-word tiles are sized
