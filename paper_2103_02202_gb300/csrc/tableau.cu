@@ -326,13 +326,19 @@ __device__ void column_pass_mask(const TabArgs &a, uint32_t p, uint32_t py, uint
 // columns stored contiguously that is a pass over all 2n columns, with rows
 // stored contiguously it is a few words of rows p and k. A layer with many
 // random measurements, in a circuit whose random measurements have had few
-// CNOT targets, is transposed to rows by the whole grid, walked by CTA 0
+// enough CNOT targets for one CTA (the mean target count times the row
+// length, below), is transposed to rows by the whole grid, walked by CTA 0
 // (one measurement at a time, CTA barriers only), and transposed back.
 // ---------------------------------------------------------------------------
+constexpr uint32_t kTableauMaxThreads = 512;   // the kernels' launch bound
 constexpr uint32_t kBurstMinRandom = 16;    // random measurements in the layer
-constexpr uint32_t kBurstMaxMeanTargets = 32;
+// one CTA's fan-out of a random measurement touches (targets x row words)
+// words; measured: bursts win up to about 16k (random circuits of 1000
+// qubits: 1.5x) and lose at 63k (2000 qubits: 1.7x slower)
+constexpr uint32_t kBurstMaxRowWords = 32768;
 // the other CTAs wait out a burst at one bounded barrier wait: cap its length
 constexpr uint32_t kBurstMaxOps = 20000;
+constexpr uint32_t kFanBatch = 4;           // fan-out targets loaded together
 
 // rows <- columns: word cw of row k holds bit k of physical columns 64cw .. 64cw + 63.
 __device__ void to_rows(const TabArgs &a, uint32_t gtid, uint32_t nthreads) {
@@ -389,6 +395,7 @@ __device__ void to_cols(const TabArgs &a, uint32_t gtid, uint32_t nthreads) {
 // (S if the pivot term is Y, H, X when the sign is -) makes the outcome 0.
 __device__ void burst_walk(const TabArgs &a, const DevOp *cops, uint32_t nc, uint32_t j, uint32_t meas_off) {
     __shared__ uint32_t s_pivot, s_cnt, s_py, s_fx;
+    __shared__ uint64_t s_part[3][kTableauMaxThreads];     // per-thread chunk sums of the fan-out
     const uint32_t tid = threadIdx.x, B = blockDim.x;
     for (; j < nc; j++) {
         const DevOp op = cops[j];
@@ -422,28 +429,93 @@ __device__ void burst_walk(const TabArgs &a, const DevOp *cops, uint32_t nc, uin
             a.ctl->nk_sum += cnt - 1;
             a.ctl->nk_cnt += 1;
         }
-        // CNOT fan-out p -> k, k in K \ {p}, word by word over the columns
-        for (uint32_t w = tid; w < a.nw2; w += B) {
-            const uint64_t xp = __ldcg(a.rx + (uint64_t)p * a.nw2 + w);
-            uint64_t zp = __ldcg(a.rz + (uint64_t)p * a.nw2 + w);
-            uint64_t apar = 0, b0 = 0, b1 = 0;
-            for (uint32_t t = 0; t < cnt; t++) {
-                const uint32_t k = __ldcg(a.klist + t);
-                if (k == p) continue;
-                const uint64_t xk = __ldcg(a.rx + (uint64_t)k * a.nw2 + w);
-                const uint64_t zk = __ldcg(a.rz + (uint64_t)k * a.nw2 + w);
-                apar ^= zk & ~(zp ^ xk);
-                b1 ^= b0 & zk;
-                b0 ^= zk;
-                __stcg(a.rx + (uint64_t)k * a.nw2 + w, xk ^ xp);
+        // CNOT fan-out p -> k, k in K \ {p}, word by word over the columns:
+        // x_k ^= x_p for every k; z_p ^= XOR of the z_k; the sign of each
+        // column picks up x_p times the parity of the Y and Z terms the
+        // products meet (apar) plus the second bit of the count of z_k bits
+        // (b1 b0: that count mod 4). Both are sums over k, so a row narrower
+        // than the CTA splits the targets into CH chunks per word, each
+        // thread summing its chunk, and the chunk sums are added per word.
+        // Targets are taken kFanBatch at a time so that their row loads are
+        // in flight together.
+        const uint32_t WP = a.nw2 < B ? a.nw2 : B;      // words handled side by side
+        const uint32_t CH = B / WP;                     // target chunks per word
+        const uint32_t chunk = tid / WP, wl = tid % WP;
+        const uint32_t per = (cnt + CH - 1) / CH;
+        const uint32_t t0 = chunk * per < cnt ? chunk * per : cnt;
+        const uint32_t t1 = t0 + per < cnt ? t0 + per : cnt;
+        if (chunk < CH) {
+            for (uint32_t w = wl; w < a.nw2; w += WP) {
+                const uint64_t xp = __ldcg(a.rx + (uint64_t)p * a.nw2 + w);
+                uint64_t zp = __ldcg(a.rz + (uint64_t)p * a.nw2 + w);
+                uint64_t apar = 0, b0 = 0, b1 = 0;
+                uint32_t t = t0;
+                for (; t + kFanBatch <= t1; t += kFanBatch) {
+                    uint32_t k[kFanBatch];
+                    uint64_t xk[kFanBatch], zk[kFanBatch];
+#pragma unroll
+                    for (int i = 0; i < (int)kFanBatch; i++) k[i] = __ldcg(a.klist + t + i);
+#pragma unroll
+                    for (int i = 0; i < (int)kFanBatch; i++) {
+                        xk[i] = __ldcg(a.rx + (uint64_t)k[i] * a.nw2 + w);
+                        zk[i] = __ldcg(a.rz + (uint64_t)k[i] * a.nw2 + w);
+                    }
+#pragma unroll
+                    for (int i = 0; i < (int)kFanBatch; i++) {
+                        if (k[i] == p) continue;
+                        apar ^= zk[i] & ~(zp ^ xk[i]);
+                        b1 ^= b0 & zk[i];
+                        b0 ^= zk[i];
+                        __stcg(a.rx + (uint64_t)k[i] * a.nw2 + w, xk[i] ^ xp);
+                    }
+                }
+                for (; t < t1; t++) {
+                    const uint32_t k = __ldcg(a.klist + t);
+                    if (k == p) continue;
+                    const uint64_t xk = __ldcg(a.rx + (uint64_t)k * a.nw2 + w);
+                    const uint64_t zk = __ldcg(a.rz + (uint64_t)k * a.nw2 + w);
+                    apar ^= zk & ~(zp ^ xk);
+                    b1 ^= b0 & zk;
+                    b0 ^= zk;
+                    __stcg(a.rx + (uint64_t)k * a.nw2 + w, xk ^ xp);
+                }
+                if (CH > 1) {       // one word per thread: hand the chunk sums to chunk 0
+                    s_part[0][tid] = apar;
+                    s_part[1][tid] = b0;
+                    s_part[2][tid] = b1;
+                    break;
+                }
+                const uint64_t s = __ldcg(a.rsign + w) ^ (xp & (apar ^ b1));
+                zp ^= b0;
+                __stcg(a.rz + (uint64_t)p * a.nw2 + w, zp);
+                __stcg(a.rsign + w, s);
+                if (w == cwp) {
+                    s_py = (uint32_t)((zp & bitp) != 0);     // the pivot term of Z_q is Y
+                    s_fx = (uint32_t)((s & bitp) != 0);      // its sign is -
+                }
             }
-            const uint64_t s = __ldcg(a.rsign + w) ^ (xp & (apar ^ b1));
-            zp ^= b0;
-            __stcg(a.rz + (uint64_t)p * a.nw2 + w, zp);
-            __stcg(a.rsign + w, s);
-            if (w == cwp) {
-                s_py = (uint32_t)((zp & bitp) != 0);     // the pivot term of Z_q is Y
-                s_fx = (uint32_t)((s & bitp) != 0);      // its sign is -
+        }
+        if (CH > 1) {
+            __syncthreads();
+            if (chunk == 0) {
+                const uint32_t w = wl;
+                uint64_t apar = s_part[0][w], b0 = s_part[1][w], b1 = s_part[2][w];
+                for (uint32_t c = 1; c < CH; c++) {
+                    const uint32_t o = c * WP + w;
+                    const uint64_t c0 = s_part[1][o], c1 = s_part[2][o];
+                    apar ^= s_part[0][o];
+                    b1 ^= c1 ^ (b0 & c0);       // (b1 b0) += (c1 c0) mod 4
+                    b0 ^= c0;
+                }
+                const uint64_t xp = __ldcg(a.rx + (uint64_t)p * a.nw2 + w);
+                const uint64_t zp = __ldcg(a.rz + (uint64_t)p * a.nw2 + w) ^ b0;
+                const uint64_t s = __ldcg(a.rsign + w) ^ (xp & (apar ^ b1));
+                __stcg(a.rz + (uint64_t)p * a.nw2 + w, zp);
+                __stcg(a.rsign + w, s);
+                if (w == cwp) {
+                    s_py = (uint32_t)((zp & bitp) != 0);
+                    s_fx = (uint32_t)((s & bitp) != 0);
+                }
             }
         }
         __syncthreads();
@@ -646,7 +718,7 @@ __device__ __forceinline__ void tableau_body(const TabArgs &a, uint32_t bid) {
         bool burst = false;
         if (!L1 && a.rx != nullptr && s_nrand >= kBurstMinRandom && nc - s_first <= kBurstMaxOps) {
             const uint32_t kc = ld_u32<L1>(&a.ctl->nk_cnt), ks = ld_u32<L1>(&a.ctl->nk_sum);
-            burst = kc >= 4 && ks <= kBurstMaxMeanTargets * kc;
+            burst = kc >= 4 && (uint64_t)ks * a.nw2 <= (uint64_t)kBurstMaxRowWords * kc;
         }
         for (uint32_t j = gtid; j < first; j += nthreads) {
             const DevOp op = cops[j];
@@ -684,14 +756,14 @@ __device__ __forceinline__ void tableau_body(const TabArgs &a, uint32_t bid) {
 }
 
 template <bool L1>
-__global__ void __launch_bounds__(512) tableau_kernel(TabArgs a) {
+__global__ void __launch_bounds__(kTableauMaxThreads) tableau_kernel(TabArgs a) {
     tableau_body<L1>(a, blockIdx.x);
 }
 
 // Several circuits in one cooperative launch: CTA b works for circuit
 // job_of[b] as its CTA b - first[job_of[b]]; each circuit's CTAs meet only at
 // that circuit's barrier.
-__global__ void __launch_bounds__(512) tableau_batch_kernel(const TabArgs *jobs, const uint32_t *job_of,
+__global__ void __launch_bounds__(kTableauMaxThreads) tableau_batch_kernel(const TabArgs *jobs, const uint32_t *job_of,
                                                             const uint32_t *first) {
     const uint32_t j = job_of[blockIdx.x];
     tableau_body<false>(jobs[j], blockIdx.x - first[j]);     // arguments read in place (global, cached)
