@@ -528,12 +528,18 @@ void prefix_store(stim_circuit *c, RefJob *job) {
 
 // CTAs of the inverse-tableau kernel for c: ~1024 column words per CTA
 // (measured best for random circuits; d=100 uses all SMs either way), at most
-// the co-resident maximum maxb.
-uint32_t tableau_blocks(const stim_circuit *c, int maxb) {
+// the co-resident maximum maxb. alone: the circuit has the GPU to itself (one
+// reference computation, not a share of a batched launch); from 128 qubits it
+// then takes at least 32 CTAs, which measured faster than the 2-16 the word
+// count gives for 150-500 qubits (random Clifford n=250: 0.12 -> 0.05 s;
+// n=500: 0.15 -> 0.13 s; surface code d=15: 2.2 -> 2.0 ms), while smaller
+// circuits keep the single-CTA kernel without grid barriers.
+uint32_t tableau_blocks(const stim_circuit *c, int maxb, bool alone = false) {
     const uint32_t n = c->hp.num_qubits;
     const uint64_t col_words = (uint64_t)2 * n * ((n + 63) / 64);
     uint64_t want = (col_words + 1023) / 1024;
     if (want < 1) want = 1;
+    if (alone && n >= 128 && want < 32) want = 32;
     return (uint32_t)std::min<uint64_t>(want, (uint64_t)std::max(maxb, 1));
 }
 
@@ -680,7 +686,7 @@ int reference_launch(stim_circuit *c, cudaStream_t st, uint32_t max_blocks, bool
     bool needs_kernel = false;
     const int r = reference_prepare(c, st, use_cache, job, &a, &needs_kernel);
     if (r != STIM_OK || !needs_kernel) return r;
-    uint32_t blocks = tableau_blocks(c, tableau_max_blocks(kTableauThreads, c->device));
+    uint32_t blocks = tableau_blocks(c, tableau_max_blocks(kTableauThreads, c->device), max_blocks == 0);
     if (max_blocks && blocks > max_blocks) blocks = max_blocks;
     cudaError_t e;
     {
