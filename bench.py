@@ -808,6 +808,19 @@ def main():
         dist.all_reduce(t, op=dist.ReduceOp.MAX)
         e2e_ms = float(t.item())
     e2e_dense_value = shots * e2e_steps * world * gate_targets / (e2e_ms / 1000.0)
+    # the host link this box gives one step's copy (device -> pinned host), to
+    # read the e2e figure against: best of two plain copies of the same size
+    link_ms = None
+    e2 = torch.cuda.Event(enable_timing=True)
+    e3 = torch.cuda.Event(enable_timing=True)
+    for _ in range(2):
+        e2.record(stream)
+        host_det[0].copy_(det, non_blocking=True)
+        e3.record(stream)
+        torch.cuda.synchronize()
+        t = e2.elapsed_time(e3)
+        link_ms = t if link_ms is None else min(link_ms, t)
+    link_gbs = D * nwords * 8 / (link_ms * 1e6) if link_ms else None
 
     # ---- end to end with per-shot lists of fired detectors (the paper's hits
     # form): the call samples, converts on the device and copies the count,
@@ -914,6 +927,7 @@ def main():
         "events_in_kernel": in_kernel,
         "e2e": {"value": e2e_dense_value, "unit": "shot-gates/s", "h2d_bytes_per_step": 0,
                 "d2h_bytes_per_step": D * nwords * 8, "steps": e2e_steps,
+                "ms_per_step": e2e_ms / e2e_steps, "d2h_gbs_measured": link_gbs,
                 "output": "bit-packed detection events in host memory via stim_frame_sample_ex "
                           "(STIM_HOST | STIM_ASYNC, two streams)"},
         "e2e_sparse": {"value": e2e_value, "unit": "shot-gates/s", "h2d_bytes_per_step": 0,
