@@ -65,7 +65,7 @@ def parse_args():
     ap.add_argument("--no-ttfs", action="store_true", help="skip the Bacon-Shor / random-circuit time to first sample")
     ap.add_argument("--no-c5", action="store_true", help="skip the serving sub-result")
     ap.add_argument("--c3-steps", type=int, default=3, help="timed steps of the 64-circuit batch sub-result")
-    ap.add_argument("--c5-requests", type=int, default=3000, help="requests of the serving sub-result")
+    ap.add_argument("--c5-requests", type=int, default=10000, help="requests of the serving sub-result")
     return ap.parse_args()
 
 
@@ -517,6 +517,7 @@ def measure_c5(requests, streams=16, budget=150 << 30):
                 done_ids.append(rid)
 
     th = threading.Thread(target=feeder)
+    lat, queue = [], []
     t0 = time.perf_counter()
     th.start()
     k = 0
@@ -527,7 +528,9 @@ def measure_c5(requests, streams=16, budget=150 << 30):
             time.sleep(0.0005)
             continue
         rid = done_ids[k]
-        srv.wait(rid, 600)
+        res = srv.wait(rid, 600)
+        lat.append(res.latency_s)
+        queue.append(res.queue_s)
         srv.release(rid)
         k += 1
     th.join()
@@ -581,6 +584,22 @@ def measure_c5(requests, streams=16, budget=150 << 30):
         "served_over_plain": plain_s / served_burst_s,
         "compile_s": compile_s, "reference_samples_s": ref_s,
     }
+    # where the tail comes from: waiting for admission (queue) against running
+    # (latency - queue), per request of the served stream
+    import numpy as np
+    lat_a, q_a = np.array(lat), np.array(queue)
+    if len(lat_a):
+        run_a = lat_a - q_a
+        work = np.array([r["shots"] * cs[r["circuit"]].info["num_gate_targets"] for r in reqs[:len(lat_a)]],
+                        dtype=np.float64)
+        top = work >= np.quantile(work, 0.99)
+        out["latency_breakdown"] = {
+            "p50_queue_s": float(np.quantile(q_a, 0.5)), "p99_queue_s": float(np.quantile(q_a, 0.99)),
+            "p50_run_s": float(np.quantile(run_a, 0.5)), "p99_run_s": float(np.quantile(run_a, 0.99)),
+            "mean_latency_of_largest_1pct_s": float(lat_a[top].mean()),
+            "how": "per-request queue_s and latency_s from stim_server_wait; run = latency - queue; the "
+                   "largest 1 % by shots x gate targets",
+        }
     for c in cs:
         c.close()
     return out
