@@ -958,6 +958,22 @@ def main():
         "paper_context": "Stim (paper abstract): d=100 surface code sampled at ~1 kHz on one laptop "
                          "CPU core (i7-8650U) after 15 s of analysis",
     }
+    # what limits the frame kernel: the largest of its measured fractions
+    # (issue slots, shared memory against the local figure, DRAM traffic)
+    rf = line["roofline"]
+    fracs = {}
+    if rf.get("issue"):
+        fracs["instruction issue"] = rf["issue"]["frac"]
+    if smem_local_gbs:
+        fracs["shared memory (local peak)"] = achieved / smem_local_gbs
+    if rf.get("traffic"):
+        fracs["DRAM (measured traffic)"] = rf["traffic"] / (frame_avg_ms * 1e-3) / 1e9 / hbm_peak
+    if fracs:
+        top = max(fracs, key=fracs.get)
+        reading = ("bound by %s" % top) if fracs[top] >= 0.7 else (
+            "no resource is near its peak: the kernel is latency-bound per warp step (dependent Philox "
+            "rounds, L1/L2 loads, one cluster barrier per merged layer); see the committed ncu summary")
+        rf["limited_by"] = {"resource": top, "fractions": fracs, "reading": reading}
     # ---- rows a9 and a10 on the same box: the 64-circuit batch (batched vs
     # plain) and the serving loop (served vs plain), device-resident outputs ----
     if world == 1 and not args.no_ttfs:

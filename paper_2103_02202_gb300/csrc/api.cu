@@ -1302,7 +1302,6 @@ int stim_frame_sample_ex(stim_circuit *c, uint64_t num_shots, uint64_t seed, uin
     const uint32_t n = hp.num_qubits;
     const uint64_t M = hp.num_meas, D = hp.num_det;
     const uint64_t nwords = (num_shots + 63) / 64;
-    const uint64_t last_mask = (num_shots % 64) ? ((1ull << (num_shots % 64)) - 1) : ~0ull;
     const bool shot_major = (flags & STIM_SHOT_MAJOR) != 0, host = (flags & STIM_HOST) != 0;
 
     // ---- tile choice ----
@@ -1314,7 +1313,6 @@ int stim_frame_sample_ex(stim_circuit *c, uint64_t num_shots, uint64_t seed, uin
     if (r != STIM_OK) return r;
     const int W = tc.W, C = tc.C;
     const bool gmem = tc.gmem;
-    const uint32_t threads = tc.threads;
     const uint64_t grid = (nwords + W - 1) / W;     // word tiles (clusters)
     if (grid * C > 0x7FFFFFFFull) return fail(STIM_E_UNSUPPORTED, "too many shots for one call");
 
