@@ -577,6 +577,7 @@ int reference_prepare(stim_circuit *c, cudaStream_t st, bool use_cache, RefJob *
     a->nprog = (uint32_t)hp.prog.size();
     a->pc_begin = 0;
     a->pc_end = a->nprog;
+    a->bclu = 1;
     a->ops = c->d_ops;
     a->n = n;
     a->nw = nw;

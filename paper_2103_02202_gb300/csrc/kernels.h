@@ -120,6 +120,9 @@ struct TabArgs {
     // iter_begin > 0, pc_begin is a top-level LOOP_BEGIN entered at that
     // iteration (the state of the earlier iterations resumed)
     uint32_t pc_begin, pc_end, iter_begin;
+    // CTAs that walk a row-major burst together: the first bclu CTAs, one
+    // thread-block cluster (1: CTA 0 alone, no cluster launch)
+    uint32_t bclu;
     uint32_t bar_extra;        // test knob: arrivals a barrier waits for beyond nblk (0 in normal use)
     uint64_t bar_timeout_ns;   // limit of one barrier wait
 };

@@ -339,6 +339,8 @@ constexpr uint32_t kBurstMaxRowWords = 32768;
 // the other CTAs wait out a burst at one bounded barrier wait: cap its length
 constexpr uint32_t kBurstMaxOps = 20000;
 constexpr uint32_t kFanBatch = 4;           // fan-out targets loaded together
+constexpr uint32_t kBurstCluster = 8;       // CTAs of the cluster that walks a burst
+constexpr uint32_t kBurstClusterMinQubits = 16384;
 
 // rows <- columns: word cw of row k holds bit k of physical columns 64cw .. 64cw + 63.
 __device__ void to_rows(const TabArgs &a, uint32_t gtid, uint32_t nthreads) {
@@ -393,10 +395,57 @@ __device__ void to_cols(const TabArgs &a, uint32_t gtid, uint32_t nthreads) {
 // p -> k over the other rows k updates x_k ^= x_p, z_p ^= XOR of z_k and every
 // column's sign by the closed form of the column pass, and the pivot collapse
 // (S if the pivot term is Y, H, X when the sign is -) makes the outcome 0.
-__device__ void burst_walk(const TabArgs &a, const DevOp *cops, uint32_t nc, uint32_t j, uint32_t meas_off) {
-    __shared__ uint32_t s_pivot, s_cnt, s_py, s_fx;
-    __shared__ uint64_t s_part[3][kTableauMaxThreads];     // per-thread chunk sums of the fan-out
-    const uint32_t tid = threadIdx.x, B = blockDim.x;
+// The burst's CTAs work as one: with a cluster (bclu > 1) its barrier and the
+// scalars of CTA rank 0 reached through distributed shared memory; alone,
+// the CTA barrier and its own shared memory.
+template <bool CLU>
+__device__ __forceinline__ void bw_sync() {
+    if (CLU) asm volatile("barrier.cluster.arrive.release.aligned;\n\tbarrier.cluster.wait.acquire.aligned;" ::: "memory");
+    else __syncthreads();
+}
+__device__ __forceinline__ uint32_t cl_map(uint32_t sa, uint32_t rank) {
+    uint32_t r;
+    asm volatile("mapa.shared::cluster.u32 %0, %1, %2;" : "=r"(r) : "r"(sa), "r"(rank));
+    return r;
+}
+__device__ __forceinline__ uint32_t cl_ld32(uint32_t a) {
+    uint32_t v;
+    asm volatile("ld.shared::cluster.u32 %0, [%1];" : "=r"(v) : "r"(a) : "memory");
+    return v;
+}
+__device__ __forceinline__ uint64_t cl_ld64(uint32_t a) {
+    uint64_t v;
+    asm volatile("ld.shared::cluster.u64 %0, [%1];" : "=l"(v) : "r"(a) : "memory");
+    return v;
+}
+__device__ __forceinline__ void cl_st32(uint32_t a, uint32_t v) {
+    asm volatile("st.shared::cluster.u32 [%0], %1;" ::"r"(a), "r"(v) : "memory");
+}
+__device__ __forceinline__ void cl_min32(uint32_t a, uint32_t v) {
+    asm volatile("red.shared::cluster.min.u32 [%0], %1;" ::"r"(a), "r"(v) : "memory");
+}
+__device__ __forceinline__ uint32_t cl_add32(uint32_t a, uint32_t v) {
+    uint32_t old;
+    asm volatile("atom.shared::cluster.add.u32 %0, [%1], %2;" : "=r"(old) : "r"(a), "r"(v) : "memory");
+    return old;
+}
+
+// The burst walk's shared state (one copy per CTA for both forms below).
+__shared__ uint32_t s_ctl[4];                           // pivot, count, pivot term is Y, its sign is -
+__shared__ uint64_t s_part[3][kTableauMaxThreads];     // per-thread chunk sums of the fan-out
+
+// CLU: walked by a cluster of a.bclu CTAs (rank: this CTA's), else by one CTA.
+template <bool CLU>
+__device__ void burst_walk(const TabArgs &a, const DevOp *cops, uint32_t nc, uint32_t j, uint32_t meas_off,
+                           uint32_t rank) {
+    const uint32_t CL = CLU ? a.bclu : 1u, B = blockDim.x * CL, tid = (CLU ? rank * blockDim.x : 0u) + threadIdx.x;
+    // rank 0's scalars (own shared memory without a cluster)
+    const uint32_t ctl0 = CLU ? cl_map(smem_addr(s_ctl), 0) : smem_addr(s_ctl);
+    auto ld_ctl = [&](uint32_t i) { return CLU ? cl_ld32(ctl0 + 4 * i) : s_ctl[i]; };
+    auto st_ctl = [&](uint32_t i, uint32_t v) {
+        if (CLU) cl_st32(ctl0 + 4 * i, v);
+        else s_ctl[i] = v;
+    };
     for (; j < nc; j++) {
         const DevOp op = cops[j];
         const uint32_t opc = op.a >> 24, q = op.a & kQubitMask;
@@ -404,25 +453,32 @@ __device__ void burst_walk(const TabArgs &a, const DevOp *cops, uint32_t nc, uin
         const uint32_t cwp = pc >> 6;
         const uint64_t bitp = 1ull << (pc & 63);
         if (tid == 0) {
-            s_pivot = a.n;
-            s_cnt = 0;
+            st_ctl(0, a.n);
+            st_ctl(1, 0u);
         }
-        __syncthreads();
+        bw_sync<CLU>();
         for (uint32_t k = tid; k < a.n; k += B) {
             if (__ldcg(a.rx + (uint64_t)k * a.nw2 + cwp) & bitp) {
-                atomicMin(&s_pivot, k);
-                __stcg(a.klist + atomicAdd(&s_cnt, 1u), k);
+                uint32_t slot;
+                if (CLU) {
+                    cl_min32(ctl0, k);
+                    slot = cl_add32(ctl0 + 4, 1u);
+                } else {
+                    atomicMin(&s_ctl[0], k);
+                    slot = atomicAdd(&s_ctl[1], 1u);
+                }
+                __stcg(a.klist + slot, k);
             }
         }
-        __syncthreads();
-        const uint32_t p = s_pivot, cnt = s_cnt;
+        bw_sync<CLU>();
+        const uint32_t p = ld_ctl(0), cnt = ld_ctl(1);
         if (cnt == 0) {     // deterministic: the outcome is the sign of column Z_q
             if (tid == 0) {
                 const uint64_t sw = __ldcg(a.rsign + cwp);
                 write_outcome(a, opc, op.b + meas_off, (uint32_t)((sw & bitp) != 0), 1);
                 if (opc != OP_M) __stcg(a.rsign + cwp, sw & ~bitp);
             }
-            __syncthreads();
+            bw_sync<CLU>();
             continue;
         }
         if (tid == 0) {
@@ -434,8 +490,9 @@ __device__ void burst_walk(const TabArgs &a, const DevOp *cops, uint32_t nc, uin
         // column picks up x_p times the parity of the Y and Z terms the
         // products meet (apar) plus the second bit of the count of z_k bits
         // (b1 b0: that count mod 4). Both are sums over k, so a row narrower
-        // than the CTA splits the targets into CH chunks per word, each
-        // thread summing its chunk, and the chunk sums are added per word.
+        // than the burst's threads splits the targets into CH chunks per
+        // word, each thread summing its chunk, and the chunk sums are added
+        // per word.
         // Targets are taken kFanBatch at a time so that their row loads are
         // in flight together.
         const uint32_t WP = a.nw2 < B ? a.nw2 : B;      // words handled side by side
@@ -480,9 +537,9 @@ __device__ void burst_walk(const TabArgs &a, const DevOp *cops, uint32_t nc, uin
                     __stcg(a.rx + (uint64_t)k * a.nw2 + w, xk ^ xp);
                 }
                 if (CH > 1) {       // one word per thread: hand the chunk sums to chunk 0
-                    s_part[0][tid] = apar;
-                    s_part[1][tid] = b0;
-                    s_part[2][tid] = b1;
+                    s_part[0][threadIdx.x] = apar;
+                    s_part[1][threadIdx.x] = b0;
+                    s_part[2][threadIdx.x] = b1;
                     break;
                 }
                 const uint64_t s = __ldcg(a.rsign + w) ^ (xp & (apar ^ b1));
@@ -490,20 +547,25 @@ __device__ void burst_walk(const TabArgs &a, const DevOp *cops, uint32_t nc, uin
                 __stcg(a.rz + (uint64_t)p * a.nw2 + w, zp);
                 __stcg(a.rsign + w, s);
                 if (w == cwp) {
-                    s_py = (uint32_t)((zp & bitp) != 0);     // the pivot term of Z_q is Y
-                    s_fx = (uint32_t)((s & bitp) != 0);      // its sign is -
+                    st_ctl(2, (uint32_t)((zp & bitp) != 0));     // the pivot term of Z_q is Y
+                    st_ctl(3, (uint32_t)((s & bitp) != 0));      // its sign is -
                 }
             }
         }
         if (CH > 1) {
-            __syncthreads();
+            bw_sync<CLU>();
             if (chunk == 0) {
+                // the chunk sums of thread o sit in CTA o / blockDim.x of the burst
+                auto part = [&](uint32_t i, uint32_t o) -> uint64_t {
+                    if (!CLU) return s_part[i][o];
+                    return cl_ld64(cl_map(smem_addr(&s_part[i][o % blockDim.x]), o / blockDim.x));
+                };
                 const uint32_t w = wl;
-                uint64_t apar = s_part[0][w], b0 = s_part[1][w], b1 = s_part[2][w];
+                uint64_t apar = part(0, w), b0 = part(1, w), b1 = part(2, w);
                 for (uint32_t c = 1; c < CH; c++) {
                     const uint32_t o = c * WP + w;
-                    const uint64_t c0 = s_part[1][o], c1 = s_part[2][o];
-                    apar ^= s_part[0][o];
+                    const uint64_t c0 = part(1, o), c1 = part(2, o);
+                    apar ^= part(0, o);
                     b1 ^= c1 ^ (b0 & c0);       // (b1 b0) += (c1 c0) mod 4
                     b0 ^= c0;
                 }
@@ -513,13 +575,13 @@ __device__ void burst_walk(const TabArgs &a, const DevOp *cops, uint32_t nc, uin
                 __stcg(a.rz + (uint64_t)p * a.nw2 + w, zp);
                 __stcg(a.rsign + w, s);
                 if (w == cwp) {
-                    s_py = (uint32_t)((zp & bitp) != 0);
-                    s_fx = (uint32_t)((s & bitp) != 0);
+                    st_ctl(2, (uint32_t)((zp & bitp) != 0));
+                    st_ctl(3, (uint32_t)((s & bitp) != 0));
                 }
             }
         }
-        __syncthreads();
-        const bool py = s_py != 0, fx = s_fx != 0;
+        bw_sync<CLU>();
+        const bool py = ld_ctl(2) != 0, fx = ld_ctl(3) != 0;
         for (uint32_t w = tid; w < a.nw2; w += B) {      // pivot collapse on row p
             uint64_t xp = __ldcg(a.rx + (uint64_t)p * a.nw2 + w);
             uint64_t zp = __ldcg(a.rz + (uint64_t)p * a.nw2 + w);
@@ -537,7 +599,7 @@ __device__ void burst_walk(const TabArgs &a, const DevOp *cops, uint32_t nc, uin
             __stcg(a.rz + (uint64_t)p * a.nw2 + w, zp);
             __stcg(a.rsign + w, s);
         }
-        __syncthreads();
+        bw_sync<CLU>();
         // a random outcome is 0: nothing to write (reference and flags start cleared)
     }
 }
@@ -554,7 +616,9 @@ __global__ void tableau_init_kernel(TabArgs a) {
 }
 
 // The inverse-tableau walk of one circuit by CTA bid of its a.nblk CTAs.
-template <bool L1>
+// CLU: the launch may be a cluster launch whose first a.bclu CTAs walk the
+// bursts together (the batched kernel's circuits never are).
+template <bool L1, bool CLU = false>
 __device__ __forceinline__ void tableau_body(const TabArgs &a, uint32_t bid) {
     const uint32_t lane = threadIdx.x & 31;
     const uint32_t wpb = blockDim.x >> 5;
@@ -718,7 +782,7 @@ __device__ __forceinline__ void tableau_body(const TabArgs &a, uint32_t bid) {
         bool burst = false;
         if (!L1 && a.rx != nullptr && s_nrand >= kBurstMinRandom && nc - s_first <= kBurstMaxOps) {
             const uint32_t kc = ld_u32<L1>(&a.ctl->nk_cnt), ks = ld_u32<L1>(&a.ctl->nk_sum);
-            burst = kc >= 4 && (uint64_t)ks * a.nw2 <= (uint64_t)kBurstMaxRowWords * kc;
+            burst = kc >= 4 && (uint64_t)ks * a.nw2 <= (uint64_t)kBurstMaxRowWords * a.bclu * kc;
         }
         for (uint32_t j = gtid; j < first; j += nthreads) {
             const DevOp op = cops[j];
@@ -732,7 +796,11 @@ __device__ __forceinline__ void tableau_body(const TabArgs &a, uint32_t bid) {
         if (burst) {
             to_rows(a, gtid, nthreads);
             if (!tab_barrier(a)) return;
-            if (bid == 0) burst_walk(a, cops, nc, first, meas_off);
+            if (CLU && a.bclu > 1) {
+                if (bid < a.bclu) burst_walk<true>(a, cops, nc, first, meas_off, bid);
+            } else if (bid == 0) {
+                burst_walk<false>(a, cops, nc, first, meas_off, 0u);
+            }
             if (!tab_barrier(a)) return;
             to_cols(a, gtid, nthreads);
             if (!tab_barrier(a)) return;
@@ -757,7 +825,7 @@ __device__ __forceinline__ void tableau_body(const TabArgs &a, uint32_t bid) {
 
 template <bool L1>
 __global__ void __launch_bounds__(kTableauMaxThreads) tableau_kernel(TabArgs a) {
-    tableau_body<L1>(a, blockIdx.x);
+    tableau_body<L1, !L1>(a, blockIdx.x);
 }
 
 // Several circuits in one cooperative launch: CTA b works for circuit
@@ -809,10 +877,47 @@ int tableau_max_blocks(uint32_t threads, int device) {
 cudaError_t launch_tableau(const TabArgs &a, uint32_t blocks, uint32_t threads, cudaStream_t stream) {
     TabArgs args = a;
     args.nblk = blocks;
+    args.bclu = 1;
     void *params[] = {&args};
     if (blocks == 1)    // one CTA: the tableau stays in its L1, no grid barrier
         return cudaLaunchCooperativeKernel((const void *)tableau_kernel<true>, dim3(1), dim3(threads), params, 0,
                                            stream);
+    // a large circuit with a row-major copy is launched as clusters of
+    // kBurstCluster CTAs (still cooperative: every CTA co-resident), so that
+    // cluster 0 walks its bursts with kBurstCluster times the threads. A
+    // cluster barrier costs far more than a CTA barrier, and a burst takes
+    // four per random measurement, so this pays only where each random
+    // measurement's row scan is long: from kBurstClusterMinQubits qubits
+    // (surface code d=100, 20k qubits: reference 0.31 -> 0.18 s; Bacon-Shor
+    // d=60, 10.7k qubits: 3.9 -> 4.5 s, and worse for smaller circuits).
+    if (a.rx != nullptr && a.n >= kBurstClusterMinQubits && blocks >= 2 * kBurstCluster) {
+        cudaLaunchConfig_t cfg = {};
+        cudaLaunchAttribute at[2];
+        at[0].id = cudaLaunchAttributeClusterDimension;
+        at[0].val.clusterDim.x = kBurstCluster;
+        at[0].val.clusterDim.y = 1;
+        at[0].val.clusterDim.z = 1;
+        at[1].id = cudaLaunchAttributeCooperative;
+        at[1].val.cooperative = 1;
+        cfg.blockDim = dim3(threads);
+        cfg.stream = stream;
+        cfg.attrs = at;
+        cfg.numAttrs = 1;
+        cfg.gridDim = dim3(blocks);
+        int clusters = 0;
+        if (cudaOccupancyMaxActiveClusters(&clusters, tableau_kernel<false>, &cfg) == cudaSuccess && clusters >= 2) {
+            uint32_t b = blocks < (uint32_t)clusters * kBurstCluster ? blocks : (uint32_t)clusters * kBurstCluster;
+            b -= b % kBurstCluster;
+            args.nblk = b;
+            args.bclu = kBurstCluster;
+            cfg.gridDim = dim3(b);
+            cfg.numAttrs = 2;
+            if (cudaLaunchKernelEx(&cfg, tableau_kernel<false>, args) == cudaSuccess) return cudaSuccess;
+        }
+        cudaGetLastError();     // not launched: the plain cooperative grid below
+        args.nblk = blocks;
+        args.bclu = 1;
+    }
     return cudaLaunchCooperativeKernel((const void *)tableau_kernel<false>, dim3(blocks), dim3(threads), params, 0,
                                        stream);
 }
