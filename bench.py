@@ -931,7 +931,7 @@ def main():
             "frac": achieved / hbm_peak, "traffic": profiled_traffic(shots),
             "kernel": "frame", "peak_source": peak_src,
             "algorithmic_bytes_per_launch": frame_bytes,
-            "note": "the survey's roofline for this kernel: algorithmic frame bytes against measured HBM "
+            "note": "the roofline this kernel is reported against: algorithmic frame bytes over measured HBM "
                     "bandwidth; the frame itself stays in shared memory (see smem) and the kernel is "
                     "limited by instruction issue (see issue)",
             "smem": None if not smem_local_gbs else {

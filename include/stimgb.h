@@ -310,7 +310,7 @@ int stim_frame_sample(stim_circuit *c, uint64_t num_shots, uint64_t seed,
  * set's previous copies.
  * Calls on one handle must still come from one host thread at a time.
  *
- * Detection events without records (survey NEXT-1, Section 5.6): when only
+ * Detection events without records (Section 5.6): when only
  * det_out is given and either STIM_EVENTS_IN_KERNEL is set or the records
  * would take more than 8 GiB, and the circuit has no classically controlled
  * ops and 4 x stim_info.flip_ring_rows <= M, the frame kernel keeps each

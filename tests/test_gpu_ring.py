@@ -1,7 +1,6 @@
-"""Detection events computed inside the frame kernel (survey NEXT-1, paper
-Section 5.6): when only detection events are asked for with
-STIM_EVENTS_IN_KERNEL, the frame kernel
-keeps each measurement's flip in a ring of recent measurements and evaluates
+"""Detection events computed inside the frame kernel (paper Section 5.6):
+when only detection events are asked for with STIM_EVENTS_IN_KERNEL, the
+frame kernel keeps each measurement's flip in a ring of recent measurements and evaluates
 the DETECTOR / OBSERVABLE_INCLUDE lines of each straight-line stretch between
 its layers, so no measurement record is written and the detector kernel does
 not run. The events must equal those of the record path (asked for together
