@@ -779,10 +779,15 @@ __device__ __forceinline__ void tableau_body(const TabArgs &a, uint32_t bid) {
         const uint32_t first = s_first;
         // row-major burst for this layer's random measurements: the same
         // choice in every CTA (the statistics last changed before the barrier above)
-        bool burst = false;
+        bool burst = false, wide = false;
         if (!L1 && a.rx != nullptr && s_nrand >= kBurstMinRandom && nc - s_first <= kBurstMaxOps) {
             const uint32_t kc = ld_u32<L1>(&a.ctl->nk_cnt), ks = ld_u32<L1>(&a.ctl->nk_sum);
-            burst = kc >= 4 && (uint64_t)ks * a.nw2 <= (uint64_t)kBurstMaxRowWords * a.bclu * kc;
+            // fan-out words of the random measurements so far, against what one
+            // CTA (or, in a cluster launch, the burst cluster) takes
+            const uint64_t work = (uint64_t)ks * a.nw2, one = (uint64_t)kBurstMaxRowWords * kc;
+            const bool clu = CLU && a.bclu > 1;
+            burst = kc >= 4 && (work <= one || (clu && work <= one * a.bclu));
+            wide = clu && (a.n >= kBurstClusterMinQubits || work > one);
         }
         for (uint32_t j = gtid; j < first; j += nthreads) {
             const DevOp op = cops[j];
@@ -796,7 +801,7 @@ __device__ __forceinline__ void tableau_body(const TabArgs &a, uint32_t bid) {
         if (burst) {
             to_rows(a, gtid, nthreads);
             if (!tab_barrier(a)) return;
-            if (CLU && a.bclu > 1) {
+            if (wide) {
                 if (bid < a.bclu) burst_walk<true>(a, cops, nc, first, meas_off, bid);
             } else if (bid == 0) {
                 burst_walk<false>(a, cops, nc, first, meas_off, 0u);
@@ -890,7 +895,7 @@ cudaError_t launch_tableau(const TabArgs &a, uint32_t blocks, uint32_t threads, 
     // measurement's row scan is long: from kBurstClusterMinQubits qubits
     // (surface code d=100, 20k qubits: reference 0.31 -> 0.18 s; Bacon-Shor
     // d=60, 10.7k qubits: 3.9 -> 4.5 s, and worse for smaller circuits).
-    if (a.rx != nullptr && a.n >= kBurstClusterMinQubits && blocks >= 2 * kBurstCluster) {
+    if (a.rx != nullptr && blocks >= 2 * kBurstCluster) {
         cudaLaunchConfig_t cfg = {};
         cudaLaunchAttribute at[2];
         at[0].id = cudaLaunchAttributeClusterDimension;
@@ -903,7 +908,7 @@ cudaError_t launch_tableau(const TabArgs &a, uint32_t blocks, uint32_t threads, 
         cfg.stream = stream;
         cfg.attrs = at;
         cfg.numAttrs = 1;
-        cfg.gridDim = dim3(blocks);
+        cfg.gridDim = dim3(blocks - blocks % kBurstCluster);     // the query wants whole clusters
         int clusters = 0;
         if (cudaOccupancyMaxActiveClusters(&clusters, tableau_kernel<false>, &cfg) == cudaSuccess && clusters >= 2) {
             uint32_t b = blocks < (uint32_t)clusters * kBurstCluster ? blocks : (uint32_t)clusters * kBurstCluster;

@@ -118,6 +118,26 @@ def test_reference_random_small_circuits():
         np.testing.assert_array_equal(det, odet, err_msg=text)
 
 
+def test_reference_wide_fanout_bursts_match_oracle():
+    """An 1800-qubit random Clifford circuit of depth 400: once scrambled, its
+    random measurements fan out to more rows of 57 words than one CTA takes in
+    a row-major burst, so the burst cluster walks them (the cluster-wide chunk
+    sums of the fan-out: several hundred such layers); the reference equals
+    the oracle's, recomputed as well as cold."""
+    text = W.random_clifford(1800, 400, 11)
+    ref, det = gpu_reference(text)
+    oref, odet = oracle.Circuit(text).reference()
+    np.testing.assert_array_equal(ref, oref)
+    np.testing.assert_array_equal(det, odet)
+    c = sg.Circuit(text)
+    r2, d2 = c.reference(recompute=True)
+    torch.cuda.synchronize()
+    M = c.num_measurements
+    np.testing.assert_array_equal(words_to_bits(to_np(r2)[None, :], M)[0], oref)
+    np.testing.assert_array_equal(words_to_bits(to_np(d2)[None, :], M)[0], odet)
+    c.close()
+
+
 def test_reference_recompute_is_stable():
     c = sg.Circuit(W.random_clifford(300, 30, 9))
     r1, d1 = c.reference()
