@@ -434,11 +434,11 @@ __device__ __forceinline__ uint32_t cl_add32(uint32_t a, uint32_t v) {
 __shared__ uint32_t s_ctl[4];                           // pivot, count, pivot term is Y, its sign is -
 __shared__ uint64_t s_part[3][kTableauMaxThreads];     // per-thread chunk sums of the fan-out
 
-// CLU: walked by a cluster of a.bclu CTAs (rank: this CTA's), else by one CTA.
+// CLU: walked by a cluster of bclu CTAs (rank: this CTA's in it), else by one CTA.
 template <bool CLU>
 __device__ void burst_walk(const TabArgs &a, const DevOp *cops, uint32_t nc, uint32_t j, uint32_t meas_off,
-                           uint32_t rank) {
-    const uint32_t CL = CLU ? a.bclu : 1u, B = blockDim.x * CL, tid = (CLU ? rank * blockDim.x : 0u) + threadIdx.x;
+                           uint32_t rank, uint32_t bclu) {
+    const uint32_t CL = CLU ? bclu : 1u, B = blockDim.x * CL, tid = (CLU ? rank * blockDim.x : 0u) + threadIdx.x;
     // rank 0's scalars (own shared memory without a cluster)
     const uint32_t ctl0 = CLU ? cl_map(smem_addr(s_ctl), 0) : smem_addr(s_ctl);
     auto ld_ctl = [&](uint32_t i) { return CLU ? cl_ld32(ctl0 + 4 * i) : s_ctl[i]; };
@@ -616,8 +616,8 @@ __global__ void tableau_init_kernel(TabArgs a) {
 }
 
 // The inverse-tableau walk of one circuit by CTA bid of its a.nblk CTAs.
-// CLU: the launch may be a cluster launch whose first a.bclu CTAs walk the
-// bursts together (the batched kernel's circuits never are).
+// CLU: the launch may be a cluster launch whose cluster 0 (a.bclu CTAs) walks
+// the bursts together (the batched kernel's circuits never are).
 template <bool L1, bool CLU = false>
 __device__ __forceinline__ void tableau_body(const TabArgs &a, uint32_t bid) {
     const uint32_t lane = threadIdx.x & 31;
@@ -780,13 +780,27 @@ __device__ __forceinline__ void tableau_body(const TabArgs &a, uint32_t bid) {
         // row-major burst for this layer's random measurements: the same
         // choice in every CTA (the statistics last changed before the barrier above)
         bool burst = false, wide = false;
+        // the burst cluster, taken only when the launch really is a cluster
+        // launch of that size (a launch that lost its cluster shape walks its
+        // bursts on CTA 0); crank: this CTA's rank in cluster 0, else bclu
+        uint32_t bclu = 1, crank = 0;
+        if constexpr (CLU) {
+            if (a.bclu > 1) {
+                uint32_t ncta, cx;
+                asm volatile("mov.u32 %0, %%cluster_nctarank;" : "=r"(ncta));
+                asm volatile("mov.u32 %0, %%clusterid.x;" : "=r"(cx));
+                asm volatile("mov.u32 %0, %%cluster_ctarank;" : "=r"(crank));
+                if (ncta == a.bclu && gridDim.x % a.bclu == 0) bclu = a.bclu;
+                if (cx != 0) crank = bclu;
+            }
+        }
         if (!L1 && a.rx != nullptr && s_nrand >= kBurstMinRandom && nc - s_first <= kBurstMaxOps) {
             const uint32_t kc = ld_u32<L1>(&a.ctl->nk_cnt), ks = ld_u32<L1>(&a.ctl->nk_sum);
             // fan-out words of the random measurements so far, against what one
             // CTA (or, in a cluster launch, the burst cluster) takes
             const uint64_t work = (uint64_t)ks * a.nw2, one = (uint64_t)kBurstMaxRowWords * kc;
-            const bool clu = CLU && a.bclu > 1;
-            burst = kc >= 4 && (work <= one || (clu && work <= one * a.bclu));
+            const bool clu = CLU && bclu > 1;
+            burst = kc >= 4 && (work <= one || (clu && work <= one * bclu));
             wide = clu && (a.n >= kBurstClusterMinQubits || work > one);
         }
         for (uint32_t j = gtid; j < first; j += nthreads) {
@@ -802,9 +816,9 @@ __device__ __forceinline__ void tableau_body(const TabArgs &a, uint32_t bid) {
             to_rows(a, gtid, nthreads);
             if (!tab_barrier(a)) return;
             if (wide) {
-                if (bid < a.bclu) burst_walk<true>(a, cops, nc, first, meas_off, bid);
+                if (crank < bclu) burst_walk<true>(a, cops, nc, first, meas_off, crank, bclu);
             } else if (bid == 0) {
-                burst_walk<false>(a, cops, nc, first, meas_off, 0u);
+                burst_walk<false>(a, cops, nc, first, meas_off, 0u, 1u);
             }
             if (!tab_barrier(a)) return;
             to_cols(a, gtid, nthreads);
