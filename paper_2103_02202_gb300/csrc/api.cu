@@ -1153,14 +1153,14 @@ int stim_frame_program_info_get(const stim_circuit *c, int cluster_size, stim_fr
         out->max_chain_ops = std::max(out->max_chain_ops, sg.len);
         out->deferred_ops += (uint64_t)sg.count * (sg.len - sg.defer_from);
         for (uint32_t k = 0; k < sg.count; k++) {
-            const DevOp *ch = fp.ops.data() + sg.op_begin + (size_t)k * sg.len;
             std::vector<uint32_t> qs;
             for (uint32_t j = 0; j < sg.len; j++) {
-                const uint32_t opc = ch[j].a >> 28;
+                const DevOp &op = fp.ops[sg.op_begin + (size_t)j * sg.count + k];      // step-major
+                const uint32_t opc = op.a >> 28;
                 if ((opc == OP_FFX || opc == OP_FFZ) && j > 0) out->feedforward_not_first++;
                 if (j < sg.defer_from) continue;
-                qs.push_back(global_q(ch[j].a & 0x0FFFFFFFu));
-                if (opc == OP_DEP2) qs.push_back(global_q(ch[j].b));
+                qs.push_back(global_q(op.a & 0x0FFFFFFFu));
+                if (opc == OP_DEP2) qs.push_back(global_q(op.b));
             }
             std::sort(qs.begin(), qs.end());
             if (std::adjacent_find(qs.begin(), qs.end()) != qs.end()) out->tails_repeating_qubit++;

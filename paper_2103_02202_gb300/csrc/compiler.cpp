@@ -918,8 +918,11 @@ class FrameBuilder {
                     dfrom = std::max(dfrom, d);
                 }
                 sg.defer_from = dfrom;
-                for (size_t k = i; k < j; k++)
-                    for (const DevOp &d : chains_[by_rank[r][k]].ops) {
+                // step-major: op s of chain k at op_begin + s * count + k, so the
+                // lanes of a warp (consecutive chains) read consecutive ops
+                for (uint32_t step = 0; step < sg.len; step++)
+                    for (size_t k = i; k < j; k++) {
+                        const DevOp &d = chains_[by_rank[r][k]].ops[step];
                         fp_->ops.push_back(encode(d));
                         const uint32_t opc = d.a >> 24;
                         if (op_is_gate(opc)) ng++;

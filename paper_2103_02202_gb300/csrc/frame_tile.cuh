@@ -647,23 +647,24 @@ __device__ __forceinline__ bool run_tile(const FrameArgs &a, unsigned char *dyn,
                         const uint32_t it = g - seg_start;
                         const bool act = it < items;
                         const uint32_t wo = act ? (it % (W / V)) * V : 0u;
-                        const uint32_t op0 = sv.y + (act ? it / (W / V) : 0u) * len;
+                        // ops are step-major: step j of the segment's chain c at sv.y + j * sv.z + c
+                        const uint32_t op0 = sv.y + (act ? it / (W / V) : 0u);
                         if (!have_next) nxt = __ldg(ops + op0);
                         // the thread's next item of this segment, if any
                         const uint32_t it2 = it + blockDim.x;
                         have_next = g + blockDim.x < seg_start + span;
-                        const uint32_t op2 = sv.y + (it2 < items ? it2 / (W / V) : 0u) * len;
+                        const uint32_t op2 = sv.y + (it2 < items ? it2 / (W / V) : 0u);
                         for (uint32_t j = 0; j < len; j++) {
                             const uint4 ov = nxt;
-                            if (j + 1 < len) nxt = __ldg(ops + op0 + j + 1);     // one op ahead
-                            else if (have_next) nxt = __ldg(ops + op2);         // across items
+                            if (j + 1 < len) nxt = __ldg(ops + op0 + (j + 1) * sv.z);     // one op ahead
+                            else if (have_next) nxt = __ldg(ops + op2);                 // across items
                             if (j < dfrom) {
                                 if (act) frame_op<W, C, GMEM, DETS, K>(a, key, t, as_op(ov), wo, tile0, instr_off, meas_off);
                             } else {
                                 const uint32_t hits =
                                     act ? noise_hits<V, K>(a, key, as_op(ov), (uint32_t)a.word0 + tile0 + wo, instr_off)
                                         : 0u;
-                                const uint32_t oi = op0 + j - first;       // index within the CTA's layer
+                                const uint32_t oi = op0 + j * sv.z - first;      // index within the CTA's layer
 #pragma unroll
                                 for (int i = 0; i < V; i++) {
                                     const bool h = (hits >> i) & 1u;

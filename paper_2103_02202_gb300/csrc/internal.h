@@ -193,7 +193,7 @@ struct HostProgram {
 //   slot:  target slot; DEPOLARIZE2 keeps its table index in bits 24..31
 struct FrameSeg {
     uint32_t len;         // ops per chain
-    uint32_t op_begin;    // first op of the first chain
+    uint32_t op_begin;    // ops step-major: step j of chain k at op_begin + j * count + k
     uint32_t count;       // chains
     uint32_t defer_from;  // chain steps >= defer_from are all noise ops (C > 1: on distinct qubits)
 };
