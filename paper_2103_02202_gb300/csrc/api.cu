@@ -944,7 +944,7 @@ int choose_tile(uint32_t n, uint64_t nwords, int sms, size_t smem_optin, const s
     }
     if (hint && hint->threads) {
         if ((int)hint->threads > frame_max_threads(t.W))
-            return fail(STIM_E_INVALID_ARG, "tile hint: too many threads per CTA for this many words per tile (448 for 1, 768 for 2, 512 for 4 or 8)");
+            return fail(STIM_E_INVALID_ARG, "tile hint: too many threads per CTA for this many words per tile (512 for 1 or 4 or 8, 768 for 2)");
         t.threads = hint->threads;
     } else if (t.gmem) {
         t.threads = 256;

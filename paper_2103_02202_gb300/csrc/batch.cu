@@ -53,7 +53,7 @@ constexpr uint32_t kDescBytes = 384;   // FrameArgs copy at the start of dynamic
 static_assert(sizeof(FrameArgs) <= kDescBytes, "descriptor does not fit its slot");
 
 template <int W, int C>
-__global__ void __launch_bounds__(frame_max_threads(W), frame_min_ctas(W)) batch_frame_kernel(const FrameArgs *__restrict__ descs,
+__global__ void __launch_bounds__(batch_max_threads(W), frame_min_ctas(W)) batch_frame_kernel(const FrameArgs *__restrict__ descs,
                                                               const BatchItem *__restrict__ items, uint32_t nitems,
                                                               uint32_t *counter) {
     extern __shared__ __align__(128) unsigned char smem[];
@@ -392,7 +392,7 @@ int configure(stim_batch *b, int W, uint32_t threads) {
     STIMGB_BCK(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, b->device), "attr");
     if (threads == 0 || threads % 32 != 0)
         return bfail(STIM_E_INVALID_ARG, "batch: threads per CTA must be a multiple of 32");
-    if ((int)threads > frame_max_threads(W))
+    if ((int)threads > batch_max_threads(W))
         return bfail(STIM_E_INVALID_ARG, "batch: too many threads per CTA for this many words per tile (448 for 1, 768 for 2, 512 for 4 or 8)");
     b->W = W;
     b->threads = threads;

@@ -173,6 +173,26 @@ struct Qubit<W, C, false> {
             st(1, p.z);
         }
     }
+    // word wo + i of the X and Z planes ^= (mx, mz); only this thread
+    // touches the qubit in this layer
+    __device__ __forceinline__ void xor_word(const Tile<W, C, false> &t, uint32_t i, uint64_t mx, uint64_t mz) const {
+        if constexpr (W == 1) {
+            Planes<1> p;
+            load(t, p);
+            p.x[0] ^= mx;
+            p.z[0] ^= mz;
+            store(t, p);
+        } else {
+            const uint32_t ax = at(wo + i), az = at(W + wo + i);
+            if constexpr (C > 1) {
+                stc64(ax, ldc64(ax) ^ mx);
+                stc64(az, ldc64(az) ^ mz);
+            } else {
+                sts64(ax, lds64(ax) ^ mx);
+                sts64(az, lds64(az) ^ mz);
+            }
+        }
+    }
     __device__ __forceinline__ void store_x(const Tile<W, C, false> &, const uint64_t (&x)[V]) const { st(0, x); }
     __device__ __forceinline__ void store_z(const Tile<W, C, false> &, const uint64_t (&z)[V]) const { st(1, z); }
 };
@@ -198,6 +218,10 @@ struct Qubit<W, C, true> {
             p[i] = q.x[i];
             p[t.gstride + i] = q.z[i];
         }
+    }
+    __device__ __forceinline__ void xor_word(const Tile<W, C, true> &t, uint32_t i, uint64_t mx, uint64_t mz) const {
+        p[i] ^= mx;
+        p[t.gstride + i] ^= mz;
     }
     __device__ __forceinline__ void store_x(const Tile<W, C, true> &, const uint64_t (&x)[V]) const {
 #pragma unroll
@@ -231,13 +255,8 @@ __device__ __forceinline__ void noise_op(const FrameArgs &a, const K key, const 
         if ((uint64_t)blk[i].x < g63) hits |= 1u << i;
     }
     if (!hits) return;
-    const Qubit<W, C, GMEM> qa(t, op.a & 0x0FFFFFFFu, wo);
-    Planes<V> pa, pb;
-    qa.load(t, pa);
-    if (pair) {
-        const Qubit<W, C, GMEM> qb(t, op.b, wo);
-        qb.load(t, pb);
-    }
+    // masks first, then one read-modify-write of each hit word: the frame
+    // words are not held across the gap procedure
     while (hits) {
         const int w = __ffs((int)hits) - 1;
         hits &= hits - 1u;
@@ -247,20 +266,12 @@ __device__ __forceinline__ void noise_op(const FrameArgs &a, const K key, const 
             if (w == i) b0 = blk[i];
         uint64_t mxa, mza, mxb, mzb;
         noise_masks_slow(opc, G, key, instr, slot, gw0 + (uint32_t)w, b0, mxa, mza, mxb, mzb);
-#pragma unroll
-        for (int i = 0; i < V; i++) {
-            if (w == i) {
-                pa.x[i] ^= mxa;
-                pa.z[i] ^= mza;
-                pb.x[i] ^= mxb;
-                pb.z[i] ^= mzb;
-            }
+        const Qubit<W, C, GMEM> qa(t, op.a & 0x0FFFFFFFu, wo);
+        qa.xor_word(t, (uint32_t)w, mxa, mza);
+        if (pair) {
+            const Qubit<W, C, GMEM> qb(t, op.b, wo);
+            qb.xor_word(t, (uint32_t)w, mxb, mzb);
         }
-    }
-    qa.store(t, pa);
-    if (pair) {
-        const Qubit<W, C, GMEM> qb(t, op.b, wo);
-        qb.store(t, pb);
     }
 }
 

@@ -65,8 +65,11 @@ constexpr uint32_t kTileHeaderBytes = kHitQueueOffset + 32 * kHitQueueCap * 4;
 
 // Largest CTA of a frame kernel with W words per tile: threads that apply ops
 // to two or four words at once need more registers. One-word tiles are sized
-// for two CTAs of up to 448 threads per SM (72 registers, no spills).
-constexpr int frame_max_threads(int W) { return W >= 4 ? 512 : W == 2 ? 768 : 448; }
+// for two CTAs of up to 512 threads per SM (64 registers, no spills).
+constexpr int frame_max_threads(int W) { return W >= 4 ? 512 : W == 2 ? 768 : 512; }
+// The batched kernel keeps per-circuit state besides: its one-word tiles stay
+// at 448 threads (72 registers).
+constexpr int batch_max_threads(int W) { return W == 1 ? 448 : frame_max_threads(W); }
 constexpr int frame_min_ctas(int W) { return W == 1 ? 2 : 1; }
 inline size_t tile_smem_bytes(uint32_t Q, int W, bool gmem, uint32_t meta_region) {
     return kTileHeaderBytes + meta_region + (gmem ? 0 : (size_t)Q * 2 * W * 8);
