@@ -829,17 +829,22 @@ def main():
     e2e_dense_value = shots * e2e_steps * world * gate_targets / (e2e_ms / 1000.0)
     # the host link this box gives one step's copy (device -> pinned host), to
     # read the e2e figure against: best of two plain copies of the same size
-    link_ms = None
+    # (each of the two host buffers: a buffer that copies slower than the
+    # other shows in the per-buffer figures)
     e2 = torch.cuda.Event(enable_timing=True)
     e3 = torch.cuda.Event(enable_timing=True)
-    for _ in range(2):
-        e2.record(stream)
-        host_det[0].copy_(det, non_blocking=True)
-        e3.record(stream)
-        torch.cuda.synchronize()
-        t = e2.elapsed_time(e3)
-        link_ms = t if link_ms is None else min(link_ms, t)
-    link_gbs = D * nwords * 8 / (link_ms * 1e6) if link_ms else None
+    buf_gbs = []
+    for hbuf in host_det:
+        best = None
+        for _ in range(2):
+            e2.record(stream)
+            hbuf.copy_(det, non_blocking=True)
+            e3.record(stream)
+            torch.cuda.synchronize()
+            t = e2.elapsed_time(e3)
+            best = t if best is None else min(best, t)
+        buf_gbs.append(D * nwords * 8 / (best * 1e6) if best else None)
+    link_gbs = buf_gbs[0]
 
     # ---- end to end with per-shot lists of fired detectors (the paper's hits
     # form): the call samples, converts on the device and copies the count,
@@ -870,6 +875,19 @@ def main():
         sp_ms = float(t.item())
     e2e_value = shots * e2e_steps * world * gate_targets / (sp_ms / 1000.0)
     sparse_d2h = 8 + 8 * (shots + 1) + 4 * sparse_events / e2e_steps
+    # the link into the lists' host buffer (a plain copy of its size)
+    list_gbs = None
+    flat = det.view(torch.int32).reshape(-1)
+    if flat.numel() >= hd.numel():
+        best = None
+        for _ in range(2):
+            e2.record(stream)
+            hd.copy_(flat[:hd.numel()], non_blocking=True)
+            e3.record(stream)
+            torch.cuda.synchronize()
+            t = e2.elapsed_time(e3)
+            best = t if best is None else min(best, t)
+        list_gbs = hd.numel() * 4 / (best * 1e6) if best else None
 
     if rank != 0:
         if dist:
@@ -947,10 +965,12 @@ def main():
         "e2e": {"value": e2e_dense_value, "unit": "shot-gates/s", "h2d_bytes_per_step": 0,
                 "d2h_bytes_per_step": D * nwords * 8, "steps": e2e_steps,
                 "ms_per_step": e2e_ms / e2e_steps, "d2h_gbs_measured": link_gbs,
+                "d2h_gbs_per_host_buffer": buf_gbs,
                 "output": "bit-packed detection events in host memory via stim_frame_sample_ex "
                           "(STIM_HOST | STIM_ASYNC, two streams)"},
         "e2e_sparse": {"value": e2e_value, "unit": "shot-gates/s", "h2d_bytes_per_step": 0,
                        "d2h_bytes_per_step": int(sparse_d2h), "steps": e2e_steps,
+                       "ms_per_step": sp_ms / e2e_steps, "d2h_gbs_list_buffer": list_gbs,
                        "output": "per-shot lists of fired detectors (uint64 offsets + uint32 indices) in host "
                                  "memory via stim_frame_sample_detections (synchronous)"},
         "gpu_launches": int(f_launch + d_launch),
